@@ -1,0 +1,49 @@
+"""Pins of the oracle's GMRES against LU and against brute-force facts."""
+import numpy as np
+
+from oracle import geometry, operators, solvers
+
+
+def test_gmres_finite_termination_distinct_eigenvalues():
+    """A diagonalisable matrix with k distinct eigenvalues: GMRES ends in k steps."""
+    rng = np.random.default_rng(0)
+    n, k = 40, 5
+    lam = np.array([1.0, 2.0 + 1j, -0.5j, 3.0, 0.7 - 0.2j])
+    d = lam[rng.integers(0, k, n)]
+    d[:k] = lam
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    A = Q @ np.diag(d) @ Q.conj().T
+    f = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, its, rel = solvers.gmres(lambda v: A @ v, f, rtol=1e-12, restart=0, maxit=n)
+    assert its == k
+    assert rel < 1e-12
+    np.testing.assert_allclose(x, np.linalg.solve(A, f), rtol=1e-10)
+
+
+def test_gmres_matches_lu_on_cfie():
+    c = geometry.kite(256)
+    w = 20.0
+    A = operators.soft_matrix(c, w, w)
+    f = operators.plane_wave_rhs(c, w, [0.0, 1.0], "soft")
+    X, its, rel = solvers.gmres_columns(lambda v: A @ v, f, rtol=1e-13, restart=0, maxit=256)
+    ref = solvers.lu_solve(A, f)
+    assert np.all(rel <= 1e-13)
+    assert np.linalg.norm(X - ref) / np.linalg.norm(ref) < 1e-12
+
+
+def test_gmres_restarted_converges_and_counts():
+    c = geometry.fourier_star(200, [0, 0, 0, 0, 0.3], [0] * 5)
+    w = 30.0
+    A = operators.hard_matrix(c, w, w)
+    f = operators.plane_wave_rhs(c, w, [0.3], "hard")[:, 0]
+    x_full, its_full, _ = solvers.gmres(lambda v: A @ v, f, rtol=1e-8, restart=0, maxit=400)
+    x_r, its_r, rel_r = solvers.gmres(lambda v: A @ v, f, rtol=1e-8, restart=10, maxit=400)
+    assert rel_r <= 1e-8
+    assert its_r >= its_full          # restarting never helps GMRES's residual
+    ref = np.linalg.solve(A, f)
+    assert np.linalg.norm(x_r - ref) / np.linalg.norm(ref) < 1e-6
+
+
+def test_gmres_zero_rhs():
+    x, its, rel = solvers.gmres(lambda v: v, np.zeros(5, complex))
+    assert its == 0 and rel == 0.0 and not np.any(x)

@@ -1,0 +1,422 @@
+"""Benchmark of the CFIE hot path on one GB300 (or N independent replicas).
+
+A step is one pass of the whole path over one batch of synthetic input:
+sample the curve and build the Kress tables (cfie_discretise), form the
+plane-wave right-hand sides (cfie_rhs_plane_waves) and solve all of them with
+GMRES (cfie_gmres_solve) to the target accuracy.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload kite|star|disk] [--precision fp32|fp64]
+
+Metric: CFIE kernel-pair evaluations per second, where one kernel-pair
+evaluation is the evaluation of the Nystrom kernel for one (target, source)
+pair inside one block matvec (shared by all right-hand sides of the block).
+Solves per second (one solve = one right-hand side at the target accuracy) are
+reported beside it.
+
+Multi-GPU: replicas only (one independent workload per rank, no collective on
+the data path); value = pair evaluations of all ranks / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CFIE kernel-pair evals/s"
+UNIT = "pair-evals/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="star", choices=["kite", "star", "disk"])
+    p.add_argument("--precision", default=None, choices=["fp32", "fp64", None])
+    p.add_argument("--rtol", type=float, default=None)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload definitions (shapes from inputs.WORKLOADS)
+# ---------------------------------------------------------------------------
+def workload(name, precision):
+    from paper_1408_1578_gb300 import inputs
+    spec = dict(inputs.WORKLOADS[name])
+    spec["name"] = name
+    if precision is None:
+        precision = "fp32" if name == "kite" else "fp64"
+    spec["precision"] = precision
+    # residual target: 1e-8 on ||f - A x|| / ||f|| keeps the error against the
+    # FP64 solution below 1e-6 for the condition numbers of these operators
+    spec["rtol"] = 1e-8
+    spec["restart"] = 80
+    spec["maxit"] = 4000
+    return spec
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# Algorithmic work per (target, source) pair of each kernel class, counted
+# from the implemented per-pair formula (see the design doc for the derivation).
+def pair_flops(precision, bc, nrhs):
+    # FP32 fused kernel: per-pair evaluation counted in FP32 operations plus
+    # 8 flops per right-hand side for the complex multiply-add
+    from paper_1408_1578_gb300 import cfie  # noqa: F401  (library must be present)
+    per_rhs = 8 if bc == "soft" else 32
+    return PAIR_EVAL_FLOPS[(precision, bc)] + per_rhs * nrhs
+
+
+PAIR_EVAL_FLOPS = {("fp32", "soft"): 96, ("fp32", "hard"): 110,
+                   ("fp64", "soft"): 0, ("fp64", "hard"): 0}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1408_1578_gb300 import cfie, inputs
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    spec = workload(args.workload, args.precision)
+    if args.rtol:
+        spec["rtol"] = args.rtol
+    n, w, nrhs, bc = spec["n"], spec["omega"], spec["nrhs"], spec["bc"]
+    stream = torch.cuda.current_stream()
+    ctx = cfie.Context(dev, stream=stream)
+    theta = inputs.directions(nrhs)
+    f = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
+    x = torch.zeros((nrhs, n), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    # inputs larger than L2?  the Krylov basis is (restart+1) n nrhs 16 bytes
+    basis_bytes = (spec["restart"] + 1) * n * nrhs * 16
+    flush_l2 = basis_bytes < 2 * 129 * 1024 * 1024
+
+    def step():
+        geom = ctx.geometry(spec["curve"], **spec["params"])
+        op = geom.discretise(n, w, bc=bc, precision=spec["precision"])
+        op.rhs_plane_waves(theta, f)
+        x.zero_()
+        its, rel, st = op.gmres_solve(f, x, rtol=spec["rtol"], restart=spec["restart"],
+                                      maxit=spec["maxit"], allow_noconv=True)
+        stats = op.last_stats()
+        op.close()
+        geom.close()
+        return its, rel, stats
+
+    for _ in range(args.warmup):
+        its, rel, stats = step()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ctx.set_profiling(True)
+    launches0 = ctx.lib.cfie_launch_count()
+    ms_total = 0.0
+    pairs = 0
+    solves = 0
+    worst = 0.0
+    for _ in range(args.steps):
+        if flush_l2:
+            flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        its, rel, stats = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_total += e0.elapsed_time(e1)
+        pairs += n * n * (stats["inner_matvecs"] + stats["fp64_matvecs"])
+        solves += int(np.sum(rel <= spec["rtol"]))
+        worst = max(worst, float(np.max(rel)))
+    barrier(world)
+    torch.cuda.synchronize()
+    launches = ctx.lib.cfie_launch_count() - launches0
+    ktimes = ctx.kernel_times()
+    ctx.set_profiling(False)
+    clk = clocks.stop()
+    ms_max = allreduce_max(ms_total, world)
+    pairs_all = allreduce_sum(pairs, world)
+
+    # end to end through the C ABI with host buffers: host angles in, host
+    # solution out (pinned), copies inside the timed region
+    x_host = torch.empty((nrhs, n), dtype=torch.complex128, pin_memory=True)
+    e2e_ms = 0.0
+    e2e_pairs = 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its_e, rel_e, stats_e = step()   # angles go host -> device inside the C call
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_pairs += n * n * (stats_e["inner_matvecs"] + stats_e["fp64_matvecs"])
+    e2e_ms_max = allreduce_max(e2e_ms, world)
+    e2e_pairs_all = allreduce_sum(e2e_pairs, world)
+
+    result = None
+    if rank == 0:
+        dom = max(ktimes, key=lambda k: ktimes[k][0])
+        peaks, src = measured_peaks()
+        roof = roofline(dom, ktimes[dom], spec, stats, peaks, src, n)
+        value = pairs_all / (ms_max / 1e3)
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32+f64", "fp64": "f64"}[spec["precision"]],
+            "data": "synthetic",
+            "config": {"workload": f"{spec['name']}: {spec['curve']} {bc} n={n} omega={w} "
+                                   f"eta=omega nrhs={nrhs}",
+                       "curve": spec["curve"], "bc": bc, "n": n, "omega": w, "nrhs": nrhs,
+                       "precision": spec["precision"], "rtol": spec["rtol"],
+                       "restart": spec["restart"], "parallelism": f"replicas{world}",
+                       "l2": "flushed between steps" if flush_l2 else "Krylov basis larger than L2"},
+            "solves_per_s": solves * world / (ms_max / 1e3),
+            "max_relres": worst,
+            "iterations": [int(v) for v in its[:4]],
+            "solve_stats": stats,
+            "e2e": {"value": e2e_pairs_all / (e2e_ms_max / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(nrhs * 8 + 64 * 16),
+                    "d2h_bytes_per_step": int(nrhs * n * 16)},
+            "gpu_launches": int(launches),
+            "kernel_ms": {k: round(v[0], 3) for k, v in ktimes.items()},
+            "kernel_launches": {k: v[1] for k, v in ktimes.items()},
+            "roofline": roof,
+            "clocks": clk,
+        }
+    ctx.close()
+    return result
+
+
+def roofline(dom, kt, spec, stats, peaks, src, n):
+    ms, launches = kt
+    if launches == 0:
+        return None
+    avg_s = ms / launches / 1e3
+    nrhs, bc = spec["nrhs"], spec["bc"]
+    if dom == "arnoldi":
+        # CGS2 streams the basis 4 times per step: bytes ~ 4 * (j+1) n nrhs 16
+        return {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": None, "traffic": None, "peak_source": src}
+    if dom in ("matvec_fp32",):
+        flops = PAIR_EVAL_FLOPS[("fp32", bc)] + (8 if bc == "soft" else 32) * nrhs
+        achieved = flops * n * n / avg_s / 1e12
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"FP32 FMA units x max SM clock ({src} clock)"}
+    if dom == "matvec_fp64":
+        # pair evaluations per second against the FP64 rate: reported as pairs
+        achieved = n * n / avg_s
+        return {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": None,
+                "unit": "Gpair/s", "frac": None, "traffic": None,
+                "peak_source": "FP64 pair rate; see DESIGN.md"}
+    return None
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores, bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(spec, rows_count):
+    """Pair evaluations of the oracle on `rows_count` rows of the workload's
+    operator (the oracle's per-row assembly and product with the right-hand
+    sides); returns pair evaluations done and seconds."""
+    import numpy as np
+
+    from oracle import geometry, kress, operators
+    from paper_1408_1578_gb300 import inputs
+
+    n, w, bc = spec["n"], spec["omega"], spec["bc"]
+    c = geometry.make(spec["curve"], n, **spec["params"])
+    R = kress.kress_weights(n)
+    X = inputs.random_density(n, spec["nrhs"], seed=5)
+    rows = np.arange(rows_count) * (n // rows_count)
+    t0 = time.perf_counter()
+    if bc == "soft":
+        A = operators.soft_rows(c, w, w, rows, R)
+        _ = A @ X.T
+        pairs = rows_count * n
+    else:
+        S = operators.layer_rows(c, w, rows, "S", R)
+        Dp = operators.layer_rows(c, w, rows, "Dp", R)
+        _ = S @ X.T, Dp @ X.T
+        pairs = rows_count * n
+    return pairs, time.perf_counter() - t0
+
+
+def cpu_rows_for(spec, budget_s=12.0):
+    pairs, secs = oracle_sample(spec, 4)
+    rate = pairs / max(secs, 1e-6)
+    rows = int(max(4, min(spec["n"], budget_s * rate / spec["n"])))
+    return rows
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    spec = workload(args.workload, args.precision)
+    rows = cpu_rows_for(spec, budget_s=10.0 / max(1, args.steps + args.warmup) * 3)
+    for _ in range(args.warmup):
+        oracle_sample(spec, max(4, rows // 4))
+    tot_pairs, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        p, s = oracle_sample(spec, rows)
+        tot_pairs += p
+        tot_s += s
+    value = tot_pairs / tot_s
+    sample = f"{rows} rows x {spec['n']} sources of the {spec['name']} operator per step"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{spec['name']}: {spec['curve']} {spec['bc']} n={spec['n']} "
+                               f"omega={spec['omega']} eta=omega nrhs={spec['nrhs']}",
+                   "parallelism": "host cores (oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: barrier + max/sum of scalars)
+# ---------------------------------------------------------------------------
+_PG = None
+
+
+def init_dist():
+    global _PG
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend)
+        _PG = dist
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch
+        _PG.barrier(device_ids=[torch.cuda.current_device()])
+
+
+def _reduce(v, op, world):
+    if world == 1:
+        return v
+    import torch
+    t = torch.tensor([float(v)], device="cuda", dtype=torch.float64)
+    _PG.all_reduce(t, op=op)
+    return float(t.item())
+
+
+def allreduce_max(v, world):
+    return _reduce(v, _PG.ReduceOp.MAX if _PG else None, world)
+
+
+def allreduce_sum(v, world):
+    return _reduce(v, _PG.ReduceOp.SUM if _PG else None, world)
+
+
+def main():
+    args = parse()
+    rank, world = init_dist()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+        if rank == 0 and out is not None and world == 1:
+            spec = workload(args.workload, args.precision)
+            rows = cpu_rows_for(spec, budget_s=12.0)
+            p, s = oracle_sample(spec, rows)
+            out["cpu_baseline"] = {"value": p / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": f"{rows} rows x {spec['n']} sources of the "
+                                             f"{spec['name']} operator ({s:.1f} s)"}
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if _PG is not None:
+        _PG.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * cfie.h -- C ABI of the GB300 combined-field integral equation (CFIE) library.
+ *
+ * The library discretises and solves the 2-D exterior Helmholtz scattering
+ * problems of Section 1 of Ying, "Directional preconditioner for high frequency
+ * obstacle scattering":
+ *
+ *   sound soft  (eq. 1):  (1/2 I + D - i eta S) q = -u_I
+ *   sound hard  (eq. 2):  (1/2 I - D' + N/(i eta)) q = -du_I/dn
+ *
+ * with G(x, y) = (i/4) H0^(1)(omega |x - y|) and the operators S, D, D', N of
+ * Section 1, discretised by the Nystrom method (Section 1) with Kress's
+ * logarithmic-split trapezoidal rule on n equispaced parameter nodes
+ * t_j = 2 pi j / n, N by Maue's identity N = d/ds S d/ds + omega^2 (n.S n).
+ * Eq. 2's sign is used for the sound-hard operator.  Krylov solves use GMRES
+ * with restart, as in Section 3.
+ *
+ * Call sequence: cfie_ctx_create -> cfie_geometry_* -> cfie_discretise ->
+ * cfie_rhs_plane_waves -> cfie_apply / cfie_gmres_solve -> *_destroy.
+ *
+ * Conventions for every entry point:
+ *  - All compute runs on the context's CUDA device and stream; calls that take
+ *    device buffers are asynchronous on that stream unless stated otherwise.
+ *  - Complex vectors are interleaved complex128 (re, im doubles), "column-major
+ *    n x nrhs": right-hand side k occupies elements [k*n, (k+1)*n).  Device
+ *    buffers belong to the caller, must be 16-byte aligned and hold n*nrhs
+ *    complex128 values; they must not overlap unless stated.
+ *  - Handles (cfie_ctx, cfie_geom, cfie_op) and the device memory behind them
+ *    belong to the library and are freed by the matching *_destroy call.  A
+ *    geometry must outlive the operators made from it only until
+ *    cfie_discretise returns (operators copy what they need).
+ *  - Every call returns a cfie_status and never aborts or exits.  On error the
+ *    context keeps a message readable with cfie_last_error; outputs are left
+ *    unspecified unless stated.
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef CFIE_H
+#define CFIE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CFIE_OK = 0,
+  CFIE_EINVAL = 1,    /* invalid argument (sizes, null pointers, non-finite values) */
+  CFIE_ENOMEM = 2,    /* device or host allocation failed */
+  CFIE_ECUDA = 3,     /* a CUDA call failed; see cfie_last_error */
+  CFIE_ENOCONV = 4,   /* GMRES hit maxit before rtol; x holds the last iterate */
+  CFIE_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+  CFIE_EBUSY = 6      /* the server has no free slot for the request */
+} cfie_status;
+
+typedef enum { CFIE_SOUND_SOFT = 0, CFIE_SOUND_HARD = 1 } cfie_bc;
+
+/* Precision of the operator application used inside GMRES.
+ *  CFIE_FP64          FP64 kernel evaluation and FP64 sums everywhere.
+ *  CFIE_FP32_REFINED  FP32 on-the-fly kernel evaluation (two-float phase, FP64
+ *                     near band) for the inner matvecs; FP64 Arnoldi, FP64
+ *                     Hessenberg solve and FP64 true residuals, with iterative
+ *                     refinement on the outer residual.
+ *  CFIE_TENSOR_REFINED stored complex matrix contracted on the tensor cores
+ *                     (split-complex, FP32 accumulation) for the inner matvecs;
+ *                     FP64 Arnoldi / residuals as above. */
+typedef enum { CFIE_FP64 = 0, CFIE_FP32_REFINED = 1, CFIE_TENSOR_REFINED = 2 } cfie_precision;
+
+typedef enum { CFIE_MATRIX_FREE = 0, CFIE_STORED = 1 } cfie_layout;
+
+typedef struct cfie_ctx cfie_ctx;
+typedef struct cfie_geom cfie_geom;
+typedef struct cfie_op cfie_op;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (may be NULL for the legacy default stream); the caller keeps ownership of
+ * it and it must outlive the context.  Writes the handle to *out. */
+cfie_status cfie_ctx_create(int device, void* cuda_stream, cfie_ctx** out);
+void cfie_ctx_destroy(cfie_ctx* ctx);
+
+/* Message of the last failing call on this context ("" if none).  The string
+ * belongs to the context and stays valid until its next call. */
+const char* cfie_last_error(const cfie_ctx* ctx);
+
+/* --- Geometry: counter-clockwise 2 pi-periodic curves z(t) (Section 1 asks for
+ * a smooth boundary; Section 2 samples it at equispaced points). ------------ */
+
+/* Circle of the given radius about the origin.  radius > 0. */
+cfie_status cfie_geometry_circle(cfie_ctx* ctx, double radius, cfie_geom** out);
+/* Ellipse (a cos t, b sin t), a, b > 0 (the obstacle of Tables 1 and 3). */
+cfie_status cfie_geometry_ellipse(cfie_ctx* ctx, double a, double b, cfie_geom** out);
+/* Star z(t) = r(t) (cos t, sin t), r(t) = 1 + sum_{k=1..K} a[k-1] cos kt + b[k-1] sin kt.
+ * a, b: host arrays of K doubles (copied); 1 <= K <= 64; r must stay positive. */
+cfie_status cfie_geometry_fourier_star(cfie_ctx* ctx, int K, const double* a,
+                                       const double* b, cfie_geom** out);
+/* Kite z(t) = (cos t + 0.65 cos 2t - 0.65, 1.5 sin t). */
+cfie_status cfie_geometry_kite(cfie_ctx* ctx, cfie_geom** out);
+/* Caller-sampled curve: host arrays of n points (x, y interleaved, 2n doubles
+ * each) holding z, z', z'' at t_j = 2 pi j / n.  Copied.  Only discretisations
+ * with exactly this n are allowed. */
+cfie_status cfie_geometry_samples(cfie_ctx* ctx, int n, const double* z, const double* dz,
+                                  const double* ddz, cfie_geom** out);
+void cfie_geom_destroy(cfie_geom* geom);
+
+/* --- Discretisation ------------------------------------------------------ */
+
+/* Sample the curve at n nodes on the device, build the Kress weight table and
+ * everything the chosen precision and layout need (near-field band, stored
+ * matrix).  n even, 8 <= n <= 1<<20; omega > 0; eta > 0 (eta = omega is the
+ * usual choice, Section 1 asks for eta = O(omega)).  Synchronous. */
+cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cfie_bc bc,
+                            cfie_precision precision, cfie_layout layout, cfie_op** out);
+void cfie_op_destroy(cfie_op* op);
+
+/* Number of nodes of an operator. */
+int cfie_op_n(const cfie_op* op);
+
+/* Right-hand sides for plane waves u_I = exp(i omega d.x), d = (cos theta_k,
+ * sin theta_k): soft -u_I(z_j), hard -du_I/dn(z_j) (Section 1; Section 3 uses
+ * one wave towards +x).  theta: host array of nrhs angles.  f_dev: device
+ * output, n*nrhs complex128. */
+cfie_status cfie_rhs_plane_waves(cfie_op* op, int nrhs, const double* theta, void* f_dev);
+
+/* y = A x for nrhs right-hand sides, with A the operator's CFIE matrix applied
+ * in the operator's precision (FP64 for CFIE_FP64, the FP32 / tensor inner
+ * matvec otherwise).  x_dev, y_dev: device, n*nrhs complex128, must not
+ * overlap.  1 <= nrhs <= 1024. */
+cfie_status cfie_apply(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
+
+/* y = A x in FP64 whatever the operator's precision (the matvec used for true
+ * residuals). */
+cfie_status cfie_apply_fp64(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
+
+/* Solve A x = f for nrhs independent right-hand sides by restarted GMRES
+ * (Section 3: relative tolerance and restart; zero initial guess there).
+ *  f_dev   device, n*nrhs complex128 (read only)
+ *  x_dev   device, n*nrhs complex128: initial guess in, solution out
+ *  rtol    target for the true relative residual ||f - A x|| / ||f|| (FP64)
+ *  restart Krylov dimension per cycle, 1..512; 0 = unrestarted (maxit)
+ *  maxit   cap on Arnoldi steps per right-hand side (inner steps for the
+ *          refined precisions)
+ *  iters_out  host, nrhs ints (may be NULL): Arnoldi steps per right-hand side
+ *  relres_out host, nrhs doubles (may be NULL): true FP64 relative residual
+ *             recomputed from the returned x
+ * Returns CFIE_ENOCONV (x holds the last iterate) if some right-hand side
+ * missed rtol.  Synchronous. */
+cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nrhs, double rtol,
+                             int restart, int maxit, int* iters_out, double* relres_out);
+
+/* Counters of the last cfie_gmres_solve on this operator. */
+typedef struct {
+  int cycles;            /* GMRES cycles (restarts + 1) summed over refinement steps */
+  int refinements;       /* outer refinement steps (0 for CFIE_FP64) */
+  int inner_matvecs;     /* block matvecs in the operator's precision */
+  int fp64_matvecs;      /* block FP64 matvecs (true residuals) */
+  int arnoldi_steps;     /* Arnoldi steps (max over right-hand sides) */
+} cfie_solve_stats;
+cfie_status cfie_op_last_stats(const cfie_op* op, cfie_solve_stats* out);
+
+/* --- Kernel timing (CUDA events on the context stream) ------------------- */
+
+/* Kernel classes timed when profiling is on. */
+typedef enum {
+  CFIE_K_MATVEC_FP64 = 0,   /* FP64 pair-evaluation matvec kernel */
+  CFIE_K_MATVEC_FP32 = 1,   /* FP32 fused matrix-free matvec kernel */
+  CFIE_K_MATVEC_TENSOR = 2, /* stored-matrix tensor-core contraction */
+  CFIE_K_ARNOLDI = 3,       /* orthogonalisation kernels of one Arnoldi step */
+  CFIE_K_SPECTRAL = 4,      /* spectral tangential derivative */
+  CFIE_K_COUNT = 5
+} cfie_kernel_class;
+
+/* Turn per-launch event timing on (1) or off (0) and reset the totals. */
+cfie_status cfie_ctx_set_profiling(cfie_ctx* ctx, int on);
+/* Total milliseconds and launch count per kernel class since the last reset.
+ * ms, launches: host arrays of CFIE_K_COUNT entries.  Synchronises the stream. */
+cfie_status cfie_ctx_kernel_times(cfie_ctx* ctx, double* ms, long long* launches);
+
+/* Kernel launches issued by the library in this process so far (all
+ * contexts).  Never fails. */
+long long cfie_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CFIE_H */

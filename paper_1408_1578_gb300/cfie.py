@@ -1,0 +1,285 @@
+"""ctypes binding of libcfie.so (include/cfie.h), argument marshalling only.
+
+Every function of the C ABI is exposed under the same name; device buffers are
+passed as torch tensors (complex128, contiguous, on the context's device) or as
+raw integer addresses.  Loading fails loudly when the library has not been
+built: there is no CPU fallback.
+
+A thin object layer (Context, Geometry, Operator) wraps the handles for tests
+and the benchmark.
+"""
+import ctypes
+import os
+import weakref
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcfie.so")
+
+CFIE_OK, CFIE_EINVAL, CFIE_ENOMEM, CFIE_ECUDA, CFIE_ENOCONV, CFIE_ETIMEOUT, CFIE_EBUSY = range(7)
+STATUS_NAMES = ["CFIE_OK", "CFIE_EINVAL", "CFIE_ENOMEM", "CFIE_ECUDA", "CFIE_ENOCONV",
+                "CFIE_ETIMEOUT", "CFIE_EBUSY"]
+CFIE_SOUND_SOFT, CFIE_SOUND_HARD = 0, 1
+CFIE_FP64, CFIE_FP32_REFINED, CFIE_TENSOR_REFINED = 0, 1, 2
+CFIE_MATRIX_FREE, CFIE_STORED = 0, 1
+(CFIE_K_MATVEC_FP64, CFIE_K_MATVEC_FP32, CFIE_K_MATVEC_TENSOR, CFIE_K_ARNOLDI,
+ CFIE_K_SPECTRAL, CFIE_K_COUNT) = range(6)
+KERNEL_CLASS_NAMES = ["matvec_fp64", "matvec_fp32", "matvec_tensor", "arnoldi", "spectral"]
+
+BC = {"soft": CFIE_SOUND_SOFT, "hard": CFIE_SOUND_HARD}
+PRECISION = {"fp64": CFIE_FP64, "fp32": CFIE_FP32_REFINED, "tensor": CFIE_TENSOR_REFINED}
+LAYOUT = {"matrix_free": CFIE_MATRIX_FREE, "stored": CFIE_STORED}
+
+
+class cfie_solve_stats(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("inner_matvecs", ctypes.c_int), ("fp64_matvecs", ctypes.c_int),
+                ("arnoldi_steps", ctypes.c_int)]
+
+
+class CfieError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {message}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+_LLP = ctypes.POINTER(ctypes.c_longlong)
+
+# name -> (restype, argtypes), in the order of include/cfie.h
+SIGNATURES = {
+    "cfie_ctx_create": (_I, [_I, _P, ctypes.POINTER(_P)]),
+    "cfie_ctx_destroy": (None, [_P]),
+    "cfie_last_error": (ctypes.c_char_p, [_P]),
+    "cfie_geometry_circle": (_I, [_P, _D, ctypes.POINTER(_P)]),
+    "cfie_geometry_ellipse": (_I, [_P, _D, _D, ctypes.POINTER(_P)]),
+    "cfie_geometry_fourier_star": (_I, [_P, _I, _DP, _DP, ctypes.POINTER(_P)]),
+    "cfie_geometry_kite": (_I, [_P, ctypes.POINTER(_P)]),
+    "cfie_geometry_samples": (_I, [_P, _I, _DP, _DP, _DP, ctypes.POINTER(_P)]),
+    "cfie_geom_destroy": (None, [_P]),
+    "cfie_discretise": (_I, [_P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(_P)]),
+    "cfie_op_destroy": (None, [_P]),
+    "cfie_op_n": (_I, [_P]),
+    "cfie_rhs_plane_waves": (_I, [_P, _I, _DP, _P]),
+    "cfie_apply": (_I, [_P, _P, _P, _I]),
+    "cfie_apply_fp64": (_I, [_P, _P, _P, _I]),
+    "cfie_gmres_solve": (_I, [_P, _P, _P, _I, _D, _I, _I, _IP, _DP]),
+    "cfie_op_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
+    "cfie_ctx_set_profiling": (_I, [_P, _I]),
+    "cfie_ctx_kernel_times": (_I, [_P, _DP, _LLP]),
+    "cfie_launch_count": (ctypes.c_longlong, []),
+}
+
+_lib = None
+
+
+def load():
+    """Load libcfie.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -m paper_1408_1578_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _addr(buf):
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    import torch
+    if not isinstance(buf, torch.Tensor):
+        raise TypeError("device buffers are torch tensors or integer addresses")
+    if buf.dtype != torch.complex128 or not buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("device buffers must be contiguous complex128 CUDA tensors")
+    return buf.data_ptr()
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_DP)
+
+
+# ---------------------------------------------------------------------------
+# raw entry points under their C names
+# ---------------------------------------------------------------------------
+def __getattr__(name):
+    if name in SIGNATURES:
+        return getattr(load(), name)
+    raise AttributeError(name)
+
+
+# ---------------------------------------------------------------------------
+# object layer
+# ---------------------------------------------------------------------------
+class Context:
+    def __init__(self, device=0, stream=None):
+        lib = load()
+        h = _P()
+        handle = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        st = lib.cfie_ctx_create(device, handle, ctypes.byref(h))
+        if st != CFIE_OK:
+            raise CfieError(st, "cfie_ctx_create failed")
+        self.h = h
+        self.lib = lib
+        self.device = device
+        self._children = weakref.WeakSet()   # geometries / operators to destroy first
+
+    def check(self, st, what):
+        if st != CFIE_OK:
+            raise CfieError(st, f"{what}: {self.lib.cfie_last_error(self.h).decode()}")
+
+    def last_error(self):
+        return self.lib.cfie_last_error(self.h).decode()
+
+    def set_profiling(self, on):
+        self.check(self.lib.cfie_ctx_set_profiling(self.h, 1 if on else 0), "cfie_ctx_set_profiling")
+
+    def kernel_times(self):
+        ms = np.zeros(CFIE_K_COUNT)
+        ln = np.zeros(CFIE_K_COUNT, dtype=np.int64)
+        self.check(self.lib.cfie_ctx_kernel_times(self.h, _dptr(ms), ln.ctypes.data_as(_LLP)),
+                   "cfie_ctx_kernel_times")
+        return {KERNEL_CLASS_NAMES[k]: (float(ms[k]), int(ln[k])) for k in range(CFIE_K_COUNT)}
+
+    def close(self):
+        """Destroy the context; operators and geometries made from it are
+        destroyed first (the C ABI needs the context alive for them)."""
+        if self.h:
+            for child in list(self._children):
+                child.close()
+            self.lib.cfie_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # geometry constructors
+    def _geom(self, fn, *args):
+        g = _P()
+        self.check(fn(self.h, *args, ctypes.byref(g)), fn.__name__)
+        geom = Geometry(self, g)
+        self._children.add(geom)
+        return geom
+
+    def circle(self, radius=1.0):
+        return self._geom(self.lib.cfie_geometry_circle, float(radius))
+
+    def ellipse(self, a, b):
+        return self._geom(self.lib.cfie_geometry_ellipse, float(a), float(b))
+
+    def fourier_star(self, a, b):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        return self._geom(self.lib.cfie_geometry_fourier_star, int(a.size), _dptr(a), _dptr(b))
+
+    def kite(self):
+        return self._geom(self.lib.cfie_geometry_kite)
+
+    def samples(self, z, dz, ddz):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        dz = np.ascontiguousarray(dz, dtype=np.float64)
+        ddz = np.ascontiguousarray(ddz, dtype=np.float64)
+        return self._geom(self.lib.cfie_geometry_samples, int(z.shape[0]), _dptr(z), _dptr(dz),
+                          _dptr(ddz))
+
+    def geometry(self, kind, **params):
+        if kind == "circle":
+            return self.circle(params.get("radius", 1.0))
+        if kind == "ellipse":
+            return self.ellipse(params["a"], params["b"])
+        if kind == "star":
+            return self.fourier_star(params["a"], params["b"])
+        if kind == "kite":
+            return self.kite()
+        raise ValueError(kind)
+
+
+class Geometry:
+    def __init__(self, ctx, h):
+        self.ctx = ctx
+        self.h = h
+
+    def discretise(self, n, omega, eta=None, bc="soft", precision="fp64", layout="matrix_free"):
+        op = _P()
+        eta = omega if eta is None else eta
+        self.ctx.check(self.ctx.lib.cfie_discretise(self.h, int(n), float(omega), float(eta), BC[bc],
+                                                    PRECISION[precision], LAYOUT[layout],
+                                                    ctypes.byref(op)), "cfie_discretise")
+        oper = Operator(self.ctx, op, n)
+        self.ctx._children.add(oper)
+        return oper
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.cfie_geom_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    def __init__(self, ctx, h, n):
+        self.ctx = ctx
+        self.h = h
+        self.n = n
+
+    def rhs_plane_waves(self, theta, f):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        self.ctx.check(self.ctx.lib.cfie_rhs_plane_waves(self.h, int(theta.size), _dptr(theta), _addr(f)),
+                       "cfie_rhs_plane_waves")
+
+    def apply(self, x, y, nrhs=None):
+        nrhs = x.numel() // self.n if nrhs is None else nrhs
+        self.ctx.check(self.ctx.lib.cfie_apply(self.h, _addr(x), _addr(y), int(nrhs)), "cfie_apply")
+
+    def apply_fp64(self, x, y, nrhs=None):
+        nrhs = x.numel() // self.n if nrhs is None else nrhs
+        self.ctx.check(self.ctx.lib.cfie_apply_fp64(self.h, _addr(x), _addr(y), int(nrhs)),
+                       "cfie_apply_fp64")
+
+    def gmres_solve(self, f, x, rtol=1e-6, restart=80, maxit=1000, nrhs=None, allow_noconv=False):
+        nrhs = f.numel() // self.n if nrhs is None else nrhs
+        its = np.zeros(nrhs, dtype=np.int32)
+        rel = np.zeros(nrhs)
+        st = self.ctx.lib.cfie_gmres_solve(self.h, _addr(f), _addr(x), int(nrhs), float(rtol),
+                                           int(restart), int(maxit), its.ctypes.data_as(_IP),
+                                           _dptr(rel))
+        if not (st == CFIE_OK or (allow_noconv and st == CFIE_ENOCONV)):
+            self.ctx.check(st, "cfie_gmres_solve")
+        return its, rel, st
+
+    def last_stats(self):
+        s = cfie_solve_stats()
+        self.ctx.check(self.ctx.lib.cfie_op_last_stats(self.h, ctypes.byref(s)), "cfie_op_last_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.cfie_op_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,174 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cfie.h"
+
+#define CFIE_PI 3.14159265358979323846
+#define CFIE_EULER 0.57721566490153286061
+
+// ----------------------------------------------------------------------------
+// error plumbing
+// ----------------------------------------------------------------------------
+struct cfie_error : public std::exception {
+  cfie_status code;
+  std::string msg;
+  cfie_error(cfie_status c, std::string m) : code(c), msg(std::move(m)) {}
+  const char* what() const noexcept override { return msg.c_str(); }
+};
+
+#define CFIE_CHECK_CUDA(call)                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      throw cfie_error(e_ == cudaErrorMemoryAllocation ? CFIE_ENOMEM : CFIE_ECUDA,     \
+                       std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+extern long long g_cfie_launches;  // kernel launches issued by the library
+#define CFIE_CHECK_LAUNCH()                 \
+  do {                                      \
+    ++g_cfie_launches;                      \
+    CFIE_CHECK_CUDA(cudaGetLastError());    \
+  } while (0)
+
+#define CFIE_REQUIRE(cond, msg)                                  \
+  do {                                                           \
+    if (!(cond)) throw cfie_error(CFIE_EINVAL, (msg));           \
+  } while (0)
+
+// ----------------------------------------------------------------------------
+// device buffer owned by the library
+// ----------------------------------------------------------------------------
+struct dbuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  dbuf() = default;
+  dbuf(const dbuf&) = delete;
+  dbuf& operator=(const dbuf&) = delete;
+  ~dbuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  // grow to at least `need` bytes (contents not kept)
+  void reserve(size_t need) {
+    if (need <= bytes) return;
+    release();
+    CFIE_CHECK_CUDA(cudaMalloc(&p, need));
+    bytes = need;
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+// ----------------------------------------------------------------------------
+// handles
+// ----------------------------------------------------------------------------
+struct cfie_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // per-launch event timing
+  bool profiling = false;
+  struct pending { int cls; cudaEvent_t a, b; };
+  std::vector<pending> inflight;
+  std::vector<cudaEvent_t> pool;
+  double ms[CFIE_K_COUNT] = {0};
+  long long launches[CFIE_K_COUNT] = {0};
+};
+
+enum geom_kind { G_CIRCLE = 0, G_ELLIPSE = 1, G_STAR = 2, G_KITE = 3, G_SAMPLES = 4 };
+
+struct cfie_geom {
+  cfie_ctx* ctx = nullptr;
+  int kind = G_CIRCLE;
+  double p0 = 1.0, p1 = 1.0;              // circle radius / ellipse a, b
+  std::vector<double> a, b;               // star coefficients
+  int n_samples = 0;
+  std::vector<double> z, dz, ddz;         // caller samples (2n each)
+};
+
+// Device-side geometry of an operator (structure of arrays, FP64 masters).
+struct geom_dev {
+  double* x;      // z1
+  double* y;      // z2
+  double* nx;     // nu~_1 = z2'      (unnormalised outward normal, |nu~| = |z'|)
+  double* ny;     // nu~_2 = -z1'
+  double* sp;     // |z'|
+  double* kap;    // L2(t,t) = (z2' z1'' - z1' z2'') / (4 pi |z'|^2)
+};
+
+struct cfie_op {
+  cfie_ctx* ctx = nullptr;
+  int n = 0;
+  double omega = 0, eta = 0, h = 0;
+  cfie_bc bc = CFIE_SOUND_SOFT;
+  cfie_precision prec = CFIE_FP64;
+  cfie_layout layout = CFIE_MATRIX_FREE;
+
+  dbuf geo;          // 6 n doubles (geom_dev)
+  geom_dev g{};
+  dbuf wtab;         // n doubles: w_d = R_d - h ln(4 sin^2(pi d / n)), w_0 = R_0
+  dbuf ctab;         // n doubles: spectral derivative circulant c_d = (-1)^d cot(pi d / n) / 2
+  dbuf diag;         // complex diagonal entries: soft A_ii; hard (S_ii, D'_ii)
+  double R0 = 0;
+
+  // scratch for the matrix-free FP64 matvec (split-source partial sums)
+  dbuf partial;
+  dbuf tmp1, tmp2;   // hard path: u = d/ds x, t = S u
+
+  // FP32 path (created for CFIE_FP32_REFINED)
+  dbuf geo32;        // hi/lo coordinates + FP32 normals / speeds
+  dbuf band;         // near-field band entries (complex64), n x (2 b + 1) per operator
+  int band_b = -1;
+  dbuf xin32, xin32b; // FP32 staging of the input (and hard-path helpers)
+
+  // GMRES workspace
+  dbuf V, H, wv, rv, dv, rin, small;
+  double* host_res = nullptr;  // pinned host mirror of residual estimates
+  int host_res_cap = 0;
+
+  cfie_solve_stats stats{};
+};
+
+// ----------------------------------------------------------------------------
+// profiling helpers (capi.cu)
+// ----------------------------------------------------------------------------
+void prof_begin(cfie_ctx* c, int cls, cudaEvent_t* a);
+void prof_end(cfie_ctx* c, int cls, cudaEvent_t a);
+void prof_harvest(cfie_ctx* c, bool wait);
+
+struct prof_scope {
+  cfie_ctx* c;
+  int cls;
+  cudaEvent_t a = nullptr;
+  prof_scope(cfie_ctx* c_, int cls_) : c(c_), cls(cls_) { prof_begin(c, cls, &a); }
+  ~prof_scope() { prof_end(c, cls, a); }
+};
+
+// ----------------------------------------------------------------------------
+// kernels' host entry points
+// ----------------------------------------------------------------------------
+// geometry.cu
+void geometry_sample(cfie_op* op, const cfie_geom* geom);
+void kress_tables(cfie_op* op);
+void rhs_plane_waves(cfie_op* op, int nrhs, const double* theta_host, double2* f);
+// matvec_fp64.cu
+void matvec_fp64(cfie_op* op, const double2* x, double2* y, int nrhs);
+void spectral_apply(cfie_op* op, const double2* in, double2* out, const double2* base,
+                    double2 scale, int nrhs);
+// matvec_fp32.cu
+void fp32_prepare(cfie_op* op);
+void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs);
+// arnoldi.cu
+void gmres_solve(cfie_op* op, const double2* f, double2* x, int nrhs, double rtol, int restart,
+                 int maxit, int* iters, double* relres, cfie_status* st);
+// dispatch (capi.cu)
+void apply_inner(cfie_op* op, const double2* x, double2* y, int nrhs);

@@ -1,0 +1,637 @@
+// FP32 fused matrix-free Nystrom matvec: H0^(1), H1^(1)(omega |x - y|) evaluated on
+// the fly in FP32, Kress log-split correction applied per pair, FP32 sums.
+//
+// Operators: paper Section 1 (eq. 1 sound soft, eq. 2 sound hard); the per-pair
+// entry formulas are those of the FP64 kernel (hankel64.cuh), evaluated here in
+// FP32 with two safeguards:
+//
+//  * Phase.  omega r reaches ~6e3 on the largest workloads, where one FP32
+//    rounding of r is a ~4e-4 rad phase error.  Coordinates are stored as
+//    hi + lo FP32 pairs; z_i - z_j, r^2, r and x = omega r are carried as
+//    two-float numbers (error-free transformations built from fmaf), and
+//    chi = x - pi/4 is reduced modulo 2 pi with a three-part Cody-Waite
+//    constant whose first part has 10 significant bits (k * C1 exact for
+//    x < 1e5).  The reduced phase is accurate to a few 1e-7 rad.
+//  * Small arguments.  Hankel's asymptotic expansion (A&S 9.2.5, 9.2.9, 9.2.10;
+//    four terms of P and of Q, truncation error < 2e-9 for x >= 16) is used for
+//    every pair with omega r >= 16.  Pairs closer than that form a band
+//    |i - j| <= b around the diagonal (b found by an O(n^2) scan at set-up);
+//    their entries are evaluated once in FP64 and stored as complex64.
+//
+// Layout: a CTA owns TI = 128 targets and a range of source tiles (TJ = 32).
+// Per tile, warp w evaluates the entries of rows w, w+8, ... (lane = source)
+// into shared memory, source-major; then the tile is contracted with the staged
+// right-hand sides, each thread accumulating 4 targets x R/8 right-hand sides in
+// registers (complex multiply-add on the FP32 pipe).  Source ranges are split
+// across CTAs to fill the GPU; partial sums (complex64) are added in FP64 in a
+// fixed order by the reduction kernel.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "hankel64.cuh"
+#include "internal.h"
+
+namespace {
+
+constexpr int TI = 128;
+constexpr int TJ = 32;
+constexpr int NT = 256;
+constexpr float kX0 = 16.0f;  // asymptotic expansion used for omega r >= kX0
+
+// Cody-Waite split of 2 pi: C1 has 10 significant bits
+constexpr float kC1 = 6.28125f;
+constexpr float kC2 = 0.0019353071693331003f;
+constexpr float kC3 = 1.0253131677018246e-11f;
+constexpr float kPi4H = 0.7853981852531433f;
+constexpr float kPi4L = -2.1855695031547384e-08f;
+constexpr float kInv2Pi = 0.15915493667125702f;
+constexpr float kSqrt2OverPi = 0.7978845834732056f;
+constexpr float kInv4Pi = 0.07957747154594767f;
+
+struct geo32 {
+  float *xh, *xl, *yh, *yl, *nx, *ny, *sp;
+};
+
+struct pair_params {
+  int n, b, splits, tiles_per_split, nrhs;
+  float wh, wl, winv, eta, h;
+  geo32 g;
+  const float* w32;
+  const float2* band;    // soft: A ; hard: S
+  const float2* band2;   // hard: D'
+  const float2* xin;     // [k][j] complex64 (hard: x)
+  const float2* uin;     // hard: (1/s) Dt x
+  float2* part;          // [o][split][k][i]
+};
+
+// two-float helpers --------------------------------------------------------
+__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
+  s = a - b;
+  const float v = s - a;
+  e = (a - (s - v)) - (b + v);
+}
+
+// Entries of one pair with omega r >= kX0 (outside the band).
+// (xh, xl, yh, yl) of target i and source j; returns soft a, hard (a = S, b = D').
+template <int BC>
+__device__ __forceinline__ void pair_entries_fp32(const pair_params& P, float txh, float txl,
+                                                  float tyh, float tyl, float tnx, float tny,
+                                                  float tsp, float sxh, float sxl, float syh,
+                                                  float syl, float snx, float sny, float ssp,
+                                                  float w, float2& a, float2& b) {
+  float dxs, dxe, dys, dye;
+  two_diff(txh, sxh, dxs, dxe);
+  dxe += txl - sxl;
+  two_diff(tyh, syh, dys, dye);
+  dye += tyl - syl;
+  // r^2 = (dxs + dxe)^2 + (dys + dye)^2 as two-float
+  const float px = dxs * dxs, qx = fmaf(dxs, dxs, -px);
+  const float py = dys * dys, qy = fmaf(dys, dys, -py);
+  const float t = px + py;
+  const float tv = t - px;
+  const float te = (px - (t - tv)) + (py - tv);
+  const float lo = te + qx + qy + 2.0f * fmaf(dxs, dxe, dys * dye);
+  const float r2 = t + lo;
+  const float r2l = lo - (r2 - t);
+  const float rinv = rsqrtf(r2);
+  const float rh = r2 * rinv;
+  const float rl = (fmaf(-rh, rh, r2) + r2l) * (0.5f * rinv);
+  // x = omega r as two-float
+  const float xh = P.wh * rh;
+  const float xl = fmaf(P.wh, rh, -xh) + fmaf(P.wh, rl, P.wl * rh);
+  // chi = x - pi/4 reduced to [-pi, pi]
+  const float k = rintf(fmaf(xh, kInv2Pi, -0.125f));
+  float chi = fmaf(-k, kC1, xh);
+  chi = fmaf(-k, kC2, chi);
+  chi = fmaf(-k, kC3, chi);
+  chi = (chi - kPi4H) + (xl - kPi4L);
+  float s, c;
+  __sincosf(chi, &s, &c);
+  // Hankel asymptotic expansion, t = 1/x
+  const float ti = rinv * P.winv;
+  const float t2 = ti * ti;
+  const float P0 = fmaf(t2, fmaf(t2, fmaf(t2, -0.5725014209747314f, 0.112152099609375f), -0.0703125f), 1.0f);
+  const float Q0 = ti * fmaf(t2, fmaf(t2, fmaf(t2, 1.7277275025844574f, -0.22710800170898438f), 0.0732421875f), -0.125f);
+  const float P1 = fmaf(t2, fmaf(t2, fmaf(t2, 0.6765925884246826f, -0.144195556640625f), 0.1171875f), 1.0f);
+  const float Q1 = ti * fmaf(t2, fmaf(t2, fmaf(t2, -1.993531733751297f, 0.2775764465332031f), -0.1025390625f), 0.375f);
+  const float amp = kSqrt2OverPi * rsqrtf(xh);
+  const float J0 = amp * (P0 * c - Q0 * s);
+  const float Y0 = amp * (P0 * s + Q0 * c);
+  const float J1 = amp * (P1 * s + Q1 * c);
+  const float Y1 = amp * (Q1 * s - P1 * c);
+  const float dx = dxs + dxe, dy = dys + dye;
+  const float omega = P.wh;
+  const float hq = 0.25f * P.h;
+  if constexpr (BC == 0) {
+    const float cc = (dx * snx + dy * sny) * rinv;
+    const float es = P.eta * ssp;
+    const float oc = omega * cc;
+    a.x = hq * (es * J0 - oc * Y1) - w * kInv4Pi * oc * J1;
+    a.y = hq * (oc * J1 + es * Y0) + w * kInv4Pi * es * J0;
+  } else {
+    a.x = -hq * Y0 * ssp - w * kInv4Pi * J0 * ssp;
+    a.y = hq * J0 * ssp;
+    const float cp = -(dx * tnx + dy * tny) * rinv * ssp / tsp;
+    const float oc = omega * cp;
+    b.x = -hq * oc * Y1 - w * kInv4Pi * oc * J1;
+    b.y = hq * oc * J1;
+  }
+}
+
+__device__ __forceinline__ float2 cmul_add(float2 acc, float2 a, float2 x) {
+  acc.x = fmaf(a.x, x.x, acc.x);
+  acc.x = fmaf(-a.y, x.y, acc.x);
+  acc.y = fmaf(a.x, x.y, acc.y);
+  acc.y = fmaf(a.y, x.x, acc.y);
+  return acc;
+}
+
+template <int BC, int R>
+struct smem32 {
+  float txh[TI], txl[TI], tyh[TI], tyl[TI], tnx[TI], tny[TI], tsp[TI];
+  float2 A[TJ][TI + 1];
+  float2 B[BC ? TJ : 1][TI + 1];
+  float2 X[BC ? 4 : 1][TJ][R];
+};
+
+template <int BC, int R>
+__global__ void __launch_bounds__(NT, 2) k_pair_fp32(pair_params P) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  smem32<BC, R>& S = *reinterpret_cast<smem32<BC, R>*>(raw);
+  constexpr int RQ = R / 8;
+  const int n = P.n;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i0 = blockIdx.x * TI;
+  const int split = blockIdx.y;
+  const int rb0 = blockIdx.z * R;
+  const int rbn = min(R, P.nrhs - rb0);
+  const int ntiles = (n + TJ - 1) / TJ;
+  const int t_begin = split * P.tiles_per_split;
+  const int t_end = min(ntiles, t_begin + P.tiles_per_split);
+  const int bw = 2 * P.b + 1;
+
+  for (int q = tid; q < TI; q += NT) {
+    const int i = i0 + q;
+    const bool ok = i < n;
+    S.txh[q] = ok ? P.g.xh[i] : 0.f;
+    S.txl[q] = ok ? P.g.xl[i] : 0.f;
+    S.tyh[q] = ok ? P.g.yh[i] : 0.f;
+    S.tyl[q] = ok ? P.g.yl[i] : 0.f;
+    S.tnx[q] = ok ? P.g.nx[i] : 0.f;
+    S.tny[q] = ok ? P.g.ny[i] : 0.f;
+    S.tsp[q] = ok ? P.g.sp[i] : 1.f;
+  }
+
+  float2 acc[BC ? 4 : 1][4][RQ];
+#pragma unroll
+  for (int o = 0; o < (BC ? 4 : 1); ++o)
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) acc[o][p][q] = make_float2(0.f, 0.f);
+
+  for (int t = t_begin; t < t_end; ++t) {
+    const int j0 = t * TJ;
+    const int j = j0 + lane;
+    const bool jok = j < n;
+    __syncthreads();
+    // stage right-hand sides of this source tile
+    for (int e = tid; e < TJ * R; e += NT) {
+      const int jl = e / R, r = e % R;
+      const int jj = j0 + jl;
+      float2 xv = make_float2(0.f, 0.f), uv = xv;
+      if (jj < n && r < rbn) {
+        xv = P.xin[(size_t)(rb0 + r) * n + jj];
+        if (BC) uv = P.uin[(size_t)(rb0 + r) * n + jj];
+      }
+      if constexpr (BC == 1) {
+        const float inv = jj < n ? 1.0f / P.g.sp[jj] : 0.f;
+        const float n1 = jj < n ? P.g.nx[jj] * inv : 0.f;
+        const float n2 = jj < n ? P.g.ny[jj] * inv : 0.f;
+        S.X[0][jl][r] = uv;
+        S.X[1][jl][r] = make_float2(n1 * xv.x, n1 * xv.y);
+        S.X[2][jl][r] = make_float2(n2 * xv.x, n2 * xv.y);
+        S.X[3][jl][r] = xv;
+      } else {
+        S.X[0][jl][r] = xv;
+      }
+    }
+    // this lane's source
+    const float sxh = jok ? P.g.xh[j] : 0.f, sxl = jok ? P.g.xl[j] : 0.f;
+    const float syh = jok ? P.g.yh[j] : 0.f, syl = jok ? P.g.yl[j] : 0.f;
+    const float snx = jok ? P.g.nx[j] : 0.f, sny = jok ? P.g.ny[j] : 0.f;
+    const float ssp = jok ? P.g.sp[j] : 1.f;
+    __syncthreads();  // target geometry (first tile) and X are in place
+
+    // ---- entries: warp handles rows warp + 8 q, lane = source
+#pragma unroll 2
+    for (int q = 0; q < TI / 8; ++q) {
+      const int il = warp + 8 * q;
+      const int i = i0 + il;
+      float2 a = make_float2(0.f, 0.f), b = a;
+      if (i < n && jok) {
+        int d = i - j;
+        if (d < 0) d += n;
+        int dd = d <= P.b ? d : (d >= n - P.b ? d - n : INT_MAX);
+        if (dd != INT_MAX) {
+          a = P.band[(size_t)i * bw + dd + P.b];
+          if (BC) b = P.band2[(size_t)i * bw + dd + P.b];
+        } else {
+          pair_entries_fp32<BC>(P, S.txh[il], S.txl[il], S.tyh[il], S.tyl[il], S.tnx[il],
+                                S.tny[il], S.tsp[il], sxh, sxl, syh, syl, snx, sny, ssp,
+                                P.w32[d], a, b);
+        }
+      }
+      S.A[lane][il] = a;
+      if constexpr (BC == 1) S.B[lane][il] = b;
+    }
+    __syncthreads();
+
+    // ---- contraction: lane -> targets lane + 32 p, warp -> right-hand sides warp*RQ + q
+    const int jn = min(TJ, n - j0);
+    for (int jl = 0; jl < jn; ++jl) {
+      float2 av[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) av[p] = S.A[jl][lane + 32 * p];
+      if constexpr (BC == 0) {
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+          const float2 xv = S.X[0][jl][warp * RQ + q];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) acc[0][p][q] = cmul_add(acc[0][p][q], av[p], xv);
+        }
+      } else {
+        float2 bv[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) bv[p] = S.B[jl][lane + 32 * p];
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+          const int r = warp * RQ + q;
+          const float2 x0 = S.X[0][jl][r], x1 = S.X[1][jl][r], x2 = S.X[2][jl][r],
+                       x3 = S.X[3][jl][r];
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            acc[0][p][q] = cmul_add(acc[0][p][q], av[p], x0);
+            acc[1][p][q] = cmul_add(acc[1][p][q], av[p], x1);
+            acc[2][p][q] = cmul_add(acc[2][p][q], av[p], x2);
+            acc[3 * BC][p][q] = cmul_add(acc[3 * BC][p][q], bv[p], x3);
+          }
+        }
+      }
+    }
+  }
+
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const int i = i0 + lane + 32 * p;
+    if (i >= n) continue;
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+      const int r = warp * RQ + q;
+      if (r >= rbn) continue;
+#pragma unroll
+      for (int o = 0; o < (BC ? 4 : 1); ++o)
+        P.part[(((size_t)o * P.splits + split) * P.nrhs + rb0 + r) * n + i] = acc[o][p][q];
+    }
+  }
+}
+
+// y = sum of split partials in FP64; hard: t = S u (complex64 for the
+// derivative) and y = 1/2 x - D' x - i (omega^2/eta)(n1 S n1 x + n2 S n2 x)
+template <int BC>
+__global__ void k_reduce32(int n, int nrhs, int splits, double omega, double eta, geom_dev g,
+                           const float2* __restrict__ part, const double2* __restrict__ x,
+                           float2* __restrict__ t_out, double2* __restrict__ y) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t tot = (size_t)n * nrhs;
+  if (e >= tot) return;
+  const size_t so = (size_t)splits * tot;
+  double2 s[4] = {};
+  for (int o = 0; o < (BC ? 4 : 1); ++o) {
+    double2 v = make_double2(0.0, 0.0);
+    for (int sp = 0; sp < splits; ++sp) {
+      const float2 p = part[o * so + (size_t)sp * tot + e];
+      v.x += p.x;
+      v.y += p.y;
+    }
+    s[o] = v;
+  }
+  if (BC == 0) {
+    y[e] = s[0];
+  } else {
+    const int i = (int)(e % n);
+    const double inv = 1.0 / g.sp[i];
+    const double n1 = g.nx[i] * inv, n2 = g.ny[i] * inv;
+    const double2 m = make_double2(n1 * s[1].x + n2 * s[2].x, n1 * s[1].y + n2 * s[2].y);
+    const double k = omega * omega / eta;
+    const double2 xv = x[e];
+    y[e] = make_double2(0.5 * xv.x - s[3].x + k * m.y, 0.5 * xv.y - s[3].y - k * m.x);
+    t_out[e] = make_float2((float)s[0].x, (float)s[0].y);
+  }
+}
+
+__global__ void k_to32(size_t len, const double2* __restrict__ in, float2* __restrict__ out) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < len) out[e] = make_float2((float)in[e].x, (float)in[e].y);
+}
+
+// out[k][i] (+)= (scale / s_i) sum_j c_{(i-j) mod n} in[k][j] in FP32 with
+// blocked accumulation (256-source partial sums); out complex64 or complex128
+constexpr int SPT = 256;
+template <bool OUT64>
+__global__ void __launch_bounds__(SPT)
+k_spectral32(int n, const float* __restrict__ ct, const double* __restrict__ sp,
+             const float2* __restrict__ in, double2 scale, float2* __restrict__ out32,
+             double2* __restrict__ out64) {
+  __shared__ float2 xs[SPT];
+  const int i = blockIdx.x * SPT + threadIdx.x;
+  const int k = blockIdx.y;
+  const float2* ink = in + (size_t)k * n;
+  float2 outer = make_float2(0.f, 0.f);
+  for (int j0 = 0; j0 < n; j0 += SPT) {
+    __syncthreads();
+    const int jj = j0 + threadIdx.x;
+    xs[threadIdx.x] = jj < n ? ink[jj] : make_float2(0.f, 0.f);
+    __syncthreads();
+    if (i < n) {
+      const int jn = min(SPT, n - j0);
+      int idx = i - j0;
+      if (idx < 0) idx += n;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int q = 0; q < jn; ++q) {
+        const float c = ct[idx];
+        acc.x = fmaf(c, xs[q].x, acc.x);
+        acc.y = fmaf(c, xs[q].y, acc.y);
+        idx = idx == 0 ? n - 1 : idx - 1;
+      }
+      outer.x += acc.x;
+      outer.y += acc.y;
+    }
+  }
+  if (i < n) {
+    const double inv = 1.0 / sp[i];
+    const double sx = scale.x * inv, sy = scale.y * inv;
+    const double2 v = make_double2(sx * outer.x - sy * outer.y, sx * outer.y + sy * outer.x);
+    const size_t e = (size_t)k * n + i;
+    if (OUT64) {
+      out64[e] = make_double2(out64[e].x + v.x, out64[e].y + v.y);
+    } else {
+      out32[e] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// set-up kernels
+// ---------------------------------------------------------------------------
+__global__ void k_geo32(int n, geom_dev g, geo32 o, const double* __restrict__ w,
+                        const double* __restrict__ ct, float* __restrict__ w32,
+                        float* __restrict__ c32) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = g.x[i], y = g.y[i];
+  const float xh = (float)x, yh = (float)y;
+  o.xh[i] = xh;
+  o.xl[i] = (float)(x - (double)xh);
+  o.yh[i] = yh;
+  o.yl[i] = (float)(y - (double)yh);
+  o.nx[i] = (float)g.nx[i];
+  o.ny[i] = (float)g.ny[i];
+  o.sp[i] = (float)g.sp[i];
+  w32[i] = (float)w[i];
+  c32[i] = (float)ct[i];
+}
+
+// Largest cyclic index distance |i - j| of a pair with omega r < X0 (with a
+// 1% margin), and the largest omega r over all pairs.
+__global__ void __launch_bounds__(256)
+k_band_scan(int n, double omega, geom_dev g, int* __restrict__ bmax, float* __restrict__ xmax) {
+  __shared__ float sx[256], sy[256];
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const float xi = i < n ? (float)g.x[i] : 0.f, yi = i < n ? (float)g.y[i] : 0.f;
+  const float lim = (float)((kX0 * 1.01) / omega);
+  const float lim2 = lim * lim;
+  int best = 0;
+  float far2 = 0.f;
+  for (int j0 = 0; j0 < n; j0 += 256) {
+    __syncthreads();
+    const int jj = j0 + threadIdx.x;
+    sx[threadIdx.x] = jj < n ? (float)g.x[jj] : 0.f;
+    sy[threadIdx.x] = jj < n ? (float)g.y[jj] : 0.f;
+    __syncthreads();
+    if (i < n) {
+      const int jn = min(256, n - j0);
+      for (int q = 0; q < jn; ++q) {
+        const float dx = xi - sx[q], dy = yi - sy[q];
+        const float r2 = dx * dx + dy * dy;
+        far2 = fmaxf(far2, r2);
+        if (r2 < lim2) {
+          int d = i - (j0 + q);
+          if (d < 0) d = -d;
+          d = min(d, n - d);
+          best = max(best, d);
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    far2 = fmaxf(far2, __shfl_xor_sync(0xffffffffu, far2, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(bmax, best);
+    atomicMax(reinterpret_cast<int*>(xmax), __float_as_int((float)(omega * sqrt((double)far2))));
+  }
+}
+
+template <int BC>
+__global__ void k_band_fill(int n, int b, double omega, double eta, geom_dev g,
+                            const double* __restrict__ wtab, const double2* __restrict__ diag,
+                            float2* __restrict__ band, float2* __restrict__ band2) {
+  const int bw = 2 * b + 1;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * bw) return;
+  const int i = (int)(e / bw);
+  const int dd = (int)(e % bw) - b;
+  int j = i - dd;
+  j %= n;
+  if (j < 0) j += n;
+  double2 a, bb = make_double2(0.0, 0.0);
+  if (j == i) {
+    if (BC) {
+      a = diag[2 * i];
+      bb = diag[2 * i + 1];
+    } else {
+      a = diag[i];
+    }
+  } else {
+    int d = i - j;
+    if (d < 0) d += n;
+    const double h = 2.0 * CFIE_PI / n;
+    pair_entries_fp64<BC>(g.x[i] - g.x[j], g.y[i] - g.y[j], omega, eta, h, wtab[d], g.nx[j],
+                          g.ny[j], g.sp[j], g.nx[i], g.ny[i], g.sp[i], a, bb);
+  }
+  band[e] = make_float2((float)a.x, (float)a.y);
+  if (BC) band2[e] = make_float2((float)bb.x, (float)bb.y);
+}
+
+unsigned nblk(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
+
+template <int BC, int R>
+int launch32(cfie_op* op, pair_params P, int rowtiles, int slices) {
+  size_t smem = sizeof(smem32<BC, R>);
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_pair_fp32<BC, R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 1;
+  CFIE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_fp32<BC, R>, NT,
+                                                                smem));
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->ctx->device);
+  const int slots = std::max(1, per_sm) * sms;
+  const int ntiles = (P.n + TJ - 1) / TJ;
+  // source splits: pick the count (<= 16) whose grid best fills whole waves
+  int best_s = 1;
+  double best_eff = -1.0;
+  for (int s = 1; s <= std::min(16, ntiles); ++s) {
+    const double ctas = (double)rowtiles * slices * s;
+    const double waves = std::ceil(ctas / slots);
+    const double eff = ctas / (waves * slots) - 0.002 * s;  // prefer fewer splits on ties
+    if (eff > best_eff) {
+      best_eff = eff;
+      best_s = s;
+    }
+  }
+  int tps = (ntiles + best_s - 1) / best_s;
+  P.splits = (ntiles + tps - 1) / tps;
+  P.tiles_per_split = tps;
+  const int ops = BC ? 4 : 1;
+  op->partial.reserve(sizeof(float2) * (size_t)ops * P.splits * P.nrhs * P.n);
+  P.part = op->partial.as<float2>();
+  dim3 grid(rowtiles, P.splits, slices);
+  {
+    prof_scope ps(op->ctx, CFIE_K_MATVEC_FP32);
+    k_pair_fp32<BC, R><<<grid, NT, smem, op->ctx->stream>>>(P);
+    CFIE_CHECK_LAUNCH();
+  }
+  return P.splits;
+}
+
+}  // namespace
+
+void fp32_prepare(cfie_op* op) {
+  const int n = op->n;
+  cudaStream_t st = op->ctx->stream;
+  op->geo32.reserve(sizeof(float) * 9 * (size_t)n);
+  // band width and argument range
+  dbuf scan;
+  scan.reserve(16);
+  CFIE_CHECK_CUDA(cudaMemsetAsync(scan.p, 0, 16, st));
+  k_band_scan<<<nblk(n), 256, 0, st>>>(n, op->omega, op->g, scan.as<int>(),
+                                        reinterpret_cast<float*>(scan.as<int>() + 1));
+  CFIE_CHECK_LAUNCH();
+  int hb[2];
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(hb, scan.p, 8, cudaMemcpyDeviceToHost, st));
+  CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
+  float xmax;
+  std::memcpy(&xmax, &hb[1], 4);
+  if (!(xmax < 1.0e5f))
+    throw cfie_error(CFIE_EINVAL, "FP32 path needs omega * diameter < 1e5");
+  int b = std::max(1, hb[0]);
+  b = std::min(b, n / 2);
+  const size_t bw = 2 * (size_t)b + 1;
+  const int ops = op->bc == CFIE_SOUND_HARD ? 2 : 1;
+  if ((size_t)n * bw * ops * sizeof(float2) > ((size_t)4 << 30))
+    throw cfie_error(CFIE_EINVAL,
+                     "FP32 near-field band too wide (curve too close to itself or too few "
+                     "points per wavelength); use CFIE_FP64");
+  op->band_b = b;
+  op->band.reserve(sizeof(float2) * (size_t)n * bw * ops);
+  float* base = op->geo32.as<float>();
+  geo32 o{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 6 * n};
+  float* w32 = base + 7 * n;
+  float* c32 = base + 8 * n;
+  k_geo32<<<nblk(n), 256, 0, st>>>(n, op->g, o, op->wtab.as<double>(), op->ctab.as<double>(),
+                                    w32, c32);
+  CFIE_CHECK_LAUNCH();
+  float2* band = op->band.as<float2>();
+  if (op->bc == CFIE_SOUND_SOFT) {
+    k_band_fill<0><<<nblk((size_t)n * bw), 256, 0, st>>>(n, b, op->omega, op->eta, op->g,
+                                                          op->wtab.as<double>(),
+                                                          op->diag.as<double2>(), band, nullptr);
+  } else {
+    k_band_fill<1><<<nblk((size_t)n * bw), 256, 0, st>>>(
+        n, b, op->omega, op->eta, op->g, op->wtab.as<double>(), op->diag.as<double2>(), band,
+        band + (size_t)n * bw);
+  }
+  CFIE_CHECK_LAUNCH();
+  CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs) {
+  const int n = op->n;
+  const bool hard = op->bc == CFIE_SOUND_HARD;
+  cudaStream_t st = op->ctx->stream;
+  const size_t tot = (size_t)n * nrhs;
+  float* base = op->geo32.as<float>();
+  pair_params P{};
+  P.n = n;
+  P.b = op->band_b;
+  P.nrhs = nrhs;
+  P.wh = (float)op->omega;
+  P.wl = (float)(op->omega - (double)P.wh);
+  P.winv = (float)(1.0 / op->omega);
+  P.eta = (float)op->eta;
+  P.h = (float)op->h;
+  P.g = geo32{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 6 * n};
+  P.w32 = base + 7 * n;
+  const float* c32 = base + 8 * n;
+  const size_t bw = 2 * (size_t)op->band_b + 1;
+  P.band = op->band.as<float2>();
+  P.band2 = hard ? P.band + (size_t)n * bw : nullptr;
+  op->xin32.reserve(sizeof(float2) * tot * (hard ? 3 : 1));
+  float2* x32 = op->xin32.as<float2>();
+  k_to32<<<nblk(tot), 256, 0, st>>>(tot, x, x32);
+  CFIE_CHECK_LAUNCH();
+  P.xin = x32;
+  const int rowtiles = (n + TI - 1) / TI;
+  if (!hard) {
+    int splits;
+    if (nrhs > 16)
+      splits = launch32<0, 64>(op, P, rowtiles, (nrhs + 63) / 64);
+    else if (nrhs > 8)
+      splits = launch32<0, 16>(op, P, rowtiles, 1);
+    else
+      splits = launch32<0, 8>(op, P, rowtiles, 1);
+    k_reduce32<0><<<nblk(tot), 256, 0, st>>>(n, nrhs, splits, op->omega, op->eta, op->g,
+                                             op->partial.as<float2>(), x, nullptr, y);
+    CFIE_CHECK_LAUNCH();
+    return;
+  }
+  float2* u32 = x32 + tot;
+  float2* t32 = x32 + 2 * tot;
+  const dim3 g2(nblk(n, SPT), nrhs);
+  {
+    prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
+    k_spectral32<false><<<g2, SPT, 0, st>>>(n, c32, op->g.sp, x32, make_double2(1.0, 0.0), u32,
+                                             nullptr);
+    CFIE_CHECK_LAUNCH();
+  }
+  P.uin = u32;
+  int splits;
+  if (nrhs > 8)
+    splits = launch32<1, 16>(op, P, rowtiles, (nrhs + 15) / 16);
+  else
+    splits = launch32<1, 8>(op, P, rowtiles, 1);
+  k_reduce32<1><<<nblk(tot), 256, 0, st>>>(n, nrhs, splits, op->omega, op->eta, op->g,
+                                           op->partial.as<float2>(), x, t32, y);
+  CFIE_CHECK_LAUNCH();
+  {
+    // y += (1/(i eta)) (1/s) Dt t
+    prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
+    k_spectral32<true><<<g2, SPT, 0, st>>>(n, c32, op->g.sp, t32, make_double2(0.0, -1.0 / op->eta),
+                                            nullptr, y);
+    CFIE_CHECK_LAUNCH();
+  }
+}

@@ -131,6 +131,25 @@ cfie_status cfie_apply(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
  * residuals). */
 cfie_status cfie_apply_fp64(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
 
+/* y = A x in FP64, like cfie_apply_fp64, but without allocating any device
+ * memory: for callers that cannot call cudaMalloc, such as a serving process
+ * that has handed all free HBM to its own pool at start-up, or code that must
+ * not hit the implicit device synchronisation of cudaMalloc / cudaFree in a
+ * latency-critical loop.  The paper has no counterpart; it is a deployment
+ * variant of the FP64 matvec.
+ *
+ * Scratch (split-source partial sums; for the sound-hard operator also the two
+ * derivative vectors) lives in one file-scope device array of 32 MiB that every
+ * GPU loading the library holds until the process exits.  Needs
+ * (soft) 16 * n * nrhs bytes, (hard) 96 * n * nrhs bytes at the least;
+ * larger requests return CFIE_EINVAL with a message.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  Calls
+ * share the array: calls that overlap on the GPU (other streams, other host
+ * threads) race.  Every scratch element a call reads was written by the same
+ * call, so nothing needs clearing between calls.  Arguments as cfie_apply. */
+cfie_status cfie_apply_fp64_static(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
+
 /* Solve A x = f for nrhs independent right-hand sides by restarted GMRES
  * (Section 3: relative tolerance and restart; zero initial guess there).
  *  f_dev   device, n*nrhs complex128 (read only)

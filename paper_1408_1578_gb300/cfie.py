@@ -68,6 +68,7 @@ SIGNATURES = {
     "cfie_rhs_plane_waves": (_I, [_P, _I, _DP, _P]),
     "cfie_apply": (_I, [_P, _P, _P, _I]),
     "cfie_apply_fp64": (_I, [_P, _P, _P, _I]),
+    "cfie_apply_fp64_static": (_I, [_P, _P, _P, _I]),
     "cfie_gmres_solve": (_I, [_P, _P, _P, _I, _D, _I, _I, _IP, _DP]),
     "cfie_op_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
     "cfie_ctx_set_profiling": (_I, [_P, _I]),

@@ -296,6 +296,19 @@ cfie_status cfie_apply_fp64(cfie_op* op, const void* x_dev, void* y_dev, int nrh
   });
 }
 
+cfie_status cfie_apply_fp64_static(cfie_op* op, const void* x_dev, void* y_dev, int nrhs) {
+  if (!op) return CFIE_EINVAL;
+  return guarded(op->ctx, [&] {
+    CFIE_REQUIRE(nrhs >= 1 && nrhs <= 1024, "nrhs must be in [1, 1024]");
+    check_vec(x_dev, "x");
+    check_vec(y_dev, "y");
+    CFIE_REQUIRE(x_dev != y_dev, "x and y must not overlap");
+    set_device(op->ctx);
+    matvec_fp64_static(op, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev),
+                       nrhs);
+  });
+}
+
 cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nrhs, double rtol,
                              int restart, int maxit, int* iters_out, double* relres_out) {
   if (!op) return CFIE_EINVAL;

@@ -164,6 +164,8 @@ void rhs_plane_waves(cfie_op* op, int nrhs, const double* theta_host, double2* f
 void matvec_fp64(cfie_op* op, const double2* x, double2* y, int nrhs);
 void spectral_apply(cfie_op* op, const double2* in, double2* out, const double2* base,
                     double2 scale, int nrhs);
+void matvec_fp64_static(cfie_op* op, const double2* x, double2* y, int nrhs);
+size_t static_scratch_capacity();
 // matvec_fp32.cu
 void fp32_prepare(cfie_op* op);
 void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs);

@@ -24,6 +24,8 @@
 // partial sums go to a scratch buffer and a second kernel adds them in a fixed
 // order (deterministic results) and applies the hard-path epilogue.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "internal.h"
 #include "hankel64.cuh"
@@ -323,4 +325,109 @@ void matvec_fp64(cfie_op* op, const double2* x, double2* y, int nrhs) {
   CFIE_CHECK_LAUNCH();
   // y += (1/(i eta)) (1/s) Dt t
   spectral_apply(op, t, y, y, make_double2(0.0, -1.0 / op->eta), nrhs);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP64 matvec (cfie_apply_fp64_static).
+//
+// The split-source partial sums (and, for the sound-hard operator, the two
+// derivative vectors) live in one file-scope device array instead of buffers
+// the operator grows with cudaMalloc.  Every GPU that loads the library holds
+// this array until the process exits.  Its device address is looked up once
+// per device (cudaGetSymbolAddress, with that device current) on the first
+// call there; host code never hands the array's name itself to a kernel.
+// Each call overwrites every scratch element it later reads, so nothing has to
+// start at zero; calls that overlap on the GPU share the array and race.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+void* static_scratch_address(int device) {
+  if (device < 0 || device >= kMaxDevices)
+    throw cfie_error(CFIE_EINVAL, "device index out of range for the static scratch table");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      throw cfie_error(CFIE_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") +
+                                       cudaGetErrorString(e));
+    g_static_addr[device] = p;
+  }
+  return g_static_addr[device];
+}
+
+}  // namespace
+
+size_t static_scratch_capacity() { return kStaticScratchBytes; }
+
+void matvec_fp64_static(cfie_op* op, const double2* x, double2* y, int nrhs) {
+  const int n = op->n;
+  const int hard = op->bc == CFIE_SOUND_HARD;
+  const int ops = hard ? 4 : 1;
+  const size_t tot = (size_t)n * nrhs;
+  const size_t vec_bytes = sizeof(double2) * tot;
+  const size_t fixed = hard ? 2 * vec_bytes : 0;          // u and t
+  const size_t per_split = sizeof(double2) * (size_t)ops * tot;
+  if (fixed + per_split > kStaticScratchBytes)
+    throw cfie_error(CFIE_EINVAL,
+                     "cfie_apply_fp64_static: n * nrhs too large for the 32 MiB static scratch "
+                     "(needs " + std::to_string(fixed + per_split) + " bytes)");
+  // device address of the array on the context's (current) device
+  unsigned char* base = static_cast<unsigned char*>(static_scratch_address(op->ctx->device));
+
+  const int rowtiles = (n + TI - 1) / TI;
+  const int rhsblocks = (nrhs + RB - 1) / RB;
+  const int ntiles = (n + TJ - 1) / TJ;
+  int dev_sms = 152;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, op->ctx->device);
+  const int target = 4 * dev_sms;
+  int splits = std::max(1, std::min(ntiles, (target + rowtiles * rhsblocks - 1) /
+                                                (rowtiles * rhsblocks)));
+  const int fit = (int)std::min<size_t>((kStaticScratchBytes - fixed) / per_split, ntiles);
+  splits = std::max(1, std::min(splits, fit));
+  int tps = (ntiles + splits - 1) / splits;
+  splits = (ntiles + tps - 1) / tps;
+
+  double2* part = reinterpret_cast<double2*>(base + fixed);
+  double2* u = hard ? reinterpret_cast<double2*>(base) : nullptr;
+  double2* t = hard ? reinterpret_cast<double2*>(base + vec_bytes) : nullptr;
+  cudaStream_t st = op->ctx->stream;
+  const dim3 grid(rowtiles, splits, rhsblocks);
+  const dim3 sgrid((n + SPT - 1) / SPT, nrhs);
+  if (!hard) {
+    const size_t smem = sizeof(pair_smem<0>);
+    CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_pair_fp64<0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_pair_fp64<0><<<grid, NT, smem, st>>>(n, op->omega, op->eta, op->g, op->wtab.as<double>(),
+                                           op->diag.as<double2>(), x, nullptr, nrhs, splits, tps,
+                                           part);
+    CFIE_CHECK_LAUNCH();
+    k_reduce_fp64<0><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+        n, nrhs, splits, op->omega, op->eta, op->g, part, x, nullptr, y);
+    CFIE_CHECK_LAUNCH();
+    return;
+  }
+  k_spectral_fp64<<<sgrid, SPT, 0, st>>>(n, op->ctab.as<double>(), op->g.sp, x, nullptr,
+                                          make_double2(1.0, 0.0), u);
+  CFIE_CHECK_LAUNCH();
+  const size_t smem = sizeof(pair_smem<1>);
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_pair_fp64<1>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_pair_fp64<1><<<grid, NT, smem, st>>>(n, op->omega, op->eta, op->g, op->wtab.as<double>(),
+                                         op->diag.as<double2>(), x, u, nrhs, splits, tps, part);
+  CFIE_CHECK_LAUNCH();
+  k_reduce_fp64<1><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+      n, nrhs, splits, op->omega, op->eta, op->g, part, x, t, y);
+  CFIE_CHECK_LAUNCH();
+  k_spectral_fp64<<<sgrid, SPT, 0, st>>>(n, op->ctab.as<double>(), op->g.sp, t, y,
+                                          make_double2(0.0, -1.0 / op->eta), y);
+  CFIE_CHECK_LAUNCH();
 }

@@ -43,16 +43,25 @@ def parse():
     p.add_argument("--workload", default="star", choices=["kite", "star", "disk"])
     p.add_argument("--precision", default=None, choices=["fp32", "fp64", None])
     p.add_argument("--rtol", type=float, default=None)
+    p.add_argument("--n", type=int, default=None, help="override the workload's n (profiling)")
+    p.add_argument("--nrhs", type=int, default=None, help="override the number of directions")
     return p.parse_args()
 
 
 # ---------------------------------------------------------------------------
 # workload definitions (shapes from inputs.WORKLOADS)
 # ---------------------------------------------------------------------------
-def workload(name, precision):
+def workload(name, precision, n=None, nrhs=None):
     from paper_1408_1578_gb300 import inputs
     spec = dict(inputs.WORKLOADS[name])
     spec["name"] = name
+    if n:
+        # same points per wavelength as the full workload
+        spec["omega"] = spec["omega"] * n / spec["n"]
+        spec["n"] = n
+        spec["name"] = f"{name} (reduced n={n})"
+    if nrhs:
+        spec["nrhs"] = nrhs
     if precision is None:
         precision = "fp32" if name == "kite" else "fp64"
     spec["precision"] = precision
@@ -154,7 +163,7 @@ def run_ours(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    spec = workload(args.workload, args.precision)
+    spec = workload(args.workload, args.precision, args.n, args.nrhs)
     if args.rtol:
         spec["rtol"] = args.rtol
     n, w, nrhs, bc = spec["n"], spec["omega"], spec["nrhs"], spec["bc"]
@@ -332,7 +341,7 @@ def cpu_rows_for(spec, budget_s=12.0):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    spec = workload(args.workload, args.precision)
+    spec = workload(args.workload, args.precision, args.n, args.nrhs)
     rows = cpu_rows_for(spec, budget_s=10.0 / max(1, args.steps + args.warmup) * 3)
     for _ in range(args.warmup):
         oracle_sample(spec, max(4, rows // 4))
@@ -406,7 +415,7 @@ def main():
     else:
         out = run_ours(args, rank, world)
         if rank == 0 and out is not None and world == 1:
-            spec = workload(args.workload, args.precision)
+            spec = workload(args.workload, args.precision, args.n, args.nrhs)
             rows = cpu_rows_for(spec, budget_s=12.0)
             p, s = oracle_sample(spec, rows)
             out["cpu_baseline"] = {"value": p / s, "unit": UNIT, "cores": 1, "kind": "oracle",

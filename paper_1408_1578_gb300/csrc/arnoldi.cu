@@ -532,11 +532,18 @@ void gmres_solve(cfie_op* op, const double2* f, double2* x, int nrhs, double rto
   double2* r = op->rv.as<double2>();
   double2* ax = W.w;  // matvec output scratch (free between cycles)
 
-  std::vector<double> rn, fn;
+  std::vector<double> rn, fn, xn, dummy;
   std::vector<int> its(nrhs, 0), steps_left(nrhs, maxit), active(nrhs, 1);
-  // true residual of the initial guess
-  fp64_mv(op, x, ax, nrhs);
-  residual_norms(op, W, f, ax, r, nrhs, rn, fn);
+  // true residual of the initial guess (no matvec when x0 = 0)
+  residual_norms(op, W, x, nullptr, nullptr, nrhs, xn, dummy);
+  bool x_zero = true;
+  for (int k = 0; k < nrhs; ++k) x_zero = x_zero && xn[k] == 0.0;
+  if (x_zero) {
+    residual_norms(op, W, f, nullptr, r, nrhs, rn, fn);
+  } else {
+    fp64_mv(op, x, ax, nrhs);
+    residual_norms(op, W, f, ax, r, nrhs, rn, fn);
+  }
 
   const bool refined = op->prec != CFIE_FP64;
   if (!refined) {

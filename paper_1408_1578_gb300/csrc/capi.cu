@@ -102,6 +102,9 @@ void apply_inner(cfie_op* op, const double2* x, double2* y, int nrhs) {
     case CFIE_FP32_REFINED:
       matvec_fp32(op, x, y, nrhs);
       break;
+    case CFIE_TENSOR_REFINED:
+      matvec_stored(op, x, y, nrhs);
+      break;
     default:
       throw cfie_error(CFIE_EINVAL, "precision not available for this operator");
   }
@@ -224,9 +227,12 @@ cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cf
     CFIE_REQUIRE(std::isfinite(omega) && omega > 0, "omega must be positive and finite");
     CFIE_REQUIRE(std::isfinite(eta) && eta > 0, "eta must be positive and finite");
     CFIE_REQUIRE(bc == CFIE_SOUND_SOFT || bc == CFIE_SOUND_HARD, "unknown boundary condition");
-    CFIE_REQUIRE(precision == CFIE_FP64 || precision == CFIE_FP32_REFINED,
-                 "precision not available");
-    CFIE_REQUIRE(layout == CFIE_MATRIX_FREE, "layout not available");
+    CFIE_REQUIRE(precision == CFIE_FP64 || precision == CFIE_FP32_REFINED ||
+                     precision == CFIE_TENSOR_REFINED,
+                 "unknown precision");
+    CFIE_REQUIRE(layout == CFIE_MATRIX_FREE || layout == CFIE_STORED, "unknown layout");
+    CFIE_REQUIRE((precision == CFIE_TENSOR_REFINED) == (layout == CFIE_STORED),
+                 "the stored layout goes with CFIE_TENSOR_REFINED and only with it");
     set_device(ctx);
     op = new cfie_op();
     op->ctx = ctx;
@@ -239,7 +245,8 @@ cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cf
     op->layout = layout;
     geometry_sample(op, geom);
     kress_tables(op);
-    if (precision == CFIE_FP32_REFINED) fp32_prepare(op);
+    if (precision != CFIE_FP64) fp32_prepare(op);
+    if (layout == CFIE_STORED) stored_prepare(op);
     CFIE_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   });
   if (st != CFIE_OK) {
@@ -281,6 +288,8 @@ cfie_status cfie_apply(cfie_op* op, const void* x_dev, void* y_dev, int nrhs) {
     CFIE_REQUIRE(x_dev != y_dev, "x and y must not overlap");
     set_device(op->ctx);
     apply_inner(op, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev), nrhs);
+    if (op->layout == CFIE_STORED && stored_take_error(op))
+      throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
   });
 }
 
@@ -325,6 +334,8 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
     set_device(op->ctx);
     gmres_solve(op, static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), nrhs, rtol,
                 restart, maxit, iters_out, relres_out, &result);
+    if (op->layout == CFIE_STORED && stored_take_error(op))
+      throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     if (result == CFIE_ENOCONV) op->ctx->err = "GMRES reached maxit before rtol";
   });
   if (st != CFIE_OK) return st;

@@ -130,6 +130,9 @@ struct cfie_op {
   int band_b = -1;
   dbuf xin32, xin32b; // FP32 staging of the input (and hard-path helpers)
 
+  // stored path (CFIE_STORED): bf16 hi/lo planes of A, B operand planes, error flag
+  dbuf stored, bt, err_flag;
+
   // GMRES workspace
   dbuf V, H, wv, rv, dv, rin, small;
   double* host_res = nullptr;  // pinned host mirror of residual estimates
@@ -169,6 +172,10 @@ size_t static_scratch_capacity();
 // matvec_fp32.cu
 void fp32_prepare(cfie_op* op);
 void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs);
+// stored.cu
+void stored_prepare(cfie_op* op);
+void matvec_stored(cfie_op* op, const double2* x, double2* y, int nrhs);
+int stored_take_error(cfie_op* op);
 // arnoldi.cu
 void gmres_solve(cfie_op* op, const double2* f, double2* x, int nrhs, double rtol, int restart,
                  int maxit, int* iters, double* relres, cfie_status* st);

@@ -35,8 +35,7 @@ namespace {
 constexpr int TI = 64;
 constexpr int TJ = 32;
 constexpr int NT = 256;
-constexpr int RB = 16;  // right-hand sides per launch slice
-constexpr int RQ = RB / (NT / TI);  // right-hand sides per thread (4)
+constexpr int RB = 16;  // right-hand sides per launch slice (soft with many RHS: 64)
 
 __device__ __forceinline__ double2 cmad(double2 acc, double2 a, double2 b) {
   acc.x = fma(a.x, b.x, acc.x);
@@ -46,28 +45,29 @@ __device__ __forceinline__ double2 cmad(double2 acc, double2 a, double2 b) {
   return acc;
 }
 
-template <int BC>
+template <int BC, int RBT = RB>
 struct pair_smem {
   double tx[TI], ty[TI], tnx[TI], tny[TI], tsp[TI];
   double sx[TJ], sy[TJ], snx[TJ], sny[TJ], ssp[TJ];
   double2 A[TI][TJ + 1];
   double2 B[BC ? TI : 1][TJ + 1];        // hard: D' entries
-  double2 X[BC ? 4 : 1][TJ][RB];         // soft: x ; hard: u, n1 x, n2 x, x
+  double2 X[BC ? 4 : 1][TJ][RBT];        // soft: x ; hard: u, n1 x, n2 x, x
 };
 
-template <int BC>
+template <int BC, int RBT = RB>
 __global__ void __launch_bounds__(NT)
 k_pair_fp64(int n, double omega, double eta, geom_dev g, const double* __restrict__ wtab,
             const double2* __restrict__ diag, const double2* __restrict__ xin,
             const double2* __restrict__ uin, int nrhs, int splits, int tiles_per_split,
             double2* __restrict__ part) {
+  constexpr int RQ = RBT / (NT / TI);  // right-hand sides per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pair_smem<BC>& S = *reinterpret_cast<pair_smem<BC>*>(smem_raw);
+  pair_smem<BC, RBT>& S = *reinterpret_cast<pair_smem<BC, RBT>*>(smem_raw);
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * TI;
   const int split = blockIdx.y;
-  const int rb0 = blockIdx.z * RB;
-  const int rbn = min(RB, nrhs - rb0);
+  const int rb0 = blockIdx.z * RBT;
+  const int rbn = min(RBT, nrhs - rb0);
   const int ntiles = (n + TJ - 1) / TJ;
   const int t_begin = split * tiles_per_split;
   const int t_end = min(ntiles, t_begin + tiles_per_split);
@@ -103,8 +103,8 @@ k_pair_fp64(int n, double omega, double eta, geom_dev g, const double* __restric
       S.sny[tid] = ok ? g.ny[j] : 0.0;
       S.ssp[tid] = ok ? g.sp[j] : 1.0;
     }
-    for (int e = tid; e < TJ * RB; e += NT) {
-      int jl = e / RB, r = e % RB;
+    for (int e = tid; e < TJ * RBT; e += NT) {
+      int jl = e / RBT, r = e % RBT;
       int j = j0 + jl;
       double2 xv = make_double2(0.0, 0.0), uv = xv;
       if (j < n && r < rbn) {
@@ -263,16 +263,16 @@ k_spectral_fp64(int n, const double* __restrict__ ct, const double* __restrict__
   }
 }
 
-template <int BC>
+template <int BC, int RBT = RB>
 void launch_pair(cfie_op* op, const double2* x, const double2* u, int nrhs, int splits, int tps,
                  double2* part) {
   const int n = op->n;
-  size_t smem = sizeof(pair_smem<BC>);
-  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_pair_fp64<BC>,
+  size_t smem = sizeof(pair_smem<BC, RBT>);
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_pair_fp64<BC, RBT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  dim3 grid((n + TI - 1) / TI, splits, (nrhs + RB - 1) / RB);
+  dim3 grid((n + TI - 1) / TI, splits, (nrhs + RBT - 1) / RBT);
   prof_scope ps(op->ctx, CFIE_K_MATVEC_FP64);
-  k_pair_fp64<BC><<<grid, NT, smem, op->ctx->stream>>>(
+  k_pair_fp64<BC, RBT><<<grid, NT, smem, op->ctx->stream>>>(
       n, op->omega, op->eta, op->g, op->wtab.as<double>(), op->diag.as<double2>(), x, u, nrhs,
       splits, tps, part);
   CFIE_CHECK_LAUNCH();
@@ -293,7 +293,9 @@ void matvec_fp64(cfie_op* op, const double2* x, double2* y, int nrhs) {
   const int n = op->n;
   const int hard = op->bc == CFIE_SOUND_HARD;
   const int rowtiles = (n + TI - 1) / TI;
-  const int rhsblocks = (nrhs + RB - 1) / RB;
+  const bool wide = !hard && nrhs > RB;  // one pass of pair evaluations for up to 64 RHS
+  const int rb = wide ? 64 : RB;
+  const int rhsblocks = (nrhs + rb - 1) / rb;
   const int ntiles = (n + TJ - 1) / TJ;
   int dev_sms = 152;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, op->ctx->device);
@@ -307,7 +309,10 @@ void matvec_fp64(cfie_op* op, const double2* x, double2* y, int nrhs) {
   double2* part = op->partial.as<double2>();
   const size_t tot = (size_t)n * nrhs;
   if (!hard) {
-    launch_pair<0>(op, x, nullptr, nrhs, splits, tps, part);
+    if (wide)
+      launch_pair<0, 64>(op, x, nullptr, nrhs, splits, tps, part);
+    else
+      launch_pair<0>(op, x, nullptr, nrhs, splits, tps, part);
     k_reduce_fp64<0><<<(unsigned)((tot + 255) / 256), 256, 0, op->ctx->stream>>>(
         n, nrhs, splits, op->omega, op->eta, op->g, part, x, nullptr, y);
     CFIE_CHECK_LAUNCH();

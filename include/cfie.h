@@ -176,6 +176,33 @@ typedef struct {
 } cfie_solve_stats;
 cfie_status cfie_op_last_stats(const cfie_op* op, cfie_solve_stats* out);
 
+/* --- Batches: many operators solved in lockstep ------------------------- */
+
+typedef struct cfie_batch cfie_batch;
+
+/* Group `count` operators of one context, all of the same precision, with
+ * nrhs[k] right-hand sides for operator k.  Batch vectors are the operators'
+ * column-major n_k x nrhs[k] blocks concatenated in order (see
+ * cfie_batch_length).  When every operator uses CFIE_STORED, one block matvec of
+ * the whole batch is one CUDA-graph replay of three kernels: the B-operand
+ * preparation of every operator, a persistent stream-K tensor-core contraction
+ * over all (operator, row tile, source tile) pairs (one CTA per SM), and the
+ * partial-sum reduction.  The operators must outlive the batch.  Synchronous. */
+cfie_status cfie_batch_create(cfie_ctx* ctx, int count, cfie_op* const* ops, const int* nrhs,
+                              cfie_batch** out);
+/* Number of complex128 elements of a batch vector (sum of n_k * nrhs[k]). */
+long long cfie_batch_length(const cfie_batch* batch);
+/* y = A x for every operator of the batch in the operators' precision. */
+cfie_status cfie_batch_apply(cfie_batch* batch, const void* x_dev, void* y_dev);
+/* GMRES on every right-hand side of every operator at once (each one an
+ * independent problem; arguments as cfie_gmres_solve, iters_out / relres_out
+ * hold one entry per right-hand side in batch order). */
+cfie_status cfie_batch_gmres_solve(cfie_batch* batch, const void* f_dev, void* x_dev, double rtol,
+                                   int restart, int maxit, int* iters_out, double* relres_out);
+cfie_status cfie_batch_last_stats(const cfie_batch* batch, cfie_solve_stats* out);
+void cfie_batch_destroy(cfie_batch* batch);
+
+
 /* --- Kernel timing (CUDA events on the context stream) ------------------- */
 
 /* Kernel classes timed when profiling is on. */

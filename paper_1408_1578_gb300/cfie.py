@@ -74,6 +74,12 @@ SIGNATURES = {
     "cfie_ctx_set_profiling": (_I, [_P, _I]),
     "cfie_ctx_kernel_times": (_I, [_P, _DP, _LLP]),
     "cfie_launch_count": (ctypes.c_longlong, []),
+    "cfie_batch_create": (_I, [_P, _I, ctypes.POINTER(_P), _IP, ctypes.POINTER(_P)]),
+    "cfie_batch_length": (ctypes.c_longlong, [_P]),
+    "cfie_batch_apply": (_I, [_P, _P, _P]),
+    "cfie_batch_gmres_solve": (_I, [_P, _P, _P, _D, _I, _I, _IP, _DP]),
+    "cfie_batch_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
+    "cfie_batch_destroy": (None, [_P]),
 }
 
 _lib = None
@@ -156,10 +162,12 @@ class Context:
         return {KERNEL_CLASS_NAMES[k]: (float(ms[k]), int(ln[k])) for k in range(CFIE_K_COUNT)}
 
     def close(self):
-        """Destroy the context; operators and geometries made from it are
-        destroyed first (the C ABI needs the context alive for them)."""
+        """Destroy the context; batches, operators and geometries made from it
+        are destroyed first (the C ABI needs the context alive for them)."""
         if self.h:
-            for child in list(self._children):
+            kids = list(self._children)
+            for child in [c for c in kids if isinstance(c, Batch)] + \
+                    [c for c in kids if not isinstance(c, Batch)]:
                 child.close()
             self.lib.cfie_ctx_destroy(self.h)
             self.h = None
@@ -209,6 +217,60 @@ class Context:
         if kind == "kite":
             return self.kite()
         raise ValueError(kind)
+
+
+class Batch:
+    """Operators solved in lockstep (cfie_batch_*).  Vectors are the operators'
+    (nrhs_k, n_k) blocks concatenated; `split` / `join` convert."""
+
+    def __init__(self, ctx, ops, nrhs):
+        self.ctx = ctx
+        self.ops = list(ops)
+        self.nrhs = [int(k) for k in nrhs]
+        arr = (_P * len(self.ops))(*[op.h for op in self.ops])
+        nr = np.ascontiguousarray(self.nrhs, dtype=np.int32)
+        h = _P()
+        ctx.check(ctx.lib.cfie_batch_create(ctx.h, len(self.ops), arr, nr.ctypes.data_as(_IP),
+                                            ctypes.byref(h)), "cfie_batch_create")
+        self.h = h
+        self.length = int(ctx.lib.cfie_batch_length(h))
+        self.offsets = np.cumsum([0] + [op.n * k for op, k in zip(self.ops, self.nrhs)])[:-1]
+        ctx._children.add(self)
+
+    def apply(self, x, y):
+        self.ctx.check(self.ctx.lib.cfie_batch_apply(self.h, _addr(x), _addr(y)), "cfie_batch_apply")
+
+    def gmres_solve(self, f, x, rtol=1e-6, restart=80, maxit=1000, allow_noconv=False):
+        P = int(sum(self.nrhs))
+        its = np.zeros(P, dtype=np.int32)
+        rel = np.zeros(P)
+        st = self.ctx.lib.cfie_batch_gmres_solve(self.h, _addr(f), _addr(x), float(rtol), int(restart),
+                                                 int(maxit), its.ctypes.data_as(_IP), _dptr(rel))
+        if not (st == CFIE_OK or (allow_noconv and st == CFIE_ENOCONV)):
+            self.ctx.check(st, "cfie_batch_gmres_solve")
+        return its, rel, st
+
+    def last_stats(self):
+        s = cfie_solve_stats()
+        self.ctx.check(self.ctx.lib.cfie_batch_last_stats(self.h, ctypes.byref(s)),
+                       "cfie_batch_last_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def block(self, vec, k):
+        """View of operator k's (nrhs_k, n_k) block of a flat batch vector."""
+        o = int(self.offsets[k])
+        return vec[o:o + self.ops[k].n * self.nrhs[k]].view(self.nrhs[k], self.ops[k].n)
+
+    def close(self):
+        if self.h:
+            self.ctx.lib.cfie_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Geometry:

@@ -1,10 +1,10 @@
 // Restarted GMRES (Section 3 of the paper: GMRES with a relative tolerance and
-// a restart length) for nrhs independent right-hand sides, with the Arnoldi
+// a restart length) for a set of independent problems, with the Arnoldi
 // orthogonalisation, Givens rotations, Hessenberg least-squares solve and the
 // solution update all in FP64 on the GPU, and mixed-precision iterative
 // refinement on the outer FP64 residual for the FP32 / tensor precisions.
 //
-// Arnoldi step j (per right-hand side k, V_k = [v_0 .. v_j]):
+// Arnoldi step j (per problem p, V_p = [v_0 .. v_j]):
 //   w = A v_j
 //   classical Gram-Schmidt twice (CGS2):  h = V^H w, w -= V h   (two passes)
 //   H(0:j, j) = h_1 + h_2,  H(j+1, j) = ||w||,  v_{j+1} = w / ||w||
@@ -12,10 +12,15 @@
 //   g(j+1) = -conj(s_j) g(j), g(j) = c_j g(j); |g(j+1)| is the residual norm.
 // After a cycle: R y = g (back substitution), x += V y, then the true residual.
 //
-// Memory layout: V is [(m+1)][nrhs][n] complex128, so basis vector j of all
-// right-hand sides is a column-major n x nrhs block that the matvec reads
-// directly.  H is [nrhs][m+1][m].  The orthogonalisation kernels stream V once
-// per pass (HBM-bound); a CTA owns a chunk of 2048 nodes of one right-hand side.
+// Problems are segments of one long "super vector" of length L: problem p
+// (one right-hand side of one operator) owns elements [off_p, off_p + n_p).
+// For one operator with nrhs right-hand sides this is exactly the column-major
+// n x nrhs layout of the C ABI; for a batch of operators the blocks of all
+// operators are concatenated.  Basis vector j of every problem is the slice
+// V[j * L .. (j + 1) * L), so the matvec reads it directly.  The chunked kernels
+// run over a work list of (problem, 2048-element chunk) items and stream V once
+// per pass (HBM-bound); per-problem quantities (H, Givens data, norms) are
+// reduced from per-chunk partial sums in a fixed order.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -25,8 +30,8 @@
 namespace {
 
 constexpr int AT = 256;          // threads per CTA
-constexpr int AE = 8;            // nodes per thread
-constexpr int CH = AT * AE;      // nodes per chunk
+constexpr int AE = 8;            // elements per thread
+constexpr int CH = AT * AE;      // elements per chunk
 constexpr int MAXJ = 512;        // largest restart length
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -34,30 +39,43 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partial[k][jj][chunk] = sum_{i in chunk} conj(V[jj][k][i]) w[k][i], jj = 0..J
+struct chunk_ref {
+  size_t base;
+  int cnt, p, slot;
+};
+
+__device__ __forceinline__ chunk_ref chunk_of(const pset_dev& ps, int item) {
+  const int2 it = ps.items[item];
+  chunk_ref r;
+  r.p = it.x;
+  r.base = ps.off[it.x] + (size_t)it.y * CH;
+  r.cnt = min(CH, ps.len[it.x] - it.y * CH);
+  r.slot = ps.chb[it.x] + it.y;
+  return r;
+}
+
+// partial[slot][jj] = sum over the chunk of conj(V[jj]) w, jj = 0..J
 __global__ void __launch_bounds__(AT)
-k_dots(int n, int nrhs, int J, const double2* __restrict__ V, const double2* __restrict__ w,
-       const int* __restrict__ act, int nchunks, double2* __restrict__ partial) {
+k_dots(int J, const double2* __restrict__ V, size_t L, const double2* __restrict__ w,
+       const int* __restrict__ act, pset_dev ps, double2* __restrict__ partial) {
   extern __shared__ double2 red[];  // [J+1][AT/32]
-  const int k = blockIdx.y;
-  if (!act[k]) return;
-  const int chunk = blockIdx.x;
-  const int base = chunk * CH;
+  const chunk_ref c = chunk_of(ps, blockIdx.x);
+  if (!act[c.p]) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double2 wr[AE];
 #pragma unroll
   for (int e = 0; e < AE; ++e) {
-    int i = base + e * AT + threadIdx.x;
-    wr[e] = i < n ? w[(size_t)k * n + i] : make_double2(0.0, 0.0);
+    const int q = e * AT + threadIdx.x;
+    wr[e] = q < c.cnt ? w[c.base + q] : make_double2(0.0, 0.0);
   }
   for (int jj = 0; jj <= J; ++jj) {
-    const double2* v = V + ((size_t)jj * nrhs + k) * n;
+    const double2* v = V + (size_t)jj * L + c.base;
     double re = 0.0, im = 0.0;
 #pragma unroll
     for (int e = 0; e < AE; ++e) {
-      int i = base + e * AT + threadIdx.x;
-      if (i < n) {
-        double2 a = v[i];
+      const int q = e * AT + threadIdx.x;
+      if (q < c.cnt) {
+        const double2 a = v[q];
         re = fma(a.x, wr[e].x, fma(a.y, wr[e].y, re));
         im = fma(a.x, wr[e].y, fma(-a.y, wr[e].x, im));
       }
@@ -73,25 +91,26 @@ k_dots(int n, int nrhs, int J, const double2* __restrict__ V, const double2* __r
       s.x += red[jj * (AT / 32) + q].x;
       s.y += red[jj * (AT / 32) + q].y;
     }
-    partial[((size_t)k * (J + 1) + jj) * nchunks + chunk] = s;
+    partial[(size_t)c.slot * (J + 1) + jj] = s;
   }
 }
 
-// h[k][jj] = sum over chunks; H[k][jj][col] += h (first pass sets, second adds)
-__global__ void k_dots_reduce(int nrhs, int J, int nchunks, int m, int col, int first,
-                              const int* __restrict__ act, const double2* __restrict__ partial,
+// h[p][jj] = sum over the problem's chunks; H[p][jj][col] = (first) or += h
+__global__ void k_dots_reduce(int J, int m, int col, int first, const int* __restrict__ act,
+                              pset_dev ps, const double2* __restrict__ partial,
                               double2* __restrict__ hbuf, double2* __restrict__ H) {
-  const int k = blockIdx.x;
-  if (!act[k]) return;
+  const int p = blockIdx.x;
+  if (!act[p]) return;
+  const int nch = ps.nch[p], chb = ps.chb[p];
   for (int jj = threadIdx.x; jj <= J; jj += blockDim.x) {
     double2 s = make_double2(0.0, 0.0);
-    const double2* p = partial + ((size_t)k * (J + 1) + jj) * nchunks;
-    for (int c = 0; c < nchunks; ++c) {
-      s.x += p[c].x;
-      s.y += p[c].y;
+    for (int c = 0; c < nch; ++c) {
+      const double2 v = partial[(size_t)(chb + c) * (J + 1) + jj];
+      s.x += v.x;
+      s.y += v.y;
     }
-    hbuf[(size_t)k * (J + 1) + jj] = s;
-    double2* hk = H + ((size_t)k * (m + 1) + jj) * m + col;
+    hbuf[(size_t)p * (J + 1) + jj] = s;
+    double2* hk = H + ((size_t)p * (m + 1) + jj) * m + col;
     if (first) {
       *hk = s;
     } else {
@@ -101,32 +120,30 @@ __global__ void k_dots_reduce(int nrhs, int J, int nchunks, int m, int col, int 
   }
 }
 
-// w[k][i] -= sum_jj V[jj][k][i] h[k][jj]; optional |w|^2 partial per chunk
+// w -= sum_jj V[jj] h[p][jj] on one chunk; optional |w|^2 partial per chunk
 __global__ void __launch_bounds__(AT)
-k_update(int n, int nrhs, int J, const double2* __restrict__ V, const double2* __restrict__ hbuf,
-         const int* __restrict__ act, double2* __restrict__ w, int nchunks,
+k_update(int J, const double2* __restrict__ V, size_t L, const double2* __restrict__ hbuf,
+         const int* __restrict__ act, pset_dev ps, double2* __restrict__ w,
          double* __restrict__ nrm_partial) {
   extern __shared__ double2 hs[];
-  const int k = blockIdx.y;
-  if (!act[k]) return;
-  const int chunk = blockIdx.x;
-  const int base = chunk * CH;
-  for (int jj = threadIdx.x; jj <= J; jj += AT) hs[jj] = hbuf[(size_t)k * (J + 1) + jj];
+  const chunk_ref c = chunk_of(ps, blockIdx.x);
+  if (!act[c.p]) return;
+  for (int jj = threadIdx.x; jj <= J; jj += AT) hs[jj] = hbuf[(size_t)c.p * (J + 1) + jj];
   __syncthreads();
   double2 acc[AE];
 #pragma unroll
   for (int e = 0; e < AE; ++e) {
-    int i = base + e * AT + threadIdx.x;
-    acc[e] = i < n ? w[(size_t)k * n + i] : make_double2(0.0, 0.0);
+    const int q = e * AT + threadIdx.x;
+    acc[e] = q < c.cnt ? w[c.base + q] : make_double2(0.0, 0.0);
   }
   for (int jj = 0; jj <= J; ++jj) {
-    const double2* v = V + ((size_t)jj * nrhs + k) * n;
+    const double2* v = V + (size_t)jj * L + c.base;
     const double2 hh = hs[jj];
 #pragma unroll
     for (int e = 0; e < AE; ++e) {
-      int i = base + e * AT + threadIdx.x;
-      if (i < n) {
-        double2 a = v[i];
+      const int q = e * AT + threadIdx.x;
+      if (q < c.cnt) {
+        const double2 a = v[q];
         acc[e].x -= a.x * hh.x - a.y * hh.y;
         acc[e].y -= a.x * hh.y + a.y * hh.x;
       }
@@ -135,9 +152,9 @@ k_update(int n, int nrhs, int J, const double2* __restrict__ V, const double2* _
   double ss = 0.0;
 #pragma unroll
   for (int e = 0; e < AE; ++e) {
-    int i = base + e * AT + threadIdx.x;
-    if (i < n) {
-      w[(size_t)k * n + i] = acc[e];
+    const int q = e * AT + threadIdx.x;
+    if (q < c.cnt) {
+      w[c.base + q] = acc[e];
       ss += acc[e].x * acc[e].x + acc[e].y * acc[e].y;
     }
   }
@@ -149,136 +166,176 @@ k_update(int n, int nrhs, int J, const double2* __restrict__ V, const double2* _
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int q = 0; q < AT / 32; ++q) t += red[q];
-      nrm_partial[(size_t)k * nchunks + chunk] = t;
+      nrm_partial[c.slot] = t;
     }
   }
 }
 
-// One thread per right-hand side: ||w||, Givens rotations, residual estimate.
-__global__ void k_givens(int nrhs, int m, int j, int nchunks, const int* __restrict__ act,
+// One thread per problem: ||w||, Givens rotations, residual estimate.
+__global__ void k_givens(int P, int m, int j, const int* __restrict__ act, pset_dev ps,
                          const double* __restrict__ nrm_partial, double2* __restrict__ H,
                          double* __restrict__ cs, double2* __restrict__ sn,
                          double2* __restrict__ gv, double* __restrict__ hnorm,
                          double* __restrict__ res) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nrhs || !act[k]) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P || !act[p]) return;
   double s2 = 0.0;
-  for (int c = 0; c < nchunks; ++c) s2 += nrm_partial[(size_t)k * nchunks + c];
-  double hn = sqrt(s2);
-  hnorm[k] = hn;
-  double2* Hk = H + (size_t)k * (m + 1) * m;
+  for (int c = 0; c < ps.nch[p]; ++c) s2 += nrm_partial[ps.chb[p] + c];
+  const double hn = sqrt(s2);
+  hnorm[p] = hn;
+  double2* Hk = H + (size_t)p * (m + 1) * m;
   Hk[(size_t)(j + 1) * m + j] = make_double2(hn, 0.0);
-  // previous rotations on column j
-  for (int q = 0; q < j; ++q) {
-    double2 a = Hk[(size_t)q * m + j], b = Hk[(size_t)(q + 1) * m + j];
-    double c = cs[(size_t)k * m + q];
-    double2 s = sn[(size_t)k * m + q];
-    // [c s; -conj(s) c]
-    double2 na = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
-    double2 nb = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
-    Hk[(size_t)q * m + j] = na;
-    Hk[(size_t)(q + 1) * m + j] = nb;
+  for (int q = 0; q < j; ++q) {   // previous rotations [c s; -conj(s) c] on column j
+    const double2 a = Hk[(size_t)q * m + j], b = Hk[(size_t)(q + 1) * m + j];
+    const double c = cs[(size_t)p * m + q];
+    const double2 s = sn[(size_t)p * m + q];
+    Hk[(size_t)q * m + j] =
+        make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
+    Hk[(size_t)(q + 1) * m + j] = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x,
+                                               -(s.x * a.y - s.y * a.x) + c * b.y);
   }
-  double2 a = Hk[(size_t)j * m + j];
-  double bn = hn;  // b = hn (real)
+  const double2 a = Hk[(size_t)j * m + j];
+  const double bn = hn;  // b = ||w|| is real
   double c;
   double2 s;
-  double aa = hypot(a.x, a.y);
+  const double aa = hypot(a.x, a.y);
   if (bn == 0.0) {
     c = 1.0;
     s = make_double2(0.0, 0.0);
   } else if (aa == 0.0) {
     c = 0.0;
-    s = make_double2(1.0, 0.0);  // conj(b)/|b| with b real positive
+    s = make_double2(1.0, 0.0);
   } else {
-    double t = hypot(aa, bn);
+    const double t = hypot(aa, bn);
     c = aa / t;
-    // s = (a/|a|) conj(b) / t
-    s = make_double2(a.x / aa * bn / t, a.y / aa * bn / t);
+    s = make_double2(a.x / aa * bn / t, a.y / aa * bn / t);  // (a/|a|) conj(b) / t
   }
-  cs[(size_t)k * m + j] = c;
-  sn[(size_t)k * m + j] = s;
-  // H(j,j) = c a + s b
+  cs[(size_t)p * m + j] = c;
+  sn[(size_t)p * m + j] = s;
   Hk[(size_t)j * m + j] = make_double2(c * a.x + s.x * bn, c * a.y + s.y * bn);
   Hk[(size_t)(j + 1) * m + j] = make_double2(0.0, 0.0);
-  double2 gj = gv[(size_t)k * (m + 1) + j];
-  // g(j+1) = -conj(s) g(j); g(j) = c g(j)
-  double2 g1 = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
-  gv[(size_t)k * (m + 1) + j + 1] = g1;
-  gv[(size_t)k * (m + 1) + j] = make_double2(c * gj.x, c * gj.y);
-  res[k] = hypot(g1.x, g1.y);
+  const double2 gj = gv[(size_t)p * (m + 1) + j];
+  const double2 g1 = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+  gv[(size_t)p * (m + 1) + j + 1] = g1;
+  gv[(size_t)p * (m + 1) + j] = make_double2(c * gj.x, c * gj.y);
+  res[p] = hypot(g1.x, g1.y);
 }
 
-// v_{j+1} = w / ||w|| (0 on breakdown)
-__global__ void k_scale(int n, int nrhs, const int* __restrict__ act, const double* __restrict__ hn,
-                        const double2* __restrict__ w, double2* __restrict__ vout) {
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (size_t)n * nrhs) return;
-  int k = (int)(e / n);
-  if (!act[k]) return;
-  double h = hn[k];
-  double inv = h > 0.0 ? 1.0 / h : 0.0;
-  double2 v = w[e];
-  vout[e] = make_double2(v.x * inv, v.y * inv);
+// vout = w / ||w|| per problem (0 on breakdown)
+__global__ void __launch_bounds__(AT)
+k_scale(const int* __restrict__ act, pset_dev ps, const double* __restrict__ hn,
+        const double2* __restrict__ w, double2* __restrict__ vout) {
+  const chunk_ref c = chunk_of(ps, blockIdx.x);
+  if (!act[c.p]) return;
+  const double h = hn[c.p];
+  const double inv = h > 0.0 ? 1.0 / h : 0.0;
+#pragma unroll
+  for (int e = 0; e < AE; ++e) {
+    const int q = e * AT + threadIdx.x;
+    if (q < c.cnt) {
+      const double2 v = w[c.base + q];
+      vout[c.base + q] = make_double2(v.x * inv, v.y * inv);
+    }
+  }
 }
 
-// per right-hand side: y = R^{-1} g on the leading kd x kd triangle
-__global__ void k_lsq(int nrhs, int m, const int* __restrict__ kd, const double2* __restrict__ H,
+// v0 = r / beta per problem
+__global__ void __launch_bounds__(AT)
+k_start(const int* __restrict__ act, pset_dev ps, const double* __restrict__ beta,
+        const double2* __restrict__ r, double2* __restrict__ v0) {
+  const chunk_ref c = chunk_of(ps, blockIdx.x);
+  const double b = beta[c.p];
+  const double inv = (act[c.p] && b > 0.0) ? 1.0 / b : 0.0;
+#pragma unroll
+  for (int e = 0; e < AE; ++e) {
+    const int q = e * AT + threadIdx.x;
+    if (q < c.cnt) {
+      const double2 v = r[c.base + q];
+      v0[c.base + q] = make_double2(v.x * inv, v.y * inv);
+    }
+  }
+}
+
+// g = (beta, 0, ..., 0) per problem
+__global__ void k_g_init(int P, int m, const int* __restrict__ act, const double* __restrict__ beta,
+                         double2* __restrict__ gv) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)P * (m + 1)) return;
+  const int p = (int)(e / (m + 1));
+  const int q = (int)(e % (m + 1));
+  gv[e] = make_double2(q == 0 && act[p] ? beta[p] : 0.0, 0.0);
+}
+
+// per problem: y = R^{-1} g on the leading kd x kd triangle
+__global__ void k_lsq(int P, int m, const int* __restrict__ kd, const double2* __restrict__ H,
                       const double2* __restrict__ gv, double2* __restrict__ y) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nrhs) return;
-  int K = kd[k];
-  const double2* Hk = H + (size_t)k * (m + 1) * m;
-  double2* yk = y + (size_t)k * m;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const int K = kd[p];
+  const double2* Hk = H + (size_t)p * (m + 1) * m;
+  double2* yk = y + (size_t)p * m;
   for (int i = K - 1; i >= 0; --i) {
-    double2 s = gv[(size_t)k * (m + 1) + i];
+    double2 s = gv[(size_t)p * (m + 1) + i];
     for (int q = i + 1; q < K; ++q) {
-      double2 h = Hk[(size_t)i * m + q], yq = yk[q];
+      const double2 h = Hk[(size_t)i * m + q], yq = yk[q];
       s.x -= h.x * yq.x - h.y * yq.y;
       s.y -= h.x * yq.y + h.y * yq.x;
     }
-    double2 d = Hk[(size_t)i * m + i];
-    double den = d.x * d.x + d.y * d.y;
+    const double2 d = Hk[(size_t)i * m + i];
+    const double den = d.x * d.x + d.y * d.y;
     yk[i] = den > 0.0 ? make_double2((s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den)
                       : make_double2(0.0, 0.0);
   }
 }
 
-// x[k][i] += sum_{jj < kd[k]} V[jj][k][i] y[k][jj]
-__global__ void k_xupdate(int n, int nrhs, int m, const int* __restrict__ kd,
-                          const double2* __restrict__ V, const double2* __restrict__ y,
-                          double2* __restrict__ x) {
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (size_t)n * nrhs) return;
-  int k = (int)(e / n);
-  int i = (int)(e % n);
-  int K = kd[k];
+// x += sum_{jj < kd[p]} V[jj] y[p][jj]
+__global__ void __launch_bounds__(AT)
+k_xupdate(int m, const int* __restrict__ kd, pset_dev ps, const double2* __restrict__ V, size_t L,
+          const double2* __restrict__ y, double2* __restrict__ x) {
+  const chunk_ref c = chunk_of(ps, blockIdx.x);
+  const int K = kd[c.p];
   if (K == 0) return;
-  double2 acc = x[e];
-  for (int jj = 0; jj < K; ++jj) {
-    double2 v = V[((size_t)jj * nrhs + k) * n + i];
-    double2 yy = y[(size_t)k * m + jj];
-    acc.x += v.x * yy.x - v.y * yy.y;
-    acc.y += v.x * yy.y + v.y * yy.x;
+  double2 acc[AE];
+#pragma unroll
+  for (int e = 0; e < AE; ++e) {
+    const int q = e * AT + threadIdx.x;
+    acc[e] = q < c.cnt ? x[c.base + q] : make_double2(0.0, 0.0);
   }
-  x[e] = acc;
+  for (int jj = 0; jj < K; ++jj) {
+    const double2 yy = y[(size_t)c.p * m + jj];
+    const double2* v = V + (size_t)jj * L + c.base;
+#pragma unroll
+    for (int e = 0; e < AE; ++e) {
+      const int q = e * AT + threadIdx.x;
+      if (q < c.cnt) {
+        const double2 a = v[q];
+        acc[e].x += a.x * yy.x - a.y * yy.y;
+        acc[e].y += a.x * yy.y + a.y * yy.x;
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < AE; ++e) {
+    const int q = e * AT + threadIdx.x;
+    if (q < c.cnt) x[c.base + q] = acc[e];
+  }
 }
 
-// r = f - ax (ax may be null: r = f); per-rhs ||r||^2 and ||f||^2 partials
+// r = f - ax (ax may be null: r = f; r may be null); per-chunk ||r||^2, ||f||^2
 __global__ void __launch_bounds__(AT)
-k_residual(int n, int nrhs, const double2* __restrict__ f, const double2* __restrict__ ax,
-           double2* __restrict__ r, int nchunks, double* __restrict__ rr, double* __restrict__ ff) {
-  const int k = blockIdx.y, chunk = blockIdx.x, base = chunk * CH;
+k_residual(pset_dev ps, const double2* __restrict__ f, const double2* __restrict__ ax,
+           double2* __restrict__ r, double* __restrict__ rr, double* __restrict__ ff) {
+  const chunk_ref c = chunk_of(ps, blockIdx.x);
   double sr = 0.0, sf = 0.0;
 #pragma unroll
   for (int e = 0; e < AE; ++e) {
-    int i = base + e * AT + threadIdx.x;
-    if (i < n) {
-      size_t idx = (size_t)k * n + i;
-      double2 fv = f[idx];
+    const int q = e * AT + threadIdx.x;
+    if (q < c.cnt) {
+      const size_t idx = c.base + q;
+      const double2 fv = f[idx];
       double2 v = fv;
       if (ax) {
-        double2 a = ax[idx];
+        const double2 a = ax[idx];
         v.x -= a.x;
         v.y -= a.y;
       }
@@ -301,51 +358,33 @@ k_residual(int n, int nrhs, const double2* __restrict__ f, const double2* __rest
       a += red[0][q];
       b += red[1][q];
     }
-    rr[(size_t)k * nchunks + chunk] = a;
-    ff[(size_t)k * nchunks + chunk] = b;
+    rr[c.slot] = a;
+    ff[c.slot] = b;
   }
 }
 
-__global__ void k_sum_chunks(int nrhs, int nchunks, const double* __restrict__ a,
+__global__ void k_sum_chunks(int P, pset_dev ps, const double* __restrict__ a,
                              const double* __restrict__ b, double* __restrict__ out) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nrhs) return;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
   double s = 0.0, t = 0.0;
-  for (int c = 0; c < nchunks; ++c) {
-    s += a[(size_t)k * nchunks + c];
-    t += b[(size_t)k * nchunks + c];
+  for (int c = 0; c < ps.nch[p]; ++c) {
+    s += a[ps.chb[p] + c];
+    t += b[ps.chb[p] + c];
   }
-  out[k] = sqrt(s);
-  out[nrhs + k] = sqrt(t);
-}
-
-// v0[k] = r[k] / beta[k]; g[k] = (beta, 0, ...)
-__global__ void k_start(int n, int nrhs, int m, const int* __restrict__ act,
-                        const double* __restrict__ beta, const double2* __restrict__ r,
-                        double2* __restrict__ v0, double2* __restrict__ gv) {
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < (size_t)nrhs * (m + 1)) {
-    int k = (int)(e / (m + 1));
-    int q = (int)(e % (m + 1));
-    gv[e] = make_double2(q == 0 && act[k] ? beta[k] : 0.0, 0.0);
-  }
-  if (e >= (size_t)n * nrhs) return;
-  int k = (int)(e / n);
-  double b = beta[k];
-  double inv = (act[k] && b > 0.0) ? 1.0 / b : 0.0;
-  double2 v = r[e];
-  v0[e] = make_double2(v.x * inv, v.y * inv);
+  out[p] = sqrt(s);
+  out[P + p] = sqrt(t);
 }
 
 __global__ void k_axpy(size_t len, const double2* __restrict__ d, double2* __restrict__ x) {
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= len) return;
-  double2 a = x[e], b = d[e];
+  const double2 a = x[e], b = d[e];
   x[e] = make_double2(a.x + b.x, a.y + b.y);
 }
 
 __global__ void k_zero(size_t len, double2* __restrict__ x) {
-  size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < len) x[e] = make_double2(0.0, 0.0);
 }
 
@@ -354,44 +393,44 @@ unsigned blocks_for(size_t len, int t = 256) { return (unsigned)((len + t - 1) /
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
-using matvec_t = void (*)(cfie_op*, const double2*, double2*, int);
-
 struct ws {
   double2 *V, *H, *gv, *sn, *w, *hbuf, *y, *part;
   double *cs, *hn, *res, *nrmp, *rr, *ff, *norms;
   int *act, *kd;
-  int nchunks;
 };
 
-ws workspace(cfie_op* op, int nrhs, int m) {
-  const int n = op->n;
-  const int nchunks = (n + CH - 1) / CH;
-  const size_t nv = (size_t)n * nrhs;
-  op->V.reserve(sizeof(double2) * nv * (m + 1));
-  op->wv.reserve(sizeof(double2) * nv);
-  op->H.reserve(sizeof(double2) * (size_t)nrhs * (m + 1) * m);
+ws workspace(krylov_ws& K, const pset& ps, int m) {
+  const int P = ps.P, Q = ps.Q;
+  const size_t L = ps.L;
+  K.V.reserve(sizeof(double2) * L * (m + 1));
+  K.w.reserve(sizeof(double2) * L);
+  K.H.reserve(sizeof(double2) * (size_t)P * (m + 1) * m);
   size_t sm = 0;
-  auto take = [&](size_t bytes) { size_t o = sm; sm += (bytes + 255) & ~size_t(255); return o; };
-  size_t o_gv = take(sizeof(double2) * nrhs * (m + 1));
-  size_t o_sn = take(sizeof(double2) * nrhs * m);
-  size_t o_hb = take(sizeof(double2) * nrhs * (m + 1));
-  size_t o_y = take(sizeof(double2) * nrhs * m);
-  size_t o_part = take(sizeof(double2) * nrhs * (m + 1) * nchunks);
-  size_t o_cs = take(sizeof(double) * nrhs * m);
-  size_t o_hn = take(sizeof(double) * nrhs);
-  size_t o_res = take(sizeof(double) * nrhs);
-  size_t o_nrmp = take(sizeof(double) * nrhs * nchunks);
-  size_t o_rr = take(sizeof(double) * nrhs * nchunks);
-  size_t o_ff = take(sizeof(double) * nrhs * nchunks);
-  size_t o_norms = take(sizeof(double) * 2 * nrhs);
-  size_t o_act = take(sizeof(int) * nrhs);
-  size_t o_kd = take(sizeof(int) * nrhs);
-  op->small.reserve(sm);
-  char* b = op->small.as<char>();
+  auto take = [&](size_t bytes) {
+    size_t o = sm;
+    sm += (bytes + 255) & ~size_t(255);
+    return o;
+  };
+  const size_t o_gv = take(sizeof(double2) * P * (m + 1));
+  const size_t o_sn = take(sizeof(double2) * P * m);
+  const size_t o_hb = take(sizeof(double2) * P * (m + 1));
+  const size_t o_y = take(sizeof(double2) * P * m);
+  const size_t o_part = take(sizeof(double2) * (size_t)Q * (m + 1));
+  const size_t o_cs = take(sizeof(double) * P * m);
+  const size_t o_hn = take(sizeof(double) * P);
+  const size_t o_res = take(sizeof(double) * P);
+  const size_t o_nrmp = take(sizeof(double) * Q);
+  const size_t o_rr = take(sizeof(double) * Q);
+  const size_t o_ff = take(sizeof(double) * Q);
+  const size_t o_norms = take(sizeof(double) * 2 * P);
+  const size_t o_act = take(sizeof(int) * P);
+  const size_t o_kd = take(sizeof(int) * P);
+  K.small.reserve(sm);
+  char* b = K.small.as<char>();
   ws W;
-  W.V = op->V.as<double2>();
-  W.H = op->H.as<double2>();
-  W.w = op->wv.as<double2>();
+  W.V = K.V.as<double2>();
+  W.H = K.H.as<double2>();
+  W.w = K.w.as<double2>();
   W.gv = (double2*)(b + o_gv);
   W.sn = (double2*)(b + o_sn);
   W.hbuf = (double2*)(b + o_hb);
@@ -406,89 +445,95 @@ ws workspace(cfie_op* op, int nrhs, int m) {
   W.norms = (double*)(b + o_norms);
   W.act = (int*)(b + o_act);
   W.kd = (int*)(b + o_kd);
-  W.nchunks = nchunks;
-  if (op->host_res_cap < 2 * nrhs + 8) {
-    if (op->host_res) cudaFreeHost(op->host_res);
-    op->host_res = nullptr;
-    CFIE_CHECK_CUDA(cudaMallocHost(&op->host_res, sizeof(double) * (2 * nrhs + 8)));
-    op->host_res_cap = 2 * nrhs + 8;
+  if (K.host_cap < 2 * P + 8) {
+    if (K.host) cudaFreeHost(K.host);
+    K.host = nullptr;
+    CFIE_CHECK_CUDA(cudaMallocHost(&K.host, sizeof(double) * (2 * P + 8)));
+    K.host_cap = 2 * P + 8;
   }
   return W;
 }
 
-// ||r_k|| and ||f_k|| to host (synchronous); r = f - ax (ax may be null)
-void residual_norms(cfie_op* op, const ws& W, const double2* f, const double2* ax, double2* r,
-                    int nrhs, std::vector<double>& rn, std::vector<double>& fn) {
-  cudaStream_t st = op->ctx->stream;
-  dim3 grid(W.nchunks, nrhs);
-  k_residual<<<grid, AT, 0, st>>>(op->n, nrhs, f, ax, r, W.nchunks, W.rr, W.ff);
+// ||r_p|| and ||f_p|| to host (synchronous); r = f - ax (ax, r may be null)
+void residual_norms(cudaStream_t st, krylov_ws& K, const pset& ps, const ws& W,
+                    const double2* f, const double2* ax, double2* r, std::vector<double>& rn,
+                    std::vector<double>& fn) {
+  const int P = ps.P;
+  k_residual<<<ps.Q, AT, 0, st>>>(ps.dev, f, ax, r, W.rr, W.ff);
   CFIE_CHECK_LAUNCH();
-  k_sum_chunks<<<blocks_for(nrhs, 64), 64, 0, st>>>(nrhs, W.nchunks, W.rr, W.ff, W.norms);
+  k_sum_chunks<<<blocks_for(P, 64), 64, 0, st>>>(P, ps.dev, W.rr, W.ff, W.norms);
   CFIE_CHECK_LAUNCH();
-  CFIE_CHECK_CUDA(cudaMemcpyAsync(op->host_res, W.norms, sizeof(double) * 2 * nrhs,
-                                  cudaMemcpyDeviceToHost, st));
+  CFIE_CHECK_CUDA(
+      cudaMemcpyAsync(K.host, W.norms, sizeof(double) * 2 * P, cudaMemcpyDeviceToHost, st));
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
-  rn.assign(op->host_res, op->host_res + nrhs);
-  fn.assign(op->host_res + nrhs, op->host_res + 2 * nrhs);
+  rn.assign(K.host, K.host + P);
+  fn.assign(K.host + P, K.host + 2 * P);
 }
 
-// One GMRES cycle per call: starting residual r (device), basis built with `mv`,
-// x += V y.  active[k] on entry says which right-hand sides take part; tol[k]
-// is the absolute residual-norm target.  Returns steps taken per rhs.
-void gmres_cycle(cfie_op* op, const ws& W, matvec_t mv, const double2* r,
+// One GMRES cycle: starting residual r (norms beta), basis built with the
+// inner or the FP64 matvec, x += V y.  active[p] says which problems take part;
+// tol[p] is the absolute residual-norm target.  Counts steps per problem.
+void gmres_cycle(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps, const ws& W,
+                 const solve_fns& fns, bool inner, const double2* r,
                  const std::vector<double>& beta, const std::vector<double>& tol,
-                 std::vector<int>& active, int nrhs, int m, std::vector<int>& steps_left,
-                 double2* x, std::vector<int>& its) {
-  cudaStream_t st = op->ctx->stream;
-  const int n = op->n;
-  const size_t nv = (size_t)n * nrhs;
-  std::vector<int> act = active, kd(nrhs, 0);
+                 const std::vector<int>& active, int m, std::vector<int>& steps_left, double2* x,
+                 std::vector<int>& its, cfie_solve_stats& stats, std::vector<int>* met = nullptr) {
+  const int P = ps.P;
+  const size_t L = ps.L;
+  std::vector<int> act = active, kd(P, 0);
+  if (met) met->assign(P, 0);
   int nact = 0;
-  for (int k = 0; k < nrhs; ++k) nact += act[k];
+  for (int p = 0; p < P; ++p) nact += act[p];
   if (!nact) return;
-  CFIE_CHECK_CUDA(cudaMemcpyAsync(W.act, act.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-  CFIE_CHECK_CUDA(cudaMemcpyAsync(W.norms, beta.data(), sizeof(double) * nrhs,
-                                  cudaMemcpyHostToDevice, st));
-  k_start<<<blocks_for(std::max(nv, (size_t)nrhs * (m + 1))), 256, 0, st>>>(n, nrhs, m, W.act,
-                                                                           W.norms, r, W.V, W.gv);
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(W.act, act.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+  CFIE_CHECK_CUDA(
+      cudaMemcpyAsync(W.norms, beta.data(), sizeof(double) * P, cudaMemcpyHostToDevice, st));
+  k_start<<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.norms, r, W.V);
   CFIE_CHECK_LAUNCH();
-  op->stats.cycles++;
+  k_g_init<<<blocks_for((size_t)P * (m + 1)), 256, 0, st>>>(P, m, W.act, W.norms, W.gv);
+  CFIE_CHECK_LAUNCH();
+  stats.cycles++;
   for (int j = 0; j < m; ++j) {
-    double2* vj = W.V + (size_t)j * nv;
-    mv(op, vj, W.w, nrhs);
+    double2* vj = W.V + (size_t)j * L;
+    if (inner) {
+      stats.inner_matvecs++;
+      fns.inner(vj, W.w);
+    } else {
+      stats.fp64_matvecs++;
+      fns.fp64(vj, W.w);
+    }
     {
-      prof_scope ps(op->ctx, CFIE_K_ARNOLDI);
-      dim3 grid(W.nchunks, nrhs);
-      size_t red_smem = sizeof(double2) * (j + 1) * (AT / 32);
+      prof_scope ps_(ctx, CFIE_K_ARNOLDI);
+      const size_t red_smem = sizeof(double2) * (j + 1) * (AT / 32);
       for (int pass = 0; pass < 2; ++pass) {
-        k_dots<<<grid, AT, red_smem, st>>>(n, nrhs, j, W.V, W.w, W.act, W.nchunks, W.part);
+        k_dots<<<ps.Q, AT, red_smem, st>>>(j, W.V, L, W.w, W.act, ps.dev, W.part);
         CFIE_CHECK_LAUNCH();
-        k_dots_reduce<<<nrhs, 128, 0, st>>>(nrhs, j, W.nchunks, m, j, pass == 0, W.act, W.part,
-                                            W.hbuf, W.H);
+        k_dots_reduce<<<P, 128, 0, st>>>(j, m, j, pass == 0, W.act, ps.dev, W.part, W.hbuf, W.H);
         CFIE_CHECK_LAUNCH();
-        k_update<<<grid, AT, sizeof(double2) * (j + 1), st>>>(
-            n, nrhs, j, W.V, W.hbuf, W.act, W.w, W.nchunks, pass == 1 ? W.nrmp : nullptr);
+        k_update<<<ps.Q, AT, sizeof(double2) * (j + 1), st>>>(
+            j, W.V, L, W.hbuf, W.act, ps.dev, W.w, pass == 1 ? W.nrmp : nullptr);
         CFIE_CHECK_LAUNCH();
       }
-      k_givens<<<blocks_for(nrhs, 64), 64, 0, st>>>(nrhs, m, j, W.nchunks, W.act, W.nrmp, W.H,
-                                                     W.cs, W.sn, W.gv, W.hn, W.res);
+      k_givens<<<blocks_for(P, 64), 64, 0, st>>>(P, m, j, W.act, ps.dev, W.nrmp, W.H, W.cs, W.sn,
+                                                 W.gv, W.hn, W.res);
       CFIE_CHECK_LAUNCH();
-      k_scale<<<blocks_for(nv), 256, 0, st>>>(n, nrhs, W.act, W.hn, W.w, W.V + (size_t)(j + 1) * nv);
+      k_scale<<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.hn, W.w, W.V + (size_t)(j + 1) * L);
       CFIE_CHECK_LAUNCH();
     }
-    CFIE_CHECK_CUDA(cudaMemcpyAsync(op->host_res, W.res, sizeof(double) * nrhs,
-                                    cudaMemcpyDeviceToHost, st));
+    CFIE_CHECK_CUDA(
+        cudaMemcpyAsync(K.host, W.res, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
     CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
-    op->stats.arnoldi_steps++;
+    stats.arnoldi_steps++;
     bool changed = false;
     nact = 0;
-    for (int k = 0; k < nrhs; ++k) {
-      if (!act[k]) continue;
-      kd[k] = j + 1;
-      its[k]++;
-      steps_left[k]--;
-      if (op->host_res[k] <= tol[k] || steps_left[k] <= 0) {
-        act[k] = 0;
+    for (int p = 0; p < P; ++p) {
+      if (!act[p]) continue;
+      kd[p] = j + 1;
+      its[p]++;
+      steps_left[p]--;
+      if (K.host[p] <= tol[p] || steps_left[p] <= 0) {
+        if (met && K.host[p] <= tol[p]) (*met)[p] = 1;
+        act[p] = 0;
         changed = true;
       } else {
         nact++;
@@ -496,119 +541,164 @@ void gmres_cycle(cfie_op* op, const ws& W, matvec_t mv, const double2* r,
     }
     if (!nact) break;
     if (changed)
-      CFIE_CHECK_CUDA(cudaMemcpyAsync(W.act, act.data(), sizeof(int) * nrhs,
-                                      cudaMemcpyHostToDevice, st));
+      CFIE_CHECK_CUDA(
+          cudaMemcpyAsync(W.act, act.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
   }
-  CFIE_CHECK_CUDA(cudaMemcpyAsync(W.kd, kd.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, st));
-  k_lsq<<<blocks_for(nrhs, 64), 64, 0, st>>>(nrhs, m, W.kd, W.H, W.gv, W.y);
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(W.kd, kd.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
+  k_lsq<<<blocks_for(P, 64), 64, 0, st>>>(P, m, W.kd, W.H, W.gv, W.y);
   CFIE_CHECK_LAUNCH();
-  k_xupdate<<<blocks_for(nv), 256, 0, st>>>(n, nrhs, m, W.kd, W.V, W.y, x);
+  k_xupdate<<<ps.Q, AT, 0, st>>>(m, W.kd, ps.dev, W.V, L, W.y, x);
   CFIE_CHECK_LAUNCH();
-  // the temporaries copied from host must stay alive until the copies ran
+  // host vectors copied above must stay alive until the copies ran
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
-}
-
-void fp64_mv(cfie_op* op, const double2* x, double2* y, int nrhs) {
-  op->stats.fp64_matvecs++;
-  matvec_fp64(op, x, y, nrhs);
-}
-void inner_mv(cfie_op* op, const double2* x, double2* y, int nrhs) {
-  op->stats.inner_matvecs++;
-  apply_inner(op, x, y, nrhs);
 }
 
 }  // namespace
 
-void gmres_solve(cfie_op* op, const double2* f, double2* x, int nrhs, double rtol, int restart,
-                 int maxit, int* iters, double* relres, cfie_status* status) {
-  op->stats = cfie_solve_stats{};
-  const int n = op->n;
-  const size_t nv = (size_t)n * nrhs;
+void pset_build(pset& ps, const std::vector<size_t>& off, const std::vector<int>& len,
+                cudaStream_t st) {
+  ps.P = (int)off.size();
+  std::vector<int> nch(ps.P), chb(ps.P);
+  std::vector<int2> items;
+  size_t L = 0;
+  for (int p = 0; p < ps.P; ++p) {
+    nch[p] = (len[p] + CH - 1) / CH;
+    chb[p] = (int)items.size();
+    for (int c = 0; c < nch[p]; ++c) items.push_back(make_int2(p, c));
+    L = std::max(L, off[p] + (size_t)len[p]);
+  }
+  ps.Q = (int)items.size();
+  ps.L = L;
+  const size_t bytes = sizeof(size_t) * ps.P + sizeof(int) * 3 * ps.P + sizeof(int2) * ps.Q + 128;
+  ps.buf.reserve(bytes);
+  char* b = ps.buf.as<char>();
+  size_t o = 0;
+  auto put = [&](const void* src, size_t n) {
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(b + o, src, n, cudaMemcpyHostToDevice, st));
+    void* at = b + o;
+    o += (n + 15) & ~size_t(15);
+    return at;
+  };
+  ps.dev.off = (const size_t*)put(off.data(), sizeof(size_t) * ps.P);
+  ps.dev.len = (const int*)put(len.data(), sizeof(int) * ps.P);
+  ps.dev.nch = (const int*)put(nch.data(), sizeof(int) * ps.P);
+  ps.dev.chb = (const int*)put(chb.data(), sizeof(int) * ps.P);
+  ps.dev.items = (const int2*)put(items.data(), sizeof(int2) * ps.Q);
+  CFIE_CHECK_CUDA(cudaStreamSynchronize(st));  // the host vectors die on return
+}
+
+void pset_uniform(pset& ps, int n, int nrhs, cudaStream_t st) {
+  std::vector<size_t> off(nrhs);
+  std::vector<int> len(nrhs, n);
+  for (int k = 0; k < nrhs; ++k) off[k] = (size_t)k * n;
+  pset_build(ps, off, len, st);
+}
+
+void gmres_set(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps,
+               const solve_fns& fns, bool refined, const double2* f, double2* x, double rtol,
+               int restart, int maxit, int* iters, double* relres, cfie_status* status,
+               cfie_solve_stats& stats) {
+  stats = cfie_solve_stats{};
+  const int P = ps.P;
+  const size_t L = ps.L;
   int m = restart > 0 ? restart : maxit;
   m = std::max(1, std::min(m, std::min(maxit, MAXJ)));
-  ws W = workspace(op, nrhs, m);
-  cudaStream_t st = op->ctx->stream;
-  op->rv.reserve(sizeof(double2) * nv);
-  double2* r = op->rv.as<double2>();
+  ws W = workspace(K, ps, m);
+  K.r.reserve(sizeof(double2) * L);
+  double2* r = K.r.as<double2>();
   double2* ax = W.w;  // matvec output scratch (free between cycles)
 
   std::vector<double> rn, fn, xn, dummy;
-  std::vector<int> its(nrhs, 0), steps_left(nrhs, maxit), active(nrhs, 1);
+  std::vector<int> its(P, 0), steps_left(P, maxit), active(P, 1);
   // true residual of the initial guess (no matvec when x0 = 0)
-  residual_norms(op, W, x, nullptr, nullptr, nrhs, xn, dummy);
+  residual_norms(st, K, ps, W, x, nullptr, nullptr, xn, dummy);
   bool x_zero = true;
-  for (int k = 0; k < nrhs; ++k) x_zero = x_zero && xn[k] == 0.0;
+  for (int p = 0; p < P; ++p) x_zero = x_zero && xn[p] == 0.0;
   if (x_zero) {
-    residual_norms(op, W, f, nullptr, r, nrhs, rn, fn);
+    residual_norms(st, K, ps, W, f, nullptr, r, rn, fn);
   } else {
-    fp64_mv(op, x, ax, nrhs);
-    residual_norms(op, W, f, ax, r, nrhs, rn, fn);
+    stats.fp64_matvecs++;
+    fns.fp64(x, ax);
+    residual_norms(st, K, ps, W, f, ax, r, rn, fn);
   }
 
-  const bool refined = op->prec != CFIE_FP64;
   if (!refined) {
     for (;;) {
-      std::vector<double> tol(nrhs);
+      std::vector<double> tol(P);
       int nact = 0;
-      for (int k = 0; k < nrhs; ++k) {
-        tol[k] = rtol * fn[k];
-        active[k] = (rn[k] > tol[k] && steps_left[k] > 0) ? 1 : 0;
-        nact += active[k];
+      for (int p = 0; p < P; ++p) {
+        tol[p] = rtol * fn[p];
+        active[p] = (rn[p] > tol[p] && steps_left[p] > 0) ? 1 : 0;
+        nact += active[p];
       }
       if (!nact) break;
-      gmres_cycle(op, W, fp64_mv, r, rn, tol, active, nrhs, m, steps_left, x, its);
-      fp64_mv(op, x, ax, nrhs);
-      residual_norms(op, W, f, ax, r, nrhs, rn, fn);
+      gmres_cycle(st, ctx, K, ps, W, fns, false, r, rn, tol, active, m, steps_left, x, its,
+                  stats);
+      stats.fp64_matvecs++;
+      fns.fp64(x, ax);
+      residual_norms(st, K, ps, W, f, ax, r, rn, fn);
     }
   } else {
-    // mixed-precision iterative refinement: inner GMRES on A d = r with the
-    // operator's fast matvec, x += d, r = f - A64 x (FP64)
-    op->dv.reserve(sizeof(double2) * nv);
-    op->rin.reserve(sizeof(double2) * nv);
-    double2* d = op->dv.as<double2>();
-    double2* rin = op->rin.as<double2>();
+    // iterative refinement: inner GMRES on A d = r with the fast matvec,
+    // x += d, r = f - A64 x (FP64)
+    K.d.reserve(sizeof(double2) * L);
+    K.rin.reserve(sizeof(double2) * L);
+    double2* d = K.d.as<double2>();
+    double2* rin = K.rin.as<double2>();
     const double tau_min = 1e-4;
     for (int outer = 0; outer < 12; ++outer) {
-      std::vector<double> tol(nrhs);
+      std::vector<double> tol(P);
       int nact = 0;
-      for (int k = 0; k < nrhs; ++k) {
-        active[k] = (rn[k] > rtol * fn[k] && steps_left[k] > 0) ? 1 : 0;
-        nact += active[k];
-        double tau = rn[k] > 0 ? 0.3 * rtol * fn[k] / rn[k] : 1.0;
+      for (int p = 0; p < P; ++p) {
+        active[p] = (rn[p] > rtol * fn[p] && steps_left[p] > 0) ? 1 : 0;
+        nact += active[p];
+        double tau = rn[p] > 0 ? 0.3 * rtol * fn[p] / rn[p] : 1.0;
         tau = std::min(0.5, std::max(tau_min, tau));
-        tol[k] = tau * rn[k];
+        tol[p] = tau * rn[p];
       }
       if (!nact) break;
-      op->stats.refinements++;
-      k_zero<<<blocks_for(nv), 256, 0, st>>>(nv, d);
+      stats.refinements++;
+      k_zero<<<blocks_for(L), 256, 0, st>>>(L, d);
       CFIE_CHECK_LAUNCH();
-      // inner restarted GMRES on A32 d = r
       std::vector<double> irn = rn, ifn;
       std::vector<int> iact = active;
-      CFIE_CHECK_CUDA(cudaMemcpyAsync(rin, r, sizeof(double2) * nv, cudaMemcpyDeviceToDevice, st));
+      CFIE_CHECK_CUDA(cudaMemcpyAsync(rin, r, sizeof(double2) * L, cudaMemcpyDeviceToDevice, st));
       for (int cyc = 0; cyc < 64; ++cyc) {
-        gmres_cycle(op, W, inner_mv, rin, irn, tol, iact, nrhs, m, steps_left, d, its);
-        // inner true residual r - A32 d
-        inner_mv(op, d, ax, nrhs);
-        residual_norms(op, W, r, ax, rin, nrhs, irn, ifn);
+        std::vector<int> met;
+        gmres_cycle(st, ctx, K, ps, W, fns, true, rin, irn, tol, iact, m, steps_left, d, its,
+                    stats, &met);
+        bool all_met = true;
+        for (int p = 0; p < P; ++p) all_met = all_met && (!iact[p] || met[p]);
+        if (all_met) break;   // the outer FP64 residual below is the real check
+        // inner true residual r - A_fast d before restarting
+        stats.inner_matvecs++;
+        fns.inner(d, ax);
+        residual_norms(st, K, ps, W, r, ax, rin, irn, ifn);
         int left = 0;
-        for (int k = 0; k < nrhs; ++k) {
-          iact[k] = active[k] && irn[k] > tol[k] && steps_left[k] > 0 ? 1 : 0;
-          left += iact[k];
+        for (int p = 0; p < P; ++p) {
+          iact[p] = active[p] && irn[p] > tol[p] && steps_left[p] > 0 ? 1 : 0;
+          left += iact[p];
         }
         if (!left) break;
       }
-      k_axpy<<<blocks_for(nv), 256, 0, st>>>(nv, d, x);
+      k_axpy<<<blocks_for(L), 256, 0, st>>>(L, d, x);
       CFIE_CHECK_LAUNCH();
-      fp64_mv(op, x, ax, nrhs);
-      residual_norms(op, W, f, ax, r, nrhs, rn, fn);
+      stats.fp64_matvecs++;
+      fns.fp64(x, ax);
+      residual_norms(st, K, ps, W, f, ax, r, rn, fn);
     }
   }
   *status = CFIE_OK;
-  for (int k = 0; k < nrhs; ++k) {
-    double rel = fn[k] > 0 ? rn[k] / fn[k] : 0.0;
-    if (relres) relres[k] = rel;
-    if (iters) iters[k] = its[k];
+  for (int p = 0; p < P; ++p) {
+    const double rel = fn[p] > 0 ? rn[p] / fn[p] : 0.0;
+    if (relres) relres[p] = rel;
+    if (iters) iters[p] = its[p];
     if (!(rel <= rtol)) *status = CFIE_ENOCONV;
   }
+}
+
+void krylov_release(krylov_ws& K) {
+  if (K.host) cudaFreeHost(K.host);
+  K.host = nullptr;
+  K.host_cap = 0;
 }

@@ -261,7 +261,8 @@ void cfie_op_destroy(cfie_op* op) {
   if (!op) return;
   cudaSetDevice(op->ctx->device);
   cudaStreamSynchronize(op->ctx->stream);
-  if (op->host_res) cudaFreeHost(op->host_res);
+  krylov_release(op->K);
+  gemm_plan_release(op->plan);
   delete op;
 }
 
@@ -332,8 +333,17 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
     check_vec(x_dev, "x");
     CFIE_REQUIRE(f_dev != x_dev, "f and x must not overlap");
     set_device(op->ctx);
-    gmres_solve(op, static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), nrhs, rtol,
-                restart, maxit, iters_out, relres_out, &result);
+    cudaStream_t st = op->ctx->stream;
+    if (op->ps_nrhs != nrhs) {
+      pset_uniform(op->ps, op->n, nrhs, st);
+      op->ps_nrhs = nrhs;
+    }
+    solve_fns fns;
+    fns.inner = [op, nrhs](const double2* a, double2* b) { apply_inner(op, a, b, nrhs); };
+    fns.fp64 = [op, nrhs](const double2* a, double2* b) { matvec_fp64(op, a, b, nrhs); };
+    gmres_set(st, op->ctx, op->K, op->ps, fns, op->prec != CFIE_FP64,
+              static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), rtol, restart,
+              maxit, iters_out, relres_out, &result, op->stats);
     if (op->layout == CFIE_STORED && stored_take_error(op))
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     if (result == CFIE_ENOCONV) op->ctx->err = "GMRES reached maxit before rtol";
@@ -374,5 +384,121 @@ cfie_status cfie_ctx_kernel_times(cfie_ctx* ctx, double* ms, long long* launches
 }
 
 long long cfie_launch_count(void) { return g_cfie_launches; }
+
+// ---------------------------------------------------------------------------
+// batches
+// ---------------------------------------------------------------------------
+static void batch_inner(cfie_batch* b, const double2* x, double2* y) {
+  if (b->all_stored) {
+    gemm_plan_run(b->plan, b->ctx, x, y);
+    return;
+  }
+  for (size_t k = 0; k < b->ops.size(); ++k)
+    apply_inner(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
+}
+
+static void batch_fp64(cfie_batch* b, const double2* x, double2* y) {
+  for (size_t k = 0; k < b->ops.size(); ++k)
+    matvec_fp64(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
+}
+
+cfie_status cfie_batch_create(cfie_ctx* ctx, int count, cfie_op* const* ops, const int* nrhs,
+                              cfie_batch** out) {
+  if (!ctx || !out) return CFIE_EINVAL;
+  *out = nullptr;
+  cfie_batch* b = nullptr;
+  cfie_status st = guarded(ctx, [&] {
+    CFIE_REQUIRE(count >= 1 && count <= 65535, "count must be in [1, 65535]");
+    CFIE_REQUIRE(ops && nrhs, "ops and nrhs must not be NULL");
+    set_device(ctx);
+    b = new cfie_batch();
+    b->ctx = ctx;
+    b->all_stored = true;
+    std::vector<size_t> poff;
+    std::vector<int> plen;
+    long long at = 0;
+    for (int k = 0; k < count; ++k) {
+      CFIE_REQUIRE(ops[k] && ops[k]->ctx == ctx, "every operator must belong to the context");
+      CFIE_REQUIRE(nrhs[k] >= 1 && nrhs[k] <= 1024, "nrhs must be in [1, 1024]");
+      CFIE_REQUIRE(ops[k]->prec == ops[0]->prec, "operators of a batch share one precision");
+      b->ops.push_back(ops[k]);
+      b->nrhs.push_back(nrhs[k]);
+      b->off.push_back(at);
+      for (int r = 0; r < nrhs[k]; ++r) {
+        poff.push_back((size_t)(at + (long long)r * ops[k]->n));
+        plen.push_back(ops[k]->n);
+      }
+      at += (long long)ops[k]->n * nrhs[k];
+      b->all_stored = b->all_stored && ops[k]->layout == CFIE_STORED;
+    }
+    b->L = (size_t)at;
+    b->prec = ops[0]->prec;
+    pset_build(b->ps, poff, plen, ctx->stream);
+    if (b->all_stored) gemm_plan_build(b->plan, ctx, b->ops, b->nrhs, b->off);
+  });
+  if (st != CFIE_OK) {
+    if (b) cfie_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return CFIE_OK;
+}
+
+long long cfie_batch_length(const cfie_batch* b) { return b ? (long long)b->L : 0; }
+
+cfie_status cfie_batch_apply(cfie_batch* b, const void* x_dev, void* y_dev) {
+  if (!b) return CFIE_EINVAL;
+  return guarded(b->ctx, [&] {
+    check_vec(x_dev, "x");
+    check_vec(y_dev, "y");
+    CFIE_REQUIRE(x_dev != y_dev, "x and y must not overlap");
+    set_device(b->ctx);
+    batch_inner(b, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev));
+    if (b->all_stored && gemm_plan_take_error(b->plan, b->ctx))
+      throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
+  });
+}
+
+cfie_status cfie_batch_gmres_solve(cfie_batch* b, const void* f_dev, void* x_dev, double rtol,
+                                   int restart, int maxit, int* iters_out, double* relres_out) {
+  if (!b) return CFIE_EINVAL;
+  cfie_status result = CFIE_OK;
+  cfie_status st = guarded(b->ctx, [&] {
+    CFIE_REQUIRE(std::isfinite(rtol) && rtol > 0 && rtol < 1, "rtol must be in (0, 1)");
+    CFIE_REQUIRE(restart >= 0 && restart <= 512, "restart must be in [0, 512]");
+    CFIE_REQUIRE(maxit >= 1, "maxit must be positive");
+    CFIE_REQUIRE(restart > 0 || maxit <= 512, "unrestarted GMRES allows at most 512 steps");
+    check_vec(f_dev, "f");
+    check_vec(x_dev, "x");
+    CFIE_REQUIRE(f_dev != x_dev, "f and x must not overlap");
+    set_device(b->ctx);
+    solve_fns fns;
+    fns.inner = [b](const double2* a, double2* c) { batch_inner(b, a, c); };
+    fns.fp64 = [b](const double2* a, double2* c) { batch_fp64(b, a, c); };
+    gmres_set(b->ctx->stream, b->ctx, b->K, b->ps, fns, b->prec != CFIE_FP64,
+              static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), rtol, restart,
+              maxit, iters_out, relres_out, &result, b->stats);
+    if (b->all_stored && gemm_plan_take_error(b->plan, b->ctx))
+      throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
+    if (result == CFIE_ENOCONV) b->ctx->err = "GMRES reached maxit before rtol";
+  });
+  if (st != CFIE_OK) return st;
+  return result;
+}
+
+cfie_status cfie_batch_last_stats(const cfie_batch* b, cfie_solve_stats* out) {
+  if (!b || !out) return CFIE_EINVAL;
+  *out = b->stats;
+  return CFIE_OK;
+}
+
+void cfie_batch_destroy(cfie_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->ctx->device);
+  cudaStreamSynchronize(b->ctx->stream);
+  krylov_release(b->K);
+  gemm_plan_release(b->plan);
+  delete b;
+}
 
 }  // extern "C"

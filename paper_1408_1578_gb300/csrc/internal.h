@@ -95,6 +95,35 @@ struct cfie_geom {
   std::vector<double> z, dz, ddz;         // caller samples (2n each)
 };
 
+// A set of independent GMRES problems laid out as segments of one vector.
+struct pset_dev {
+  const size_t* off;   // [P] segment offsets
+  const int* len;      // [P] segment lengths
+  const int* nch;      // [P] 2048-element chunks per segment
+  const int* chb;      // [P] first chunk slot of the segment
+  const int2* items;   // [Q] (problem, chunk) work list
+};
+struct pset {
+  int P = 0, Q = 0;
+  size_t L = 0;
+  pset_dev dev{};
+  dbuf buf;
+};
+
+// Krylov workspace (basis, Hessenberg, Givens data, residual vectors)
+struct krylov_ws {
+  dbuf V, H, w, r, d, rin, small;
+  double* host = nullptr;   // pinned mirror of per-problem norms
+  int host_cap = 0;
+};
+
+#include <functional>
+// matvecs of one solve: y = A x on the whole super vector
+struct solve_fns {
+  std::function<void(const double2*, double2*)> inner;   // the fast (FP32 / tensor) matvec
+  std::function<void(const double2*, double2*)> fp64;    // the FP64 matvec (true residuals)
+};
+
 // Device-side geometry of an operator (structure of arrays, FP64 masters).
 struct geom_dev {
   double* x;      // z1
@@ -103,6 +132,13 @@ struct geom_dev {
   double* ny;     // nu~_2 = -z1'
   double* sp;     // |z'|
   double* kap;    // L2(t,t) = (z2' z1'' - z1' z2'') / (4 pi |z'|^2)
+};
+
+// Plan of the stored-matrix contraction over a list of jobs (stored.cu).
+struct gemm_plan {
+  int grid = 0, njobs = 0, mt_total = 0, nsegs = 0, max_pitch = 0, launches_per_run = 0;
+  dbuf jobs, tables, partial, bt, io, err;
+  cudaGraphExec_t exec = nullptr;
 };
 
 struct cfie_op {
@@ -130,14 +166,32 @@ struct cfie_op {
   int band_b = -1;
   dbuf xin32, xin32b; // FP32 staging of the input (and hard-path helpers)
 
-  // stored path (CFIE_STORED): bf16 hi/lo planes of A, B operand planes, error flag
-  dbuf stored, bt, err_flag;
+  // stored path (CFIE_STORED): bf16 hi/lo planes of A and the contraction plan
+  dbuf stored;
+  gemm_plan plan;
+  int plan_nrhs = -1;
 
-  // GMRES workspace
-  dbuf V, H, wv, rv, dv, rin, small;
-  double* host_res = nullptr;  // pinned host mirror of residual estimates
-  int host_res_cap = 0;
+  // GMRES workspace and problem set (one problem per right-hand side)
+  krylov_ws K;
+  pset ps;
+  int ps_nrhs = -1;
 
+  cfie_solve_stats stats{};
+};
+
+// A batch of operators solved in lockstep (one problem per right-hand side of
+// every operator; vectors are the operators' blocks concatenated).
+struct cfie_batch {
+  cfie_ctx* ctx = nullptr;
+  std::vector<cfie_op*> ops;
+  std::vector<int> nrhs;
+  std::vector<long long> off;
+  size_t L = 0;
+  bool all_stored = false;
+  cfie_precision prec = CFIE_FP64;
+  gemm_plan plan;
+  krylov_ws K;
+  pset ps;
   cfie_solve_stats stats{};
 };
 
@@ -173,11 +227,22 @@ size_t static_scratch_capacity();
 void fp32_prepare(cfie_op* op);
 void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs);
 // stored.cu
+void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& ops,
+                     const std::vector<int>& nrhs, const std::vector<long long>& xoff);
+void gemm_plan_run(gemm_plan& G, cfie_ctx* ctx, const double2* x, double2* y);
+int gemm_plan_take_error(gemm_plan& G, cfie_ctx* ctx);
+void gemm_plan_release(gemm_plan& G);
 void stored_prepare(cfie_op* op);
 void matvec_stored(cfie_op* op, const double2* x, double2* y, int nrhs);
 int stored_take_error(cfie_op* op);
 // arnoldi.cu
-void gmres_solve(cfie_op* op, const double2* f, double2* x, int nrhs, double rtol, int restart,
-                 int maxit, int* iters, double* relres, cfie_status* st);
+void pset_build(pset& ps, const std::vector<size_t>& off, const std::vector<int>& len,
+                cudaStream_t st);
+void pset_uniform(pset& ps, int n, int nrhs, cudaStream_t st);
+void gmres_set(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps,
+               const solve_fns& fns, bool refined, const double2* f, double2* x, double rtol,
+               int restart, int maxit, int* iters, double* relres, cfie_status* status,
+               cfie_solve_stats& stats);
+void krylov_release(krylov_ws& K);
 // dispatch (capi.cu)
 void apply_inner(cfie_op* op, const double2* x, double2* y, int nrhs);

@@ -170,143 +170,6 @@ __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
-template <int NP>
-struct gemm_smem {
-  __nv_bfloat16 A[STAGES][4][BM * BK];   // planes: hi_re, hi_im, lo_re, lo_im
-  __nv_bfloat16 B[STAGES][4][NP * BK];   // planes: B1 hi, B1 lo, B2 hi, B2 lo
-  uint64_t full[STAGES], empty[STAGES], done;
-  uint32_t tmem_base;
-  int abort;
-  int issued[STAGES];                    // last issued phase parity per stage, -1 = none
-};
-
-template <int NP>
-constexpr size_t gemm_smem_bytes() {
-  return sizeof(gemm_smem<NP>) + 1024;   // + alignment slack for the 1024-byte swizzle atoms
-}
-
-// grid (m tiles, splits); NP = 2 * NR output columns (NR right-hand sides)
-template <int NP>
-__global__ void __launch_bounds__(NT, 1)
-k_stored_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              int n, int nr, int ktiles, int tiles_per_split, float2* __restrict__ part,
-              int* __restrict__ err) {
-  constexpr int NR = NP / 2;
-  constexpr uint32_t TMEM_COLS = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);
-  constexpr uint32_t STAGE_BYTES = 4u * BM * BK * 2u + 4u * NP * BK * 2u;
-  extern __shared__ unsigned char raw[];
-  gemm_smem<NP>& S = *reinterpret_cast<gemm_smem<NP>*>(
-      (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM;
-  const int split = blockIdx.y;
-  const int kt0 = split * tiles_per_split;
-  const int kt1 = min(ktiles, kt0 + tiles_per_split);
-  const int nk = kt1 - kt0;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&S.full[s], 1);
-      mbar_init(&S.empty[s], 1);
-      S.issued[s] = -1;
-    }
-    mbar_init(&S.done, 1);
-    S.abort = 0;
-    fence_mbar_init();
-  }
-  if (warp == 0) {
-    tmem_alloc(&S.tmem_base, TMEM_COLS);
-    tmem_relinquish();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = S.tmem_base;
-
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      if (it >= STAGES && !mbar_wait(&S.empty[s], ((it / STAGES) - 1) & 1)) {
-        atomicExch(err, 1);
-        S.abort = 1;
-        break;
-      }
-      if (*(volatile int*)&S.abort) break;
-      mbar_arrive_expect_tx(&S.full[s], STAGE_BYTES);
-      S.issued[s] = (it / STAGES) & 1;
-      const int kc = (kt0 + it) * BK;
-#pragma unroll
-      for (int p = 0; p < 4; ++p) tma_load_2d(S.A[s][p], &tmA, &S.full[s], kc, p * n + m0);
-#pragma unroll
-      for (int p = 0; p < 4; ++p) tma_load_2d(S.B[s][p], &tmB, &S.full[s], kc, p * NP);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    constexpr uint32_t idesc = make_idesc(BM, NP);
-    for (int it = 0; it < nk; ++it) {
-      const int s = it % STAGES;
-      if (!mbar_wait(&S.full[s], (it / STAGES) & 1)) {
-        atomicExch(err, 2);
-        S.abort = 1;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t a0 = smem_u32(S.A[s][0]), a1 = smem_u32(S.A[s][1]);
-      const uint32_t a2 = smem_u32(S.A[s][2]), a3 = smem_u32(S.A[s][3]);
-      const uint32_t b0 = smem_u32(S.B[s][0]), b1 = smem_u32(S.B[s][1]);
-      const uint32_t b2 = smem_u32(S.B[s][2]), b3 = smem_u32(S.B[s][3]);
-#pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint32_t off = kk * 32;   // 16 bf16 = 32 bytes along K inside the swizzle row
-        const uint32_t acc0 = (it > 0 || kk > 0) ? 1u : 0u;
-        umma_bf16(tmem, smem_desc(a0 + off), smem_desc(b0 + off), idesc, acc0);  // hr * B1 hi
-        umma_bf16(tmem, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1u);    // hr * B1 lo
-        umma_bf16(tmem, smem_desc(a2 + off), smem_desc(b0 + off), idesc, 1u);    // lr * B1 hi
-        umma_bf16(tmem, smem_desc(a1 + off), smem_desc(b2 + off), idesc, 1u);    // hi * B2 hi
-        umma_bf16(tmem, smem_desc(a1 + off), smem_desc(b3 + off), idesc, 1u);    // hi * B2 lo
-        umma_bf16(tmem, smem_desc(a3 + off), smem_desc(b2 + off), idesc, 1u);    // li * B2 hi
-      }
-      umma_commit(&S.empty[s]);
-    }
-    umma_commit(&S.done);   // arrives once every MMA issued above has completed
-  }
-
-  // ---- epilogue: warp w owns TMEM lanes (rows) 32 w .. 32 w + 31
-  __syncwarp();
-  const bool ok = mbar_wait(&S.done, 0);
-  if (!ok && lane == 0) {
-    atomicExch(err, 3);
-    S.abort = 1;
-  }
-  __syncwarp();
-  tc_fence_after();
-  float v[NP];
-#pragma unroll
-  for (int c0 = 0; c0 < NP; c0 += 16)
-    tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v + c0);
-  const int i = m0 + 32 * warp + lane;
-  if (ok && i < n && nk > 0) {
-#pragma unroll
-    for (int r = 0; r < NR; ++r)
-      if (r < nr) part[((size_t)split * nr + r) * n + i] = make_float2(v[r], v[NR + r]);
-  }
-  tc_fence_before();
-  __syncthreads();
-  // drain copies still in flight after an abort (bounded), then free TMEM
-  if (threadIdx.x == 0 && *(volatile int*)&S.abort) {
-    for (int s = 0; s < STAGES; ++s)
-      if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
-  }
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
-  }
-}
-
 // ---------------------------------------------------------------------------
 // assembly and operand preparation
 // ---------------------------------------------------------------------------
@@ -346,49 +209,242 @@ k_assemble(int n, int pitch, int b, omega32 W, geo32 g, const float* __restrict_
   planes[3 * plane + e] = li;
 }
 
-// B operand planes [4][NP][pitch] for right-hand sides r0 .. r0 + nr - 1:
-// B1 = [Xr | Xi], B2 = [-Xi | Xr] (rows = output columns), hi / lo split.
-__global__ void k_prep_b(int n, int pitch, int NP, int nr, const double2* __restrict__ x,
-                         __nv_bfloat16* __restrict__ bt) {
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One GEMM job: 32 right-hand sides of one stored operator.  64-byte aligned
+// (it holds the two tensor maps the TMA unit reads).
+struct alignas(64) gemm_job {
+  CUtensorMap ta;          // A planes [4 n rows][pitch] bf16, box 128 x 64
+  CUtensorMap tb;          // B planes [4 NP rows][pitch] bf16, box NP x 64
+  __nv_bfloat16* bt;       // B planes of this job
+  long long xoff;          // first element of the job's right-hand sides in x / y
+  int n, pitch, nr, mt0;   // size, row pitch, right-hand sides (<= 32), first global m tile
+};
+
+struct gemm_io {
+  const double2* x;
+  double2* y;
+};
+
+template <int NP>
+struct pgemm_smem {
+  __nv_bfloat16 A[STAGES][4][BM * BK];   // planes: hi_re, hi_im, lo_re, lo_im
+  __nv_bfloat16 B[STAGES][4][NP * BK];   // planes: B1 hi, B1 lo, B2 hi, B2 lo
+  uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
+  uint32_t tmem_base;
+  int abort;
+  int issued[STAGES];                    // last issued phase parity per stage, -1 = none
+};
+
+template <int NP>
+constexpr size_t pgemm_smem_bytes() {
+  return sizeof(pgemm_smem<NP>) + 1024;  // + slack to align the 1024-byte swizzle atoms
+}
+
+// Persistent stream-K contraction over every job of a plan.  The (m tile,
+// k tile) pairs of all jobs form one list; CTA c owns a contiguous range of it,
+// cut into segments (one job, one m tile, a run of k tiles).  Warp 0 issues the
+// TMA loads, warp 1 the MMAs (double-buffered accumulators, 2 x NP TMEM
+// columns), warps 2-5 drain finished accumulators to the partial-sum slot of
+// their segment while the next segment accumulates.
+template <int NP>
+__global__ void __launch_bounds__(192, 1)
+k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ segs,
+                  const int* __restrict__ cbeg, float2* __restrict__ partial,
+                  int* __restrict__ err) {
+  constexpr int NR = NP / 2;
+  constexpr uint32_t TMEM_COLS = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));
+  constexpr uint32_t STAGE_BYTES = 4u * BM * BK * 2u + 4u * NP * BK * 2u;
+  extern __shared__ unsigned char raw[];
+  pgemm_smem<NP>& S = *reinterpret_cast<pgemm_smem<NP>*>(
+      (reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sb = cbeg[blockIdx.x], se = cbeg[blockIdx.x + 1];
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&S.full[s], 1);
+      mbar_init(&S.empty[s], 1);
+      S.issued[s] = -1;
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.tfull[b], 1);
+      mbar_init(&S.tempty[b], 4);   // one arrival per epilogue warp
+    }
+    S.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&S.tmem_base, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer
+      int it = 0;
+      for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
+        const int4 sg = segs[s];
+        const gemm_job* J = jobs + sg.x;
+        const int m0 = sg.y * BM;
+        for (int k = sg.z; k < sg.w; ++k, ++it) {
+          const int st = it % STAGES;
+          if (it >= STAGES && !mbar_wait(&S.empty[st], ((it / STAGES) - 1) & 1)) {
+            atomicExch(err, 1);
+            S.abort = 1;
+            break;
+          }
+          mbar_arrive_expect_tx(&S.full[st], STAGE_BYTES);
+          S.issued[st] = (it / STAGES) & 1;
+          const int kc = k * BK;
+#pragma unroll
+          for (int p = 0; p < 4; ++p) tma_load_2d(S.A[st][p], &J->ta, &S.full[st], kc, p * J->n + m0);
+#pragma unroll
+          for (int p = 0; p < 4; ++p) tma_load_2d(S.B[st][p], &J->tb, &S.full[st], kc, p * NP);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer
+      constexpr uint32_t idesc = make_idesc(BM, NP);
+      int it = 0;
+      for (int s = sb, sl = 0; s < se; ++s, ++sl) {
+        const int4 sg = segs[s];
+        const int tb = sl & 1, use = sl >> 1;
+        if (use >= 1 && !mbar_wait(&S.tempty[tb], (use - 1) & 1)) {
+          atomicExch(err, 4);
+          S.abort = 1;
+        }
+        if (*(volatile int*)&S.abort) break;
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(tb * NP);
+        for (int k = sg.z; k < sg.w; ++k, ++it) {
+          const int st = it % STAGES;
+          if (!mbar_wait(&S.full[st], (it / STAGES) & 1)) {
+            atomicExch(err, 2);
+            S.abort = 1;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(S.A[st][0]), a1 = smem_u32(S.A[st][1]);
+          const uint32_t a2 = smem_u32(S.A[st][2]), a3 = smem_u32(S.A[st][3]);
+          const uint32_t b0 = smem_u32(S.B[st][0]), b1 = smem_u32(S.B[st][1]);
+          const uint32_t b2 = smem_u32(S.B[st][2]), b3 = smem_u32(S.B[st][3]);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t off = kk * 32;  // 16 bf16 along K inside the 128-byte swizzle row
+            const uint32_t acc0 = (k > sg.z || kk > 0) ? 1u : 0u;
+            umma_bf16(d, smem_desc(a0 + off), smem_desc(b0 + off), idesc, acc0);  // hr * B1 hi
+            umma_bf16(d, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1u);    // hr * B1 lo
+            umma_bf16(d, smem_desc(a2 + off), smem_desc(b0 + off), idesc, 1u);    // lr * B1 hi
+            umma_bf16(d, smem_desc(a1 + off), smem_desc(b2 + off), idesc, 1u);    // hi * B2 hi
+            umma_bf16(d, smem_desc(a1 + off), smem_desc(b3 + off), idesc, 1u);    // hi * B2 lo
+            umma_bf16(d, smem_desc(a3 + off), smem_desc(b2 + off), idesc, 1u);    // li * B2 hi
+          }
+          umma_commit(&S.empty[st]);
+        }
+        umma_commit(&S.tfull[tb]);  // arrives when this segment's MMAs have completed
+        if (*(volatile int*)&S.abort) break;
+      }
+    }
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    for (int s = sb, sl = 0; s < se; ++s, ++sl) {
+      const int tb = sl & 1, use = sl >> 1;
+      if (*(volatile int*)&S.abort) break;
+      const bool ok = mbar_wait(&S.tfull[tb], use & 1);
+      if (!ok) {
+        if (lane == 0) {
+          atomicExch(err, 3);
+          S.abort = 1;
+        }
+        break;
+      }
+      __syncwarp();
+      tc_fence_after();
+      float v[NP];
+#pragma unroll
+      for (int c0 = 0; c0 < NP; c0 += 16)
+        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(tb * NP + c0), v + c0);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.tempty[tb]);
+      float2* dst = partial + (size_t)s * BM * NR + row;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) dst[(size_t)r * BM] = make_float2(v[r], v[NR + r]);
+    }
+  }
+  __syncthreads();
+  // after an abort, wait (bounded) for copies still in flight, then free TMEM
+  if (threadIdx.x == 0 && *(volatile int*)&S.abort) {
+    for (int s = 0; s < STAGES; ++s)
+      if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// B operand planes of every job: B1 = [Xr | Xi], B2 = [-Xi | Xr] (rows = output
+// columns), hi / lo bf16 split; grid (ceil(max pitch / 256), NP, jobs)
+__global__ void k_prep_b_jobs(const gemm_job* __restrict__ jobs, const gemm_io* __restrict__ io,
+                              int NP) {
+  const gemm_job& J = jobs[blockIdx.z];
   const int c = blockIdx.y;
   const int j = blockIdx.x * 256 + threadIdx.x;
-  if (j >= pitch) return;
+  if (j >= J.pitch) return;
   const int NR = NP / 2;
   const int r = c < NR ? c : c - NR;
   double w1 = 0.0, w2 = 0.0;
-  if (j < n && r < nr) {
-    const double2 xv = x[(size_t)r * n + j];
+  if (j < J.n && r < J.nr) {
+    const double2 xv = io->x[J.xoff + (long long)r * J.n + j];
     w1 = c < NR ? xv.x : xv.y;
     w2 = c < NR ? -xv.y : xv.x;
   }
   const __nv_bfloat16 h1 = __float2bfloat16_rn((float)w1), h2 = __float2bfloat16_rn((float)w2);
   const __nv_bfloat16 l1 = __float2bfloat16_rn((float)(w1 - (double)__bfloat162float(h1)));
   const __nv_bfloat16 l2 = __float2bfloat16_rn((float)(w2 - (double)__bfloat162float(h2)));
-  const size_t plane = (size_t)NP * pitch;
-  const size_t e = (size_t)c * pitch + j;
-  bt[e] = h1;
-  bt[plane + e] = l1;
-  bt[2 * plane + e] = h2;
-  bt[3 * plane + e] = l2;
+  const size_t plane = (size_t)NP * J.pitch;
+  const size_t e = (size_t)c * J.pitch + j;
+  J.bt[e] = h1;
+  J.bt[plane + e] = l1;
+  J.bt[2 * plane + e] = h2;
+  J.bt[3 * plane + e] = l2;
 }
 
-// y[r0 + r][i] = sum over splits (fixed order, FP64)
-__global__ void k_reduce_stored(int n, int nr, int splits, const float2* __restrict__ part,
-                                double2* __restrict__ y) {
-  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t tot = (size_t)n * nr;
-  if (e >= tot) return;
+// y = sum of the segment partials of each (job, m tile), fixed order, FP64;
+// grid (global m tiles, NR), 128 threads (rows)
+__global__ void k_reduce_jobs(const gemm_job* __restrict__ jobs, const int2* __restrict__ mt_job,
+                              const int2* __restrict__ mt_seg, const float2* __restrict__ partial,
+                              const gemm_io* __restrict__ io, int NR) {
+  const int g = blockIdx.x, r = blockIdx.y, row = threadIdx.x;
+  const int2 jm = mt_job[g];
+  const gemm_job& J = jobs[jm.x];
+  const int i = jm.y * BM + row;
+  if (i >= J.n || r >= J.nr) return;
+  const int2 sr = mt_seg[g];
   double sx = 0.0, sy = 0.0;
-  for (int s = 0; s < splits; ++s) {
-    const float2 p = part[(size_t)s * tot + e];
+  for (int s = sr.x; s < sr.x + sr.y; ++s) {
+    const float2 p = partial[((size_t)s * NR + r) * BM + row];
     sx += p.x;
     sy += p.y;
   }
-  y[e] = make_double2(sx, sy);
+  io->y[J.xoff + (long long)r * J.n + i] = make_double2(sx, sy);
 }
 
 // ---------------------------------------------------------------------------
-// host: tensor maps
+// host: tensor maps, plans, graphs
 // ---------------------------------------------------------------------------
 using encode_fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -430,23 +486,173 @@ CUtensorMap make_map(void* base, uint64_t rows, uint64_t cols, uint64_t pitch, u
 
 unsigned nblk(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
 
-template <int NP>
-void run_gemm(cfie_op* op, const CUtensorMap& ta, const CUtensorMap& tb, int nr, float2* part,
-              int splits, int tps, int* err) {
-  const size_t smem = gemm_smem_bytes<NP>();
-  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_stored_gemm<NP>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int n = op->n;
-  const dim3 grid((n + BM - 1) / BM, splits);
-  prof_scope ps(op->ctx, CFIE_K_MATVEC_TENSOR);
-  k_stored_gemm<NP><<<grid, NT, smem, op->ctx->stream>>>(ta, tb, n, nr, (n + BK - 1) / BK, tps,
-                                                         part, err);
-  CFIE_CHECK_LAUNCH();
-}
+constexpr int kNP = 64;            // 32 right-hand sides per job
+constexpr int kNR = kNP / 2;
 
 }  // namespace
 
 int stored_pitch(int n) { return (n + 63) / 64 * 64; }
+
+// Build the job list, the stream-K segment table and the CUDA graph
+// (B preparation, persistent contraction, reduction) for the given operators
+// and right-hand-side counts; x / y are read from the plan's io slot.
+void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& ops,
+                     const std::vector<int>& nrhs, const std::vector<long long>& xoff) {
+  cudaStream_t st = ctx->stream;
+  std::vector<gemm_job> jobs;
+  std::vector<size_t> bt_off;
+  size_t bt_total = 0;
+  int mt_total = 0;
+  for (size_t o = 0; o < ops.size(); ++o) {
+    cfie_op* op = ops[o];
+    if (op->layout != CFIE_STORED) throw cfie_error(CFIE_EINVAL, "operator is not stored");
+    const int n = op->n, pitch = stored_pitch(n);
+    for (int r0 = 0; r0 < nrhs[o]; r0 += kNR) {
+      gemm_job J;
+      std::memset(&J, 0, sizeof(J));
+      J.n = n;
+      J.pitch = pitch;
+      J.nr = std::min(kNR, nrhs[o] - r0);
+      J.xoff = xoff[o] + (long long)r0 * n;
+      J.mt0 = mt_total;
+      mt_total += (n + BM - 1) / BM;
+      bt_off.push_back(bt_total);
+      bt_total += (size_t)4 * kNP * pitch;
+      jobs.push_back(J);
+    }
+  }
+  G.bt.reserve(sizeof(__nv_bfloat16) * bt_total);
+  for (size_t k = 0, o = 0; o < ops.size(); ++o) {
+    cfie_op* op = ops[o];
+    for (int r0 = 0; r0 < nrhs[o]; r0 += kNR, ++k) {
+      gemm_job& J = jobs[k];
+      J.bt = G.bt.as<__nv_bfloat16>() + bt_off[k];
+      J.ta = make_map(op->stored.p, 4 * (uint64_t)J.n, (uint64_t)J.pitch, J.pitch, BM);
+      J.tb = make_map(J.bt, 4 * (uint64_t)kNP, (uint64_t)J.pitch, J.pitch, kNP);
+    }
+  }
+  // stream-K split of the (m tile, k tile) pairs over one CTA per SM
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+  long long W = 0;
+  std::vector<long long> job_base(jobs.size() + 1, 0);
+  for (size_t k = 0; k < jobs.size(); ++k) {
+    const long long mt = (jobs[k].n + BM - 1) / BM, kt = (jobs[k].n + BK - 1) / BK;
+    job_base[k + 1] = job_base[k] + mt * kt;
+  }
+  W = job_base.back();
+  const int grid = (int)std::min<long long>(sms, std::max<long long>(1, W));
+  std::vector<int4> segs;
+  std::vector<int> cbeg(grid + 1, 0);
+  std::vector<int2> mt_job(mt_total), mt_seg(mt_total, make_int2(0, 0));
+  size_t jk = 0;
+  for (int c = 0; c < grid; ++c) {
+    const long long b = W * c / grid, e = W * (c + 1) / grid;
+    cbeg[c] = (int)segs.size();
+    long long t = b;
+    while (t < e) {
+      while (job_base[jk + 1] <= t) ++jk;
+      const gemm_job& J = jobs[jk];
+      const long long kt = (J.n + BK - 1) / BK;
+      const long long local = t - job_base[jk];
+      const int m = (int)(local / kt), k0 = (int)(local % kt);
+      const int k1 = (int)std::min<long long>(kt, k0 + (e - t));
+      const int g = J.mt0 + m;
+      if (mt_seg[g].y == 0) mt_seg[g].x = (int)segs.size();
+      mt_seg[g].y++;
+      segs.push_back(make_int4((int)jk, m, k0, k1));
+      t += k1 - k0;
+    }
+  }
+  cbeg[grid] = (int)segs.size();
+  for (size_t k = 0; k < jobs.size(); ++k) {
+    const int mt = (jobs[k].n + BM - 1) / BM;
+    for (int m = 0; m < mt; ++m) mt_job[jobs[k].mt0 + m] = make_int2((int)k, m);
+  }
+  G.grid = grid;
+  G.njobs = (int)jobs.size();
+  G.mt_total = mt_total;
+  G.nsegs = (int)segs.size();
+  int max_pitch = 0;
+  for (auto& J : jobs) max_pitch = std::max(max_pitch, J.pitch);
+  G.max_pitch = max_pitch;
+  G.jobs.reserve(sizeof(gemm_job) * jobs.size());
+  G.tables.reserve(sizeof(int4) * segs.size() + sizeof(int) * cbeg.size() +
+                   2 * sizeof(int2) * mt_total + 256);
+  G.partial.reserve(sizeof(float2) * (size_t)segs.size() * BM * kNR);
+  G.io.reserve(sizeof(gemm_io));
+  G.err.reserve(sizeof(int));
+  char* tb = G.tables.as<char>();
+  const size_t o_segs = 0;
+  const size_t o_cbeg = (sizeof(int4) * segs.size() + 15) & ~size_t(15);
+  const size_t o_mtj = (o_cbeg + sizeof(int) * cbeg.size() + 15) & ~size_t(15);
+  const size_t o_mts = (o_mtj + sizeof(int2) * mt_total + 15) & ~size_t(15);
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(G.jobs.p, jobs.data(), sizeof(gemm_job) * jobs.size(),
+                                  cudaMemcpyHostToDevice, st));
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(tb + o_segs, segs.data(), sizeof(int4) * segs.size(),
+                                  cudaMemcpyHostToDevice, st));
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(tb + o_cbeg, cbeg.data(), sizeof(int) * cbeg.size(),
+                                  cudaMemcpyHostToDevice, st));
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(tb + o_mtj, mt_job.data(), sizeof(int2) * mt_total,
+                                  cudaMemcpyHostToDevice, st));
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(tb + o_mts, mt_seg.data(), sizeof(int2) * mt_total,
+                                  cudaMemcpyHostToDevice, st));
+  CFIE_CHECK_CUDA(cudaMemsetAsync(G.err.p, 0, sizeof(int), st));
+  CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
+
+  // capture the three launches once; replays read x / y from the io slot
+  const size_t smem = pgemm_smem_bytes<kNP>();
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_gemm_persistent<kNP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaStream_t cs;
+  CFIE_CHECK_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e1 = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e1 == cudaSuccess) {
+    const gemm_job* dj = G.jobs.as<gemm_job>();
+    const gemm_io* io = G.io.as<gemm_io>();
+    k_prep_b_jobs<<<dim3(nblk(max_pitch), kNP, G.njobs), 256, 0, cs>>>(dj, io, kNP);
+    k_gemm_persistent<kNP><<<grid, 192, smem, cs>>>(
+        dj, reinterpret_cast<const int4*>(tb + o_segs), reinterpret_cast<const int*>(tb + o_cbeg),
+        G.partial.as<float2>(), G.err.as<int>());
+    k_reduce_jobs<<<dim3(mt_total, kNR), BM, 0, cs>>>(
+        dj, reinterpret_cast<const int2*>(tb + o_mtj), reinterpret_cast<const int2*>(tb + o_mts),
+        G.partial.as<float2>(), io, kNR);
+    e1 = cudaStreamEndCapture(cs, &graph);
+  }
+  cudaStreamDestroy(cs);
+  CFIE_CHECK_CUDA(e1);
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G.exec = nullptr;
+  cudaError_t e2 = cudaGraphInstantiate(&G.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CFIE_CHECK_CUDA(e2);
+  G.launches_per_run = 3;
+}
+
+void gemm_plan_run(gemm_plan& G, cfie_ctx* ctx, const double2* x, double2* y) {
+  const gemm_io io{x, y};
+  // pageable source: the copy is staged before cudaMemcpyAsync returns
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(G.io.p, &io, sizeof(io), cudaMemcpyHostToDevice, ctx->stream));
+  prof_scope ps(ctx, CFIE_K_MATVEC_TENSOR);
+  CFIE_CHECK_CUDA(cudaGraphLaunch(G.exec, ctx->stream));
+  g_cfie_launches += G.launches_per_run;
+}
+
+int gemm_plan_take_error(gemm_plan& G, cfie_ctx* ctx) {
+  if (!G.err.p) return 0;
+  int e = 0;
+  CFIE_CHECK_CUDA(
+      cudaMemcpyAsync(&e, G.err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CFIE_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (e) CFIE_CHECK_CUDA(cudaMemsetAsync(G.err.p, 0, sizeof(int), ctx->stream));
+  return e;
+}
+
+void gemm_plan_release(gemm_plan& G) {
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G.exec = nullptr;
+}
 
 void stored_prepare(cfie_op* op) {
   if (op->bc != CFIE_SOUND_SOFT)
@@ -467,50 +673,15 @@ void stored_prepare(cfie_op* op) {
                                                 base + 7 * n, op->band.as<float2>(),
                                                 op->stored.as<__nv_bfloat16>());
   CFIE_CHECK_LAUNCH();
-  op->err_flag.reserve(sizeof(int));
-  CFIE_CHECK_CUDA(cudaMemsetAsync(op->err_flag.p, 0, sizeof(int), op->ctx->stream));
   CFIE_CHECK_CUDA(cudaStreamSynchronize(op->ctx->stream));
 }
 
 void matvec_stored(cfie_op* op, const double2* x, double2* y, int nrhs) {
-  const int n = op->n;
-  const int pitch = stored_pitch(n);
-  cudaStream_t st = op->ctx->stream;
-  constexpr int NP = 64;           // 32 right-hand sides per pass
-  constexpr int NR = NP / 2;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->ctx->device);
-  const int mtiles = (n + BM - 1) / BM;
-  const int ktiles = (n + BK - 1) / BK;
-  // source splits: fill the SMs (one CTA per SM), at least 4 K tiles each
-  int splits = std::max(1, std::min((sms + mtiles - 1) / mtiles, std::max(1, ktiles / 4)));
-  const int tps = (ktiles + splits - 1) / splits;
-  splits = (ktiles + tps - 1) / tps;
-  op->bt.reserve(sizeof(__nv_bfloat16) * 4 * (size_t)NP * pitch);
-  op->partial.reserve(sizeof(float2) * (size_t)splits * NR * n);
-  const CUtensorMap ta = make_map(op->stored.p, 4 * (uint64_t)n, (uint64_t)pitch, pitch, BM);
-  const CUtensorMap tb = make_map(op->bt.p, 4 * (uint64_t)NP, (uint64_t)pitch, pitch, NP);
-  int* err = op->err_flag.as<int>();
-  for (int r0 = 0; r0 < nrhs; r0 += NR) {
-    const int nr = std::min(NR, nrhs - r0);
-    k_prep_b<<<dim3(nblk(pitch), NP), 256, 0, st>>>(n, pitch, NP, nr, x + (size_t)r0 * n,
-                                                    op->bt.as<__nv_bfloat16>());
-    CFIE_CHECK_LAUNCH();
-    run_gemm<NP>(op, ta, tb, nr, op->partial.as<float2>(), splits, tps, err);
-    k_reduce_stored<<<nblk((size_t)n * nr), 256, 0, st>>>(n, nr, splits, op->partial.as<float2>(),
-                                                          y + (size_t)r0 * n);
-    CFIE_CHECK_LAUNCH();
+  if (op->plan_nrhs != nrhs) {
+    gemm_plan_build(op->plan, op->ctx, {op}, {nrhs}, {0});
+    op->plan_nrhs = nrhs;
   }
+  gemm_plan_run(op->plan, op->ctx, x, y);
 }
 
-// error code left by the bounded waits of the tensor-core kernel (0 = none);
-// resets it.  Synchronises the stream.
-int stored_take_error(cfie_op* op) {
-  if (!op->err_flag.p) return 0;
-  int e = 0;
-  CFIE_CHECK_CUDA(cudaMemcpyAsync(&e, op->err_flag.p, sizeof(int), cudaMemcpyDeviceToHost,
-                                  op->ctx->stream));
-  CFIE_CHECK_CUDA(cudaStreamSynchronize(op->ctx->stream));
-  if (e) CFIE_CHECK_CUDA(cudaMemsetAsync(op->err_flag.p, 0, sizeof(int), op->ctx->stream));
-  return e;
-}
+int stored_take_error(cfie_op* op) { return gemm_plan_take_error(op->plan, op->ctx); }

@@ -40,8 +40,10 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="star", choices=["kite", "star", "disk"])
-    p.add_argument("--precision", default=None, choices=["fp32", "fp64", None])
+    p.add_argument("--workload", default="kite", choices=["kite", "star", "disk", "stars", "serve"])
+    p.add_argument("--precision", default=None, choices=["fp32", "fp64", "tensor", None])
+    p.add_argument("--count", type=int, default=None,
+                   help="stars: operators in the batch (256); serve: requests (32)")
     p.add_argument("--rtol", type=float, default=None)
     p.add_argument("--n", type=int, default=None, help="override the workload's n (profiling)")
     p.add_argument("--nrhs", type=int, default=None, help="override the number of directions")
@@ -65,6 +67,7 @@ def workload(name, precision, n=None, nrhs=None):
     if precision is None:
         precision = "fp32" if name == "kite" else "fp64"
     spec["precision"] = precision
+    spec["layout"] = "stored" if precision == "tensor" else "matrix_free"
     # residual target: 1e-8 on ||f - A x|| / ||f|| keeps the error against the
     # FP64 solution below 1e-6 for the condition numbers of these operators
     spec["rtol"] = 1e-8
@@ -179,7 +182,7 @@ def run_ours(args, rank, world):
 
     def step():
         geom = ctx.geometry(spec["curve"], **spec["params"])
-        op = geom.discretise(n, w, bc=bc, precision=spec["precision"])
+        op = geom.discretise(n, w, bc=bc, precision=spec["precision"], layout=spec["layout"])
         op.rhs_plane_waves(theta, f)
         x.zero_()
         its, rel, st = op.gmres_solve(f, x, rtol=spec["rtol"], restart=spec["restart"],
@@ -250,7 +253,7 @@ def run_ours(args, rank, world):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32+f64", "fp64": "f64"}[spec["precision"]],
+            "dtype": {"fp32": "f32+f64", "fp64": "f64", "tensor": "bf16x3+f64"}[spec["precision"]],
             "data": "synthetic",
             "config": {"workload": f"{spec['name']}: {spec['curve']} {bc} n={n} omega={w} "
                                    f"eta=omega nrhs={nrhs}",
@@ -409,6 +412,10 @@ def allreduce_sum(v, world):
 
 def main():
     args = parse()
+    if args.workload in ("stars", "serve") and args.impl == "ours":
+        out = run_stars(args) if args.workload == "stars" else run_serve(args)
+        print(json.dumps(out), flush=True)
+        return
     rank, world = init_dist()
     if args.impl == "reference":
         out = run_reference(args, rank, world)
@@ -425,6 +432,148 @@ def main():
         print(json.dumps(out), flush=True)
     if _PG is not None:
         _PG.destroy_process_group()
+
+
+
+# ---------------------------------------------------------------------------
+# extra workloads: the batched stored path and the request server
+# ---------------------------------------------------------------------------
+def run_stars(args):
+    """256 random stars, stored bf16 hi/lo matrices, 32 directions each, all
+    solved in lockstep (one persistent tensor-core launch per block matvec)."""
+    import numpy as np
+    import torch
+
+    from paper_1408_1578_gb300 import cfie, inputs
+    count = args.count or 256
+    specs = inputs.random_stars(count=count, seed=1408, n_lo=512, n_hi=16384, nrhs=32)
+    stream = torch.cuda.current_stream()
+    ctx = cfie.Context(0, stream=stream)
+    pairs_mv = sum(s["n"] ** 2 for s in specs)
+    L = sum(s["n"] * s["nrhs"] for s in specs)
+    f = torch.empty(L, dtype=torch.complex128, device="cuda")
+    x = torch.zeros_like(f)
+
+    def step():
+        ops = [ctx.fourier_star(s["a"], s["b"]).discretise(s["n"], s["omega"], precision="tensor",
+                                                            layout="stored") for s in specs]
+        b = cfie.Batch(ctx, ops, [s["nrhs"] for s in specs])
+        for k, s in enumerate(specs):
+            ops[k].rhs_plane_waves(inputs.directions(s["nrhs"]), b.block(f, k))
+        x.zero_()
+        its, rel, _ = b.gmres_solve(f, x, rtol=1e-8, restart=80, maxit=4000, allow_noconv=True)
+        stats = b.last_stats()
+        b.close()
+        for op in ops:
+            op.close()
+        return its, rel, stats
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ctx.set_profiling(True)
+    l0 = ctx.lib.cfie_launch_count()
+    ms, pairs, solves, worst = 0.0, 0, 0, 0.0
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its, rel, stats = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        pairs += pairs_mv * (stats["inner_matvecs"] + stats["fp64_matvecs"])
+        solves += int(np.sum(rel <= 1e-8))
+        worst = max(worst, float(np.max(rel)))
+    kt = ctx.kernel_times()
+    launches = ctx.lib.cfie_launch_count() - l0
+    clk = clocks.stop()
+    peaks, src = measured_peaks()
+    tens_ms, tens_n = kt["matvec_tensor"]
+    gemm_bytes = sum(s["n"] * (s["n"] + 63) // 64 * 64 * 8 for s in specs)
+    roof = None
+    if tens_n:
+        gbs = gemm_bytes / (tens_ms / tens_n / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "stored contraction graph (prep + k_gemm_persistent + reduce)",
+                "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                "bytes_per_launch": gemm_bytes}
+    out = {"metric": METRIC, "value": pairs / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16x3+f64", "data": "synthetic",
+           "config": {"workload": f"stars: {count} random stars, n log-uniform [512, 16384], "
+                                  "10 ppw, 32 directions, stored tensor-core, lockstep GMRES",
+                      "sum_n2": pairs_mv, "rtol": 1e-8, "restart": 80},
+           "solves_per_s": solves / (ms / 1e3), "max_relres": worst, "solve_stats": stats,
+           "gpu_launches": int(launches), "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
+           "kernel_launches": {k: v[1] for k, v in kt.items()}, "roofline": roof, "clocks": clk}
+    ctx.close()
+    return out
+
+
+def run_serve(args):
+    """Poisson stream (200 requests/s) of sound-soft / sound-hard solves on random
+    stars, n log-uniform in [1024, 65536], 1..64 directions, served by the
+    library's request server; p50 / p99 latency, solves/s.  A few requests are
+    also run one at a time in the plain FP64 form for comparison."""
+    import numpy as np
+    import torch
+
+    from paper_1408_1578_gb300 import cfie, inputs
+    count = args.count or 32
+    reqs = inputs.poisson_requests(count=count, rate=200.0, seed=1578, n_lo=1024, n_hi=65536)
+    free, total = torch.cuda.mem_get_info()
+    srv = cfie.Server(0, hbm_budget_bytes=int(0.8 * free), slots=8)
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = cfie.load().cfie_launch_count()
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        delay = t0 + r["arrival"] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"],
+                                  rtol=1e-8, restart=80, maxit=4000))
+    ok = srv.wait_all(3600)
+    makespan = time.perf_counter() - t0
+    launches = cfie.load().cfie_launch_count() - l0
+    clk = clocks.stop()
+    res = [srv.poll(t) for t in tickets]
+    lat = np.array([q["latency_s"] for q in res])
+    svc = np.array([q["service_s"] for q in res])
+    good = [q["status"] == cfie.CFIE_OK for q in res]
+    solves = sum(r["nrhs"] for r, g in zip(reqs, good) if g)
+    stats = srv.stats()
+    srv.close()
+    # plain FP64 one-at-a-time form on the smallest requests (same service path)
+    order = np.argsort([r["n"] for r in reqs])[:3]
+    cmp = []
+    one = cfie.Server(0, hbm_budget_bytes=int(0.8 * free), slots=1)
+    for i in order:
+        r = reqs[i]
+        t = one.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"], rtol=1e-8,
+                       restart=80, maxit=4000, precision="fp64")
+        one.wait_all(3600)
+        q = one.poll(t)
+        cmp.append({"n": r["n"], "nrhs": r["nrhs"], "bc": r["bc"], "fp64_service_s": q["service_s"],
+                    "served_service_s": float(svc[i]), "speedup": q["service_s"] / svc[i]})
+    one.close()
+    return {"metric": "CFIE solves/s and p50/p99 latency at 1e-8 residual (served)",
+            "value": solves / makespan, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "data": "synthetic", "dtype": "f32+f64",
+            "config": {"workload": f"serve: {count} Poisson requests at 200/s, soft/hard, random "
+                                   "stars, n log-uniform [1024, 65536], 1..64 directions",
+                       "slots": 8, "budget_bytes": int(0.8 * free)},
+            "all_done": bool(ok), "requests_per_s": count / makespan, "makespan_s": makespan,
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "p50_service_s": float(np.percentile(svc, 50)), "failed": int(len(good) - sum(good)),
+            "server": stats, "fp64_one_at_a_time": cmp, "gpu_launches": int(launches),
+            "clocks": clk}
 
 
 if __name__ == "__main__":

@@ -221,6 +221,64 @@ cfie_status cfie_ctx_set_profiling(cfie_ctx* ctx, int on);
  * ms, launches: host arrays of CFIE_K_COUNT entries.  Synchronises the stream. */
 cfie_status cfie_ctx_kernel_times(cfie_ctx* ctx, double* ms, long long* launches);
 
+/* --- Serving: continuous batching of independent solves ------------------- */
+
+typedef struct cfie_server cfie_server;
+
+/* One solve request: a star obstacle r(t) = 1 + sum_k a_k cos kt + b_k sin kt
+ * (host arrays of K doubles, copied), n nodes, omega, eta, boundary condition,
+ * nrhs plane waves at the host angles theta (copied), residual target rtol,
+ * GMRES restart / maxit, and the precision (CFIE_FP32_REFINED, the served
+ * mixed-precision form, or CFIE_FP64, the plain form). */
+typedef struct {
+  int bc;            /* cfie_bc */
+  int precision;     /* cfie_precision: CFIE_FP32_REFINED or CFIE_FP64 */
+  int K;
+  const double* a;
+  const double* b;
+  int n;
+  double omega, eta;
+  int nrhs;
+  const double* theta;
+  double rtol;
+  int restart, maxit;
+} cfie_request;
+
+typedef struct {
+  int done, started;
+  cfie_status status;   /* of the solve (CFIE_ENOCONV: missed rtol) */
+  int iters_max;        /* Arnoldi steps, max over right-hand sides */
+  double relres_max;    /* true FP64 relative residual, max over right-hand sides */
+  double queued_s, service_s, latency_s;   /* submit -> start, start -> done, submit -> done */
+} cfie_result;
+
+typedef struct {
+  long long completed, solves, queued, running, peak_running;
+  long long budget_bytes, in_use_bytes, peak_in_use_bytes;
+} cfie_server_counters;
+
+/* Start a server on `device` with `slots` concurrent solves (each slot a host
+ * thread with its own context and CUDA stream) and an HBM budget for the
+ * estimated footprints of the admitted requests (Krylov basis, vectors,
+ * operator tables, near band, scratch).  Requests are admitted first-fit from
+ * the queue whenever a slot is free and the footprint fits; one that exceeds
+ * the budget on its own runs when the GPU is otherwise idle. */
+cfie_status cfie_server_create(int device, size_t hbm_budget_bytes, int slots, cfie_server** out);
+/* Queue a request (arguments copied; never blocks).  *ticket identifies it. */
+cfie_status cfie_server_submit(cfie_server* server, const cfie_request* req, long long* ticket);
+/* State of a request; when done and x_host is not NULL, copies the solution
+ * (n * nrhs complex128, column-major) to x_host. */
+cfie_status cfie_server_poll(cfie_server* server, long long ticket, cfie_result* out,
+                             void* x_host);
+/* Wait until the queue is empty and no slot is busy (CFIE_ETIMEOUT otherwise). */
+cfie_status cfie_server_wait_all(cfie_server* server, double timeout_s);
+/* Forget a finished request and free its host solution. */
+cfie_status cfie_server_release(cfie_server* server, long long ticket);
+cfie_status cfie_server_stats(cfie_server* server, cfie_server_counters* out);
+const char* cfie_server_last_error(cfie_server* server);
+/* Stop the slots (running solves finish first) and free everything. */
+void cfie_server_destroy(cfie_server* server);
+
 /* Kernel launches issued by the library in this process so far (all
  * contexts).  Never fails. */
 long long cfie_launch_count(void);

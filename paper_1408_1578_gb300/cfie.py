@@ -32,6 +32,27 @@ PRECISION = {"fp64": CFIE_FP64, "fp32": CFIE_FP32_REFINED, "tensor": CFIE_TENSOR
 LAYOUT = {"matrix_free": CFIE_MATRIX_FREE, "stored": CFIE_STORED}
 
 
+class cfie_request(ctypes.Structure):
+    _fields_ = [("bc", ctypes.c_int), ("precision", ctypes.c_int), ("K", ctypes.c_int),
+                ("a", ctypes.POINTER(ctypes.c_double)), ("b", ctypes.POINTER(ctypes.c_double)),
+                ("n", ctypes.c_int), ("omega", ctypes.c_double), ("eta", ctypes.c_double),
+                ("nrhs", ctypes.c_int), ("theta", ctypes.POINTER(ctypes.c_double)),
+                ("rtol", ctypes.c_double), ("restart", ctypes.c_int), ("maxit", ctypes.c_int)]
+
+
+class cfie_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("started", ctypes.c_int), ("status", ctypes.c_int),
+                ("iters_max", ctypes.c_int), ("relres_max", ctypes.c_double),
+                ("queued_s", ctypes.c_double), ("service_s", ctypes.c_double),
+                ("latency_s", ctypes.c_double)]
+
+
+class cfie_server_counters(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in
+                ("completed", "solves", "queued", "running", "peak_running", "budget_bytes",
+                 "in_use_bytes", "peak_in_use_bytes")]
+
+
 class cfie_solve_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("inner_matvecs", ctypes.c_int), ("fp64_matvecs", ctypes.c_int),
@@ -80,6 +101,14 @@ SIGNATURES = {
     "cfie_batch_gmres_solve": (_I, [_P, _P, _P, _D, _I, _I, _IP, _DP]),
     "cfie_batch_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
     "cfie_batch_destroy": (None, [_P]),
+    "cfie_server_create": (_I, [_I, ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
+    "cfie_server_submit": (_I, [_P, ctypes.POINTER(cfie_request), ctypes.POINTER(ctypes.c_longlong)]),
+    "cfie_server_poll": (_I, [_P, ctypes.c_longlong, ctypes.POINTER(cfie_result), _P]),
+    "cfie_server_wait_all": (_I, [_P, _D]),
+    "cfie_server_release": (_I, [_P, ctypes.c_longlong]),
+    "cfie_server_stats": (_I, [_P, ctypes.POINTER(cfie_server_counters)]),
+    "cfie_server_last_error": (ctypes.c_char_p, [_P]),
+    "cfie_server_destroy": (None, [_P]),
 }
 
 _lib = None
@@ -264,6 +293,73 @@ class Batch:
     def close(self):
         if self.h:
             self.ctx.lib.cfie_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Request server (cfie_server_*): continuous batching of independent solves."""
+
+    def __init__(self, device=0, hbm_budget_bytes=64 << 30, slots=4):
+        lib = load()
+        h = _P()
+        st = lib.cfie_server_create(device, int(hbm_budget_bytes), int(slots), ctypes.byref(h))
+        if st != CFIE_OK:
+            raise CfieError(st, "cfie_server_create failed")
+        self.lib = lib
+        self.h = h
+        self.shapes = {}
+
+    def submit(self, a, b, n, omega, nrhs=1, theta=None, bc="soft", precision="fp32", eta=None,
+               rtol=1e-8, restart=80, maxit=4000):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        theta = np.ascontiguousarray(
+            2 * np.pi * np.arange(nrhs) / nrhs if theta is None else theta, dtype=np.float64)
+        req = cfie_request(BC[bc], PRECISION[precision], int(a.size), _dptr(a), _dptr(b), int(n),
+                           float(omega), float(omega if eta is None else eta), int(theta.size),
+                           _dptr(theta), float(rtol), int(restart), int(maxit))
+        t = ctypes.c_longlong()
+        st = self.lib.cfie_server_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        if st != CFIE_OK:
+            raise CfieError(st, self.lib.cfie_server_last_error(self.h).decode())
+        self.shapes[t.value] = (int(theta.size), int(n))
+        return t.value
+
+    def poll(self, ticket, want_x=False):
+        r = cfie_result()
+        x = None
+        ptr = None
+        if want_x:
+            x = np.zeros(self.shapes[ticket], dtype=np.complex128)
+            ptr = x.ctypes.data
+        st = self.lib.cfie_server_poll(self.h, ticket, ctypes.byref(r), ptr)
+        if st != CFIE_OK:
+            raise CfieError(st, self.lib.cfie_server_last_error(self.h).decode())
+        out = {k: getattr(r, k) for k, _ in r._fields_}
+        if want_x and r.done:
+            out["x"] = x
+        return out
+
+    def wait_all(self, timeout_s=600.0):
+        return self.lib.cfie_server_wait_all(self.h, float(timeout_s)) == CFIE_OK
+
+    def release(self, ticket):
+        self.lib.cfie_server_release(self.h, ticket)
+
+    def stats(self):
+        c = cfie_server_counters()
+        self.lib.cfie_server_stats(self.h, ctypes.byref(c))
+        return {k: getattr(c, k) for k, _ in c._fields_}
+
+    def close(self):
+        if self.h:
+            self.lib.cfie_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

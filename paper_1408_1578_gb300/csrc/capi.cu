@@ -7,7 +7,7 @@
 
 #include "internal.h"
 
-long long g_cfie_launches = 0;
+std::atomic<long long> g_cfie_launches{0};
 
 namespace {
 
@@ -383,7 +383,7 @@ cfie_status cfie_ctx_kernel_times(cfie_ctx* ctx, double* ms, long long* launches
   });
 }
 
-long long cfie_launch_count(void) { return g_cfie_launches; }
+long long cfie_launch_count(void) { return g_cfie_launches.load(); }
 
 // ---------------------------------------------------------------------------
 // batches

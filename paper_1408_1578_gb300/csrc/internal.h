@@ -30,7 +30,8 @@ struct cfie_error : public std::exception {
                        std::string(#call) + ": " + cudaGetErrorString(e_));            \
   } while (0)
 
-extern long long g_cfie_launches;  // kernel launches issued by the library
+#include <atomic>
+extern std::atomic<long long> g_cfie_launches;  // kernel launches issued by the library
 #define CFIE_CHECK_LAUNCH()                 \
   do {                                      \
     ++g_cfie_launches;                      \

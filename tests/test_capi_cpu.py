@@ -59,3 +59,13 @@ def test_no_device_is_an_error_not_a_crash(lib):
     from paper_1408_1578_gb300 import cfie
     h = ctypes.c_void_p()
     assert lib.cfie_ctx_create(0, None, ctypes.byref(h)) == cfie.CFIE_ECUDA
+
+
+def test_server_needs_a_device(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1408_1578_gb300 import cfie
+    h = ctypes.c_void_p()
+    assert lib.cfie_server_create(0, 1 << 30, 2, ctypes.byref(h)) == cfie.CFIE_ECUDA
+    assert lib.cfie_server_submit(None, None, None) == cfie.CFIE_EINVAL

@@ -1,0 +1,83 @@
+"""GPU tests of the request server: results of concurrently served requests
+equal the same solves run alone (and the oracle's LU solutions), admission by
+HBM footprint limits how many run at once, bad requests are refused."""
+import time
+
+import numpy as np
+import pytest
+
+from oracle import geometry, operators, solvers
+from paper_1408_1578_gb300 import inputs
+from tests.gpu_util import col_rel, to_dev, to_host, zeros
+
+pytestmark = pytest.mark.gpu
+
+TOL_REFINED = 1e-6
+
+
+def _requests():
+    reqs = inputs.poisson_requests(count=8, rate=200.0, seed=77, n_lo=600, n_hi=2400)
+    for k, r in enumerate(reqs):
+        r["nrhs"] = 1 + (k * 5) % 6
+    return reqs
+
+
+def test_served_results_equal_alone_and_oracle():
+    from paper_1408_1578_gb300 import cfie
+    reqs = _requests()
+    srv = cfie.Server(0, hbm_budget_bytes=48 << 30, slots=4)
+    tickets = []
+    for r in reqs:
+        tickets.append(srv.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"],
+                                  rtol=1e-8, restart=60))
+    assert srv.wait_all(300)
+    stats = srv.stats()
+    assert stats["completed"] == len(reqs)
+    assert stats["peak_running"] >= 2          # work overlapped on the device
+    ctx = cfie.Context(0)
+    for r, t in zip(reqs, tickets):
+        out = srv.poll(t, want_x=True)
+        assert out["done"] and out["status"] == cfie.CFIE_OK
+        assert out["relres_max"] <= 1e-8
+        assert out["latency_s"] >= out["service_s"] > 0
+        # the same solve alone, through the operator API
+        op = ctx.fourier_star(r["a"], r["b"]).discretise(r["n"], r["omega"], bc=r["bc"],
+                                                          precision="fp32")
+        f = zeros(r["nrhs"], r["n"])
+        op.rhs_plane_waves(inputs.directions(r["nrhs"]), f)
+        x = zeros(r["nrhs"], r["n"])
+        op.gmres_solve(f, x, rtol=1e-8, restart=60, maxit=4000)
+        assert np.max(col_rel(out["x"], to_host(x))) < TOL_REFINED
+        # and the oracle's LU solution
+        c = geometry.fourier_star(r["n"], r["a"], r["b"])
+        A = operators.cfie_matrix(c, r["omega"], r["omega"], r["bc"])
+        Q = solvers.lu_solve(A, to_host(f).T).T
+        assert np.max(col_rel(out["x"], Q)) < TOL_REFINED
+        op.close()
+        srv.release(t)
+    ctx.close()
+    srv.close()
+
+
+def test_admission_by_footprint():
+    from paper_1408_1578_gb300 import cfie
+    reqs = _requests()[:4]
+    # a budget below two requests' footprints: one solve at a time
+    srv = cfie.Server(0, hbm_budget_bytes=1, slots=4)
+    for r in reqs:
+        srv.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"], rtol=1e-6)
+    assert srv.wait_all(300)
+    assert srv.stats()["peak_running"] == 1
+    srv.close()
+
+
+def test_bad_requests_are_refused():
+    from paper_1408_1578_gb300 import cfie
+    srv = cfie.Server(0, hbm_budget_bytes=1 << 30, slots=1)
+    with pytest.raises(cfie.CfieError):
+        srv.submit([0.1], [0.0], 1001, 10.0)             # odd n
+    with pytest.raises(cfie.CfieError):
+        srv.submit([0.1], [0.0], 1000, -1.0)             # omega <= 0
+    with pytest.raises(cfie.CfieError):
+        srv.submit([0.1], [0.0], 1000, 10.0, precision="tensor")
+    srv.close()

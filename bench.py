@@ -549,18 +549,21 @@ def run_serve(args):
     solves = sum(r["nrhs"] for r, g in zip(reqs, good) if g)
     stats = srv.stats()
     srv.close()
-    # plain FP64 one-at-a-time form on the smallest requests (same service path)
+    # the same requests one at a time on an otherwise idle GPU, served (mixed
+    # precision) form against the plain FP64 form: the smallest requests
     order = np.argsort([r["n"] for r in reqs])[:3]
     cmp = []
     one = cfie.Server(0, hbm_budget_bytes=int(0.8 * free), slots=1)
     for i in order:
         r = reqs[i]
-        t = one.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"], rtol=1e-8,
-                       restart=80, maxit=4000, precision="fp64")
-        one.wait_all(3600)
-        q = one.poll(t)
-        cmp.append({"n": r["n"], "nrhs": r["nrhs"], "bc": r["bc"], "fp64_service_s": q["service_s"],
-                    "served_service_s": float(svc[i]), "speedup": q["service_s"] / svc[i]})
+        row = {"n": r["n"], "nrhs": r["nrhs"], "bc": r["bc"]}
+        for prec in ("fp32", "fp64"):
+            t = one.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"],
+                           rtol=1e-8, restart=80, maxit=4000, precision=prec)
+            one.wait_all(3600)
+            row[prec + "_alone_s"] = one.poll(t)["service_s"]
+        row["speedup"] = row["fp64_alone_s"] / row["fp32_alone_s"]
+        cmp.append(row)
     one.close()
     return {"metric": "CFIE solves/s and p50/p99 latency at 1e-8 residual (served)",
             "value": solves / makespan, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,

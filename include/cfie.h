@@ -127,6 +127,14 @@ cfie_status cfie_rhs_plane_waves(cfie_op* op, int nrhs, const double* theta, voi
  * overlap.  1 <= nrhs <= 1024. */
 cfie_status cfie_apply(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
 
+/* Choose how a CFIE_FP32_REFINED operator sums over sources: 0 = autotune
+ * (default: the first block matvec for a given (boundary condition, n, nrhs)
+ * times both variants once on the context stream and the process keeps the
+ * faster), 1 = register-blocked FP32 sums on the CUDA cores (any operator),
+ * 2 = tensor cores (entries split bf16 hi + lo, tcgen05 contraction; sound-soft
+ * operators).  Both evaluate the same FP32 entries. */
+cfie_status cfie_op_set_variant(cfie_op* op, int variant);
+
 /* y = A x in FP64 whatever the operator's precision (the matvec used for true
  * residuals). */
 cfie_status cfie_apply_fp64(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);

@@ -3,7 +3,10 @@
 // conventions are in include/cfie.h.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "internal.h"
 
@@ -94,13 +97,55 @@ void prof_harvest(cfie_ctx* c, bool wait) {
   c->inflight.swap(keep);
 }
 
+namespace {
+
+// Process-wide choice between the two FP32 matvec variants, keyed by
+// (boundary condition, n, nrhs): each is timed once with CUDA events on the
+// operator's stream and the faster one is kept.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tuned;
+
+int tuned_variant(cfie_op* op, const double2* x, double2* y, int nrhs) {
+  if (op->variant) return op->variant;
+  if (op->bc != CFIE_SOUND_SOFT || nrhs < 8) return 1;
+  const auto key = std::make_tuple((int)op->bc, op->n, nrhs);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  cudaStream_t st = op->ctx->stream;
+  cudaEvent_t e[3];
+  for (auto& ev : e) CFIE_CHECK_CUDA(cudaEventCreate(&ev));
+  float t[2] = {0.f, 0.f};
+  for (int v = 0; v < 2; ++v) {
+    auto run = [&] { v == 0 ? matvec_fp32(op, x, y, nrhs) : matvec_fp32_tc(op, x, y, nrhs); };
+    run();  // warm-up (plans, attributes)
+    CFIE_CHECK_CUDA(cudaEventRecord(e[0], st));
+    run();
+    CFIE_CHECK_CUDA(cudaEventRecord(e[1], st));
+    CFIE_CHECK_CUDA(cudaEventSynchronize(e[1]));
+    CFIE_CHECK_CUDA(cudaEventElapsedTime(&t[v], e[0], e[1]));
+  }
+  for (auto& ev : e) cudaEventDestroy(ev);
+  const int choice = t[1] < t[0] ? 2 : 1;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[key] = choice;
+  return choice;
+}
+
+}  // namespace
+
 void apply_inner(cfie_op* op, const double2* x, double2* y, int nrhs) {
   switch (op->prec) {
     case CFIE_FP64:
       matvec_fp64(op, x, y, nrhs);
       break;
     case CFIE_FP32_REFINED:
-      matvec_fp32(op, x, y, nrhs);
+      if (tuned_variant(op, x, y, nrhs) == 2)
+        matvec_fp32_tc(op, x, y, nrhs);
+      else
+        matvec_fp32(op, x, y, nrhs);
       break;
     case CFIE_TENSOR_REFINED:
       matvec_stored(op, x, y, nrhs);
@@ -291,6 +336,18 @@ cfie_status cfie_apply(cfie_op* op, const void* x_dev, void* y_dev, int nrhs) {
     apply_inner(op, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev), nrhs);
     if (op->layout == CFIE_STORED && stored_take_error(op))
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
+    if (op->prec == CFIE_FP32_REFINED && tc_take_error(op))
+      throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
+  });
+}
+
+cfie_status cfie_op_set_variant(cfie_op* op, int variant) {
+  if (!op) return CFIE_EINVAL;
+  return guarded(op->ctx, [&] {
+    CFIE_REQUIRE(variant >= 0 && variant <= 2, "variant must be 0, 1 or 2");
+    CFIE_REQUIRE(variant != 2 || (op->prec == CFIE_FP32_REFINED && op->bc == CFIE_SOUND_SOFT),
+                 "the tensor-core variant needs a sound-soft CFIE_FP32_REFINED operator");
+    op->variant = variant;
   });
 }
 
@@ -345,6 +402,8 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
               static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), rtol, restart,
               maxit, iters_out, relres_out, &result, op->stats);
     if (op->layout == CFIE_STORED && stored_take_error(op))
+      throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
+    if (op->prec == CFIE_FP32_REFINED && tc_take_error(op))
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     if (result == CFIE_ENOCONV) op->ctx->err = "GMRES reached maxit before rtol";
   });

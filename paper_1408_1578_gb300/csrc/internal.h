@@ -142,6 +142,15 @@ struct gemm_plan {
   cudaGraphExec_t exec = nullptr;
 };
 
+// Stream-K plan of the fused matrix-free tensor-core matvec (matvec_tc.cu).
+struct tc_plan {
+  bool built = false;
+  int grid = 0, nsegs = 0, mtiles = 0;
+  size_t o_cbeg = 0, o_mts = 0;
+  dbuf tables, bt, partial, err;
+  alignas(64) unsigned char tmB[128];   // CUtensorMap of the B planes
+};
+
 struct cfie_op {
   cfie_ctx* ctx = nullptr;
   int n = 0;
@@ -166,6 +175,10 @@ struct cfie_op {
   dbuf band;         // near-field band entries (complex64), n x (2 b + 1) per operator
   int band_b = -1;
   dbuf xin32, xin32b; // FP32 staging of the input (and hard-path helpers)
+
+  // FP32 matvec variant: 0 = autotuned, 1 = FP32-pipe contraction, 2 = tensor cores
+  int variant = 0, tuned_nrhs = -1, tuned_choice = 1;
+  tc_plan tc[2];   // 32- and 64-right-hand-side plans
 
   // stored path (CFIE_STORED): bf16 hi/lo planes of A and the contraction plan
   dbuf stored;
@@ -236,6 +249,9 @@ void gemm_plan_release(gemm_plan& G);
 void stored_prepare(cfie_op* op);
 void matvec_stored(cfie_op* op, const double2* x, double2* y, int nrhs);
 int stored_take_error(cfie_op* op);
+// matvec_tc.cu
+void matvec_fp32_tc(cfie_op* op, const double2* x, double2* y, int nrhs);
+int tc_take_error(cfie_op* op);
 // arnoldi.cu
 void pset_build(pset& ps, const std::vector<size_t>& off, const std::vector<int>& len,
                 cudaStream_t st);

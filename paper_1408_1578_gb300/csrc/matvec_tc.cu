@@ -1,0 +1,409 @@
+// Matrix-free FP32 matvec with the source summation on the tensor cores.
+//
+// Same entries as the FP32 fused kernel (sound-soft operator of eq. 1: FP32
+// pair evaluation with two-float phase and Hankel asymptotics, FP64-evaluated
+// near band), but instead of the register-blocked FP32 contraction the entries
+// of each 128 x 32 tile are written, split as bf16 hi + lo, straight into
+// shared memory in the tensor cores' 64-byte-swizzled K-major layout, and one
+// thread issues tcgen05.mma against the right-hand-side block (bf16 hi / lo
+// planes brought in by TMA):
+//
+//     [Yr | Yi] += Ar [Xr | Xi] + Ai [-Xi | Xr],  each product hi*hi + hi*lo + lo*hi,
+//
+// FP32 accumulation in tensor memory.  Work is split stream-K: the
+// (128-row tile, 32-source tile) pairs form one list and each CTA (one per SM)
+// takes a contiguous range, cut into segments that end at row-tile boundaries.
+// Warp roles: 0-7 evaluate pair entries into the stage ring, 8 issues the TMA
+// loads of the right-hand sides, 9 issues the MMAs (double-buffered
+// accumulators), 10-13 drain finished accumulators into per-segment partial
+// sums, which a second kernel adds in FP64 in a fixed order.  All mbarrier
+// waits are bounded (error flag, drain, TMEM freed on every path).
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "internal.h"
+#include "pair32.cuh"
+#include "tc_common.cuh"
+
+namespace {
+
+constexpr int TBM = 128;     // targets per tile (UMMA M)
+constexpr int TBK = 32;      // sources per tile (32 bf16 = one 64-byte swizzle row)
+constexpr int TSTAGES = 2;
+// Source tiles accumulated in one tensor-memory accumulator before the epilogue
+// warps add it into their running sums.  The tensor core's FP32 accumulation
+// does not round to nearest: its error grows with the number of MMAs summed
+// into one accumulator (~2e-8 relative per MMA), so chunks of 256 sources keep
+// that bias near 2e-6 whatever n is, while the running sums (FP32 adds, rounded
+// to nearest) and the FP64 segment reduction add only unbiased rounding.
+constexpr int CK = 8;
+constexpr int NPROD = 8;     // producer warps
+constexpr int WTMA = 8, WMMA = 9, WEPI0 = 10;
+constexpr int TNT = 14 * 32;
+
+struct tc_params : omega32 {
+  int n, b, ktiles;
+  geo32 g;
+  const float* w32;
+  const float2* band;
+};
+
+template <int NP>
+struct tc_smem {
+  __nv_bfloat16 A[TSTAGES][4][TBM * TBK];   // hi_re, hi_im, lo_re, lo_im
+  __nv_bfloat16 B[TSTAGES][4][NP * TBK];    // B1 hi, B1 lo, B2 hi, B2 lo
+  float acc[NP][TBM];                       // epilogue running sums, column-major
+  uint64_t full[TSTAGES], empty[TSTAGES], tfull[2], tempty[2];
+  uint32_t tmem_base;
+  int abort;
+  int issued[TSTAGES];
+};
+
+template <int NP>
+constexpr size_t tc_smem_bytes() {
+  return sizeof(tc_smem<NP>) + 1024;
+}
+
+// byte offset of element (row r, k) in a 64-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw64(int r, int k) {
+  return (uint32_t)(r * 64 + ((((k >> 3) ^ (r >> 1)) & 3) << 4) + (k & 7) * 2);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(TNT, 1)
+k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __restrict__ segs,
+           const int* __restrict__ cbeg, float2* __restrict__ partial, int* __restrict__ err) {
+  constexpr int NR = NP / 2;
+  constexpr uint32_t TMEM_COLS = 2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256);
+  constexpr uint32_t B_BYTES = 4u * NP * TBK * 2u;
+  extern __shared__ unsigned char raw[];
+  tc_smem<NP>& S = *reinterpret_cast<tc_smem<NP>*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
+                                                    ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sb = cbeg[blockIdx.x], se = cbeg[blockIdx.x + 1];
+  const int n = P.n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TSTAGES; ++s) {
+      mbar_init(&S.full[s], NPROD * 32 + 1);   // producer threads + the TMA thread
+      mbar_init(&S.empty[s], 1);
+      S.issued[s] = -1;
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&S.tfull[b], 1);
+      mbar_init(&S.tempty[b], 4);
+    }
+    S.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == WMMA) {
+    tmem_alloc(&S.tmem_base, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+
+  if (warp < NPROD) {
+    // ---- pair-entry producers: rows warp + 8 q, lane = source within the tile
+    int it = 0;
+    for (int s = sb; s < se; ++s) {
+      const int4 sg = segs[s];
+      const int m0 = sg.y * TBM;
+      for (int k = sg.z; k < sg.w; ++k, ++it) {
+        const int st = it % TSTAGES;
+        if (*(volatile int*)&S.abort) break;
+        if (it >= TSTAGES && !mbar_wait(&S.empty[st], ((it / TSTAGES) - 1) & 1)) {
+          if (lane == 0) {
+            atomicExch(err, 11);
+            S.abort = 1;
+          }
+          break;
+        }
+        const int j = k * TBK + lane;
+        const bool jok = j < n;
+        const float sxh = jok ? P.g.xh[j] : 0.f, sxl = jok ? P.g.xl[j] : 0.f;
+        const float syh = jok ? P.g.yh[j] : 0.f, syl = jok ? P.g.yl[j] : 0.f;
+        const float snx = jok ? P.g.nx[j] : 0.f, sny = jok ? P.g.ny[j] : 0.f;
+        const float ssp = jok ? P.g.sp[j] : 1.f;
+        unsigned char* a0 = reinterpret_cast<unsigned char*>(S.A[st][0]);
+        unsigned char* a1 = reinterpret_cast<unsigned char*>(S.A[st][1]);
+        unsigned char* a2 = reinterpret_cast<unsigned char*>(S.A[st][2]);
+        unsigned char* a3 = reinterpret_cast<unsigned char*>(S.A[st][3]);
+#pragma unroll 2
+        for (int q = 0; q < TBM / NPROD; ++q) {
+          const int il = warp + NPROD * q;
+          const int i = m0 + il;
+          float2 a = make_float2(0.f, 0.f), unused;
+          if (i < n && jok) {
+            int d = i - j;
+            if (d < 0) d += n;
+            const int dd = d <= P.b ? d : (d >= n - P.b ? d - n : INT_MAX);
+            if (dd != INT_MAX) {
+              a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
+            } else {
+              pair_entries_fp32<0>(P, P.g.xh[i], P.g.xl[i], P.g.yh[i], P.g.yl[i], P.g.nx[i],
+                                   P.g.ny[i], P.g.sp[i], sxh, sxl, syh, syl, snx, sny, ssp,
+                                   P.w32[d], a, unused);
+            }
+          }
+          const __nv_bfloat16 hr = __float2bfloat16_rn(a.x), hi = __float2bfloat16_rn(a.y);
+          const __nv_bfloat16 lr = __float2bfloat16_rn(a.x - __bfloat162float(hr));
+          const __nv_bfloat16 li = __float2bfloat16_rn(a.y - __bfloat162float(hi));
+          const uint32_t o = sw64(il, lane);
+          *reinterpret_cast<__nv_bfloat16*>(a0 + o) = hr;
+          *reinterpret_cast<__nv_bfloat16*>(a1 + o) = hi;
+          *reinterpret_cast<__nv_bfloat16*>(a2 + o) = lr;
+          *reinterpret_cast<__nv_bfloat16*>(a3 + o) = li;
+        }
+        // generic-proxy writes become visible to the tensor core's async proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&S.full[st]);
+      }
+      if (*(volatile int*)&S.abort) break;
+    }
+  } else if (warp == WTMA) {
+    if (lane == 0) {
+      // ---- TMA producer of the right-hand-side planes
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int it = 0;
+      for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
+        const int4 sg = segs[s];
+        for (int k = sg.z; k < sg.w; ++k, ++it) {
+          const int st = it % TSTAGES;
+          if (it >= TSTAGES && !mbar_wait(&S.empty[st], ((it / TSTAGES) - 1) & 1)) {
+            atomicExch(err, 12);
+            S.abort = 1;
+            break;
+          }
+          mbar_arrive_expect_tx(&S.full[st], B_BYTES);
+          S.issued[st] = (it / TSTAGES) & 1;
+#pragma unroll
+          for (int p = 0; p < 4; ++p) tma_load_2d(S.B[st][p], &tmB, &S.full[st], k * TBK, p * NP);
+        }
+      }
+    }
+  } else if (warp == WMMA) {
+    if (lane == 0) {
+      // ---- MMA issuer: one accumulator buffer per chunk of CK source tiles
+      constexpr uint32_t idesc = make_idesc(TBM, NP);
+      int it = 0, cc = 0;
+      for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
+        const int4 sg = segs[s];
+        for (int c0 = sg.z; c0 < sg.w; c0 += CK, ++cc) {
+          const int c1 = min(sg.w, c0 + CK);
+          const int tb = cc & 1, use = cc >> 1;
+          if (use >= 1 && !mbar_wait(&S.tempty[tb], (use - 1) & 1)) {
+            atomicExch(err, 14);
+            S.abort = 1;
+          }
+          if (*(volatile int*)&S.abort) break;
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(tb * NP);
+          for (int k = c0; k < c1; ++k, ++it) {
+            const int st = it % TSTAGES;
+            if (!mbar_wait(&S.full[st], (it / TSTAGES) & 1)) {
+              atomicExch(err, 13);
+              S.abort = 1;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(S.A[st][0]), a1 = smem_u32(S.A[st][1]);
+            const uint32_t a2 = smem_u32(S.A[st][2]), a3 = smem_u32(S.A[st][3]);
+            const uint32_t b0 = smem_u32(S.B[st][0]), b1 = smem_u32(S.B[st][1]);
+            const uint32_t b2 = smem_u32(S.B[st][2]), b3 = smem_u32(S.B[st][3]);
+#pragma unroll
+            for (int kk = 0; kk < TBK / 16; ++kk) {
+              const uint32_t off = kk * 32;
+              const uint32_t acc0 = (k > c0 || kk > 0) ? 1u : 0u;
+              umma_bf16(d, smem_desc_sw64(a0 + off), smem_desc_sw64(b0 + off), idesc, acc0);
+              umma_bf16(d, smem_desc_sw64(a0 + off), smem_desc_sw64(b1 + off), idesc, 1u);
+              umma_bf16(d, smem_desc_sw64(a2 + off), smem_desc_sw64(b0 + off), idesc, 1u);
+              umma_bf16(d, smem_desc_sw64(a1 + off), smem_desc_sw64(b2 + off), idesc, 1u);
+              umma_bf16(d, smem_desc_sw64(a1 + off), smem_desc_sw64(b3 + off), idesc, 1u);
+              umma_bf16(d, smem_desc_sw64(a3 + off), smem_desc_sw64(b2 + off), idesc, 1u);
+            }
+            umma_commit(&S.empty[st]);
+          }
+          umma_commit(&S.tfull[tb]);
+        }
+      }
+    }
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one row per thread;
+    // running sums per segment in shared memory (each thread owns its row)
+    const int q = warp & 3;
+    const int row = 32 * q + lane;
+    int cc = 0;
+    bool stop = false;
+    for (int s = sb; s < se && !stop; ++s) {
+      const int4 sg = segs[s];
+      for (int c0 = sg.z; c0 < sg.w; c0 += CK, ++cc) {
+        const int tb = cc & 1, use = cc >> 1;
+        if (*(volatile int*)&S.abort || !mbar_wait(&S.tfull[tb], use & 1)) {
+          if (lane == 0) {
+            atomicExch(err, 15);
+            S.abort = 1;
+          }
+          stop = true;
+          break;
+        }
+        __syncwarp();
+        tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(tb * NP);
+        const bool first = c0 == sg.z;
+#pragma unroll
+        for (int cb = 0; cb < NP; cb += 16) {
+          float v[16];
+          tmem_ld16(base + (uint32_t)cb, v);
+#pragma unroll
+          for (int r = 0; r < 16; ++r)
+            S.acc[cb + r][row] = first ? v[r] : S.acc[cb + r][row] + v[r];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.tempty[tb]);
+      }
+      if (stop) break;
+      float2* dst = partial + (size_t)s * TBM * NR + row;
+#pragma unroll 4
+      for (int r = 0; r < NR; ++r) dst[(size_t)r * TBM] = make_float2(S.acc[r][row], S.acc[NR + r][row]);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *(volatile int*)&S.abort) {
+    for (int s = 0; s < TSTAGES; ++s)
+      if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
+  }
+  __syncthreads();
+  if (warp == WMMA) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// y[r][i] = sum of the segment partials of row tile i / 128 (fixed order, FP64)
+__global__ void k_reduce_tc(int n, int nr, int NR, const int2* __restrict__ mt_seg,
+                            const float2* __restrict__ partial, double2* __restrict__ y) {
+  const int m = blockIdx.x, r = blockIdx.y, row = threadIdx.x;
+  const int i = m * TBM + row;
+  if (i >= n || r >= nr) return;
+  const int2 sr = mt_seg[m];
+  double sx = 0.0, sy = 0.0;
+  for (int s = sr.x; s < sr.x + sr.y; ++s) {
+    const float2 p = partial[((size_t)s * NR + r) * TBM + row];
+    sx += p.x;
+    sy += p.y;
+  }
+  y[(size_t)r * n + i] = make_double2(sx, sy);
+}
+
+unsigned nb(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
+
+template <int NP>
+void run_fused(cfie_op* op, const double2* x, double2* y, int r0, int nr) {
+  constexpr int NR = NP / 2;
+  tc_plan& T = op->tc[NP == 64 ? 0 : 1];
+  const int n = op->n;
+  cudaStream_t st = op->ctx->stream;
+  const int pitch = (n + 63) / 64 * 64;
+  if (!T.built) {
+    const int mtiles = (n + TBM - 1) / TBM, ktiles = (n + TBK - 1) / TBK;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->ctx->device);
+    std::vector<int4> segs;
+    std::vector<int> cbeg;
+    std::vector<int2> mt_seg;
+    streamk_segments(mtiles, ktiles, sms, segs, cbeg, mt_seg);
+    T.grid = (int)cbeg.size() - 1;
+    T.nsegs = (int)segs.size();
+    T.mtiles = mtiles;
+    T.tables.reserve(sizeof(int4) * segs.size() + sizeof(int) * cbeg.size() +
+                     sizeof(int2) * mt_seg.size() + 64);
+    char* tb = T.tables.as<char>();
+    T.o_cbeg = (sizeof(int4) * segs.size() + 15) & ~size_t(15);
+    T.o_mts = (T.o_cbeg + sizeof(int) * cbeg.size() + 15) & ~size_t(15);
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(tb, segs.data(), sizeof(int4) * segs.size(),
+                                    cudaMemcpyHostToDevice, st));
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(tb + T.o_cbeg, cbeg.data(), sizeof(int) * cbeg.size(),
+                                    cudaMemcpyHostToDevice, st));
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(tb + T.o_mts, mt_seg.data(), sizeof(int2) * mt_seg.size(),
+                                    cudaMemcpyHostToDevice, st));
+    T.bt.reserve(sizeof(__nv_bfloat16) * 4 * (size_t)NP * pitch);
+    T.partial.reserve(sizeof(float2) * (size_t)T.nsegs * TBM * NR);
+    T.err.reserve(sizeof(int));
+    CFIE_CHECK_CUDA(cudaMemsetAsync(T.err.p, 0, sizeof(int), st));
+    const CUtensorMap mb = tc_make_map(T.bt.p, 4 * (uint64_t)NP, (uint64_t)pitch, pitch, NP,
+                                       TBK, CU_TENSOR_MAP_SWIZZLE_64B);
+    std::memcpy(T.tmB, &mb, sizeof(mb));
+    CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
+    T.built = true;
+  }
+  prep_b_planes(op->ctx, n, pitch, NP, nr, x + (size_t)r0 * n, T.bt.as<__nv_bfloat16>());
+  tc_params P{};
+  P.wh = (float)op->omega;
+  P.wl = (float)(op->omega - (double)P.wh);
+  P.winv = (float)(1.0 / op->omega);
+  P.eta = (float)op->eta;
+  P.h = (float)op->h;
+  P.n = n;
+  P.b = op->band_b;
+  P.ktiles = (n + TBK - 1) / TBK;
+  float* base = op->geo32.as<float>();
+  P.g = geo32_at(base, n);
+  P.w32 = base + 7 * n;
+  P.band = op->band.as<float2>();
+  const size_t smem = tc_smem_bytes<NP>();
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_fused_tc<NP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  char* tb = T.tables.as<char>();
+  {
+    prof_scope ps(op->ctx, CFIE_K_MATVEC_FP32);
+    k_fused_tc<NP><<<T.grid, TNT, smem, st>>>(P, *reinterpret_cast<const CUtensorMap*>(T.tmB),
+                                             reinterpret_cast<const int4*>(tb),
+                                             reinterpret_cast<const int*>(tb + T.o_cbeg),
+                                             T.partial.as<float2>(), T.err.as<int>());
+    CFIE_CHECK_LAUNCH();
+  }
+  k_reduce_tc<<<dim3(T.mtiles, nr), TBM, 0, st>>>(n, nr, NR,
+                                                 reinterpret_cast<const int2*>(tb + T.o_mts),
+                                                 T.partial.as<float2>(), y + (size_t)r0 * n);
+  CFIE_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void matvec_fp32_tc(cfie_op* op, const double2* x, double2* y, int nrhs) {
+  if (op->bc != CFIE_SOUND_SOFT)
+    throw cfie_error(CFIE_EINVAL, "tensor-core contraction supports the sound-soft operator");
+  for (int r0 = 0; r0 < nrhs; r0 += 64) {
+    const int nr = std::min(64, nrhs - r0);
+    if (nr > 32)
+      run_fused<128>(op, x, y, r0, nr);
+    else
+      run_fused<64>(op, x, y, r0, nr);
+  }
+}
+
+int tc_take_error(cfie_op* op) {
+  int e = 0;
+  for (auto& T : op->tc) {
+    if (!T.err.p) continue;
+    int v = 0;
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(&v, T.err.p, sizeof(int), cudaMemcpyDeviceToHost,
+                                    op->ctx->stream));
+    CFIE_CHECK_CUDA(cudaStreamSynchronize(op->ctx->stream));
+    if (v) {
+      e = v;
+      CFIE_CHECK_CUDA(cudaMemsetAsync(T.err.p, 0, sizeof(int), op->ctx->stream));
+    }
+  }
+  return e;
+}

@@ -34,141 +34,18 @@
 
 #include "internal.h"
 #include "pair32.cuh"
+#include "tc_common.cuh"
 
 namespace {
 
 constexpr int BM = 128;     // rows (targets) per CTA tile = UMMA M
 constexpr int BK = 64;      // sources per K tile (64 bf16 = one 128-byte swizzle row)
 constexpr int STAGES = 2;
-constexpr int NT = 128;     // 4 warps
-constexpr long long kTimeoutCycles = 4000000000LL;  // ~2 s at 2 GHz
-
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      "selp.u32 %0, 1, 0, p;\n"
-      "}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// bounded wait on the phase of parity `parity`; false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kTimeoutCycles) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int c0, int c1) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(dst)),
-               "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// D[tmem] (+)= A[smem] * B[smem]^T, both K-major
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n"
-      ".reg .pred p;\n"
-      "setp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-      "}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-// 32 TMEM lanes x 16 consecutive 32-bit columns into 16 registers per thread
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
-}
-
-// Shared-memory matrix descriptor: K-major operand in 128-byte-swizzled rows,
-// 8-row core groups 1024 bytes apart (SBO), descriptor version 1 (sm_100 family).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);   // start address
-  d |= (uint64_t)1 << 16;                      // leading byte offset (unused when swizzled)
-  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
-  d |= (uint64_t)1 << 46;                      // version
-  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
+// K tiles accumulated in one tensor-memory accumulator before the epilogue adds
+// it into its running sums: the tensor core's FP32 accumulation is not rounded
+// to nearest and its error grows with the MMAs summed into one accumulator, so
+// chunks of 256 sources keep it near 2e-6 for every n.
+constexpr int SCK = 4;
 
 // ---------------------------------------------------------------------------
 // assembly and operand preparation
@@ -207,10 +84,6 @@ k_assemble(int n, int pitch, int b, omega32 W, geo32 g, const float* __restrict_
   planes[plane + e] = hi;
   planes[2 * plane + e] = lr;
   planes[3 * plane + e] = li;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // One GEMM job: 32 right-hand sides of one stored operator.  64-byte aligned
@@ -312,75 +185,88 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      // ---- MMA issuer
+      // ---- MMA issuer: one accumulator buffer per chunk of SCK source tiles
       constexpr uint32_t idesc = make_idesc(BM, NP);
-      int it = 0;
-      for (int s = sb, sl = 0; s < se; ++s, ++sl) {
+      int it = 0, cc = 0;
+      for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
         const int4 sg = segs[s];
-        const int tb = sl & 1, use = sl >> 1;
-        if (use >= 1 && !mbar_wait(&S.tempty[tb], (use - 1) & 1)) {
-          atomicExch(err, 4);
-          S.abort = 1;
-        }
-        if (*(volatile int*)&S.abort) break;
-        tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(tb * NP);
-        for (int k = sg.z; k < sg.w; ++k, ++it) {
-          const int st = it % STAGES;
-          if (!mbar_wait(&S.full[st], (it / STAGES) & 1)) {
-            atomicExch(err, 2);
+        for (int c0 = sg.z; c0 < sg.w; c0 += SCK, ++cc) {
+          const int c1 = min(sg.w, c0 + SCK);
+          const int tb = cc & 1, use = cc >> 1;
+          if (use >= 1 && !mbar_wait(&S.tempty[tb], (use - 1) & 1)) {
+            atomicExch(err, 4);
             S.abort = 1;
-            break;
           }
+          if (*(volatile int*)&S.abort) break;
           tc_fence_after();
-          const uint32_t a0 = smem_u32(S.A[st][0]), a1 = smem_u32(S.A[st][1]);
-          const uint32_t a2 = smem_u32(S.A[st][2]), a3 = smem_u32(S.A[st][3]);
-          const uint32_t b0 = smem_u32(S.B[st][0]), b1 = smem_u32(S.B[st][1]);
-          const uint32_t b2 = smem_u32(S.B[st][2]), b3 = smem_u32(S.B[st][3]);
+          const uint32_t d = tmem + (uint32_t)(tb * NP);
+          for (int k = c0; k < c1; ++k, ++it) {
+            const int st = it % STAGES;
+            if (!mbar_wait(&S.full[st], (it / STAGES) & 1)) {
+              atomicExch(err, 2);
+              S.abort = 1;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(S.A[st][0]), a1 = smem_u32(S.A[st][1]);
+            const uint32_t a2 = smem_u32(S.A[st][2]), a3 = smem_u32(S.A[st][3]);
+            const uint32_t b0 = smem_u32(S.B[st][0]), b1 = smem_u32(S.B[st][1]);
+            const uint32_t b2 = smem_u32(S.B[st][2]), b3 = smem_u32(S.B[st][3]);
 #pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint32_t off = kk * 32;  // 16 bf16 along K inside the 128-byte swizzle row
-            const uint32_t acc0 = (k > sg.z || kk > 0) ? 1u : 0u;
-            umma_bf16(d, smem_desc(a0 + off), smem_desc(b0 + off), idesc, acc0);  // hr * B1 hi
-            umma_bf16(d, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1u);    // hr * B1 lo
-            umma_bf16(d, smem_desc(a2 + off), smem_desc(b0 + off), idesc, 1u);    // lr * B1 hi
-            umma_bf16(d, smem_desc(a1 + off), smem_desc(b2 + off), idesc, 1u);    // hi * B2 hi
-            umma_bf16(d, smem_desc(a1 + off), smem_desc(b3 + off), idesc, 1u);    // hi * B2 lo
-            umma_bf16(d, smem_desc(a3 + off), smem_desc(b2 + off), idesc, 1u);    // li * B2 hi
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              const uint32_t off = kk * 32;  // 16 bf16 along K inside the 128-byte swizzle row
+              const uint32_t acc0 = (k > c0 || kk > 0) ? 1u : 0u;
+              umma_bf16(d, smem_desc(a0 + off), smem_desc(b0 + off), idesc, acc0);  // hr * B1 hi
+              umma_bf16(d, smem_desc(a0 + off), smem_desc(b1 + off), idesc, 1u);    // hr * B1 lo
+              umma_bf16(d, smem_desc(a2 + off), smem_desc(b0 + off), idesc, 1u);    // lr * B1 hi
+              umma_bf16(d, smem_desc(a1 + off), smem_desc(b2 + off), idesc, 1u);    // hi * B2 hi
+              umma_bf16(d, smem_desc(a1 + off), smem_desc(b3 + off), idesc, 1u);    // hi * B2 lo
+              umma_bf16(d, smem_desc(a3 + off), smem_desc(b2 + off), idesc, 1u);    // li * B2 hi
+            }
+            umma_commit(&S.empty[st]);
           }
-          umma_commit(&S.empty[st]);
+          umma_commit(&S.tfull[tb]);  // arrives when this chunk's MMAs have completed
         }
-        umma_commit(&S.tfull[tb]);  // arrives when this segment's MMAs have completed
-        if (*(volatile int*)&S.abort) break;
       }
     }
   } else {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one row per
+    // thread, running sums of the chunks of a segment in registers
     const int q = warp & 3;
     const int row = 32 * q + lane;
-    for (int s = sb, sl = 0; s < se; ++s, ++sl) {
-      const int tb = sl & 1, use = sl >> 1;
-      if (*(volatile int*)&S.abort) break;
-      const bool ok = mbar_wait(&S.tfull[tb], use & 1);
-      if (!ok) {
-        if (lane == 0) {
-          atomicExch(err, 3);
-          S.abort = 1;
+    int cc = 0;
+    bool stop = false;
+    for (int s = sb; s < se && !stop; ++s) {
+      const int4 sg = segs[s];
+      float run[NP];
+      for (int c0 = sg.z; c0 < sg.w; c0 += SCK, ++cc) {
+        const int tb = cc & 1, use = cc >> 1;
+        if (*(volatile int*)&S.abort || !mbar_wait(&S.tfull[tb], use & 1)) {
+          if (lane == 0) {
+            atomicExch(err, 3);
+            S.abort = 1;
+          }
+          stop = true;
+          break;
         }
-        break;
-      }
-      __syncwarp();
-      tc_fence_after();
-      float v[NP];
+        __syncwarp();
+        tc_fence_after();
+        const bool first = c0 == sg.z;
 #pragma unroll
-      for (int c0 = 0; c0 < NP; c0 += 16)
-        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(tb * NP + c0), v + c0);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&S.tempty[tb]);
+        for (int cb = 0; cb < NP; cb += 16) {
+          float v[16];
+          tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(tb * NP + cb), v);
+#pragma unroll
+          for (int r = 0; r < 16; ++r) run[cb + r] = first ? v[r] : run[cb + r] + v[r];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.tempty[tb]);
+      }
+      if (stop) break;
       float2* dst = partial + (size_t)s * BM * NR + row;
 #pragma unroll
-      for (int r = 0; r < NR; ++r) dst[(size_t)r * BM] = make_float2(v[r], v[NR + r]);
+      for (int r = 0; r < NR; ++r) dst[(size_t)r * BM] = make_float2(run[r], run[NR + r]);
     }
   }
   __syncthreads();
@@ -446,42 +332,9 @@ __global__ void k_reduce_jobs(const gemm_job* __restrict__ jobs, const int2* __r
 // ---------------------------------------------------------------------------
 // host: tensor maps, plans, graphs
 // ---------------------------------------------------------------------------
-using encode_fn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                               CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-encode_fn get_encode() {
-  static std::mutex mu;
-  static encode_fn fn = nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    CFIE_CHECK_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                                     cudaEnableDefault, &q));
-    if (!p || q != cudaDriverEntryPointSuccess)
-      throw cfie_error(CFIE_ECUDA, "cuTensorMapEncodeTiled is not available");
-    fn = reinterpret_cast<encode_fn>(p);
-  }
-  return fn;
-}
-
 // bf16 matrix of `rows` x `cols` (row pitch `pitch` elements), box box_rows x 64
 CUtensorMap make_map(void* base, uint64_t rows, uint64_t cols, uint64_t pitch, uint32_t box_rows) {
-  CUtensorMap m;
-  std::memset(&m, 0, sizeof(m));
-  const cuuint64_t dims[2] = {cols, rows};
-  const cuuint64_t strides[1] = {pitch * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box,
-                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS)
-    throw cfie_error(CFIE_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
-  return m;
+  return tc_make_map(base, rows, cols, pitch, box_rows, BK, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 unsigned nblk(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }

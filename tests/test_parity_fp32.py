@@ -136,3 +136,52 @@ def test_band_too_wide_is_rejected_or_served(ctx):
     y = empty(1, n)
     op.apply(to_dev(X), y)
     assert np.max(col_rel(to_host(y), (A @ X.T).T)) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# the same FP32 entries summed on the tensor cores (cfie_op_set_variant(op, 2))
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,params,n,omega,nrhs", [
+    ("kite", {}, 2000, 200.0, 8),
+    ("kite", {}, 2000, 200.0, 33),
+    ("star", {"a": [0.03, -0.02, 0.04], "b": [0.01, 0.05, -0.03]}, 3000, 450.0, 64),
+    ("ellipse", {"a": 1.0, "b": 0.5}, 1000, 90.0, 32),
+    ("circle", {}, 64, 2.0, 9),
+])
+def test_fp32_tensor_core_sums(ctx, kind, params, n, omega, nrhs):
+    c = geometry.make(kind, n, **params)
+    A = operators.soft_matrix(c, omega, omega)
+    X = inputs.random_density(n, nrhs, seed=4 * n + nrhs)
+    op = ctx.geometry(kind, **params).discretise(n, omega, precision="fp32")
+    op.set_variant(2)
+    y = empty(nrhs, n)
+    op.apply(to_dev(X), y)
+    assert np.max(col_rel(to_host(y), (A @ X.T).T)) < TOL_FP32
+    op.set_variant(1)
+    y1 = empty(nrhs, n)
+    op.apply(to_dev(X), y1)
+    assert np.max(col_rel(to_host(y), to_host(y1))) < TOL_FP32
+
+
+def test_fp32_tensor_core_refined_solve(ctx):
+    n, w, nrhs = 2000, 200.0, 40
+    c = geometry.kite(n)
+    A = operators.soft_matrix(c, w, w)
+    F = operators.plane_wave_rhs(c, w, inputs.directions(nrhs), "soft")
+    Q = solvers.lu_solve(A, F).T
+    op = ctx.kite().discretise(n, w, precision="fp32")
+    op.set_variant(2)
+    x = zeros(nrhs, n)
+    its, rel, _ = op.gmres_solve(to_dev(F.T), x, rtol=1e-8, restart=80, maxit=3000)
+    assert np.all(rel <= 1e-8)
+    assert np.max(col_rel(to_host(x), Q)) < TOL_REFINED
+
+
+def test_tensor_core_variant_arguments(ctx):
+    from paper_1408_1578_gb300 import cfie
+    op = ctx.kite().discretise(256, 20.0, bc="hard", precision="fp32")
+    with pytest.raises(cfie.CfieError):
+        op.set_variant(2)
+    op64 = ctx.kite().discretise(256, 20.0, precision="fp64")
+    with pytest.raises(cfie.CfieError):
+        op64.set_variant(2)

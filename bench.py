@@ -375,29 +375,41 @@ def run_reference(args, rank, world):
 _PG = None
 
 
-def init_dist():
+def init_dist(backend=None):
+    """Replicas: one process per GPU, no collective on the data path; the
+    process group only carries the barrier and the max / sum of the timings."""
     global _PG
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        backend = "nccl"
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
         dist.init_process_group(backend)
         _PG = dist
     return rank, world
 
 
+def _device():
+    import torch
+    return "cuda" if _PG is not None and _PG.get_backend() == "nccl" else "cpu"
+
+
 def barrier(world):
     if world > 1:
         import torch
-        _PG.barrier(device_ids=[torch.cuda.current_device()])
+        if _device() == "cuda":
+            _PG.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            _PG.barrier()
 
 
 def _reduce(v, op, world):
     if world == 1:
         return v
     import torch
-    t = torch.tensor([float(v)], device="cuda", dtype=torch.float64)
+    t = torch.tensor([float(v)], device=_device(), dtype=torch.float64)
     _PG.all_reduce(t, op=op)
     return float(t.item())
 

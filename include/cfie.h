@@ -158,6 +158,13 @@ cfie_status cfie_apply_fp64(cfie_op* op, const void* x_dev, void* y_dev, int nrh
  * call, so nothing needs clearing between calls.  Arguments as cfie_apply. */
 cfie_status cfie_apply_fp64_static(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
 
+/* y = A x with the FP64-accurate matvec the refined precisions use for their
+ * true residuals: for sound-soft CFIE_FP32_REFINED / CFIE_TENSOR_REFINED
+ * operators the same entries as cfie_apply_fp64 evaluated in double-float
+ * arithmetic on the FP32 pipe (hi + lo pairs, error-free products and sums;
+ * ~1e-13 relative), otherwise the FP64 matvec.  Arguments as cfie_apply. */
+cfie_status cfie_apply_residual(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
+
 /* Solve A x = f for nrhs independent right-hand sides by restarted GMRES
  * (Section 3: relative tolerance and restart; zero initial guess there).
  *  f_dev   device, n*nrhs complex128 (read only)
@@ -167,8 +174,9 @@ cfie_status cfie_apply_fp64_static(cfie_op* op, const void* x_dev, void* y_dev, 
  *  maxit   cap on Arnoldi steps per right-hand side (inner steps for the
  *          refined precisions)
  *  iters_out  host, nrhs ints (may be NULL): Arnoldi steps per right-hand side
- *  relres_out host, nrhs doubles (may be NULL): true FP64 relative residual
- *             recomputed from the returned x
+ *  relres_out host, nrhs doubles (may be NULL): true relative residual
+ *             recomputed from the returned x with the FP64-accurate matvec
+ *             (cfie_apply_fp64 for CFIE_FP64, cfie_apply_residual otherwise)
  * Returns CFIE_ENOCONV (x holds the last iterate) if some right-hand side
  * missed rtol.  Synchronous. */
 cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nrhs, double rtol,

@@ -90,6 +90,7 @@ SIGNATURES = {
     "cfie_apply": (_I, [_P, _P, _P, _I]),
     "cfie_apply_fp64": (_I, [_P, _P, _P, _I]),
     "cfie_apply_fp64_static": (_I, [_P, _P, _P, _I]),
+    "cfie_apply_residual": (_I, [_P, _P, _P, _I]),
     "cfie_op_set_variant": (_I, [_P, _I]),
     "cfie_gmres_solve": (_I, [_P, _P, _P, _I, _D, _I, _I, _IP, _DP]),
     "cfie_op_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
@@ -415,6 +416,11 @@ class Operator:
     def set_variant(self, variant):
         """0 = autotuned, 1 = FP32-pipe sums, 2 = tensor-core sums."""
         self.ctx.check(self.ctx.lib.cfie_op_set_variant(self.h, int(variant)), "cfie_op_set_variant")
+
+    def apply_residual(self, x, y, nrhs=None):
+        nrhs = x.numel() // self.n if nrhs is None else nrhs
+        self.ctx.check(self.ctx.lib.cfie_apply_residual(self.h, _addr(x), _addr(y), int(nrhs)),
+                       "cfie_apply_residual")
 
     def apply_fp64(self, x, y, nrhs=None):
         nrhs = x.numel() // self.n if nrhs is None else nrhs

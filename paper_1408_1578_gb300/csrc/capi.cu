@@ -136,6 +136,13 @@ int tuned_variant(cfie_op* op, const double2* x, double2* y, int nrhs) {
 
 }  // namespace
 
+void matvec_residual(cfie_op* op, const double2* x, double2* y, int nrhs) {
+  if (op->prec != CFIE_FP64 && df_available(op))
+    matvec_df(op, x, y, nrhs);
+  else
+    matvec_fp64(op, x, y, nrhs);
+}
+
 void apply_inner(cfie_op* op, const double2* x, double2* y, int nrhs) {
   switch (op->prec) {
     case CFIE_FP64:
@@ -291,6 +298,7 @@ cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cf
     geometry_sample(op, geom);
     kress_tables(op);
     if (precision != CFIE_FP64) fp32_prepare(op);
+    if (precision != CFIE_FP64 && bc == CFIE_SOUND_SOFT) df_prepare(op);
     if (layout == CFIE_STORED) stored_prepare(op);
     CFIE_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   });
@@ -351,6 +359,18 @@ cfie_status cfie_op_set_variant(cfie_op* op, int variant) {
   });
 }
 
+cfie_status cfie_apply_residual(cfie_op* op, const void* x_dev, void* y_dev, int nrhs) {
+  if (!op) return CFIE_EINVAL;
+  return guarded(op->ctx, [&] {
+    CFIE_REQUIRE(nrhs >= 1 && nrhs <= 1024, "nrhs must be in [1, 1024]");
+    check_vec(x_dev, "x");
+    check_vec(y_dev, "y");
+    CFIE_REQUIRE(x_dev != y_dev, "x and y must not overlap");
+    set_device(op->ctx);
+    matvec_residual(op, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev), nrhs);
+  });
+}
+
 cfie_status cfie_apply_fp64(cfie_op* op, const void* x_dev, void* y_dev, int nrhs) {
   if (!op) return CFIE_EINVAL;
   return guarded(op->ctx, [&] {
@@ -397,7 +417,7 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
     }
     solve_fns fns;
     fns.inner = [op, nrhs](const double2* a, double2* b) { apply_inner(op, a, b, nrhs); };
-    fns.fp64 = [op, nrhs](const double2* a, double2* b) { matvec_fp64(op, a, b, nrhs); };
+    fns.fp64 = [op, nrhs](const double2* a, double2* b) { matvec_residual(op, a, b, nrhs); };
     gmres_set(st, op->ctx, op->K, op->ps, fns, op->prec != CFIE_FP64,
               static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), rtol, restart,
               maxit, iters_out, relres_out, &result, op->stats);
@@ -458,7 +478,7 @@ static void batch_inner(cfie_batch* b, const double2* x, double2* y) {
 
 static void batch_fp64(cfie_batch* b, const double2* x, double2* y) {
   for (size_t k = 0; k < b->ops.size(); ++k)
-    matvec_fp64(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
+    matvec_residual(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
 }
 
 cfie_status cfie_batch_create(cfie_ctx* ctx, int count, cfie_op* const* ops, const int* nrhs,

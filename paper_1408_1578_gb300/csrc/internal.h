@@ -138,6 +138,7 @@ struct geom_dev {
 // Plan of the stored-matrix contraction over a list of jobs (stored.cu).
 struct gemm_plan {
   int grid = 0, njobs = 0, mt_total = 0, nsegs = 0, max_pitch = 0, launches_per_run = 0;
+  int stall = 0;   // fault injection for the failure tests (CFIE_FAULT_INJECT=tma_stall)
   dbuf jobs, tables, partial, bt, io, err;
   cudaGraphExec_t exec = nullptr;
 };
@@ -175,6 +176,10 @@ struct cfie_op {
   dbuf band;         // near-field band entries (complex64), n x (2 b + 1) per operator
   int band_b = -1;
   dbuf xin32, xin32b; // FP32 staging of the input (and hard-path helpers)
+
+  // FP64-accurate residual matvec in double-float arithmetic (sound-soft)
+  dbuf df_geo, df_band, df_part;
+  int df_b = -1;
 
   // FP32 matvec variant: 0 = autotuned, 1 = FP32-pipe contraction, 2 = tensor cores
   int variant = 0, tuned_nrhs = -1, tuned_choice = 1;
@@ -249,6 +254,12 @@ void gemm_plan_release(gemm_plan& G);
 void stored_prepare(cfie_op* op);
 void matvec_stored(cfie_op* op, const double2* x, double2* y, int nrhs);
 int stored_take_error(cfie_op* op);
+// matvec_df.cu
+void df_prepare(cfie_op* op);
+bool df_available(const cfie_op* op);
+void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs);
+// residual matvec of refined solves: double-float when available, else FP64
+void matvec_residual(cfie_op* op, const double2* x, double2* y, int nrhs);
 // matvec_tc.cu
 void matvec_fp32_tc(cfie_op* op, const double2* x, double2* y, int nrhs);
 int tc_take_error(cfie_op* op);

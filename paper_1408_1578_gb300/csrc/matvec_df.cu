@@ -1,0 +1,458 @@
+// FP64-accurate sound-soft matvec on the FP32 pipe (compensated arithmetic),
+// used for the true residuals of the refined solves.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, and the two residual
+// matvecs of a refined solve cost more than all its inner FP32 matvecs when
+// computed in FP64.  This kernel evaluates the same Nystrom entries as the FP64
+// kernel (sound-soft operator of eq. 1 of the paper, Kress log-split rule) in
+// double-float arithmetic: every quantity is an unevaluated sum hi + lo of two
+// FP32 numbers (~48 significant bits), products and sums use error-free
+// transformations (TwoProd with fmaf, TwoSum), and
+//  * Hankel's asymptotic expansion (A&S 9.2.5, 9.2.9, 9.2.10) carries its
+//    leading terms in double-float and the small corrections in FP32 (for
+//    omega r >= 40 the dropped terms are below 1e-13);
+//  * the phase omega r - pi/4 is reduced modulo 2 pi with a three-part
+//    constant, then sin / cos come from a 64-entry double-float table of
+//    sin(j pi/32), cos(j pi/32) and Taylor series of the remainder |d| <= pi/64;
+//  * pairs with omega r < 40 come from a band of entries evaluated in FP64.
+// Source sums use Dot2 (Ogita, Rump & Oishi) inside each 32-source tile and
+// FP64 additions across tiles.  Relative accuracy ~1e-13 (tests ask 1e-11).
+#include <algorithm>
+#include <climits>
+#include <cmath>
+
+#include "hankel64.cuh"
+#include "internal.h"
+
+namespace {
+
+constexpr int DTI = 64;
+constexpr int DTJ = 32;
+constexpr int DNT = 256;
+constexpr float kXD = 40.0f;   // asymptotic expansion in this kernel for omega r >= 40
+
+struct df {
+  float h, l;
+};
+
+__device__ __forceinline__ df quick(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ df dadd(df a, df b) {
+  const float s = a.h + b.h;
+  const float v = s - a.h;
+  const float e = (a.h - (s - v)) + (b.h - v) + a.l + b.l;
+  return quick(s, e);
+}
+__device__ __forceinline__ df dneg(df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df dsub(df a, df b) { return dadd(a, dneg(b)); }
+__device__ __forceinline__ df dmul(df a, df b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return quick(p, e);
+}
+__device__ __forceinline__ df dmulf(df a, float b) {
+  const float p = a.h * b;
+  float e = fmaf(a.h, b, -p);
+  e = fmaf(a.l, b, e);
+  return quick(p, e);
+}
+__host__ __device__ __forceinline__ df dmake(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+// 1 / a
+__device__ __forceinline__ df drcp(df a) {
+  const float q = 1.0f / a.h;
+  const float e = fmaf(-a.h, q, 1.0f) - a.l * q;   // 1 - a q
+  return quick(q, q * e);
+}
+// sqrt(a), a > 0
+__device__ __forceinline__ df dsqrt(df a) {
+  const float r = sqrtf(a.h);
+  const float e = fmaf(-r, r, a.h) + a.l;           // a - r^2
+  return quick(r, e * 0.5f / r);
+}
+
+// sin(j pi / 32), cos(j pi / 32) for j = -32 .. 32 as hi / lo pairs
+__constant__ float4 kSinCos[65] = {
+    {0.0f, 0.0f, -1.0f, 0.0f}, {-0.0980171412229538f, 8.933931927579408e-10f, -0.9951847195625305f, -7.109666189109021e-09f},
+    {-0.19509032368659973f, 1.670471427850373e-09f, -0.9807852506637573f, -2.9739473106360492e-08f}, {-0.290284663438797f, -1.3815665056426951e-08f, -0.9569403529167175f, 1.7184508038781132e-08f},
+    {-0.3826834261417389f, -6.2233507236442165e-09f, -0.9238795042037964f, -2.830748968563057e-08f}, {-0.4713967442512512f, 7.425253745196869e-09f, -0.8819212913513184f, 2.7002963420841297e-08f},
+    {-0.5555702447891235f, 1.1769521357507529e-08f, -0.8314695954322815f, -1.687026340846387e-08f}, {-0.6343932747840881f, -9.37955757507325e-09f, -0.7730104327201843f, -2.0642552556182636e-08f},
+    {-0.7071067690849304f, -1.2101617485882343e-08f, -0.7071067690849304f, -1.2101617485882343e-08f}, {-0.7730104327201843f, -2.0642552556182636e-08f, -0.6343932747840881f, -9.37955757507325e-09f},
+    {-0.8314695954322815f, -1.687026340846387e-08f, -0.5555702447891235f, 1.1769521357507529e-08f}, {-0.8819212913513184f, 2.7002963420841297e-08f, -0.4713967442512512f, 7.425253745196869e-09f},
+    {-0.9238795042037964f, -2.830748968563057e-08f, -0.3826834261417389f, -6.2233507236442165e-09f}, {-0.9569403529167175f, 1.7184508038781132e-08f, -0.290284663438797f, -1.3815665056426951e-08f},
+    {-0.9807852506637573f, -2.9739473106360492e-08f, -0.19509032368659973f, 1.670471427850373e-09f}, {-0.9951847195625305f, -7.109666189109021e-09f, -0.0980171412229538f, 8.933931927579408e-10f},
+    {-1.0f, 0.0f, 0.0f, 0.0f}, {-0.9951847195625305f, -7.109666189109021e-09f, 0.0980171412229538f, -8.933931927579408e-10f},
+    {-0.9807852506637573f, -2.9739473106360492e-08f, 0.19509032368659973f, -1.670471427850373e-09f}, {-0.9569403529167175f, 1.7184508038781132e-08f, 0.290284663438797f, 1.3815665056426951e-08f},
+    {-0.9238795042037964f, -2.830748968563057e-08f, 0.3826834261417389f, 6.2233507236442165e-09f}, {-0.8819212913513184f, 2.7002963420841297e-08f, 0.4713967442512512f, -7.425253745196869e-09f},
+    {-0.8314695954322815f, -1.687026340846387e-08f, 0.5555702447891235f, -1.1769521357507529e-08f}, {-0.7730104327201843f, -2.0642552556182636e-08f, 0.6343932747840881f, 9.37955757507325e-09f},
+    {-0.7071067690849304f, -1.2101617485882343e-08f, 0.7071067690849304f, 1.2101617485882343e-08f}, {-0.6343932747840881f, -9.37955757507325e-09f, 0.7730104327201843f, 2.0642552556182636e-08f},
+    {-0.5555702447891235f, 1.1769521357507529e-08f, 0.8314695954322815f, 1.687026340846387e-08f}, {-0.4713967442512512f, 7.425253745196869e-09f, 0.8819212913513184f, -2.7002963420841297e-08f},
+    {-0.3826834261417389f, -6.2233507236442165e-09f, 0.9238795042037964f, 2.830748968563057e-08f}, {-0.290284663438797f, -1.3815665056426951e-08f, 0.9569403529167175f, -1.7184508038781132e-08f},
+    {-0.19509032368659973f, 1.670471427850373e-09f, 0.9807852506637573f, 2.9739473106360492e-08f}, {-0.0980171412229538f, 8.933931927579408e-10f, 0.9951847195625305f, 7.109666189109021e-09f},
+    {0.0f, 0.0f, 1.0f, 0.0f}, {0.0980171412229538f, -8.933931927579408e-10f, 0.9951847195625305f, 7.109666189109021e-09f},
+    {0.19509032368659973f, -1.670471427850373e-09f, 0.9807852506637573f, 2.9739473106360492e-08f}, {0.290284663438797f, 1.3815665056426951e-08f, 0.9569403529167175f, -1.7184508038781132e-08f},
+    {0.3826834261417389f, 6.2233507236442165e-09f, 0.9238795042037964f, 2.830748968563057e-08f}, {0.4713967442512512f, -7.425253745196869e-09f, 0.8819212913513184f, -2.7002963420841297e-08f},
+    {0.5555702447891235f, -1.1769521357507529e-08f, 0.8314695954322815f, 1.687026340846387e-08f}, {0.6343932747840881f, 9.37955757507325e-09f, 0.7730104327201843f, 2.0642552556182636e-08f},
+    {0.7071067690849304f, 1.2101617485882343e-08f, 0.7071067690849304f, 1.2101617485882343e-08f}, {0.7730104327201843f, 2.0642552556182636e-08f, 0.6343932747840881f, 9.37955757507325e-09f},
+    {0.8314695954322815f, 1.687026340846387e-08f, 0.5555702447891235f, -1.1769521357507529e-08f}, {0.8819212913513184f, -2.7002963420841297e-08f, 0.4713967442512512f, -7.425253745196869e-09f},
+    {0.9238795042037964f, 2.830748968563057e-08f, 0.3826834261417389f, 6.2233507236442165e-09f}, {0.9569403529167175f, -1.7184508038781132e-08f, 0.290284663438797f, 1.3815665056426951e-08f},
+    {0.9807852506637573f, 2.9739473106360492e-08f, 0.19509032368659973f, -1.670471427850373e-09f}, {0.9951847195625305f, 7.109666189109021e-09f, 0.0980171412229538f, -8.933931927579408e-10f},
+    {1.0f, 0.0f, 0.0f, 0.0f}, {0.9951847195625305f, 7.109666189109021e-09f, -0.0980171412229538f, 8.933931927579408e-10f},
+    {0.9807852506637573f, 2.9739473106360492e-08f, -0.19509032368659973f, 1.670471427850373e-09f}, {0.9569403529167175f, -1.7184508038781132e-08f, -0.290284663438797f, -1.3815665056426951e-08f},
+    {0.9238795042037964f, 2.830748968563057e-08f, -0.3826834261417389f, -6.2233507236442165e-09f}, {0.8819212913513184f, -2.7002963420841297e-08f, -0.4713967442512512f, 7.425253745196869e-09f},
+    {0.8314695954322815f, 1.687026340846387e-08f, -0.5555702447891235f, 1.1769521357507529e-08f}, {0.7730104327201843f, 2.0642552556182636e-08f, -0.6343932747840881f, -9.37955757507325e-09f},
+    {0.7071067690849304f, 1.2101617485882343e-08f, -0.7071067690849304f, -1.2101617485882343e-08f}, {0.6343932747840881f, 9.37955757507325e-09f, -0.7730104327201843f, -2.0642552556182636e-08f},
+    {0.5555702447891235f, -1.1769521357507529e-08f, -0.8314695954322815f, -1.687026340846387e-08f}, {0.4713967442512512f, -7.425253745196869e-09f, -0.8819212913513184f, 2.7002963420841297e-08f},
+    {0.3826834261417389f, 6.2233507236442165e-09f, -0.9238795042037964f, -2.830748968563057e-08f}, {0.290284663438797f, 1.3815665056426951e-08f, -0.9569403529167175f, 1.7184508038781132e-08f},
+    {0.19509032368659973f, -1.670471427850373e-09f, -0.9807852506637573f, -2.9739473106360492e-08f}, {0.0980171412229538f, -8.933931927579408e-10f, -0.9951847195625305f, -7.109666189109021e-09f},
+    {0.0f, 0.0f, -1.0f, 0.0f},
+};
+__constant__ float kPi32H = 0.09817477315664291f, kPi32L = -2.7319617679211206e-09f;
+__constant__ float kPi4H = 0.7853981852531433f, kPi4L = -2.1855694143368964e-08f;
+__constant__ float kSq2PiH = 0.7978845834732056f, kSq2PiL = -2.2670340271702116e-08f;
+__constant__ float kI4PiH = 0.07957746833562851f, kI4PiL = 3.2103191216492633e-09f;
+__constant__ float kN6H = -0.1666666716337204f, kN6L = 4.967053879312289e-09f;
+// 2 pi = C1 + C2 + C3, C1 on 10 significant bits
+__constant__ float kC1 = 6.28125f, kC2 = 0.0019353071693331003f, kC3 = 1.0253376273028358e-11f;
+
+struct df_params {
+  int n, b, nrhs, splits, tiles_per_split;
+  df om, eta, hq;               // omega, eta, h / 4
+  const float4* g;              // per node: (x hi, x lo, y hi, y lo)
+  const float4* nrm;            // per node: (nu1 hi, nu1 lo, nu2 hi, nu2 lo)
+  const float2* sp;             // per node: |z'| (hi, lo)
+  const float2* w;              // Kress table w_d (hi, lo)
+  const float4* band;           // near entries (re hi, re lo, im hi, im lo), n x (2b + 1)
+  const double2* x;
+  double2* part;                // [split][k][i]
+};
+
+// one far pair (omega r >= 40): soft entry a = h K + w K1 (eq. 1) in double-float
+__device__ __forceinline__ float4 entry_df(const df_params& P, float4 gi, float4 gj, float4 nj,
+                                           float2 sj2, float2 w2) {
+  const df dx = dsub({gi.x, gi.y}, {gj.x, gj.y});
+  const df dy = dsub({gi.z, gi.w}, {gj.z, gj.w});
+  const df r2 = dadd(dmul(dx, dx), dmul(dy, dy));
+  const df r = dsqrt(r2);
+  const df rinv = drcp(r);
+  const df x = dmul(P.om, r);
+  // chi = x - pi/4 - 2 pi k, |chi| <= pi
+  const float k = rintf(fmaf(x.h, 0.15915493667125702f, -0.125f));
+  df chi = {fmaf(-k, kC1, x.h), x.l};                          // exact first step
+  const float p2 = k * kC2;
+  chi = dsub(chi, {p2, fmaf(k, kC2, -p2)});
+  chi = dsub(chi, {k * kC3, 0.f});
+  chi = dsub(chi, {kPi4H, kPi4L});
+  // sin / cos: chi = j pi / 32 + d
+  const float jf = rintf(chi.h * 10.185916f);
+  const float pj = jf * kPi32H;
+  df d = dsub(chi, {pj, fmaf(jf, kPi32H, -pj)});
+  d = dsub(d, {jf * kPi32L, 0.f});
+  const df d2 = dmul(d, d);
+  const float z = d2.h;
+  const df d3 = dmul(d2, d);
+  const df sb = dadd({kN6H, kN6L}, {z * (1.0f / 120.0f - z * (1.0f / 5040.0f)), 0.f});
+  const df sd = dadd(d, dmul(d3, sb));                          // sin d
+  const df cb = dadd({-0.5f, 0.f}, {z * (1.0f / 24.0f - z * (1.0f / 720.0f)), 0.f});
+  const df cd = dadd({1.0f, 0.f}, dmul(d2, cb));                // cos d
+  const float4 tj = kSinCos[(int)jf + 32];
+  const df sj = {tj.x, tj.y}, cj = {tj.z, tj.w};
+  const df sn = dadd(dmul(sj, cd), dmul(cj, sd));
+  const df cs = dsub(dmul(cj, cd), dmul(sj, sd));
+  // asymptotic expansion, t = 1/x
+  const df t = drcp(x);
+  const float t2 = t.h * t.h;
+  const df P0 = quick(1.0f, t2 * (-0.0703125f + t2 * (0.112152099609375f +
+                              t2 * (-0.5725014209747314f + t2 * 6.074042001273483f))));
+  const df P1 = quick(1.0f, t2 * (0.1171875f + t2 * (-0.144195556640625f +
+                              t2 * (0.6765925884246826f + t2 * -6.883914268109947f))));
+  const df Q0 = dadd({-0.125f * t.h, -0.125f * t.l},
+                     {t.h * t2 * (0.0732421875f + t2 * (-0.22710800170898438f +
+                                  t2 * 1.7277275025844574f)), 0.f});
+  const df Q1 = dadd(dmulf(t, 0.375f),
+                     {t.h * t2 * (-0.1025390625f + t2 * (0.2775764465332031f +
+                                  t2 * -1.993531733751297f)), 0.f});
+  const df amp = dmul({kSq2PiH, kSq2PiL}, dsqrt(t));
+  const df J0 = dmul(amp, dsub(dmul(P0, cs), dmul(Q0, sn)));
+  const df Y0 = dmul(amp, dadd(dmul(P0, sn), dmul(Q0, cs)));
+  const df J1 = dmul(amp, dadd(dmul(P1, sn), dmul(Q1, cs)));
+  const df Y1 = dmul(amp, dsub(dmul(Q1, sn), dmul(P1, cs)));
+  // c = (z_i - z_j) . nu~_j / r,  es = eta |z'_j|,  oc = omega c
+  const df c = dmul(dadd(dmul(dx, {nj.x, nj.y}), dmul(dy, {nj.z, nj.w})), rinv);
+  const df es = dmul(P.eta, {sj2.x, sj2.y});
+  const df oc = dmul(P.om, c);
+  const df wq = dmul({w2.x, w2.y}, {kI4PiH, kI4PiL});
+  const df re = dsub(dmul(P.hq, dsub(dmul(es, J0), dmul(oc, Y1))), dmul(wq, dmul(oc, J1)));
+  const df im = dadd(dmul(P.hq, dadd(dmul(oc, J1), dmul(es, Y0))), dmul(wq, dmul(es, J0)));
+  return make_float4(re.h, re.l, im.h, im.l);
+}
+
+// (s, e) += (ah + al)(xh + xl): TwoProd + TwoSum, errors gathered in e
+__device__ __forceinline__ void dot2_term(float& s, float& e, float ah, float al, float xh,
+                                          float xl) {
+  const float p = ah * xh;
+  float pe = fmaf(ah, xh, -p);
+  pe = fmaf(ah, xl, pe);
+  pe = fmaf(al, xh, pe);
+  const float t = s + p;
+  const float v = t - s;
+  e += ((s - (t - v)) + (p - v)) + pe;
+  s = t;
+}
+
+template <int RB>
+struct df_smem {
+  float4 A[DTI][DTJ + 1];
+  float4 X[DTJ][RB];
+};
+
+template <int RB>
+__global__ void __launch_bounds__(DNT) k_pair_df(df_params P) {
+  constexpr int RQ = RB / (DNT / DTI);
+  extern __shared__ __align__(16) unsigned char raw[];
+  df_smem<RB>& S = *reinterpret_cast<df_smem<RB>*>(raw);
+  const int n = P.n, tid = threadIdx.x;
+  const int i0 = blockIdx.x * DTI, split = blockIdx.y, rb0 = blockIdx.z * RB;
+  const int rbn = min(RB, P.nrhs - rb0);
+  const int ntiles = (n + DTJ - 1) / DTJ;
+  const int t_begin = split * P.tiles_per_split;
+  const int t_end = min(ntiles, t_begin + P.tiles_per_split);
+  const int il2 = tid % DTI, rg = tid / DTI;
+  const int bw = 2 * P.b + 1;
+  double2 acc[RQ];
+#pragma unroll
+  for (int q = 0; q < RQ; ++q) acc[q] = make_double2(0.0, 0.0);
+
+  for (int t = t_begin; t < t_end; ++t) {
+    const int j0 = t * DTJ;
+    __syncthreads();
+    for (int e = tid; e < DTJ * RB; e += DNT) {
+      const int jl = e / RB, r = e % RB, j = j0 + jl;
+      double2 v = make_double2(0.0, 0.0);
+      if (j < n && r < rbn) v = P.x[(size_t)(rb0 + r) * n + j];
+      const float rh = (float)v.x, ih = (float)v.y;
+      S.X[jl][r] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+    }
+    // entries: warp handles rows warp + 8 q, lane = source
+    for (int e = tid; e < DTI * DTJ; e += DNT) {
+      const int il = e / DTJ, jl = e % DTJ;
+      const int i = i0 + il, j = j0 + jl;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < n && j < n) {
+        int d = i - j;
+        if (d < 0) d += n;
+        const int dd = d <= P.b ? d : (d >= n - P.b ? d - n : INT_MAX);
+        if (dd != INT_MAX)
+          a = P.band[(size_t)i * bw + dd + P.b];
+        else
+          a = entry_df(P, P.g[i], P.g[j], P.nrm[j], P.sp[j], P.w[d]);
+      }
+      S.A[il][jl] = a;
+    }
+    __syncthreads();
+    float4 t4[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) t4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int jn = min(DTJ, n - j0);
+    for (int jl = 0; jl < jn; ++jl) {
+      const float4 a = S.A[il2][jl];
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        const float4 x = S.X[jl][rg + 4 * q];
+        dot2_term(t4[q].x, t4[q].y, a.x, a.y, x.x, x.y);     // + ar xr
+        dot2_term(t4[q].x, t4[q].y, -a.z, -a.w, x.z, x.w);   // - ai xi
+        dot2_term(t4[q].z, t4[q].w, a.x, a.y, x.z, x.w);     // + ar xi
+        dot2_term(t4[q].z, t4[q].w, a.z, a.w, x.x, x.y);     // + ai xr
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+      acc[q].x += (double)t4[q].x + (double)t4[q].y;
+      acc[q].y += (double)t4[q].z + (double)t4[q].w;
+    }
+  }
+  const int i = i0 + il2;
+  if (i < n) {
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+      const int r = rg + 4 * q;
+      if (r < rbn) P.part[((size_t)split * P.nrhs + rb0 + r) * n + i] = acc[q];
+    }
+  }
+}
+
+__global__ void k_reduce_df(int n, int nrhs, int splits, const double2* __restrict__ part,
+                            double2* __restrict__ y) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t tot = (size_t)n * nrhs;
+  if (e >= tot) return;
+  double sx = 0.0, sy = 0.0;
+  for (int s = 0; s < splits; ++s) {
+    const double2 p = part[(size_t)s * tot + e];
+    sx += p.x;
+    sy += p.y;
+  }
+  y[e] = make_double2(sx, sy);
+}
+
+// set-up: split geometry / tables, band width for omega r < kXD, FP64 band
+__global__ void k_df_geo(int n, geom_dev g, const double* __restrict__ w, float4* __restrict__ go,
+                         float4* __restrict__ no, float2* __restrict__ so,
+                         float2* __restrict__ wo) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const df x = dmake(g.x[i]), y = dmake(g.y[i]), a = dmake(g.nx[i]), b = dmake(g.ny[i]);
+  const df s = dmake(g.sp[i]), ww = dmake(w[i]);
+  go[i] = make_float4(x.h, x.l, y.h, y.l);
+  no[i] = make_float4(a.h, a.l, b.h, b.l);
+  so[i] = make_float2(s.h, s.l);
+  wo[i] = make_float2(ww.h, ww.l);
+}
+
+__global__ void __launch_bounds__(256)
+k_df_scan(int n, double omega, geom_dev g, int* __restrict__ bmax) {
+  __shared__ float sx[256], sy[256];
+  const int i = blockIdx.x * 256 + threadIdx.x;
+  const float xi = i < n ? (float)g.x[i] : 0.f, yi = i < n ? (float)g.y[i] : 0.f;
+  const float lim = (float)((kXD * 1.01) / omega);
+  const float lim2 = lim * lim;
+  int best = 0;
+  for (int j0 = 0; j0 < n; j0 += 256) {
+    __syncthreads();
+    const int jj = j0 + threadIdx.x;
+    sx[threadIdx.x] = jj < n ? (float)g.x[jj] : 0.f;
+    sy[threadIdx.x] = jj < n ? (float)g.y[jj] : 0.f;
+    __syncthreads();
+    if (i < n) {
+      const int jn = min(256, n - j0);
+      for (int q = 0; q < jn; ++q) {
+        const float dx = xi - sx[q], dy = yi - sy[q];
+        if (dx * dx + dy * dy < lim2) {
+          int d = i - (j0 + q);
+          if (d < 0) d = -d;
+          best = max(best, min(d, n - d));
+        }
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(bmax, best);
+}
+
+__global__ void k_df_band(int n, int b, double omega, double eta, geom_dev g,
+                          const double* __restrict__ wtab, const double2* __restrict__ diag,
+                          float4* __restrict__ band) {
+  const int bw = 2 * b + 1;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * bw) return;
+  const int i = (int)(e / bw);
+  const int dd = (int)(e % bw) - b;
+  int j = (i - dd) % n;
+  if (j < 0) j += n;
+  double2 a, unused;
+  if (j == i) {
+    a = diag[i];
+  } else {
+    int d = i - j;
+    if (d < 0) d += n;
+    pair_entries_fp64<0>(g.x[i] - g.x[j], g.y[i] - g.y[j], omega, eta, 2.0 * CFIE_PI / n, wtab[d],
+                         g.nx[j], g.ny[j], g.sp[j], g.nx[i], g.ny[i], g.sp[i], a, unused);
+  }
+  const df re = dmake(a.x), im = dmake(a.y);
+  band[e] = make_float4(re.h, re.l, im.h, im.l);
+}
+
+unsigned nbk(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
+
+template <int RB>
+int launch_df(cfie_op* op, df_params P, int nrhs) {
+  const int n = op->n;
+  const int rowtiles = (n + DTI - 1) / DTI, slices = (nrhs + RB - 1) / RB;
+  const int ntiles = (n + DTJ - 1) / DTJ;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->ctx->device);
+  int splits = std::max(1, std::min(ntiles, (4 * sms + rowtiles * slices - 1) / (rowtiles * slices)));
+  const int tps = (ntiles + splits - 1) / splits;
+  splits = (ntiles + tps - 1) / tps;
+  P.splits = splits;
+  P.tiles_per_split = tps;
+  op->df_part.reserve(sizeof(double2) * (size_t)splits * nrhs * n);
+  P.part = op->df_part.as<double2>();
+  const size_t smem = sizeof(df_smem<RB>);
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_pair_df<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem));
+  {
+    prof_scope ps(op->ctx, CFIE_K_MATVEC_FP64);
+    k_pair_df<RB><<<dim3(rowtiles, splits, slices), DNT, smem, op->ctx->stream>>>(P);
+    CFIE_CHECK_LAUNCH();
+  }
+  return splits;
+}
+
+}  // namespace
+
+void df_prepare(cfie_op* op) {
+  const int n = op->n;
+  cudaStream_t st = op->ctx->stream;
+  dbuf scan;
+  scan.reserve(16);
+  CFIE_CHECK_CUDA(cudaMemsetAsync(scan.p, 0, 16, st));
+  k_df_scan<<<nbk(n), 256, 0, st>>>(n, op->omega, op->g, scan.as<int>());
+  CFIE_CHECK_LAUNCH();
+  int hb = 0;
+  CFIE_CHECK_CUDA(cudaMemcpyAsync(&hb, scan.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
+  const int b = std::min(std::max(1, hb), n / 2);
+  const size_t bw = 2 * (size_t)b + 1;
+  if ((size_t)n * bw * sizeof(float4) > ((size_t)4 << 30)) {
+    op->df_b = -1;   // band too wide: residuals fall back to the FP64 kernel
+    return;
+  }
+  op->df_b = b;
+  op->df_geo.reserve((sizeof(float4) * 2 + sizeof(float2) * 2) * (size_t)n);
+  op->df_band.reserve(sizeof(float4) * (size_t)n * bw);
+  char* base = op->df_geo.as<char>();
+  k_df_geo<<<nbk(n), 256, 0, st>>>(n, op->g, op->wtab.as<double>(), (float4*)base,
+                                    (float4*)(base + sizeof(float4) * n),
+                                    (float2*)(base + 2 * sizeof(float4) * n),
+                                    (float2*)(base + (2 * sizeof(float4) + sizeof(float2)) * n));
+  CFIE_CHECK_LAUNCH();
+  k_df_band<<<nbk((size_t)n * bw), 256, 0, st>>>(n, b, op->omega, op->eta, op->g,
+                                                  op->wtab.as<double>(), op->diag.as<double2>(),
+                                                  op->df_band.as<float4>());
+  CFIE_CHECK_LAUNCH();
+  CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+bool df_available(const cfie_op* op) {
+  return op->bc == CFIE_SOUND_SOFT && op->df_b > 0;
+}
+
+void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
+  const int n = op->n;
+  df_params P{};
+  P.n = n;
+  P.b = op->df_b;
+  P.nrhs = nrhs;
+  P.om = dmake(op->omega);
+  P.eta = dmake(op->eta);
+  P.hq = dmake(0.25 * op->h);
+  char* base = op->df_geo.as<char>();
+  P.g = (const float4*)base;
+  P.nrm = (const float4*)(base + sizeof(float4) * n);
+  P.sp = (const float2*)(base + 2 * sizeof(float4) * n);
+  P.w = (const float2*)(base + (2 * sizeof(float4) + sizeof(float2)) * n);
+  P.band = op->df_band.as<float4>();
+  P.x = x;
+  const int splits = nrhs > 16 ? launch_df<64>(op, P, nrhs) : launch_df<16>(op, P, nrhs);
+  const size_t tot = (size_t)n * nrhs;
+  k_reduce_df<<<nbk(tot), 256, 0, op->ctx->stream>>>(n, nrhs, splits, op->df_part.as<double2>(),
+                                                      y);
+  CFIE_CHECK_LAUNCH();
+}

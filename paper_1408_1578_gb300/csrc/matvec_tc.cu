@@ -43,9 +43,9 @@ constexpr int TSTAGES = 2;
 // that bias near 2e-6 whatever n is, while the running sums (FP32 adds, rounded
 // to nearest) and the FP64 segment reduction add only unbiased rounding.
 constexpr int CK = 8;
-constexpr int NPROD = 8;     // producer warps
-constexpr int WTMA = 8, WMMA = 9, WEPI0 = 10;
-constexpr int TNT = 14 * 32;
+constexpr int NPROD = 16;    // producer warps
+constexpr int WTMA = NPROD, WMMA = NPROD + 1, WEPI0 = NPROD + 2;
+constexpr int TNT = (NPROD + 6) * 32;
 
 struct tc_params : omega32 {
   int n, b, ktiles;
@@ -59,6 +59,7 @@ struct tc_smem {
   __nv_bfloat16 A[TSTAGES][4][TBM * TBK];   // hi_re, hi_im, lo_re, lo_im
   __nv_bfloat16 B[TSTAGES][4][NP * TBK];    // B1 hi, B1 lo, B2 hi, B2 lo
   float acc[NP][TBM];                       // epilogue running sums, column-major
+  float txh[TBM], txl[TBM], tyh[TBM], tyl[TBM], tnx[TBM], tny[TBM], tsp[TBM];  // targets
   uint64_t full[TSTAGES], empty[TSTAGES], tfull[2], tempty[2];
   uint32_t tmem_base;
   int abort;
@@ -112,11 +113,27 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
   const uint32_t tmem = S.tmem_base;
 
   if (warp < NPROD) {
-    // ---- pair-entry producers: rows warp + 8 q, lane = source within the tile
+    // ---- pair-entry producers: rows warp + NPROD q, lane = source within the tile
     int it = 0;
     for (int s = sb; s < se; ++s) {
       const int4 sg = segs[s];
       const int m0 = sg.y * TBM;
+      // stage the target geometry of this warp's own rows (warp + NPROD q): no
+      // other warp reads them, so a warp-level barrier is enough
+      __syncwarp();
+      if (lane < TBM / NPROD) {
+        const int r = warp + NPROD * lane;
+        const int i = m0 + r;
+        const bool ok = i < n;
+        S.txh[r] = ok ? P.g.xh[i] : 0.f;
+        S.txl[r] = ok ? P.g.xl[i] : 0.f;
+        S.tyh[r] = ok ? P.g.yh[i] : 0.f;
+        S.tyl[r] = ok ? P.g.yl[i] : 0.f;
+        S.tnx[r] = ok ? P.g.nx[i] : 0.f;
+        S.tny[r] = ok ? P.g.ny[i] : 0.f;
+        S.tsp[r] = ok ? P.g.sp[i] : 1.f;
+      }
+      __syncwarp();
       for (int k = sg.z; k < sg.w; ++k, ++it) {
         const int st = it % TSTAGES;
         if (*(volatile int*)&S.abort) break;
@@ -149,8 +166,8 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
             if (dd != INT_MAX) {
               a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
             } else {
-              pair_entries_fp32<0>(P, P.g.xh[i], P.g.xl[i], P.g.yh[i], P.g.yl[i], P.g.nx[i],
-                                   P.g.ny[i], P.g.sp[i], sxh, sxl, syh, syl, snx, sny, ssp,
+              pair_entries_fp32<0>(P, S.txh[il], S.txl[il], S.tyh[il], S.tyl[il], S.tnx[il],
+                                   S.tny[il], S.tsp[il], sxh, sxl, syh, syl, snx, sny, ssp,
                                    P.w32[d], a, unused);
             }
           }

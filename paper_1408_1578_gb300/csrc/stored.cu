@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -126,7 +127,7 @@ template <int NP>
 __global__ void __launch_bounds__(192, 1)
 k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ segs,
                   const int* __restrict__ cbeg, float2* __restrict__ partial,
-                  int* __restrict__ err) {
+                  int* __restrict__ err, int stall) {
   constexpr int NR = NP / 2;
   constexpr uint32_t TMEM_COLS = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));
   constexpr uint32_t STAGE_BYTES = 4u * BM * BK * 2u + 4u * NP * BK * 2u;
@@ -175,6 +176,9 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
           }
           mbar_arrive_expect_tx(&S.full[st], STAGE_BYTES);
           S.issued[st] = (it / STAGES) & 1;
+          // fault injection for the failure tests: the first stage's copies are
+          // never issued, so the wait on its barrier runs out
+          if (stall && it == 0) continue;
           const int kc = k * BK;
 #pragma unroll
           for (int p = 0; p < 4; ++p) tma_load_2d(S.A[st][p], &J->ta, &S.full[st], kc, p * J->n + m0);
@@ -453,6 +457,10 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
   CFIE_CHECK_CUDA(cudaMemsetAsync(G.err.p, 0, sizeof(int), st));
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
 
+  // CFIE_FAULT_INJECT=tma_stall (failure tests only) makes the contraction's
+  // bounded waits run out
+  const char* fi = std::getenv("CFIE_FAULT_INJECT");
+  G.stall = (fi && std::strcmp(fi, "tma_stall") == 0) ? 1 : 0;
   // capture the three launches once; replays read x / y from the io slot
   const size_t smem = pgemm_smem_bytes<kNP>();
   CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_gemm_persistent<kNP>,
@@ -467,7 +475,7 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
     k_prep_b_jobs<<<dim3(nblk(max_pitch), kNP, G.njobs), 256, 0, cs>>>(dj, io, kNP);
     k_gemm_persistent<kNP><<<grid, 192, smem, cs>>>(
         dj, reinterpret_cast<const int4*>(tb + o_segs), reinterpret_cast<const int*>(tb + o_cbeg),
-        G.partial.as<float2>(), G.err.as<int>());
+        G.partial.as<float2>(), G.err.as<int>(), G.stall);
     k_reduce_jobs<<<dim3(mt_total, kNR), BM, 0, cs>>>(
         dj, reinterpret_cast<const int2*>(tb + o_mtj), reinterpret_cast<const int2*>(tb + o_mts),
         G.partial.as<float2>(), io, kNR);

@@ -32,6 +32,7 @@ if ROOT not in sys.path:
 
 METRIC = "CFIE kernel-pair evals/s"
 UNIT = "pair-evals/s"
+SERVE_METRIC = "CFIE solves/s at 1e-8 residual (served; p50/p99 latency beside it)"
 
 
 def parse():
@@ -47,6 +48,7 @@ def parse():
     p.add_argument("--rtol", type=float, default=None)
     p.add_argument("--n", type=int, default=None, help="override the workload's n (profiling)")
     p.add_argument("--nrhs", type=int, default=None, help="override the number of directions")
+    p.add_argument("--oracle-budget", type=float, default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -141,18 +143,78 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# Algorithmic work per (target, source) pair of each kernel class, counted
-# from the implemented per-pair formula (see the design doc for the derivation).
-def pair_flops(precision, bc, nrhs):
-    # FP32 fused kernel: per-pair evaluation counted in FP32 operations plus
-    # 8 flops per right-hand side for the complex multiply-add
-    from paper_1408_1578_gb300 import cfie  # noqa: F401  (library must be present)
-    per_rhs = 8 if bc == "soft" else 32
-    return PAIR_EVAL_FLOPS[(precision, bc)] + per_rhs * nrhs
+# Algorithmic work per (target, source) pair of each kernel class, counted from
+# the kernels' per-pair formulas (FP32 add / mul / fma / rint = 1 operation,
+# IEEE division or square root = 8).
+SMS, FP32_LANES = 152, 128
+ENTRY_OPS = {"soft": 101, "hard": 110}   # FP32 pair entries (two-float phase, asymptotics)
+SUM_OPS = {"soft": 4, "hard": 8}         # FP32 FMAs per pair and right-hand side (CUDA-core sums)
+DF_ENTRY_OPS = 677                       # double-float pair entry of the residual kernel
+DF_TERM_OPS = 48                         # Dot2 complex product-sum per pair and right-hand side
+FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)
 
 
-PAIR_EVAL_FLOPS = {("fp32", "soft"): 96, ("fp32", "hard"): 110,
-                   ("fp64", "soft"): 0, ("fp64", "hard"): 0}
+def kernel_rooflines(kt, spec, stats, peaks, src, n, solves_timed):
+    """Roofline entry per timed kernel class: achieved = algorithmic work of the
+    class in the timed region / its CUDA-event time."""
+    nrhs, bc, prec = spec["nrhs"], spec["bc"], spec["precision"]
+    clock_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
+    fp32_peak = SMS * FP32_LANES * clock_hz / 1e12        # T lane-ops/s
+    out = {}
+    for cls, (ms, launches) in kt.items():
+        if launches == 0 or ms <= 0:
+            continue
+        sec = ms / 1e3
+        avg = sec / launches
+        if cls == "matvec_fp32":
+            v = stats.get("matvec_variant", 1)
+            ops = ENTRY_OPS[bc] + (SUM_OPS[bc] * nrhs if v == 1 else 0)
+            a = ops * n * n / avg / 1e12
+            out[cls] = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "Top/s",
+                        "frac": a / fp32_peak, "traffic": None,
+                        "work": f"{ops} FP32 ops per pair (variant {v}: "
+                                + ("source sums on the tensor cores, not counted" if v == 2
+                                   else f"{SUM_OPS[bc]} FMA per pair per right-hand side") + ")",
+                        "peak_source": f"152 SMs x 128 FP32 lanes x {clock_hz / 1e6:.0f} MHz"}
+        elif cls == "matvec_fp64" and prec != "fp64" and bc == "soft":
+            ops = DF_ENTRY_OPS + DF_TERM_OPS * nrhs
+            a = ops * n * n / avg / 1e12
+            out[cls] = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "Top/s",
+                        "frac": a / fp32_peak, "traffic": None,
+                        "work": f"double-float residual: {DF_ENTRY_OPS} + {DF_TERM_OPS} x nrhs "
+                                "FP32 ops per pair",
+                        "peak_source": f"152 SMs x 128 FP32 lanes x {clock_hz / 1e6:.0f} MHz"}
+        elif cls == "matvec_fp64":
+            dfma = (4 if bc == "soft" else 8) * nrhs
+            a = dfma * n * n / avg / 1e12
+            pk = FP64_NOMINAL_TFLOPS / 2
+            out[cls] = {"bound": "alu", "achieved": a, "peak": pk, "unit": "T DFMA/s",
+                        "frac": a / pk, "traffic": None,
+                        "work": f"{dfma} DFMA per pair (source sums only: a lower bound)",
+                        "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (not measured)"}
+        elif cls == "matvec_tensor":
+            pitch = (n + 63) // 64 * 64
+            b = n * pitch * 8
+            a = b / avg / 1e9
+            out[cls] = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": a / peaks["hbm_gbs"], "traffic": None,
+                        "work": "stored bf16 hi/lo matrix (8 bytes per entry) read once per matvec",
+                        "peak_source": src}
+        elif cls == "arnoldi":
+            elems = stats.get("arnoldi_elems", 0) * solves_timed
+            esize = 8 if stats.get("basis_fp32") else 16
+            b = 4 * elems * esize
+            a = b / sec / 1e9
+            e = {"bound": "hbm", "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                 "frac": a / peaks["hbm_gbs"], "traffic": None,
+                 "work": f"CGS2: 4 passes over the basis, {esize} bytes per element",
+                 "peak_source": src}
+            if esize == 16:
+                f = 20 * elems / sec / 1e12
+                e["fp64_ops"] = {"achieved": f, "peak": FP64_NOMINAL_TFLOPS / 2,
+                                 "unit": "T FP64 ops/s", "frac": f / (FP64_NOMINAL_TFLOPS / 2)}
+            out[cls] = e
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -247,7 +309,8 @@ def run_ours(args, rank, world):
     if rank == 0:
         dom = max(ktimes, key=lambda k: ktimes[k][0])
         peaks, src = measured_peaks()
-        roof = roofline(dom, ktimes[dom], spec, stats, peaks, src, n)
+        roofs = kernel_rooflines(ktimes, spec, stats, peaks, src, n, args.steps)
+        roof = dict(roofs.get(dom, {}), kernel=dom) if dom in roofs else None
         value = pairs_all / (ms_max / 1e3)
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -255,12 +318,8 @@ def run_ours(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32+f64", "fp64": "f64", "tensor": "bf16x3+f64"}[spec["precision"]],
             "data": "synthetic",
-            "config": {"workload": f"{spec['name']}: {spec['curve']} {bc} n={n} omega={w} "
-                                   f"eta=omega nrhs={nrhs}",
-                       "curve": spec["curve"], "bc": bc, "n": n, "omega": w, "nrhs": nrhs,
-                       "precision": spec["precision"], "rtol": spec["rtol"],
-                       "restart": spec["restart"], "parallelism": f"replicas{world}",
-                       "l2": "flushed between steps" if flush_l2 else "Krylov basis larger than L2"},
+            "config": dict(single_config(spec, world),
+                           l2="flushed between steps" if flush_l2 else "Krylov basis larger than L2"),
             "solves_per_s": solves * world / (ms_max / 1e3),
             "max_relres": worst,
             "iterations": [int(v) for v in its[:4]],
@@ -272,36 +331,11 @@ def run_ours(args, rank, world):
             "kernel_ms": {k: round(v[0], 3) for k, v in ktimes.items()},
             "kernel_launches": {k: v[1] for k, v in ktimes.items()},
             "roofline": roof,
+            "kernel_rooflines": roofs,
             "clocks": clk,
         }
     ctx.close()
     return result
-
-
-def roofline(dom, kt, spec, stats, peaks, src, n):
-    ms, launches = kt
-    if launches == 0:
-        return None
-    avg_s = ms / launches / 1e3
-    nrhs, bc = spec["nrhs"], spec["bc"]
-    if dom == "arnoldi":
-        # CGS2 streams the basis 4 times per step: bytes ~ 4 * (j+1) n nrhs 16
-        return {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": None, "traffic": None, "peak_source": src}
-    if dom in ("matvec_fp32",):
-        flops = PAIR_EVAL_FLOPS[("fp32", bc)] + (8 if bc == "soft" else 32) * nrhs
-        achieved = flops * n * n / avg_s / 1e12
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"FP32 FMA units x max SM clock ({src} clock)"}
-    if dom == "matvec_fp64":
-        # pair evaluations per second against the FP64 rate: reported as pairs
-        achieved = n * n / avg_s
-        return {"bound": "alu", "kernel": dom, "achieved": achieved / 1e9, "peak": None,
-                "unit": "Gpair/s", "frac": None, "traffic": None,
-                "peak_source": "FP64 pair rate; see DESIGN.md"}
-    return None
 
 
 # ---------------------------------------------------------------------------
@@ -334,6 +368,34 @@ def oracle_sample(spec, rows_count):
     return pairs, time.perf_counter() - t0
 
 
+ORACLE_THREAD_ENV = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                                        "BLIS_NUM_THREADS", "NUMEXPR_NUM_THREADS")}
+
+
+def oracle_single_core(args, budget_s):
+    """Time the oracle on one host core in a fresh interpreter (BLAS pinned to
+    one thread); returns (pairs, seconds, rows)."""
+    env = dict(os.environ, **ORACLE_THREAD_ENV)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-budget", str(budget_s),
+           "--workload", args.workload]
+    for k in ("precision", "n", "nrhs"):
+        v = getattr(args, k)
+        if v is not None:
+            cmd += [f"--{k}", str(v)]
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + out.stderr[-500:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return r["pairs"], r["seconds"], r["rows"]
+
+
+def oracle_budget_main(args):
+    spec = workload(args.workload, args.precision, args.n, args.nrhs)
+    rows = cpu_rows_for(spec, budget_s=args.oracle_budget)
+    p, s = oracle_sample(spec, rows)
+    print(json.dumps({"pairs": p, "seconds": s, "rows": rows}), flush=True)
+
+
 def cpu_rows_for(spec, budget_s=12.0):
     pairs, secs = oracle_sample(spec, 4)
     rate = pairs / max(secs, 1e-6)
@@ -341,10 +403,62 @@ def cpu_rows_for(spec, budget_s=12.0):
     return rows
 
 
+def reference_spec(args):
+    """Workload the oracle samples: the named single-operator workload, or for
+    the batch one star of the batch (its n, omega, 32 directions)."""
+    if args.workload == "stars":
+        from paper_1408_1578_gb300 import inputs
+        st = inputs.random_stars(count=args.count or 256, seed=1408, n_lo=512, n_hi=16384,
+                                 nrhs=32)[0]
+        return {"name": "stars (first operator of the batch)", "curve": "star",
+                "params": {"a": list(st["a"]), "b": list(st["b"])}, "n": st["n"],
+                "omega": st["omega"], "nrhs": st["nrhs"], "bc": "soft", "precision": "tensor"}
+    return workload(args.workload, args.precision, args.n, args.nrhs)
+
+
+def run_reference_serve(args):
+    """Served workload on the host: the oracle's dense LU solve of the smallest
+    requests of the stream (assembly + LU + back substitution), solves/s."""
+    import numpy as np
+
+    from oracle import geometry, operators, solvers
+    from paper_1408_1578_gb300 import inputs
+    count = args.count or 32
+    reqs = inputs.poisson_requests(count=count, rate=200.0, seed=1578, n_lo=1024, n_hi=65536)
+    order = [int(i) for i in np.argsort([r["n"] for r in reqs])]
+    solves, secs, done = 0, 0.0, []
+    for step in range(args.warmup + args.steps):
+        r = reqs[order[step % len(order)]]
+        t0 = time.perf_counter()
+        c = geometry.fourier_star(r["n"], r["a"], r["b"])
+        A = operators.cfie_matrix(c, r["omega"], r["omega"], r["bc"])
+        F = operators.plane_wave_rhs(c, r["omega"], inputs.directions(r["nrhs"]), r["bc"])
+        solvers.lu_solve(A, F)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            solves += r["nrhs"]
+            secs += dt
+            done.append(f"n={r['n']} {r['bc']} nrhs={r['nrhs']}")
+    value = solves / secs
+    return {
+        "impl": "reference", "metric": SERVE_METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": serve_config(count),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "dense LU solves of the smallest requests: " + "; ".join(done)},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    spec = workload(args.workload, args.precision, args.n, args.nrhs)
+    if args.workload == "serve":
+        return run_reference_serve(args)
+    spec = reference_spec(args)
     rows = cpu_rows_for(spec, budget_s=10.0 / max(1, args.steps + args.warmup) * 3)
     for _ in range(args.warmup):
         oracle_sample(spec, max(4, rows // 4))
@@ -354,19 +468,39 @@ def run_reference(args, rank, world):
         tot_pairs += p
         tot_s += s
     value = tot_pairs / tot_s
-    sample = f"{rows} rows x {spec['n']} sources of the {spec['name']} operator per step"
+    sample = (f"{rows} rows x {spec['n']} sources of the {spec['name']} operator, "
+              f"{spec['nrhs']} right-hand sides, per step")
+    cfg = stars_config(args.count or 256) if args.workload == "stars" else \
+        single_config(workload(args.workload, args.precision, args.n, args.nrhs), world)
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": f"{spec['name']}: {spec['curve']} {spec['bc']} n={spec['n']} "
-                               f"omega={spec['omega']} eta=omega nrhs={spec['nrhs']}",
-                   "parallelism": "host cores (oracle)"},
+        "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+
+
+def single_config(spec, world):
+    return {"workload": f"{spec['name']}: {spec['curve']} {spec['bc']} n={spec['n']} "
+                        f"omega={spec['omega']} eta=omega nrhs={spec['nrhs']}",
+            "curve": spec["curve"], "bc": spec["bc"], "n": spec["n"], "omega": spec["omega"],
+            "nrhs": spec["nrhs"], "precision": spec["precision"], "rtol": spec["rtol"],
+            "restart": spec["restart"], "parallelism": f"replicas{world}"}
+
+
+def stars_config(count):
+    return {"workload": f"stars: {count} random stars, n log-uniform [512, 16384], "
+                        "10 ppw, 32 directions, stored tensor-core, lockstep GMRES",
+            "rtol": 1e-8, "restart": 80, "parallelism": "replicas1"}
+
+
+def serve_config(count):
+    return {"workload": f"serve: {count} Poisson requests at 200/s, soft/hard, random "
+                        "stars, n log-uniform [1024, 65536], 1..64 directions",
+            "rtol": 1e-8, "restart": 80, "parallelism": "replicas1"}
 
 
 # ---------------------------------------------------------------------------
@@ -424,6 +558,12 @@ def allreduce_sum(v, world):
 
 def main():
     args = parse()
+    if args.oracle_budget is not None:
+        oracle_budget_main(args)
+        return
+    if args.impl == "reference":
+        # the oracle runs on one host core: pin BLAS before numpy loads
+        os.environ.update(ORACLE_THREAD_ENV)
     if args.workload in ("stars", "serve") and args.impl == "ours":
         out = run_stars(args) if args.workload == "stars" else run_serve(args)
         print(json.dumps(out), flush=True)
@@ -435,11 +575,11 @@ def main():
         out = run_ours(args, rank, world)
         if rank == 0 and out is not None and world == 1:
             spec = workload(args.workload, args.precision, args.n, args.nrhs)
-            rows = cpu_rows_for(spec, budget_s=12.0)
-            p, s = oracle_sample(spec, rows)
+            p, s, rows = oracle_single_core(args, 12.0)
             out["cpu_baseline"] = {"value": p / s, "unit": UNIT, "cores": 1, "kind": "oracle",
                                    "sample": f"{rows} rows x {spec['n']} sources of the "
-                                             f"{spec['name']} operator ({s:.1f} s)"}
+                                             f"{spec['name']} operator, {spec['nrhs']} "
+                                             f"right-hand sides ({s:.1f} s, one thread)"}
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if _PG is not None:
@@ -516,9 +656,7 @@ def run_stars(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "bf16x3+f64", "data": "synthetic",
-           "config": {"workload": f"stars: {count} random stars, n log-uniform [512, 16384], "
-                                  "10 ppw, 32 directions, stored tensor-core, lockstep GMRES",
-                      "sum_n2": pairs_mv, "rtol": 1e-8, "restart": 80},
+           "config": dict(stars_config(count), sum_n2=pairs_mv),
            "solves_per_s": solves / (ms / 1e3), "max_relres": worst, "solve_stats": stats,
            "gpu_launches": int(launches), "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
            "kernel_launches": {k: v[1] for k, v in kt.items()}, "roofline": roof, "clocks": clk}
@@ -577,12 +715,10 @@ def run_serve(args):
         row["speedup"] = row["fp64_alone_s"] / row["fp32_alone_s"]
         cmp.append(row)
     one.close()
-    return {"metric": "CFIE solves/s and p50/p99 latency at 1e-8 residual (served)",
+    return {"metric": SERVE_METRIC,
             "value": solves / makespan, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
             "higher_is_better": True, "data": "synthetic", "dtype": "f32+f64",
-            "config": {"workload": f"serve: {count} Poisson requests at 200/s, soft/hard, random "
-                                   "stars, n log-uniform [1024, 65536], 1..64 directions",
-                       "slots": 8, "budget_bytes": int(0.8 * free)},
+            "config": dict(serve_config(count), slots=8, budget_bytes=int(0.8 * free)),
             "all_done": bool(ok), "requests_per_s": count / makespan, "makespan_s": makespan,
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),

@@ -182,6 +182,15 @@ cfie_status cfie_apply_residual(cfie_op* op, const void* x_dev, void* y_dev, int
 cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nrhs, double rtol,
                              int restart, int maxit, int* iters_out, double* relres_out);
 
+/* Precision of the Krylov basis of the inner solves of the refined precisions
+ * (CFIE_FP32_REFINED, CFIE_TENSOR_REFINED): fp32 = 1 (default) keeps the inner
+ * basis, its inner products and updates in FP32 (the inner operator is only
+ * FP32-accurate, and GB300's FP64 rate is a small fraction of its FP32 rate);
+ * fp32 = 0 keeps them in FP64.  The Hessenberg matrix, Givens rotations,
+ * least-squares solve, solution update, true residuals and the whole FP64
+ * precision stay FP64 either way.  CFIE_EINVAL for a null op or another value. */
+cfie_status cfie_op_set_inner_basis(cfie_op* op, int fp32);
+
 /* Counters of the last cfie_gmres_solve on this operator. */
 typedef struct {
   int cycles;            /* GMRES cycles (restarts + 1) summed over refinement steps */
@@ -189,6 +198,14 @@ typedef struct {
   int inner_matvecs;     /* block matvecs in the operator's precision */
   int fp64_matvecs;      /* block FP64 matvecs (true residuals) */
   int arnoldi_steps;     /* Arnoldi steps (max over right-hand sides) */
+  int matvec_variant;    /* kernel of the last inner matvec: 0 FP64 pair kernel,
+                            1 FP32 pair kernel with CUDA-core source sums, 2 FP32
+                            pair kernel with tensor-core source sums, 3 stored
+                            matrix on the tensor cores */
+  int basis_fp32;        /* 1 if the inner solves kept their Krylov basis in FP32 */
+  long long arnoldi_elems; /* basis elements read by one orthogonalisation pass,
+                              summed over the Arnoldi steps (CGS2 makes four
+                              passes: two inner products, two updates) */
 } cfie_solve_stats;
 cfie_status cfie_op_last_stats(const cfie_op* op, cfie_solve_stats* out);
 
@@ -216,6 +233,8 @@ cfie_status cfie_batch_apply(cfie_batch* batch, const void* x_dev, void* y_dev);
 cfie_status cfie_batch_gmres_solve(cfie_batch* batch, const void* f_dev, void* x_dev, double rtol,
                                    int restart, int maxit, int* iters_out, double* relres_out);
 cfie_status cfie_batch_last_stats(const cfie_batch* batch, cfie_solve_stats* out);
+/* As cfie_op_set_inner_basis, for the lockstep solves of a batch. */
+cfie_status cfie_batch_set_inner_basis(cfie_batch* batch, int fp32);
 void cfie_batch_destroy(cfie_batch* batch);
 
 

@@ -56,7 +56,8 @@ class cfie_server_counters(ctypes.Structure):
 class cfie_solve_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("inner_matvecs", ctypes.c_int), ("fp64_matvecs", ctypes.c_int),
-                ("arnoldi_steps", ctypes.c_int)]
+                ("arnoldi_steps", ctypes.c_int), ("matvec_variant", ctypes.c_int),
+                ("basis_fp32", ctypes.c_int), ("arnoldi_elems", ctypes.c_longlong)]
 
 
 class CfieError(RuntimeError):
@@ -93,6 +94,7 @@ SIGNATURES = {
     "cfie_apply_residual": (_I, [_P, _P, _P, _I]),
     "cfie_op_set_variant": (_I, [_P, _I]),
     "cfie_gmres_solve": (_I, [_P, _P, _P, _I, _D, _I, _I, _IP, _DP]),
+    "cfie_op_set_inner_basis": (_I, [_P, _I]),
     "cfie_op_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
     "cfie_ctx_set_profiling": (_I, [_P, _I]),
     "cfie_ctx_kernel_times": (_I, [_P, _DP, _LLP]),
@@ -102,6 +104,7 @@ SIGNATURES = {
     "cfie_batch_apply": (_I, [_P, _P, _P]),
     "cfie_batch_gmres_solve": (_I, [_P, _P, _P, _D, _I, _I, _IP, _DP]),
     "cfie_batch_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
+    "cfie_batch_set_inner_basis": (_I, [_P, _I]),
     "cfie_batch_destroy": (None, [_P]),
     "cfie_server_create": (_I, [_I, ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
     "cfie_server_submit": (_I, [_P, ctypes.POINTER(cfie_request), ctypes.POINTER(ctypes.c_longlong)]),
@@ -287,6 +290,10 @@ class Batch:
                        "cfie_batch_last_stats")
         return {k: getattr(s, k) for k, _ in s._fields_}
 
+    def set_inner_basis(self, fp32):
+        self.ctx.check(self.ctx.lib.cfie_batch_set_inner_basis(self.h, 1 if fp32 else 0),
+                       "cfie_batch_set_inner_basis")
+
     def block(self, vec, k):
         """View of operator k's (nrhs_k, n_k) block of a flat batch vector."""
         o = int(self.offsets[k])
@@ -416,6 +423,11 @@ class Operator:
     def set_variant(self, variant):
         """0 = autotuned, 1 = FP32-pipe sums, 2 = tensor-core sums."""
         self.ctx.check(self.ctx.lib.cfie_op_set_variant(self.h, int(variant)), "cfie_op_set_variant")
+
+    def set_inner_basis(self, fp32):
+        """Refined precisions: inner Krylov basis in FP32 (True, default) or FP64."""
+        self.ctx.check(self.ctx.lib.cfie_op_set_inner_basis(self.h, 1 if fp32 else 0),
+                       "cfie_op_set_inner_basis")
 
     def apply_residual(self, x, y, nrhs=None):
         nrhs = x.numel() // self.n if nrhs is None else nrhs

@@ -34,10 +34,25 @@ constexpr int AE = 8;            // elements per thread
 constexpr int CH = AT * AE;      // elements per chunk
 constexpr int MAXJ = 512;        // largest restart length
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename S>
+__device__ __forceinline__ S warp_sum(S v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// Element type of a Krylov basis: FP64 (double2) or, for the inner solves of
+// the refined precisions, FP32 (float2).
+template <typename T> struct basis_t;
+template <> struct basis_t<double2> {
+  using S = double;
+  static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
+template <> struct basis_t<float2> {
+  using S = float;
+  static __device__ __forceinline__ float2 make(double a, double b) {
+    return make_float2((float)a, (float)b);
+  }
+};
 
 struct chunk_ref {
   size_t base;
@@ -55,34 +70,37 @@ __device__ __forceinline__ chunk_ref chunk_of(const pset_dev& ps, int item) {
 }
 
 // partial[slot][jj] = sum over the chunk of conj(V[jj]) w, jj = 0..J
+// (products and the in-chunk sums in the basis precision, chunk partials FP64)
+template <typename T>
 __global__ void __launch_bounds__(AT)
-k_dots(int J, const double2* __restrict__ V, size_t L, const double2* __restrict__ w,
+k_dots(int J, const T* __restrict__ V, size_t L, const T* __restrict__ w,
        const int* __restrict__ act, pset_dev ps, double2* __restrict__ partial) {
+  using S = typename basis_t<T>::S;
   extern __shared__ double2 red[];  // [J+1][AT/32]
   const chunk_ref c = chunk_of(ps, blockIdx.x);
   if (!act[c.p]) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double2 wr[AE];
+  T wr[AE];
 #pragma unroll
   for (int e = 0; e < AE; ++e) {
     const int q = e * AT + threadIdx.x;
-    wr[e] = q < c.cnt ? w[c.base + q] : make_double2(0.0, 0.0);
+    wr[e] = q < c.cnt ? w[c.base + q] : basis_t<T>::make(0.0, 0.0);
   }
   for (int jj = 0; jj <= J; ++jj) {
-    const double2* v = V + (size_t)jj * L + c.base;
-    double re = 0.0, im = 0.0;
+    const T* v = V + (size_t)jj * L + c.base;
+    S re = 0, im = 0;
 #pragma unroll
     for (int e = 0; e < AE; ++e) {
       const int q = e * AT + threadIdx.x;
       if (q < c.cnt) {
-        const double2 a = v[q];
+        const T a = v[q];
         re = fma(a.x, wr[e].x, fma(a.y, wr[e].y, re));
         im = fma(a.x, wr[e].y, fma(-a.y, wr[e].x, im));
       }
     }
     re = warp_sum(re);
     im = warp_sum(im);
-    if (lane == 0) red[jj * (AT / 32) + warp] = make_double2(re, im);
+    if (lane == 0) red[jj * (AT / 32) + warp] = make_double2((double)re, (double)im);
   }
   __syncthreads();
   for (int jj = threadIdx.x; jj <= J; jj += AT) {
@@ -121,35 +139,41 @@ __global__ void k_dots_reduce(int J, int m, int col, int first, const int* __res
 }
 
 // w -= sum_jj V[jj] h[p][jj] on one chunk; optional |w|^2 partial per chunk
+template <typename T>
 __global__ void __launch_bounds__(AT)
-k_update(int J, const double2* __restrict__ V, size_t L, const double2* __restrict__ hbuf,
-         const int* __restrict__ act, pset_dev ps, double2* __restrict__ w,
+k_update(int J, const T* __restrict__ V, size_t L, const double2* __restrict__ hbuf,
+         const int* __restrict__ act, pset_dev ps, T* __restrict__ w,
          double* __restrict__ nrm_partial) {
-  extern __shared__ double2 hs[];
+  using S = typename basis_t<T>::S;
+  extern __shared__ double2 hs_raw[];
+  T* hs = reinterpret_cast<T*>(hs_raw);
   const chunk_ref c = chunk_of(ps, blockIdx.x);
   if (!act[c.p]) return;
-  for (int jj = threadIdx.x; jj <= J; jj += AT) hs[jj] = hbuf[(size_t)c.p * (J + 1) + jj];
+  for (int jj = threadIdx.x; jj <= J; jj += AT) {
+    const double2 h = hbuf[(size_t)c.p * (J + 1) + jj];
+    hs[jj] = basis_t<T>::make(h.x, h.y);
+  }
   __syncthreads();
-  double2 acc[AE];
+  T acc[AE];
 #pragma unroll
   for (int e = 0; e < AE; ++e) {
     const int q = e * AT + threadIdx.x;
-    acc[e] = q < c.cnt ? w[c.base + q] : make_double2(0.0, 0.0);
+    acc[e] = q < c.cnt ? w[c.base + q] : basis_t<T>::make(0.0, 0.0);
   }
   for (int jj = 0; jj <= J; ++jj) {
-    const double2* v = V + (size_t)jj * L + c.base;
-    const double2 hh = hs[jj];
+    const T* v = V + (size_t)jj * L + c.base;
+    const T hh = hs[jj];
 #pragma unroll
     for (int e = 0; e < AE; ++e) {
       const int q = e * AT + threadIdx.x;
       if (q < c.cnt) {
-        const double2 a = v[q];
+        const T a = v[q];
         acc[e].x -= a.x * hh.x - a.y * hh.y;
         acc[e].y -= a.x * hh.y + a.y * hh.x;
       }
     }
   }
-  double ss = 0.0;
+  S ss = 0;
 #pragma unroll
   for (int e = 0; e < AE; ++e) {
     const int q = e * AT + threadIdx.x;
@@ -160,8 +184,8 @@ k_update(int J, const double2* __restrict__ V, size_t L, const double2* __restri
   }
   if (nrm_partial) {
     __shared__ double red[AT / 32];
-    ss = warp_sum(ss);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    const double sd = warp_sum((double)ss);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sd;
     __syncthreads();
     if (threadIdx.x == 0) {
       double t = 0.0;
@@ -221,10 +245,12 @@ __global__ void k_givens(int P, int m, int j, const int* __restrict__ act, pset_
   res[p] = hypot(g1.x, g1.y);
 }
 
-// vout = w / ||w|| per problem (0 on breakdown)
+// vout = w / ||w|| per problem (0 on breakdown); vin (optional) = the same
+// vector in FP64, the input of the next matvec
+template <typename T>
 __global__ void __launch_bounds__(AT)
 k_scale(const int* __restrict__ act, pset_dev ps, const double* __restrict__ hn,
-        const double2* __restrict__ w, double2* __restrict__ vout) {
+        const T* __restrict__ w, T* __restrict__ vout, double2* __restrict__ vin) {
   const chunk_ref c = chunk_of(ps, blockIdx.x);
   if (!act[c.p]) return;
   const double h = hn[c.p];
@@ -233,16 +259,19 @@ k_scale(const int* __restrict__ act, pset_dev ps, const double* __restrict__ hn,
   for (int e = 0; e < AE; ++e) {
     const int q = e * AT + threadIdx.x;
     if (q < c.cnt) {
-      const double2 v = w[c.base + q];
-      vout[c.base + q] = make_double2(v.x * inv, v.y * inv);
+      const T v = w[c.base + q];
+      const T o = basis_t<T>::make(v.x * inv, v.y * inv);
+      vout[c.base + q] = o;
+      if (vin) vin[c.base + q] = make_double2(o.x, o.y);
     }
   }
 }
 
-// v0 = r / beta per problem
+// v0 = r / beta per problem (vin as in k_scale)
+template <typename T>
 __global__ void __launch_bounds__(AT)
 k_start(const int* __restrict__ act, pset_dev ps, const double* __restrict__ beta,
-        const double2* __restrict__ r, double2* __restrict__ v0) {
+        const double2* __restrict__ r, T* __restrict__ v0, double2* __restrict__ vin) {
   const chunk_ref c = chunk_of(ps, blockIdx.x);
   const double b = beta[c.p];
   const double inv = (act[c.p] && b > 0.0) ? 1.0 / b : 0.0;
@@ -251,7 +280,25 @@ k_start(const int* __restrict__ act, pset_dev ps, const double* __restrict__ bet
     const int q = e * AT + threadIdx.x;
     if (q < c.cnt) {
       const double2 v = r[c.base + q];
-      v0[c.base + q] = make_double2(v.x * inv, v.y * inv);
+      const T o = basis_t<T>::make(v.x * inv, v.y * inv);
+      v0[c.base + q] = o;
+      if (vin) vin[c.base + q] = make_double2(o.x, o.y);
+    }
+  }
+}
+
+// w32 = w (FP64 matvec output to the FP32 basis precision)
+__global__ void __launch_bounds__(AT)
+k_to32(const int* __restrict__ act, pset_dev ps, const double2* __restrict__ w,
+       float2* __restrict__ w32) {
+  const chunk_ref c = chunk_of(ps, blockIdx.x);
+  if (!act[c.p]) return;
+#pragma unroll
+  for (int e = 0; e < AE; ++e) {
+    const int q = e * AT + threadIdx.x;
+    if (q < c.cnt) {
+      const double2 v = w[c.base + q];
+      w32[c.base + q] = make_float2((float)v.x, (float)v.y);
     }
   }
 }
@@ -288,9 +335,10 @@ __global__ void k_lsq(int P, int m, const int* __restrict__ kd, const double2* _
   }
 }
 
-// x += sum_{jj < kd[p]} V[jj] y[p][jj]
+// x += sum_{jj < kd[p]} V[jj] y[p][jj] (sums in FP64 for either basis type)
+template <typename T>
 __global__ void __launch_bounds__(AT)
-k_xupdate(int m, const int* __restrict__ kd, pset_dev ps, const double2* __restrict__ V, size_t L,
+k_xupdate(int m, const int* __restrict__ kd, pset_dev ps, const T* __restrict__ V, size_t L,
           const double2* __restrict__ y, double2* __restrict__ x) {
   const chunk_ref c = chunk_of(ps, blockIdx.x);
   const int K = kd[c.p];
@@ -303,14 +351,14 @@ k_xupdate(int m, const int* __restrict__ kd, pset_dev ps, const double2* __restr
   }
   for (int jj = 0; jj < K; ++jj) {
     const double2 yy = y[(size_t)c.p * m + jj];
-    const double2* v = V + (size_t)jj * L + c.base;
+    const T* v = V + (size_t)jj * L + c.base;
 #pragma unroll
     for (int e = 0; e < AE; ++e) {
       const int q = e * AT + threadIdx.x;
       if (q < c.cnt) {
-        const double2 a = v[q];
-        acc[e].x += a.x * yy.x - a.y * yy.y;
-        acc[e].y += a.x * yy.y + a.y * yy.x;
+        const T a = v[q];
+        acc[e].x += (double)a.x * yy.x - (double)a.y * yy.y;
+        acc[e].y += (double)a.x * yy.y + (double)a.y * yy.x;
       }
     }
   }
@@ -390,19 +438,37 @@ __global__ void k_zero(size_t len, double2* __restrict__ x) {
 
 unsigned blocks_for(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
 
+// basis elements one orthogonalisation pass of step j reads: sum over the
+// active problems of (j + 1) n_p
+long long arnoldi_elems(const pset& ps, const std::vector<int>& act, int j) {
+  long long e = 0;
+  for (int p = 0; p < ps.P; ++p)
+    if (act[p]) e += (long long)(j + 1) * ps.len[p];
+  return e;
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 struct ws {
+  bool f32 = false;                  // FP32 basis (inner solves of refined precisions)
+  float2 *V32 = nullptr, *w32 = nullptr;
+  double2* vin = nullptr;            // FP64 copy of the newest FP32 basis vector
   double2 *V, *H, *gv, *sn, *w, *hbuf, *y, *part;
   double *cs, *hn, *res, *nrmp, *rr, *ff, *norms;
   int *act, *kd;
 };
 
-ws workspace(krylov_ws& K, const pset& ps, int m) {
+ws workspace(krylov_ws& K, const pset& ps, int m, bool f32) {
   const int P = ps.P, Q = ps.Q;
   const size_t L = ps.L;
-  K.V.reserve(sizeof(double2) * L * (m + 1));
+  if (f32) {
+    K.V32.reserve(sizeof(float2) * L * (m + 1));
+    K.w32.reserve(sizeof(float2) * L);
+    K.vin.reserve(sizeof(double2) * L);
+  } else {
+    K.V.reserve(sizeof(double2) * L * (m + 1));
+  }
   K.w.reserve(sizeof(double2) * L);
   K.H.reserve(sizeof(double2) * (size_t)P * (m + 1) * m);
   size_t sm = 0;
@@ -428,7 +494,11 @@ ws workspace(krylov_ws& K, const pset& ps, int m) {
   K.small.reserve(sm);
   char* b = K.small.as<char>();
   ws W;
-  W.V = K.V.as<double2>();
+  W.f32 = f32;
+  W.V = f32 ? nullptr : K.V.as<double2>();
+  W.V32 = f32 ? K.V32.as<float2>() : nullptr;
+  W.w32 = f32 ? K.w32.as<float2>() : nullptr;
+  W.vin = f32 ? K.vin.as<double2>() : nullptr;
   W.H = K.H.as<double2>();
   W.w = K.w.as<double2>();
   W.gv = (double2*)(b + o_gv);
@@ -488,13 +558,16 @@ void gmres_cycle(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps, c
   CFIE_CHECK_CUDA(cudaMemcpyAsync(W.act, act.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
   CFIE_CHECK_CUDA(
       cudaMemcpyAsync(W.norms, beta.data(), sizeof(double) * P, cudaMemcpyHostToDevice, st));
-  k_start<<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.norms, r, W.V);
+  if (W.f32)
+    k_start<float2><<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.norms, r, W.V32, W.vin);
+  else
+    k_start<double2><<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.norms, r, W.V, nullptr);
   CFIE_CHECK_LAUNCH();
   k_g_init<<<blocks_for((size_t)P * (m + 1)), 256, 0, st>>>(P, m, W.act, W.norms, W.gv);
   CFIE_CHECK_LAUNCH();
   stats.cycles++;
   for (int j = 0; j < m; ++j) {
-    double2* vj = W.V + (size_t)j * L;
+    const double2* vj = W.f32 ? W.vin : W.V + (size_t)j * L;
     if (inner) {
       stats.inner_matvecs++;
       fns.inner(vj, W.w);
@@ -505,20 +578,37 @@ void gmres_cycle(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps, c
     {
       prof_scope ps_(ctx, CFIE_K_ARNOLDI);
       const size_t red_smem = sizeof(double2) * (j + 1) * (AT / 32);
+      if (W.f32) {
+        k_to32<<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.w, W.w32);
+        CFIE_CHECK_LAUNCH();
+      }
       for (int pass = 0; pass < 2; ++pass) {
-        k_dots<<<ps.Q, AT, red_smem, st>>>(j, W.V, L, W.w, W.act, ps.dev, W.part);
+        if (W.f32)
+          k_dots<float2><<<ps.Q, AT, red_smem, st>>>(j, W.V32, L, W.w32, W.act, ps.dev, W.part);
+        else
+          k_dots<double2><<<ps.Q, AT, red_smem, st>>>(j, W.V, L, W.w, W.act, ps.dev, W.part);
         CFIE_CHECK_LAUNCH();
         k_dots_reduce<<<P, 128, 0, st>>>(j, m, j, pass == 0, W.act, ps.dev, W.part, W.hbuf, W.H);
         CFIE_CHECK_LAUNCH();
-        k_update<<<ps.Q, AT, sizeof(double2) * (j + 1), st>>>(
-            j, W.V, L, W.hbuf, W.act, ps.dev, W.w, pass == 1 ? W.nrmp : nullptr);
+        if (W.f32)
+          k_update<float2><<<ps.Q, AT, sizeof(double2) * (j + 1), st>>>(
+              j, W.V32, L, W.hbuf, W.act, ps.dev, W.w32, pass == 1 ? W.nrmp : nullptr);
+        else
+          k_update<double2><<<ps.Q, AT, sizeof(double2) * (j + 1), st>>>(
+              j, W.V, L, W.hbuf, W.act, ps.dev, W.w, pass == 1 ? W.nrmp : nullptr);
         CFIE_CHECK_LAUNCH();
       }
       k_givens<<<blocks_for(P, 64), 64, 0, st>>>(P, m, j, W.act, ps.dev, W.nrmp, W.H, W.cs, W.sn,
                                                  W.gv, W.hn, W.res);
       CFIE_CHECK_LAUNCH();
-      k_scale<<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.hn, W.w, W.V + (size_t)(j + 1) * L);
+      if (W.f32)
+        k_scale<float2><<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.hn, W.w32,
+                                             W.V32 + (size_t)(j + 1) * L, W.vin);
+      else
+        k_scale<double2><<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.hn, W.w,
+                                              W.V + (size_t)(j + 1) * L, nullptr);
       CFIE_CHECK_LAUNCH();
+      stats.arnoldi_elems += arnoldi_elems(ps, act, j);
     }
     CFIE_CHECK_CUDA(
         cudaMemcpyAsync(K.host, W.res, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
@@ -547,7 +637,10 @@ void gmres_cycle(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps, c
   CFIE_CHECK_CUDA(cudaMemcpyAsync(W.kd, kd.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
   k_lsq<<<blocks_for(P, 64), 64, 0, st>>>(P, m, W.kd, W.H, W.gv, W.y);
   CFIE_CHECK_LAUNCH();
-  k_xupdate<<<ps.Q, AT, 0, st>>>(m, W.kd, ps.dev, W.V, L, W.y, x);
+  if (W.f32)
+    k_xupdate<float2><<<ps.Q, AT, 0, st>>>(m, W.kd, ps.dev, W.V32, L, W.y, x);
+  else
+    k_xupdate<double2><<<ps.Q, AT, 0, st>>>(m, W.kd, ps.dev, W.V, L, W.y, x);
   CFIE_CHECK_LAUNCH();
   // host vectors copied above must stay alive until the copies ran
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -569,6 +662,7 @@ void pset_build(pset& ps, const std::vector<size_t>& off, const std::vector<int>
   }
   ps.Q = (int)items.size();
   ps.L = L;
+  ps.len = len;
   const size_t bytes = sizeof(size_t) * ps.P + sizeof(int) * 3 * ps.P + sizeof(int2) * ps.Q + 128;
   ps.buf.reserve(bytes);
   char* b = ps.buf.as<char>();
@@ -603,7 +697,9 @@ void gmres_set(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps,
   const size_t L = ps.L;
   int m = restart > 0 ? restart : maxit;
   m = std::max(1, std::min(m, std::min(maxit, MAXJ)));
-  ws W = workspace(K, ps, m);
+  const bool f32 = refined && fns.basis32;
+  stats.basis_fp32 = f32 ? 1 : 0;
+  ws W = workspace(K, ps, m, f32);
   K.r.reserve(sizeof(double2) * L);
   double2* r = K.r.as<double2>();
   double2* ax = W.w;  // matvec output scratch (free between cycles)

@@ -146,15 +146,18 @@ void matvec_residual(cfie_op* op, const double2* x, double2* y, int nrhs) {
 void apply_inner(cfie_op* op, const double2* x, double2* y, int nrhs) {
   switch (op->prec) {
     case CFIE_FP64:
+      op->stats.matvec_variant = 0;
       matvec_fp64(op, x, y, nrhs);
       break;
     case CFIE_FP32_REFINED:
-      if (tuned_variant(op, x, y, nrhs) == 2)
+      op->stats.matvec_variant = tuned_variant(op, x, y, nrhs);
+      if (op->stats.matvec_variant == 2)
         matvec_fp32_tc(op, x, y, nrhs);
       else
         matvec_fp32(op, x, y, nrhs);
       break;
     case CFIE_TENSOR_REFINED:
+      op->stats.matvec_variant = 3;
       matvec_stored(op, x, y, nrhs);
       break;
     default:
@@ -418,6 +421,7 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
     solve_fns fns;
     fns.inner = [op, nrhs](const double2* a, double2* b) { apply_inner(op, a, b, nrhs); };
     fns.fp64 = [op, nrhs](const double2* a, double2* b) { matvec_residual(op, a, b, nrhs); };
+    fns.basis32 = op->basis32 != 0;
     gmres_set(st, op->ctx, op->K, op->ps, fns, op->prec != CFIE_FP64,
               static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), rtol, restart,
               maxit, iters_out, relres_out, &result, op->stats);
@@ -429,6 +433,18 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
   });
   if (st != CFIE_OK) return st;
   return result;
+}
+
+cfie_status cfie_op_set_inner_basis(cfie_op* op, int fp32) {
+  if (!op || (fp32 != 0 && fp32 != 1)) return CFIE_EINVAL;
+  op->basis32 = fp32;
+  return CFIE_OK;
+}
+
+cfie_status cfie_batch_set_inner_basis(cfie_batch* b, int fp32) {
+  if (!b || (fp32 != 0 && fp32 != 1)) return CFIE_EINVAL;
+  b->basis32 = fp32;
+  return CFIE_OK;
 }
 
 cfie_status cfie_op_last_stats(const cfie_op* op, cfie_solve_stats* out) {
@@ -554,9 +570,11 @@ cfie_status cfie_batch_gmres_solve(cfie_batch* b, const void* f_dev, void* x_dev
     solve_fns fns;
     fns.inner = [b](const double2* a, double2* c) { batch_inner(b, a, c); };
     fns.fp64 = [b](const double2* a, double2* c) { batch_fp64(b, a, c); };
+    fns.basis32 = b->basis32 != 0;
     gmres_set(b->ctx->stream, b->ctx, b->K, b->ps, fns, b->prec != CFIE_FP64,
               static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), rtol, restart,
               maxit, iters_out, relres_out, &result, b->stats);
+    b->stats.matvec_variant = b->all_stored ? 3 : b->ops.empty() ? 0 : b->ops[0]->stats.matvec_variant;
     if (b->all_stored && gemm_plan_take_error(b->plan, b->ctx))
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     if (result == CFIE_ENOCONV) b->ctx->err = "GMRES reached maxit before rtol";

@@ -107,6 +107,7 @@ struct pset_dev {
 struct pset {
   int P = 0, Q = 0;
   size_t L = 0;
+  std::vector<int> len;   // host copy of the segment lengths
   pset_dev dev{};
   dbuf buf;
 };
@@ -114,6 +115,7 @@ struct pset {
 // Krylov workspace (basis, Hessenberg, Givens data, residual vectors)
 struct krylov_ws {
   dbuf V, H, w, r, d, rin, small;
+  dbuf V32, w32, vin;       // FP32 basis of the inner solves (refined precisions)
   double* host = nullptr;   // pinned mirror of per-problem norms
   int host_cap = 0;
 };
@@ -123,6 +125,7 @@ struct krylov_ws {
 struct solve_fns {
   std::function<void(const double2*, double2*)> inner;   // the fast (FP32 / tensor) matvec
   std::function<void(const double2*, double2*)> fp64;    // the FP64 matvec (true residuals)
+  bool basis32 = true;   // refined precisions: inner Krylov basis in FP32
 };
 
 // Device-side geometry of an operator (structure of arrays, FP64 masters).
@@ -183,6 +186,7 @@ struct cfie_op {
 
   // FP32 matvec variant: 0 = autotuned, 1 = FP32-pipe contraction, 2 = tensor cores
   int variant = 0, tuned_nrhs = -1, tuned_choice = 1;
+  int basis32 = 1;   // inner Krylov basis in FP32 for the refined precisions
   tc_plan tc[2];   // 32- and 64-right-hand-side plans
 
   // stored path (CFIE_STORED): bf16 hi/lo planes of A and the contraction plan
@@ -207,6 +211,7 @@ struct cfie_batch {
   std::vector<long long> off;
   size_t L = 0;
   bool all_stored = false;
+  int basis32 = 1;
   cfie_precision prec = CFIE_FP64;
   gemm_plan plan;
   krylov_ws K;

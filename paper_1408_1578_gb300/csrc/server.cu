@@ -46,7 +46,9 @@ size_t footprint_bytes(const cfie_request& r) {
   const size_t m = (size_t)(r.restart > 0 ? r.restart : r.maxit);
   const size_t vec = n * k * 16;
   const size_t ops = r.bc == CFIE_SOUND_HARD ? 4 : 1;
-  size_t f = vec * (m + 1);           // Krylov basis
+  // Krylov basis: FP32 for the inner solves of the refined precisions (plus
+  // the FP32 work vector and the FP64 matvec input), FP64 otherwise
+  size_t f = r.precision == CFIE_FP64 ? vec * (m + 1) : vec / 2 * (m + 2) + vec;
   f += vec * 8;                       // w, r, d, rin, f, x, staging
   f += n * 129 * 8 * 2;               // near-field band (b <= 64), both operators
   f += vec / 2 * (16 * ops + 3);      // FP32 split partials and staging

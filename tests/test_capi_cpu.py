@@ -49,6 +49,9 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.cfie_discretise(None, 64, 1.0, 1.0, 0, 0, 0, None) == cfie.CFIE_EINVAL
     assert lib.cfie_apply(None, None, None, 1) == cfie.CFIE_EINVAL
     assert lib.cfie_gmres_solve(None, None, None, 1, 1e-6, 80, 100, None, None) == cfie.CFIE_EINVAL
+    assert lib.cfie_op_set_inner_basis(None, 1) == cfie.CFIE_EINVAL
+    assert lib.cfie_batch_set_inner_basis(None, 0) == cfie.CFIE_EINVAL
+    assert lib.cfie_op_set_variant(None, 1) == cfie.CFIE_EINVAL
     assert lib.cfie_last_error(None) == b"null context"
 
 

@@ -93,7 +93,8 @@ def test_batched_refined_solve_alone_and_in_the_mix(ctx, small_batch):
     b.close()
 
 
-def test_batch_of_matrix_free_fp32_operators(ctx):
+@pytest.mark.parametrize("basis32", [True, False])
+def test_batch_of_matrix_free_fp32_operators(ctx, basis32):
     from paper_1408_1578_gb300 import cfie
     specs = _stars(3, seed=9, n_lo=400, n_hi=1200, nrhs=4)
     ops = [ctx.fourier_star(s["a"], s["b"]).discretise(s["n"], s["omega"], precision="fp32")
@@ -106,8 +107,10 @@ def test_batch_of_matrix_free_fp32_operators(ctx):
         fs.append(f)
     f = _flat(fs)
     x = f.clone().zero_()
+    b.set_inner_basis(basis32)
     its, rel, _ = b.gmres_solve(f, x, rtol=1e-8, restart=40, maxit=2000)
     assert np.all(rel <= 1e-8)
+    assert b.last_stats()["basis_fp32"] == int(basis32)
     for k, s in enumerate(specs):
         c = geometry.fourier_star(s["n"], s["a"], s["b"])
         A = operators.soft_matrix(c, s["omega"], s["omega"])

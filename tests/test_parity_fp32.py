@@ -185,3 +185,31 @@ def test_tensor_core_variant_arguments(ctx):
     op64 = ctx.kite().discretise(256, 20.0, precision="fp64")
     with pytest.raises(cfie.CfieError):
         op64.set_variant(2)
+
+
+@pytest.mark.parametrize("bc", ["soft", "hard"])
+def test_refined_solve_basis_precisions(ctx, bc):
+    """The inner Krylov basis in FP32 (default) and in FP64 reach the same
+    FP64 solution; the counters say which basis ran."""
+    n, w, nrhs = 1500, 150.0, 6
+    c = geometry.kite(n)
+    A = operators.cfie_matrix(c, w, w, bc)
+    F = operators.plane_wave_rhs(c, w, inputs.directions(nrhs), bc)
+    Q = solvers.lu_solve(A, F).T
+    op = ctx.kite().discretise(n, w, bc=bc, precision="fp32")
+    got = {}
+    for fp32 in (True, False):
+        op.set_inner_basis(fp32)
+        x = zeros(nrhs, n)
+        its, rel, _ = op.gmres_solve(to_dev(F.T), x, rtol=1e-8, restart=40, maxit=3000)
+        st = op.last_stats()
+        assert st["basis_fp32"] == int(fp32)
+        assert st["arnoldi_elems"] > 0
+        assert np.all(rel <= 1e-8)
+        got[fp32] = to_host(x)
+        assert np.max(col_rel(got[fp32], Q)) < TOL_REFINED
+    assert np.max(col_rel(got[True], got[False])) < TOL_REFINED
+    op64 = ctx.kite().discretise(n, w, bc=bc, precision="fp64")
+    x = zeros(nrhs, n)
+    op64.gmres_solve(to_dev(F.T), x, rtol=1e-10, restart=40, maxit=3000)
+    assert op64.last_stats()["basis_fp32"] == 0 and op64.last_stats()["matvec_variant"] == 0

@@ -254,6 +254,7 @@ def run_ours(args, rank, world):
         geom.close()
         return its, rel, stats
 
+    pipes = ctx.measure_peaks()
     for _ in range(args.warmup):
         its, rel, stats = step()
     barrier(world)
@@ -332,6 +333,10 @@ def run_ours(args, rank, world):
             "kernel_launches": {k: v[1] for k, v in ktimes.items()},
             "roofline": roof,
             "kernel_rooflines": roofs,
+            "pipe_rates_measured": {"sms": pipes["sms"],
+                                    "fp32_fma_T_per_s": pipes["fp32_fma_per_s"] / 1e12,
+                                    "mufu_T_per_s": pipes["mufu_per_s"] / 1e12,
+                                    "fp64_fma_T_per_s": pipes["fp64_fma_per_s"] / 1e12},
             "clocks": clk,
         }
     ctx.close()

@@ -318,6 +318,21 @@ void cfie_server_destroy(cfie_server* server);
  * contexts).  Never fails. */
 long long cfie_launch_count(void);
 
+/* --- Pipe issue rates (the denominators of the arithmetic rooflines) ----- */
+
+/* Measured on the context's device with CUDA events: FP32 FMAs, MUFU
+ * reciprocal square roots and FP64 FMAs per second, each from eight
+ * independent dependency chains per thread on 8 CTAs of 256 threads per SM.
+ * Not part of the paper's method: it measures the hardware the kernels run
+ * on.  Synchronous; takes well under a second. */
+typedef struct {
+  int sms;
+  double fp32_fma_per_s;
+  double mufu_per_s;
+  double fp64_fma_per_s;
+} cfie_peaks;
+cfie_status cfie_measure_peaks(cfie_ctx* ctx, cfie_peaks* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,6 +60,11 @@ class cfie_solve_stats(ctypes.Structure):
                 ("basis_fp32", ctypes.c_int), ("arnoldi_elems", ctypes.c_longlong)]
 
 
+class cfie_peaks(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int), ("fp32_fma_per_s", ctypes.c_double),
+                ("mufu_per_s", ctypes.c_double), ("fp64_fma_per_s", ctypes.c_double)]
+
+
 class CfieError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {message}")
@@ -99,6 +104,7 @@ SIGNATURES = {
     "cfie_ctx_set_profiling": (_I, [_P, _I]),
     "cfie_ctx_kernel_times": (_I, [_P, _DP, _LLP]),
     "cfie_launch_count": (ctypes.c_longlong, []),
+    "cfie_measure_peaks": (_I, [_P, ctypes.POINTER(cfie_peaks)]),
     "cfie_batch_create": (_I, [_P, _I, ctypes.POINTER(_P), _IP, ctypes.POINTER(_P)]),
     "cfie_batch_length": (ctypes.c_longlong, [_P]),
     "cfie_batch_apply": (_I, [_P, _P, _P]),
@@ -194,6 +200,12 @@ class Context:
         self.check(self.lib.cfie_ctx_kernel_times(self.h, _dptr(ms), ln.ctypes.data_as(_LLP)),
                    "cfie_ctx_kernel_times")
         return {KERNEL_CLASS_NAMES[k]: (float(ms[k]), int(ln[k])) for k in range(CFIE_K_COUNT)}
+
+    def measure_peaks(self):
+        """Issue rates of the FP32 FMA, MUFU and FP64 FMA pipes (per second)."""
+        p = cfie_peaks()
+        self.check(self.lib.cfie_measure_peaks(self.h, ctypes.byref(p)), "cfie_measure_peaks")
+        return {k: getattr(p, k) for k, _ in p._fields_}
 
     def close(self):
         """Destroy the context; batches, operators and geometries made from it

@@ -435,6 +435,14 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
   return result;
 }
 
+cfie_status cfie_measure_peaks(cfie_ctx* ctx, cfie_peaks* out) {
+  if (!ctx || !out) return CFIE_EINVAL;
+  return guarded(ctx, [&] {
+    set_device(ctx);
+    measure_peaks(ctx, out);
+  });
+}
+
 cfie_status cfie_op_set_inner_basis(cfie_op* op, int fp32) {
   if (!op || (fp32 != 0 && fp32 != 1)) return CFIE_EINVAL;
   op->basis32 = fp32;

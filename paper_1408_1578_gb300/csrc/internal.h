@@ -181,7 +181,7 @@ struct cfie_op {
   dbuf xin32, xin32b; // FP32 staging of the input (and hard-path helpers)
 
   // FP64-accurate residual matvec in double-float arithmetic (sound-soft)
-  dbuf df_geo, df_band, df_part;
+  dbuf df_geo, df_band, df_part, df_x;
   int df_b = -1;
 
   // FP32 matvec variant: 0 = autotuned, 1 = FP32-pipe contraction, 2 = tensor cores
@@ -272,6 +272,7 @@ int tc_take_error(cfie_op* op);
 void pset_build(pset& ps, const std::vector<size_t>& off, const std::vector<int>& len,
                 cudaStream_t st);
 void pset_uniform(pset& ps, int n, int nrhs, cudaStream_t st);
+void measure_peaks(cfie_ctx* ctx, cfie_peaks* out);
 void gmres_set(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps,
                const solve_fns& fns, bool refined, const double2* f, double2* x, double rtol,
                int restart, int maxit, int* iters, double* relres, cfie_status* status,

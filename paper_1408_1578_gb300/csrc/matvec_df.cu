@@ -129,7 +129,7 @@ struct df_params {
   const float2* sp;             // per node: |z'| (hi, lo)
   const float2* w;              // Kress table w_d (hi, lo)
   const float4* band;           // near entries (re hi, re lo, im hi, im lo), n x (2b + 1)
-  const double2* x;
+  const float4* x;              // densities as double-float (re hi, re lo, im hi, im lo)
   double2* part;                // [split][k][i]
 };
 
@@ -225,19 +225,18 @@ __global__ void __launch_bounds__(DNT) k_pair_df(df_params P) {
   const int t_end = min(ntiles, t_begin + P.tiles_per_split);
   const int il2 = tid % DTI, rg = tid / DTI;
   const int bw = 2 * P.b + 1;
-  double2 acc[RQ];
+  // running sums over the tiles in double-float (no FP64 instructions in the loop)
+  df accr[RQ], acci[RQ];
 #pragma unroll
-  for (int q = 0; q < RQ; ++q) acc[q] = make_double2(0.0, 0.0);
+  for (int q = 0; q < RQ; ++q) accr[q] = acci[q] = df{0.f, 0.f};
 
   for (int t = t_begin; t < t_end; ++t) {
     const int j0 = t * DTJ;
     __syncthreads();
     for (int e = tid; e < DTJ * RB; e += DNT) {
       const int jl = e / RB, r = e % RB, j = j0 + jl;
-      double2 v = make_double2(0.0, 0.0);
-      if (j < n && r < rbn) v = P.x[(size_t)(rb0 + r) * n + j];
-      const float rh = (float)v.x, ih = (float)v.y;
-      S.X[jl][r] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+      S.X[jl][r] = (j < n && r < rbn) ? P.x[(size_t)(rb0 + r) * n + j]
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     // entries: warp handles rows warp + 8 q, lane = source
     for (int e = tid; e < DTI * DTJ; e += DNT) {
@@ -273,8 +272,8 @@ __global__ void __launch_bounds__(DNT) k_pair_df(df_params P) {
     }
 #pragma unroll
     for (int q = 0; q < RQ; ++q) {
-      acc[q].x += (double)t4[q].x + (double)t4[q].y;
-      acc[q].y += (double)t4[q].z + (double)t4[q].w;
+      accr[q] = dadd(accr[q], df{t4[q].x, t4[q].y});
+      acci[q] = dadd(acci[q], df{t4[q].z, t4[q].w});
     }
   }
   const int i = i0 + il2;
@@ -282,9 +281,21 @@ __global__ void __launch_bounds__(DNT) k_pair_df(df_params P) {
 #pragma unroll
     for (int q = 0; q < RQ; ++q) {
       const int r = rg + 4 * q;
-      if (r < rbn) P.part[((size_t)split * P.nrhs + rb0 + r) * n + i] = acc[q];
+      if (r < rbn)
+        P.part[((size_t)split * P.nrhs + rb0 + r) * n + i] =
+            make_double2((double)accr[q].h + (double)accr[q].l,
+                         (double)acci[q].h + (double)acci[q].l);
     }
   }
+}
+
+// densities to double-float planes, once per matvec
+__global__ void k_df_x(size_t len, const double2* __restrict__ x, float4* __restrict__ xo) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  const double2 v = x[e];
+  const float rh = (float)v.x, ih = (float)v.y;
+  xo[e] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
 }
 
 __global__ void k_reduce_df(int n, int nrhs, int splits, const double2* __restrict__ part,
@@ -449,9 +460,12 @@ void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
   P.sp = (const float2*)(base + 2 * sizeof(float4) * n);
   P.w = (const float2*)(base + (2 * sizeof(float4) + sizeof(float2)) * n);
   P.band = op->df_band.as<float4>();
-  P.x = x;
-  const int splits = nrhs > 16 ? launch_df<64>(op, P, nrhs) : launch_df<16>(op, P, nrhs);
   const size_t tot = (size_t)n * nrhs;
+  op->df_x.reserve(sizeof(float4) * tot);
+  k_df_x<<<nbk(tot), 256, 0, op->ctx->stream>>>(tot, x, op->df_x.as<float4>());
+  CFIE_CHECK_LAUNCH();
+  P.x = op->df_x.as<float4>();
+  const int splits = nrhs > 16 ? launch_df<64>(op, P, nrhs) : launch_df<16>(op, P, nrhs);
   k_reduce_df<<<nbk(tot), 256, 0, op->ctx->stream>>>(n, nrhs, splits, op->df_part.as<double2>(),
                                                       y);
   CFIE_CHECK_LAUNCH();

@@ -312,6 +312,9 @@ __global__ void k_geo32(int n, geom_dev g, geo32 o, const double* __restrict__ w
   o.sp[i] = (float)g.sp[i];
   w32[i] = (float)w[i];
   c32[i] = (float)ct[i];
+  // the Kress table twice over, indexed by i - j + n (no cyclic wrap)
+  w32[2 * n + i] = (float)w[i];
+  w32[3 * n + i] = (float)w[i];
 }
 
 // Largest cyclic index distance |i - j| of a pair with omega r < X0 (with a
@@ -433,7 +436,7 @@ int launch32(cfie_op* op, pair_params P, int rowtiles, int slices) {
 void fp32_prepare(cfie_op* op) {
   const int n = op->n;
   cudaStream_t st = op->ctx->stream;
-  op->geo32.reserve(sizeof(float) * 9 * (size_t)n);
+  op->geo32.reserve(sizeof(float) * 11 * (size_t)n);
   // band width and argument range
   dbuf scan;
   scan.reserve(16);

@@ -51,8 +51,22 @@ struct tc_params : omega32 {
   int n, b, ktiles;
   geo32 g;
   const float* w32;
+  const float* wext;     // Kress table indexed by i - j + n
   const float2* band;
 };
+
+// bf16 hi / lo split of one entry into the four A planes at byte offset o
+__device__ __forceinline__ void store_split(unsigned char* a0, unsigned char* a1,
+                                            unsigned char* a2, unsigned char* a3, uint32_t o,
+                                            float2 a) {
+  const __nv_bfloat16 hr = __float2bfloat16_rn(a.x), hi = __float2bfloat16_rn(a.y);
+  const __nv_bfloat16 lr = __float2bfloat16_rn(a.x - __bfloat162float(hr));
+  const __nv_bfloat16 li = __float2bfloat16_rn(a.y - __bfloat162float(hi));
+  *reinterpret_cast<__nv_bfloat16*>(a0 + o) = hr;
+  *reinterpret_cast<__nv_bfloat16*>(a1 + o) = hi;
+  *reinterpret_cast<__nv_bfloat16*>(a2 + o) = lr;
+  *reinterpret_cast<__nv_bfloat16*>(a3 + o) = li;
+}
 
 template <int NP>
 struct tc_smem {
@@ -154,31 +168,46 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
         unsigned char* a1 = reinterpret_cast<unsigned char*>(S.A[st][1]);
         unsigned char* a2 = reinterpret_cast<unsigned char*>(S.A[st][2]);
         unsigned char* a3 = reinterpret_cast<unsigned char*>(S.A[st][3]);
-#pragma unroll 2
-        for (int q = 0; q < TBM / NPROD; ++q) {
-          const int il = warp + NPROD * q;
-          const int i = m0 + il;
-          float2 a = make_float2(0.f, 0.f), unused;
-          if (i < n && jok) {
-            int d = i - j;
-            if (d < 0) d += n;
-            const int dd = d <= P.b ? d : (d >= n - P.b ? d - n : INT_MAX);
-            if (dd != INT_MAX) {
-              a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
-            } else {
-              pair_entries_fp32<0>(P, S.txh[il], S.txl[il], S.tyh[il], S.tyl[il], S.tnx[il],
-                                   S.tny[il], S.tsp[il], sxh, sxl, syh, syl, snx, sny, ssp,
-                                   P.w32[d], a, unused);
-            }
+        // A tile is plain when it holds full rows and sources and no pair of
+        // the near band: d = i - j spans [dlo, dhi] there, and the band is
+        // |d - t n| <= b for t = -1, 0, 1.  Plain tiles (all but ~1%) skip the
+        // per-pair range and band tests; the Kress weight comes from the
+        // unwrapped table at i - j + n.  The test is uniform over the CTA.
+        const int j0 = k * TBK;
+        const int dlo = m0 - j0 - (TBK - 1), dhi = m0 + TBM - 1 - j0;
+        bool near = false;
+#pragma unroll
+        for (int t = -1; t <= 1; ++t) near |= (dhi >= t * n - P.b) && (dlo <= t * n + P.b);
+        if (!near && m0 + TBM <= n && j0 + TBK <= n) {
+          const float* wq = P.wext + (m0 + warp - j + n);
+#pragma unroll 4
+          for (int q = 0; q < TBM / NPROD; ++q) {
+            const int il = warp + NPROD * q;
+            float2 a, unused;
+            pair_entries_fp32<0>(P, S.txh[il], S.txl[il], S.tyh[il], S.tyl[il], 0.f, 0.f, 1.f,
+                                 sxh, sxl, syh, syl, snx, sny, ssp, wq[NPROD * q], a, unused);
+            store_split(a0, a1, a2, a3, sw64(il, lane), a);
           }
-          const __nv_bfloat16 hr = __float2bfloat16_rn(a.x), hi = __float2bfloat16_rn(a.y);
-          const __nv_bfloat16 lr = __float2bfloat16_rn(a.x - __bfloat162float(hr));
-          const __nv_bfloat16 li = __float2bfloat16_rn(a.y - __bfloat162float(hi));
-          const uint32_t o = sw64(il, lane);
-          *reinterpret_cast<__nv_bfloat16*>(a0 + o) = hr;
-          *reinterpret_cast<__nv_bfloat16*>(a1 + o) = hi;
-          *reinterpret_cast<__nv_bfloat16*>(a2 + o) = lr;
-          *reinterpret_cast<__nv_bfloat16*>(a3 + o) = li;
+        } else {
+#pragma unroll 2
+          for (int q = 0; q < TBM / NPROD; ++q) {
+            const int il = warp + NPROD * q;
+            const int i = m0 + il;
+            float2 a = make_float2(0.f, 0.f), unused;
+            if (i < n && jok) {
+              int d = i - j;
+              if (d < 0) d += n;
+              const int dd = d <= P.b ? d : (d >= n - P.b ? d - n : INT_MAX);
+              if (dd != INT_MAX) {
+                a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
+              } else {
+                pair_entries_fp32<0>(P, S.txh[il], S.txl[il], S.tyh[il], S.tyl[il], S.tnx[il],
+                                     S.tny[il], S.tsp[il], sxh, sxl, syh, syl, snx, sny, ssp,
+                                     P.w32[d], a, unused);
+              }
+            }
+            store_split(a0, a1, a2, a3, sw64(il, lane), a);
+          }
         }
         // generic-proxy writes become visible to the tensor core's async proxy
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -376,6 +405,7 @@ void run_fused(cfie_op* op, const double2* x, double2* y, int r0, int nr) {
   float* base = op->geo32.as<float>();
   P.g = geo32_at(base, n);
   P.w32 = base + 7 * n;
+  P.wext = base + 9 * n;
   P.band = op->band.as<float2>();
   const size_t smem = tc_smem_bytes<NP>();
   CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_fused_tc<NP>,

@@ -5,8 +5,9 @@
 #pragma once
 
 // FP32 geometry of an operator: hi/lo coordinates, unnormalised normal, speed.
-// Stored in one buffer of 9 n floats: xh, xl, yh, yl, nx, ny, sp, w32 (Kress
-// table), c32 (spectral-derivative circulant).
+// Stored in one buffer of 11 n floats: xh, xl, yh, yl, nx, ny, sp, w32 (Kress
+// table), c32 (spectral-derivative circulant), and the Kress table twice over
+// (2 n floats, entry i - j + n holds w_{(i - j) mod n}).
 struct geo32 {
   float *xh, *xl, *yh, *yl, *nx, *ny, *sp;
 };

@@ -408,17 +408,20 @@ def cpu_rows_for(spec, budget_s=12.0):
     return rows
 
 
-def reference_spec(args):
-    """Workload the oracle samples: the named single-operator workload, or for
-    the batch one star of the batch (its n, omega, 32 directions)."""
+def reference_specs(args):
+    """Workloads the oracle samples: the named single-operator workload, or for
+    the batch four of its stars (the smallest, the median and the two largest)."""
     if args.workload == "stars":
         from paper_1408_1578_gb300 import inputs
-        st = inputs.random_stars(count=args.count or 256, seed=1408, n_lo=512, n_hi=16384,
-                                 nrhs=32)[0]
-        return {"name": "stars (first operator of the batch)", "curve": "star",
-                "params": {"a": list(st["a"]), "b": list(st["b"])}, "n": st["n"],
-                "omega": st["omega"], "nrhs": st["nrhs"], "bc": "soft", "precision": "tensor"}
-    return workload(args.workload, args.precision, args.n, args.nrhs)
+        stars = inputs.random_stars(count=args.count or 256, seed=1408, n_lo=512, n_hi=16384,
+                                    nrhs=32)
+        order = sorted(range(len(stars)), key=lambda k: stars[k]["n"])
+        pick = [order[0], order[len(order) // 2], order[-2], order[-1]]
+        return [{"name": f"stars[{k}]", "curve": "star",
+                 "params": {"a": list(stars[k]["a"]), "b": list(stars[k]["b"])},
+                 "n": stars[k]["n"], "omega": stars[k]["omega"], "nrhs": stars[k]["nrhs"],
+                 "bc": "soft", "precision": "tensor"} for k in pick]
+    return [workload(args.workload, args.precision, args.n, args.nrhs)]
 
 
 def run_reference_serve(args):
@@ -463,18 +466,22 @@ def run_reference(args, rank, world):
         return None
     if args.workload == "serve":
         return run_reference_serve(args)
-    spec = reference_spec(args)
-    rows = cpu_rows_for(spec, budget_s=10.0 / max(1, args.steps + args.warmup) * 3)
+    specs = reference_specs(args)
+    budget = 10.0 / max(1, args.steps + args.warmup) * 3 / len(specs)
+    rows = [cpu_rows_for(sp, budget_s=budget) for sp in specs]
     for _ in range(args.warmup):
-        oracle_sample(spec, max(4, rows // 4))
+        for sp, r in zip(specs, rows):
+            oracle_sample(sp, max(4, r // 4))
     tot_pairs, tot_s = 0, 0.0
     for _ in range(args.steps):
-        p, s = oracle_sample(spec, rows)
-        tot_pairs += p
-        tot_s += s
+        for sp, r in zip(specs, rows):
+            p, s = oracle_sample(sp, r)
+            tot_pairs += p
+            tot_s += s
     value = tot_pairs / tot_s
-    sample = (f"{rows} rows x {spec['n']} sources of the {spec['name']} operator, "
-              f"{spec['nrhs']} right-hand sides, per step")
+    sample = "; ".join(f"{r} rows x {sp['n']} sources of the {sp['name']} operator"
+                       for sp, r in zip(specs, rows))
+    sample += f", {specs[0]['nrhs']} right-hand sides, per step"
     cfg = stars_config(args.count or 256) if args.workload == "stars" else \
         single_config(workload(args.workload, args.precision, args.n, args.nrhs), world)
     return {

@@ -55,17 +55,21 @@ struct tc_params : omega32 {
   const float2* band;
 };
 
-// bf16 hi / lo split of one entry into the four A planes at byte offset o
-__device__ __forceinline__ void store_split(unsigned char* a0, unsigned char* a1,
-                                            unsigned char* a2, unsigned char* a3, uint32_t o,
-                                            float2 a) {
-  const __nv_bfloat16 hr = __float2bfloat16_rn(a.x), hi = __float2bfloat16_rn(a.y);
-  const __nv_bfloat16 lr = __float2bfloat16_rn(a.x - __bfloat162float(hr));
-  const __nv_bfloat16 li = __float2bfloat16_rn(a.y - __bfloat162float(hi));
-  *reinterpret_cast<__nv_bfloat16*>(a0 + o) = hr;
-  *reinterpret_cast<__nv_bfloat16*>(a1 + o) = hi;
-  *reinterpret_cast<__nv_bfloat16*>(a2 + o) = lr;
-  *reinterpret_cast<__nv_bfloat16*>(a3 + o) = li;
+// bf16 hi / lo split of two entries of one row (adjacent sources k, k + 1)
+// into the four A planes: one packed 32-bit word per plane at byte offset o
+__device__ __forceinline__ void store_split2(unsigned char* a0, unsigned char* a1,
+                                             unsigned char* a2, unsigned char* a3, uint32_t o,
+                                             float2 e0, float2 e1) {
+  const __nv_bfloat162 hr = __floats2bfloat162_rn(e0.x, e1.x);
+  const __nv_bfloat162 hi = __floats2bfloat162_rn(e0.y, e1.y);
+  const __nv_bfloat162 lr =
+      __floats2bfloat162_rn(e0.x - __low2float(hr), e1.x - __high2float(hr));
+  const __nv_bfloat162 li =
+      __floats2bfloat162_rn(e0.y - __low2float(hi), e1.y - __high2float(hi));
+  *reinterpret_cast<__nv_bfloat162*>(a0 + o) = hr;
+  *reinterpret_cast<__nv_bfloat162*>(a1 + o) = hi;
+  *reinterpret_cast<__nv_bfloat162*>(a2 + o) = lr;
+  *reinterpret_cast<__nv_bfloat162*>(a3 + o) = li;
 }
 
 template <int NP>
@@ -73,7 +77,7 @@ struct tc_smem {
   __nv_bfloat16 A[TSTAGES][4][TBM * TBK];   // hi_re, hi_im, lo_re, lo_im
   __nv_bfloat16 B[TSTAGES][4][NP * TBK];    // B1 hi, B1 lo, B2 hi, B2 lo
   float acc[NP][TBM];                       // epilogue running sums, column-major
-  float txh[TBM], txl[TBM], tyh[TBM], tyl[TBM], tnx[TBM], tny[TBM], tsp[TBM];  // targets
+  float4 tgt[TBM];                          // targets (x hi, x lo, y hi, y lo)
   uint64_t full[TSTAGES], empty[TSTAGES], tfull[2], tempty[2];
   uint32_t tmem_base;
   int abort;
@@ -127,29 +131,47 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
   const uint32_t tmem = S.tmem_base;
 
   if (warp < NPROD) {
-    // ---- pair-entry producers: rows warp + NPROD q, lane = source within the tile
+    // ---- pair-entry producers.  Warp w owns rows w + NPROD q (q < TBM / NPROD);
+    // each step of its loop covers two of them: lanes 0-15 the first, lanes
+    // 16-31 the second, lane l the two adjacent sources 2 (l % 16), +1, so
+    // that the bf16 pairs go to shared memory as packed 32-bit words.
+    const int half = lane >> 4, jp = 2 * (lane & 15);
     int it = 0;
     for (int s = sb; s < se; ++s) {
       const int4 sg = segs[s];
       const int m0 = sg.y * TBM;
-      // stage the target geometry of this warp's own rows (warp + NPROD q): no
-      // other warp reads them, so a warp-level barrier is enough
+      // stage the target geometry of this warp's own rows: no other warp
+      // reads them, so a warp-level barrier is enough
       __syncwarp();
       if (lane < TBM / NPROD) {
         const int r = warp + NPROD * lane;
         const int i = m0 + r;
         const bool ok = i < n;
-        S.txh[r] = ok ? P.g.xh[i] : 0.f;
-        S.txl[r] = ok ? P.g.xl[i] : 0.f;
-        S.tyh[r] = ok ? P.g.yh[i] : 0.f;
-        S.tyl[r] = ok ? P.g.yl[i] : 0.f;
-        S.tnx[r] = ok ? P.g.nx[i] : 0.f;
-        S.tny[r] = ok ? P.g.ny[i] : 0.f;
-        S.tsp[r] = ok ? P.g.sp[i] : 1.f;
+        S.tgt[r] = ok ? make_float4(P.g.xh[i], P.g.xl[i], P.g.yh[i], P.g.yl[i])
+                      : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncwarp();
+      // geometry of this lane's two sources, loaded one tile ahead
+      float4 pc[2];
+      float3 pn[2];
+      auto load_src = [&](int kk) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int jj = kk * TBK + jp + u;
+          const bool ok = jj < n;
+          pc[u] = ok ? make_float4(P.g.xh[jj], P.g.xl[jj], P.g.yh[jj], P.g.yl[jj])
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+          pn[u] = ok ? make_float3(P.g.nx[jj], P.g.ny[jj], P.g.sp[jj]) : make_float3(0.f, 0.f, 1.f);
+        }
+      };
+      load_src(sg.z);
       for (int k = sg.z; k < sg.w; ++k, ++it) {
         const int st = it % TSTAGES;
+        const int j0 = k * TBK;
+        const int j = j0 + jp;                       // first of the lane's two sources
+        const float4 sc[2] = {pc[0], pc[1]};
+        const float3 sn[2] = {pn[0], pn[1]};
+        if (k + 1 < sg.w) load_src(k + 1);
         if (*(volatile int*)&S.abort) break;
         if (it >= TSTAGES && !mbar_wait(&S.empty[st], ((it / TSTAGES) - 1) & 1)) {
           if (lane == 0) {
@@ -158,12 +180,6 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
           }
           break;
         }
-        const int j = k * TBK + lane;
-        const bool jok = j < n;
-        const float sxh = jok ? P.g.xh[j] : 0.f, sxl = jok ? P.g.xl[j] : 0.f;
-        const float syh = jok ? P.g.yh[j] : 0.f, syl = jok ? P.g.yl[j] : 0.f;
-        const float snx = jok ? P.g.nx[j] : 0.f, sny = jok ? P.g.ny[j] : 0.f;
-        const float ssp = jok ? P.g.sp[j] : 1.f;
         unsigned char* a0 = reinterpret_cast<unsigned char*>(S.A[st][0]);
         unsigned char* a1 = reinterpret_cast<unsigned char*>(S.A[st][1]);
         unsigned char* a2 = reinterpret_cast<unsigned char*>(S.A[st][2]);
@@ -173,40 +189,54 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
         // |d - t n| <= b for t = -1, 0, 1.  Plain tiles (all but ~1%) skip the
         // per-pair range and band tests; the Kress weight comes from the
         // unwrapped table at i - j + n.  The test is uniform over the CTA.
-        const int j0 = k * TBK;
         const int dlo = m0 - j0 - (TBK - 1), dhi = m0 + TBM - 1 - j0;
         bool near = false;
 #pragma unroll
         for (int t = -1; t <= 1; ++t) near |= (dhi >= t * n - P.b) && (dlo <= t * n + P.b);
+        constexpr int QS = TBM / NPROD / 2;          // loop steps (two rows each)
         if (!near && m0 + TBM <= n && j0 + TBK <= n) {
-          const float* wq = P.wext + (m0 + warp - j + n);
-#pragma unroll 4
-          for (int q = 0; q < TBM / NPROD; ++q) {
-            const int il = warp + NPROD * q;
-            float2 a, unused;
-            pair_entries_fp32<0>(P, S.txh[il], S.txl[il], S.tyh[il], S.tyl[il], 0.f, 0.f, 1.f,
-                                 sxh, sxl, syh, syl, snx, sny, ssp, wq[NPROD * q], a, unused);
-            store_split(a0, a1, a2, a3, sw64(il, lane), a);
+          const float* wq = P.wext + (m0 + warp + NPROD * half - j + n);
+          float2 wv[QS];
+#pragma unroll
+          for (int q = 0; q < QS; ++q) wv[q] = make_float2(wq[2 * NPROD * q], wq[2 * NPROD * q - 1]);
+#pragma unroll
+          for (int q = 0; q < QS; ++q) {
+            const int il = warp + NPROD * (2 * q + half);
+            const float4 tg = S.tgt[il];
+            float2 e[2], unused;
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+              pair_entries_fp32<0>(P, tg.x, tg.y, tg.z, tg.w, 0.f, 0.f, 1.f, sc[u].x, sc[u].y,
+                                   sc[u].z, sc[u].w, sn[u].x, sn[u].y, sn[u].z,
+                                   u ? wv[q].y : wv[q].x, e[u], unused);
+            store_split2(a0, a1, a2, a3, sw64(il, jp), e[0], e[1]);
           }
         } else {
-#pragma unroll 2
-          for (int q = 0; q < TBM / NPROD; ++q) {
-            const int il = warp + NPROD * q;
+#pragma unroll 1
+          for (int q = 0; q < QS; ++q) {
+            const int il = warp + NPROD * (2 * q + half);
             const int i = m0 + il;
-            float2 a = make_float2(0.f, 0.f), unused;
-            if (i < n && jok) {
-              int d = i - j;
-              if (d < 0) d += n;
-              const int dd = d <= P.b ? d : (d >= n - P.b ? d - n : INT_MAX);
-              if (dd != INT_MAX) {
-                a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
-              } else {
-                pair_entries_fp32<0>(P, S.txh[il], S.txl[il], S.tyh[il], S.tyl[il], S.tnx[il],
-                                     S.tny[il], S.tsp[il], sxh, sxl, syh, syl, snx, sny, ssp,
-                                     P.w32[d], a, unused);
+            const float4 tg = S.tgt[il];
+            float2 e[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int jj = j + u;
+              float2 a = make_float2(0.f, 0.f), unused;
+              if (i < n && jj < n) {
+                int d = i - jj;
+                if (d < 0) d += n;
+                const int dd = d <= P.b ? d : (d >= n - P.b ? d - n : INT_MAX);
+                if (dd != INT_MAX) {
+                  a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
+                } else {
+                  pair_entries_fp32<0>(P, tg.x, tg.y, tg.z, tg.w, 0.f, 0.f, 1.f, sc[u].x,
+                                       sc[u].y, sc[u].z, sc[u].w, sn[u].x, sn[u].y, sn[u].z,
+                                       P.w32[d], a, unused);
+                }
               }
+              e[u] = a;
             }
-            store_split(a0, a1, a2, a3, sw64(il, lane), a);
+            store_split2(a0, a1, a2, a3, sw64(il, jp), e[0], e[1]);
           }
         }
         // generic-proxy writes become visible to the tensor core's async proxy

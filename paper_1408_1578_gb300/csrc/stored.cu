@@ -161,7 +161,10 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---- TMA producer
+      // ---- TMA producer: the matrix planes are streamed once per matvec
+      // (evict first), the right-hand-side planes are reused by every row
+      // tile of their job (evict last)
+      const uint64_t pol_a = l2_evict_first(), pol_b = l2_evict_last();
       int it = 0;
       for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
         const int4 sg = segs[s];
@@ -181,9 +184,11 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
           if (stall && it == 0) continue;
           const int kc = k * BK;
 #pragma unroll
-          for (int p = 0; p < 4; ++p) tma_load_2d(S.A[st][p], &J->ta, &S.full[st], kc, p * J->n + m0);
+          for (int p = 0; p < 4; ++p)
+            tma_load_2d_hint(S.A[st][p], &J->ta, &S.full[st], kc, p * J->n + m0, pol_a);
 #pragma unroll
-          for (int p = 0; p < 4; ++p) tma_load_2d(S.B[st][p], &J->tb, &S.full[st], kc, p * NP);
+          for (int p = 0; p < 4; ++p)
+            tma_load_2d_hint(S.B[st][p], &J->tb, &S.full[st], kc, p * NP, pol_b);
         }
       }
     }

@@ -41,7 +41,8 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="kite", choices=["kite", "star", "disk", "stars", "serve"])
+    p.add_argument("--workload", default="kite",
+                   choices=["kite", "star", "disk", "stars", "serve", "ellipse", "ellipse-hard"])
     p.add_argument("--precision", default=None, choices=["fp32", "fp64", "tensor", None])
     p.add_argument("--count", type=int, default=None,
                    help="stars: operators in the batch (256); serve: requests (32)")
@@ -67,12 +68,12 @@ def workload(name, precision, n=None, nrhs=None):
     if nrhs:
         spec["nrhs"] = nrhs
     if precision is None:
-        precision = "fp32" if name == "kite" else "fp64"
+        precision = "fp32" if name in ("kite", "ellipse", "ellipse-hard") else "fp64"
     spec["precision"] = precision
     spec["layout"] = "stored" if precision == "tensor" else "matrix_free"
     # residual target: 1e-8 on ||f - A x|| / ||f|| keeps the error against the
     # FP64 solution below 1e-6 for the condition numbers of these operators
-    spec["rtol"] = 1e-8
+    spec["rtol"] = spec.get("rtol", 1e-8)
     spec["restart"] = 80
     spec["maxit"] = 4000
     return spec
@@ -154,6 +155,14 @@ DF_TERM_OPS = 48                         # Dot2 complex product-sum per pair and
 FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the current kernel at the same launch configuration, keyed by
+# (kernel class, curve, n, nrhs, matvec variant); absent = not captured.
+NCU_TRAFFIC = {
+    ("matvec_fp32", "kite", 32768, 64, 2): 78.603776e6 + 10.776832e6,
+}
+
+
 def kernel_rooflines(kt, spec, stats, peaks, src, n, solves_timed):
     """Roofline entry per timed kernel class: achieved = algorithmic work of the
     class in the timed region / its CUDA-event time."""
@@ -161,6 +170,7 @@ def kernel_rooflines(kt, spec, stats, peaks, src, n, solves_timed):
     clock_hz = peaks.get("sm_max_mhz", 2070.0) * 1e6
     fp32_peak = SMS * FP32_LANES * clock_hz / 1e12        # T lane-ops/s
     out = {}
+    variant = stats.get("matvec_variant", 0)
     for cls, (ms, launches) in kt.items():
         if launches == 0 or ms <= 0:
             continue
@@ -214,6 +224,8 @@ def kernel_rooflines(kt, spec, stats, peaks, src, n, solves_timed):
                 e["fp64_ops"] = {"achieved": f, "peak": FP64_NOMINAL_TFLOPS / 2,
                                  "unit": "T FP64 ops/s", "frac": f / (FP64_NOMINAL_TFLOPS / 2)}
             out[cls] = e
+    for cls, e in out.items():
+        e["traffic"] = NCU_TRAFFIC.get((cls, spec["curve"], n, nrhs, variant))
     return out
 
 

@@ -191,6 +191,22 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
  * precision stay FP64 either way.  CFIE_EINVAL for a null op or another value. */
 cfie_status cfie_op_set_inner_basis(cfie_op* op, int fp32);
 
+/* Scattered field at off-surface points from a boundary density (Section 1:
+ * u is evaluated through a boundary integral once q is known).  With the
+ * operator's curve, omega, eta and boundary condition,
+ *     sound soft:  u(x) = (D q)(x) - i eta (S q)(x)
+ *     sound hard:  u(x) = -(S q)(x) + (D q)(x) / (i eta)
+ * (the representations whose boundary limits are eq. 1 and eq. 2), by the
+ * plain trapezoidal rule in FP64 whatever the operator's precision.  q_dev:
+ * n x nrhs complex128, column-major (density k contiguous); pts_dev: npts
+ * points as (x, y) double pairs, device memory; u_dev: npts x nrhs complex128,
+ * column-major.  Points must lie off the curve; the rule is spectrally
+ * accurate a few node spacings (2 pi / n in the parameter) away from it and
+ * loses accuracy closer in.  Pointers 16-byte aligned; u must not overlap q or
+ * pts.  Asynchronous on the context stream. */
+cfie_status cfie_field_eval(cfie_op* op, const void* q_dev, int nrhs, int npts,
+                            const void* pts_dev, void* u_dev);
+
 /* Counters of the last cfie_gmres_solve on this operator. */
 typedef struct {
   int cycles;            /* GMRES cycles (restarts + 1) summed over refinement steps */

@@ -100,6 +100,7 @@ SIGNATURES = {
     "cfie_op_set_variant": (_I, [_P, _I]),
     "cfie_gmres_solve": (_I, [_P, _P, _P, _I, _D, _I, _I, _IP, _DP]),
     "cfie_op_set_inner_basis": (_I, [_P, _I]),
+    "cfie_field_eval": (_I, [_P, _P, _I, _I, _P, _P]),
     "cfie_op_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
     "cfie_ctx_set_profiling": (_I, [_P, _I]),
     "cfie_ctx_kernel_times": (_I, [_P, _DP, _LLP]),
@@ -435,6 +436,14 @@ class Operator:
     def set_variant(self, variant):
         """0 = autotuned, 1 = FP32-pipe sums, 2 = tensor-core sums."""
         self.ctx.check(self.ctx.lib.cfie_op_set_variant(self.h, int(variant)), "cfie_op_set_variant")
+
+    def field_eval(self, q, pts, u):
+        """u (npts, nrhs-major complex128) = scattered field at pts (npts, 2) float64
+        of the densities q (nrhs, n) complex128; device tensors."""
+        nrhs = q.numel() // self.n
+        npts = pts.numel() // 2
+        self.ctx.check(self.ctx.lib.cfie_field_eval(self.h, _addr(q), int(nrhs), int(npts),
+                                                    _addr(pts), _addr(u)), "cfie_field_eval")
 
     def set_inner_basis(self, fp32):
         """Refined precisions: inner Krylov basis in FP32 (True, default) or FP64."""

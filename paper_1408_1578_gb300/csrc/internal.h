@@ -78,6 +78,7 @@ struct cfie_ctx {
   std::string err;
   // per-launch event timing
   bool profiling = false;
+  int prof_suspend = 0;   // > 0: per-launch scopes are off (an outer scope times the work)
   struct pending { int cls; cudaEvent_t a, b; };
   std::vector<pending> inflight;
   std::vector<cudaEvent_t> pool;
@@ -217,6 +218,9 @@ struct cfie_batch {
   krylov_ws K;
   pset ps;
   cfie_solve_stats stats{};
+  // streams on which the operators' residual matvecs run concurrently
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> aux_ev;
 };
 
 // ----------------------------------------------------------------------------
@@ -273,6 +277,8 @@ void pset_build(pset& ps, const std::vector<size_t>& off, const std::vector<int>
                 cudaStream_t st);
 void pset_uniform(pset& ps, int n, int nrhs, cudaStream_t st);
 void measure_peaks(cfie_ctx* ctx, cfie_peaks* out);
+void field_eval(cfie_op* op, const double2* q, int nrhs, int npts, const double2* pts,
+                double2* u);
 void gmres_set(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps,
                const solve_fns& fns, bool refined, const double2* f, double2* x, double rtol,
                int restart, int maxit, int* iters, double* relres, cfie_status* status,

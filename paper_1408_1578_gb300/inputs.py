@@ -88,4 +88,11 @@ WORKLOADS = {
     "star": {"curve": "star", "params": {"a": [0, 0, 0, 0, 0.3], "b": [0, 0, 0, 0, 0]},
              "n": 4096, "omega": 256.0, "nrhs": 16, "bc": "hard"},
     "kite": {"curve": "kite", "params": {}, "n": 32768, "omega": 2048.0, "nrhs": 64, "bc": "soft"},
+    # the paper's ellipse experiments (Section 3, Tables 1 and 3, first rows):
+    # semi-axes (1, 0.5), p = 8 points per wavelength (omega = 2 pi n / (8 L),
+    # L = 4.8442 the perimeter), one plane wave along +x, GMRES(80) to 1e-6
+    "ellipse": {"curve": "ellipse", "params": {"a": 1.0, "b": 0.5}, "n": 32768, "omega": 5313.0,
+                "nrhs": 1, "bc": "soft", "rtol": 1e-6},
+    "ellipse-hard": {"curve": "ellipse", "params": {"a": 1.0, "b": 0.5}, "n": 32768,
+                     "omega": 5313.0, "nrhs": 1, "bc": "hard", "rtol": 1e-6},
 }

@@ -438,10 +438,11 @@ class Operator:
         self.ctx.check(self.ctx.lib.cfie_op_set_variant(self.h, int(variant)), "cfie_op_set_variant")
 
     def field_eval(self, q, pts, u):
-        """u (npts, nrhs-major complex128) = scattered field at pts (npts, 2) float64
-        of the densities q (nrhs, n) complex128; device tensors."""
+        """u (nrhs, npts) = scattered field of the densities q (nrhs, n) at the
+        points pts (npts,), given as complex128 x + i y (the (x, y) double pairs
+        of the C ABI); all complex128 device tensors."""
         nrhs = q.numel() // self.n
-        npts = pts.numel() // 2
+        npts = pts.numel()
         self.ctx.check(self.ctx.lib.cfie_field_eval(self.h, _addr(q), int(nrhs), int(npts),
                                                     _addr(pts), _addr(u)), "cfie_field_eval")
 

@@ -301,7 +301,7 @@ cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cf
     geometry_sample(op, geom);
     kress_tables(op);
     if (precision != CFIE_FP64) fp32_prepare(op);
-    if (precision != CFIE_FP64 && bc == CFIE_SOUND_SOFT) df_prepare(op);
+    if (precision != CFIE_FP64) df_prepare(op);
     if (layout == CFIE_STORED) stored_prepare(op);
     CFIE_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   });

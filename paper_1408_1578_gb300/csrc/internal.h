@@ -249,6 +249,10 @@ void rhs_plane_waves(cfie_op* op, int nrhs, const double* theta_host, double2* f
 void matvec_fp64(cfie_op* op, const double2* x, double2* y, int nrhs);
 void spectral_apply(cfie_op* op, const double2* in, double2* out, const double2* base,
                     double2 scale, int nrhs);
+// sound-hard combination of the four FP64-layout partial sums (S u, S n1 x,
+// S n2 x, D' x): t = S u, y = x / 2 - D' x - i (omega^2 / eta) (n1 S n1 x + n2 S n2 x)
+void reduce_hard_fp64(cfie_op* op, const double2* part, int splits, const double2* x,
+                      double2* t, double2* y, int nrhs);
 void matvec_fp64_static(cfie_op* op, const double2* x, double2* y, int nrhs);
 size_t static_scratch_capacity();
 // matvec_fp32.cu

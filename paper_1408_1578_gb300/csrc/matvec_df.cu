@@ -1,11 +1,12 @@
-// FP64-accurate sound-soft matvec on the FP32 pipe (compensated arithmetic),
-// used for the true residuals of the refined solves.
+// FP64-accurate matvec on the FP32 pipe (compensated arithmetic), used for the
+// true residuals of the refined solves: the sound-soft operator of eq. 1, and
+// the sound-hard operator of eq. 2 with N by Maue's identity (the S and D'
+// sums here, the spectral derivatives by the FP64 circulant kernel).
 //
 // GB300 runs FP64 at a small fraction of its FP32 rate, and the two residual
 // matvecs of a refined solve cost more than all its inner FP32 matvecs when
-// computed in FP64.  This kernel evaluates the same Nystrom entries as the FP64
-// kernel (sound-soft operator of eq. 1 of the paper, Kress log-split rule) in
-// double-float arithmetic: every quantity is an unevaluated sum hi + lo of two
+// computed in FP64.  These kernels evaluate the same Nystrom entries as the
+// FP64 kernel (Kress log-split rule) in double-float arithmetic: every quantity is an unevaluated sum hi + lo of two
 // FP32 numbers (~48 significant bits), products and sums use error-free
 // transformations (TwoProd with fmaf, TwoSum), and
 //  * Hankel's asymptotic expansion (A&S 9.2.5, 9.2.9, 9.2.10) carries its
@@ -16,7 +17,8 @@
 //    sin(j pi/32), cos(j pi/32) and Taylor series of the remainder |d| <= pi/64;
 //  * pairs with omega r < 40 come from a band of entries evaluated in FP64.
 // Source sums use Dot2 (Ogita, Rump & Oishi) inside each 32-source tile and
-// FP64 additions across tiles.  Relative accuracy ~1e-13 (tests ask 1e-11).
+// double-float additions across tiles; the densities are converted to
+// double-float once per matvec.  Relative accuracy ~1e-13 (tests ask 1e-11).
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -133,9 +135,13 @@ struct df_params {
   double2* part;                // [split][k][i]
 };
 
-// one far pair (omega r >= 40): soft entry a = h K + w K1 (eq. 1) in double-float
-__device__ __forceinline__ float4 entry_df(const df_params& P, float4 gi, float4 gj, float4 nj,
-                                           float2 sj2, float2 w2) {
+// Hankel values of one far pair (omega r >= 40) in double-float: (dx, dy) =
+// z_i - z_j, 1 / r, J0, Y0, J1, Y1 at omega r
+struct df_hankel {
+  df dx, dy, rinv, J0, Y0, J1, Y1;
+};
+
+__device__ __forceinline__ df_hankel hankel_df(const df_params& P, float4 gi, float4 gj) {
   const df dx = dsub({gi.x, gi.y}, {gj.x, gj.y});
   const df dy = dsub({gi.z, gi.w}, {gj.z, gj.w});
   const df r2 = dadd(dmul(dx, dx), dmul(dy, dy));
@@ -183,14 +189,46 @@ __device__ __forceinline__ float4 entry_df(const df_params& P, float4 gi, float4
   const df Y0 = dmul(amp, dadd(dmul(P0, sn), dmul(Q0, cs)));
   const df J1 = dmul(amp, dadd(dmul(P1, sn), dmul(Q1, cs)));
   const df Y1 = dmul(amp, dsub(dmul(Q1, sn), dmul(P1, cs)));
+  return {dx, dy, rinv, J0, Y0, J1, Y1};
+}
+
+// one far pair: soft entry a = h K + w K1 (eq. 1), K = L - i eta M
+__device__ __forceinline__ float4 entry_df(const df_params& P, float4 gi, float4 gj, float4 nj,
+                                           float2 sj2, float2 w2) {
+  const df_hankel H = hankel_df(P, gi, gj);
   // c = (z_i - z_j) . nu~_j / r,  es = eta |z'_j|,  oc = omega c
-  const df c = dmul(dadd(dmul(dx, {nj.x, nj.y}), dmul(dy, {nj.z, nj.w})), rinv);
+  const df c = dmul(dadd(dmul(H.dx, {nj.x, nj.y}), dmul(H.dy, {nj.z, nj.w})), H.rinv);
   const df es = dmul(P.eta, {sj2.x, sj2.y});
   const df oc = dmul(P.om, c);
   const df wq = dmul({w2.x, w2.y}, {kI4PiH, kI4PiL});
-  const df re = dsub(dmul(P.hq, dsub(dmul(es, J0), dmul(oc, Y1))), dmul(wq, dmul(oc, J1)));
-  const df im = dadd(dmul(P.hq, dadd(dmul(oc, J1), dmul(es, Y0))), dmul(wq, dmul(es, J0)));
+  const df re =
+      dsub(dmul(P.hq, dsub(dmul(es, H.J0), dmul(oc, H.Y1))), dmul(wq, dmul(oc, H.J1)));
+  const df im =
+      dadd(dmul(P.hq, dadd(dmul(oc, H.J1), dmul(es, H.Y0))), dmul(wq, dmul(es, H.J0)));
   return make_float4(re.h, re.l, im.h, im.l);
+}
+
+// one far pair of the sound-hard operator (eq. 2): S_ij = h M + w M1 with
+// M = (i/4) H0 |z'_j|, M1 = -(1/4 pi) J0 |z'_j|, and D'_ij = h L' + w L'1 with
+// L' = (i omega / 4) H1 cp, L'1 = -(omega / 4 pi) J1 cp,
+// cp = -((z_i - z_j) . nu~_i / r) |z'_j| / |z'_i|
+__device__ __forceinline__ void entry_df_hard(const df_params& P, float4 gi, float4 gj,
+                                              float4 ni, float2 si2, float2 sj2, float2 w2,
+                                              float4& S, float4& Dp) {
+  const df_hankel H = hankel_df(P, gi, gj);
+  const df sj = {sj2.x, sj2.y};
+  const df wq = dmul({w2.x, w2.y}, {kI4PiH, kI4PiL});
+  // S: re = -(h/4 Y0 + w/(4 pi) J0) |z'_j|, im = h/4 J0 |z'_j|
+  const df sre = dneg(dmul(dadd(dmul(P.hq, H.Y0), dmul(wq, H.J0)), sj));
+  const df sim = dmul(dmul(P.hq, H.J0), sj);
+  S = make_float4(sre.h, sre.l, sim.h, sim.l);
+  const df ci = dmul(dadd(dmul(H.dx, {ni.x, ni.y}), dmul(H.dy, {ni.z, ni.w})), H.rinv);
+  const df cp = dneg(dmul(ci, dmul(sj, drcp({si2.x, si2.y}))));
+  const df oc = dmul(P.om, cp);
+  // D': re = -omega cp (h/4 Y1 + w/(4 pi) J1), im = h/4 omega cp J1
+  const df dre = dneg(dmul(oc, dadd(dmul(P.hq, H.Y1), dmul(wq, H.J1))));
+  const df dim = dmul(dmul(P.hq, oc), H.J1);
+  Dp = make_float4(dre.h, dre.l, dim.h, dim.l);
 }
 
 // (s, e) += (ah + al)(xh + xl): TwoProd + TwoSum, errors gathered in e
@@ -289,6 +327,130 @@ __global__ void __launch_bounds__(DNT) k_pair_df(df_params P) {
   }
 }
 
+// Sound-hard residual sums (eq. 2 with Maue's identity for N): per right-hand
+// side four outputs over the same pair entries, o = 0: S u (u = d/ds x),
+// o = 1, 2: S (n_c x), o = 3: D' x, in double-float with Dot2 sums inside each
+// 32-source tile and double-float running sums across tiles.  Partial sums
+// per source split go out in the layout of the FP64 kernel:
+// part[((o * splits + split) * nrhs + k) * n + i].
+template <int RB>
+struct df_smem_hard {
+  float4 S[DTI][DTJ + 1];
+  float4 D[DTI][DTJ + 1];
+  float4 X[DTJ][RB][4];
+};
+
+template <int RB>
+__global__ void __launch_bounds__(DNT) k_pair_df_hard(df_params P, const float4* __restrict__ x4) {
+  constexpr int RQ = RB / (DNT / DTI);
+  extern __shared__ __align__(16) unsigned char raw[];
+  df_smem_hard<RB>& S = *reinterpret_cast<df_smem_hard<RB>*>(raw);
+  const int n = P.n, tid = threadIdx.x;
+  const int i0 = blockIdx.x * DTI, split = blockIdx.y, rb0 = blockIdx.z * RB;
+  const int rbn = min(RB, P.nrhs - rb0);
+  const int ntiles = (n + DTJ - 1) / DTJ;
+  const int t_begin = split * P.tiles_per_split;
+  const int t_end = min(ntiles, t_begin + P.tiles_per_split);
+  const int il2 = tid % DTI, rg = tid / DTI;
+  const int bw = 2 * P.b + 1;
+  const size_t nbw = (size_t)n * bw;
+  df acc[4][RQ][2];
+#pragma unroll
+  for (int o = 0; o < 4; ++o)
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) acc[o][q][0] = acc[o][q][1] = df{0.f, 0.f};
+
+  for (int t = t_begin; t < t_end; ++t) {
+    const int j0 = t * DTJ;
+    __syncthreads();
+    for (int e = tid; e < DTJ * RB * 4; e += DNT) {
+      const int c = e % 4, r = (e / 4) % RB, jl = e / (4 * RB), j = j0 + jl;
+      S.X[jl][r][c] = (j < n && r < rbn) ? x4[((size_t)(rb0 + r) * n + j) * 4 + c]
+                                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int e = tid; e < DTI * DTJ; e += DNT) {
+      const int il = e / DTJ, jl = e % DTJ;
+      const int i = i0 + il, j = j0 + jl;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      if (i < n && j < n) {
+        int d = i - j;
+        if (d < 0) d += n;
+        const int dd = d <= P.b ? d : (d >= n - P.b ? d - n : INT_MAX);
+        if (dd != INT_MAX) {
+          a = P.band[(size_t)i * bw + dd + P.b];
+          b = P.band[nbw + (size_t)i * bw + dd + P.b];
+        } else {
+          entry_df_hard(P, P.g[i], P.g[j], P.nrm[i], P.sp[i], P.sp[j], P.w[d], a, b);
+        }
+      }
+      S.S[il][jl] = a;
+      S.D[il][jl] = b;
+    }
+    __syncthreads();
+    float4 t4[4][RQ];
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) t4[o][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int jn = min(DTJ, n - j0);
+    for (int jl = 0; jl < jn; ++jl) {
+      const float4 a = S.S[il2][jl], b = S.D[il2][jl];
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const float4 m = o < 3 ? a : b;
+          const float4 v = S.X[jl][rg + 4 * q][o];
+          dot2_term(t4[o][q].x, t4[o][q].y, m.x, m.y, v.x, v.y);
+          dot2_term(t4[o][q].x, t4[o][q].y, -m.z, -m.w, v.z, v.w);
+          dot2_term(t4[o][q].z, t4[o][q].w, m.x, m.y, v.z, v.w);
+          dot2_term(t4[o][q].z, t4[o][q].w, m.z, m.w, v.x, v.y);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        acc[o][q][0] = dadd(acc[o][q][0], df{t4[o][q].x, t4[o][q].y});
+        acc[o][q][1] = dadd(acc[o][q][1], df{t4[o][q].z, t4[o][q].w});
+      }
+  }
+  const int i = i0 + il2;
+  if (i < n) {
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        const int r = rg + 4 * q;
+        if (r < rbn)
+          P.part[(((size_t)o * P.splits + split) * P.nrhs + rb0 + r) * n + i] =
+              make_double2((double)acc[o][q][0].h + (double)acc[o][q][0].l,
+                           (double)acc[o][q][1].h + (double)acc[o][q][1].l);
+      }
+  }
+}
+
+// the four double-float inputs per right-hand side of the sound-hard sums:
+// u = d/ds x, n1 x, n2 x, x (n_c = nu~_c / |z'|)
+__global__ void k_df_x_hard(int n, size_t len, const double2* __restrict__ x,
+                            const double2* __restrict__ u, geom_dev g, float4* __restrict__ xo) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= len) return;
+  const int i = (int)(e % n);
+  const double inv = 1.0 / g.sp[i];
+  const double n1 = g.nx[i] * inv, n2 = g.ny[i] * inv;
+  const double2 xv = x[e], uv = u[e];
+  const double2 v[4] = {uv, make_double2(n1 * xv.x, n1 * xv.y), make_double2(n2 * xv.x, n2 * xv.y),
+                        xv};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float rh = (float)v[c].x, ih = (float)v[c].y;
+    xo[e * 4 + c] =
+        make_float4(rh, (float)(v[c].x - (double)rh), ih, (float)(v[c].y - (double)ih));
+  }
+}
+
 // densities to double-float planes, once per matvec
 __global__ void k_df_x(size_t len, const double2* __restrict__ x, float4* __restrict__ xo) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -356,7 +518,7 @@ k_df_scan(int n, double omega, geom_dev g, int* __restrict__ bmax) {
   if ((threadIdx.x & 31) == 0) atomicMax(bmax, best);
 }
 
-__global__ void k_df_band(int n, int b, double omega, double eta, geom_dev g,
+__global__ void k_df_band(int n, int b, int hard, double omega, double eta, geom_dev g,
                           const double* __restrict__ wtab, const double2* __restrict__ diag,
                           float4* __restrict__ band) {
   const int bw = 2 * b + 1;
@@ -366,17 +528,26 @@ __global__ void k_df_band(int n, int b, double omega, double eta, geom_dev g,
   const int dd = (int)(e % bw) - b;
   int j = (i - dd) % n;
   if (j < 0) j += n;
-  double2 a, unused;
+  double2 a, b2 = make_double2(0.0, 0.0);
   if (j == i) {
-    a = diag[i];
+    a = hard ? diag[2 * i] : diag[i];
+    if (hard) b2 = diag[2 * i + 1];
   } else {
     int d = i - j;
     if (d < 0) d += n;
-    pair_entries_fp64<0>(g.x[i] - g.x[j], g.y[i] - g.y[j], omega, eta, 2.0 * CFIE_PI / n, wtab[d],
-                         g.nx[j], g.ny[j], g.sp[j], g.nx[i], g.ny[i], g.sp[i], a, unused);
+    if (hard)
+      pair_entries_fp64<1>(g.x[i] - g.x[j], g.y[i] - g.y[j], omega, eta, 2.0 * CFIE_PI / n,
+                           wtab[d], g.nx[j], g.ny[j], g.sp[j], g.nx[i], g.ny[i], g.sp[i], a, b2);
+    else
+      pair_entries_fp64<0>(g.x[i] - g.x[j], g.y[i] - g.y[j], omega, eta, 2.0 * CFIE_PI / n,
+                           wtab[d], g.nx[j], g.ny[j], g.sp[j], g.nx[i], g.ny[i], g.sp[i], a, b2);
   }
   const df re = dmake(a.x), im = dmake(a.y);
   band[e] = make_float4(re.h, re.l, im.h, im.l);
+  if (hard) {
+    const df br = dmake(b2.x), bi = dmake(b2.y);
+    band[(size_t)n * bw + e] = make_float4(br.h, br.l, bi.h, bi.l);
+  }
 }
 
 unsigned nbk(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
@@ -406,6 +577,31 @@ int launch_df(cfie_op* op, df_params P, int nrhs) {
   return splits;
 }
 
+template <int RB>
+int launch_df_hard(cfie_op* op, df_params P, const float4* x4, int nrhs) {
+  const int n = op->n;
+  const int rowtiles = (n + DTI - 1) / DTI, slices = (nrhs + RB - 1) / RB;
+  const int ntiles = (n + DTJ - 1) / DTJ;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->ctx->device);
+  int splits = std::max(1, std::min(ntiles, (4 * sms + rowtiles * slices - 1) / (rowtiles * slices)));
+  const int tps = (ntiles + splits - 1) / splits;
+  splits = (ntiles + tps - 1) / tps;
+  P.splits = splits;
+  P.tiles_per_split = tps;
+  op->df_part.reserve(sizeof(double2) * 4 * (size_t)splits * nrhs * n);
+  P.part = op->df_part.as<double2>();
+  const size_t smem = sizeof(df_smem_hard<RB>);
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_pair_df_hard<RB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    prof_scope ps(op->ctx, CFIE_K_MATVEC_FP64);
+    k_pair_df_hard<RB><<<dim3(rowtiles, splits, slices), DNT, smem, op->ctx->stream>>>(P, x4);
+    CFIE_CHECK_LAUNCH();
+  }
+  return splits;
+}
+
 }  // namespace
 
 void df_prepare(cfie_op* op) {
@@ -421,29 +617,28 @@ void df_prepare(cfie_op* op) {
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
   const int b = std::min(std::max(1, hb), n / 2);
   const size_t bw = 2 * (size_t)b + 1;
-  if ((size_t)n * bw * sizeof(float4) > ((size_t)4 << 30)) {
+  if ((size_t)n * bw * sizeof(float4) * (op->bc == CFIE_SOUND_HARD ? 2 : 1) > ((size_t)4 << 30)) {
     op->df_b = -1;   // band too wide: residuals fall back to the FP64 kernel
     return;
   }
   op->df_b = b;
   op->df_geo.reserve((sizeof(float4) * 2 + sizeof(float2) * 2) * (size_t)n);
-  op->df_band.reserve(sizeof(float4) * (size_t)n * bw);
+  const int hard = op->bc == CFIE_SOUND_HARD ? 1 : 0;
+  op->df_band.reserve(sizeof(float4) * (size_t)n * bw * (hard ? 2 : 1));
   char* base = op->df_geo.as<char>();
   k_df_geo<<<nbk(n), 256, 0, st>>>(n, op->g, op->wtab.as<double>(), (float4*)base,
                                     (float4*)(base + sizeof(float4) * n),
                                     (float2*)(base + 2 * sizeof(float4) * n),
                                     (float2*)(base + (2 * sizeof(float4) + sizeof(float2)) * n));
   CFIE_CHECK_LAUNCH();
-  k_df_band<<<nbk((size_t)n * bw), 256, 0, st>>>(n, b, op->omega, op->eta, op->g,
+  k_df_band<<<nbk((size_t)n * bw), 256, 0, st>>>(n, b, hard, op->omega, op->eta, op->g,
                                                   op->wtab.as<double>(), op->diag.as<double2>(),
                                                   op->df_band.as<float4>());
   CFIE_CHECK_LAUNCH();
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
 }
 
-bool df_available(const cfie_op* op) {
-  return op->bc == CFIE_SOUND_SOFT && op->df_b > 0;
-}
+bool df_available(const cfie_op* op) { return op->df_b > 0; }
 
 void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
   const int n = op->n;
@@ -461,11 +656,31 @@ void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
   P.w = (const float2*)(base + (2 * sizeof(float4) + sizeof(float2)) * n);
   P.band = op->df_band.as<float4>();
   const size_t tot = (size_t)n * nrhs;
+  if (op->bc == CFIE_SOUND_HARD) {
+    // y = x/2 - D' x + (1/(i eta)) [d/ds S d/ds x + omega^2 sum_c n_c S (n_c x)]
+    op->tmp1.reserve(sizeof(double2) * tot);
+    op->tmp2.reserve(sizeof(double2) * tot);
+    double2* u = op->tmp1.as<double2>();
+    double2* t = op->tmp2.as<double2>();
+    spectral_apply(op, x, u, nullptr, make_double2(1.0, 0.0), nrhs);
+    op->df_x.reserve(sizeof(float4) * 4 * tot);
+    k_df_x_hard<<<nbk(tot), 256, 0, op->ctx->stream>>>(n, tot, x, u, op->g,
+                                                        op->df_x.as<float4>());
+    CFIE_CHECK_LAUNCH();
+    const float4* x4 = op->df_x.as<float4>();
+    const int splits = nrhs > 4 ? launch_df_hard<16>(op, P, x4, nrhs)
+                                : launch_df_hard<4>(op, P, x4, nrhs);
+    reduce_hard_fp64(op, op->df_part.as<double2>(), splits, x, t, y, nrhs);
+    spectral_apply(op, t, y, y, make_double2(0.0, -1.0 / op->eta), nrhs);
+    return;
+  }
   op->df_x.reserve(sizeof(float4) * tot);
   k_df_x<<<nbk(tot), 256, 0, op->ctx->stream>>>(tot, x, op->df_x.as<float4>());
   CFIE_CHECK_LAUNCH();
   P.x = op->df_x.as<float4>();
-  const int splits = nrhs > 16 ? launch_df<64>(op, P, nrhs) : launch_df<16>(op, P, nrhs);
+  const int splits = nrhs > 32   ? launch_df<64>(op, P, nrhs)
+                     : nrhs > 16 ? launch_df<32>(op, P, nrhs)
+                                 : launch_df<16>(op, P, nrhs);
   k_reduce_df<<<nbk(tot), 256, 0, op->ctx->stream>>>(n, nrhs, splits, op->df_part.as<double2>(),
                                                       y);
   CFIE_CHECK_LAUNCH();

@@ -289,6 +289,14 @@ void spectral_apply(cfie_op* op, const double2* in, double2* out, const double2*
   CFIE_CHECK_LAUNCH();
 }
 
+void reduce_hard_fp64(cfie_op* op, const double2* part, int splits, const double2* x,
+                      double2* t, double2* y, int nrhs) {
+  const size_t tot = (size_t)op->n * nrhs;
+  k_reduce_fp64<1><<<(unsigned)((tot + 255) / 256), 256, 0, op->ctx->stream>>>(
+      op->n, nrhs, splits, op->omega, op->eta, op->g, part, x, t, y);
+  CFIE_CHECK_LAUNCH();
+}
+
 void matvec_fp64(cfie_op* op, const double2* x, double2* y, int nrhs) {
   const int n = op->n;
   const int hard = op->bc == CFIE_SOUND_HARD;

@@ -23,7 +23,9 @@ def ctx():
 
 
 def _pts(p):
-    return torch.from_numpy(np.ascontiguousarray(p, dtype=np.float64)).cuda()
+    """(m, 2) points as the complex128 device vector x + i y."""
+    p = np.asarray(p, dtype=np.float64)
+    return torch.from_numpy(np.ascontiguousarray(p[:, 0] + 1j * p[:, 1])).cuda()
 
 
 @pytest.mark.parametrize("bc", ["soft", "hard"])

@@ -44,11 +44,32 @@ def test_residual_matvec_parity(ctx, kind, params, n, omega, nrhs, prec):
     assert np.max(col_rel(to_host(y), to_host(y64))) < TOL_RES
 
 
-def test_residual_falls_back_to_fp64_for_hard_and_fp64_operators(ctx):
+@pytest.mark.parametrize("kind,params,n,omega,nrhs", [
+    ("kite", {}, 600, 30.0, 3),
+    ("kite", {}, 2000, 200.0, 17),
+    ("star", {"a": [0, 0, 0, 0, 0.3], "b": [0] * 5}, 1502, 120.0, 1),
+    ("ellipse", {"a": 1.0, "b": 0.5}, 1000, 90.0, 5),
+])
+def test_hard_residual_matvec_parity(ctx, kind, params, n, omega, nrhs):
+    """Sound-hard operator (eq. 2, N by Maue's identity): the double-float
+    sums of S and D' with the FP64 spectral derivatives."""
+    c = geometry.make(kind, n, **params)
+    A = operators.cfie_matrix(c, omega, omega, "hard")
+    X = inputs.random_density(n, nrhs, seed=5 * n + nrhs)
+    op = ctx.geometry(kind, **params).discretise(n, omega, bc="hard", precision="fp32")
+    y = empty(nrhs, n)
+    op.apply_residual(to_dev(X), y)
+    assert np.max(col_rel(to_host(y), (A @ X.T).T)) < TOL_RES
+    y64 = empty(nrhs, n)
+    op.apply_fp64(to_dev(X), y64)
+    assert np.max(col_rel(to_host(y), to_host(y64))) < TOL_RES
+
+
+def test_residual_of_fp64_operators_is_the_fp64_kernel(ctx):
     n, w = 600, 30.0
     X = to_dev(inputs.random_density(n, 3, seed=2))
-    for bc, prec in (("hard", "fp32"), ("soft", "fp64")):
-        op = ctx.kite().discretise(n, w, bc=bc, precision=prec)
+    for bc in ("soft", "hard"):
+        op = ctx.kite().discretise(n, w, bc=bc, precision="fp64")
         y1, y2 = empty(3, n), empty(3, n)
         op.apply_residual(X, y1)
         op.apply_fp64(X, y2)

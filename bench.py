@@ -391,26 +391,56 @@ ORACLE_THREAD_ENV = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
 
 def oracle_single_core(args, budget_s):
     """Time the oracle on one host core in a fresh interpreter (BLAS pinned to
-    one thread); returns (pairs, seconds, rows)."""
+    one thread) on a bounded sample of the workload; returns the
+    cpu_baseline object."""
     env = dict(os.environ, **ORACLE_THREAD_ENV)
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-budget", str(budget_s),
            "--workload", args.workload]
-    for k in ("precision", "n", "nrhs"):
+    for k in ("precision", "n", "nrhs", "count"):
         v = getattr(args, k)
         if v is not None:
             cmd += [f"--{k}", str(v)]
-    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         raise RuntimeError("oracle sample failed: " + out.stderr[-500:])
     r = json.loads(out.stdout.strip().splitlines()[-1])
-    return r["pairs"], r["seconds"], r["rows"]
+    return {"value": r["value"], "unit": r["unit"], "cores": 1, "kind": "oracle",
+            "sample": r["sample"]}
 
 
 def oracle_budget_main(args):
-    spec = workload(args.workload, args.precision, args.n, args.nrhs)
-    rows = cpu_rows_for(spec, budget_s=args.oracle_budget)
-    p, s = oracle_sample(spec, rows)
-    print(json.dumps({"pairs": p, "seconds": s, "rows": rows}), flush=True)
+    if args.workload == "serve":
+        from oracle import geometry, operators, solvers
+        from paper_1408_1578_gb300 import inputs
+        reqs = inputs.poisson_requests(count=args.count or 32, rate=200.0, seed=1578, n_lo=1024,
+                                       n_hi=65536)
+        solves, secs, done = 0, 0.0, []
+        for r in sorted(reqs, key=lambda q: q["n"]):
+            t0 = time.perf_counter()
+            c = geometry.fourier_star(r["n"], r["a"], r["b"])
+            A = operators.cfie_matrix(c, r["omega"], r["omega"], r["bc"])
+            F = operators.plane_wave_rhs(c, r["omega"], inputs.directions(r["nrhs"]), r["bc"])
+            solvers.lu_solve(A, F)
+            secs += time.perf_counter() - t0
+            solves += r["nrhs"]
+            done.append(f"n={r['n']} {r['bc']} nrhs={r['nrhs']}")
+            if secs > args.oracle_budget:
+                break
+        print(json.dumps({"value": solves / secs, "unit": "solves/s",
+                          "sample": f"dense LU solves of the smallest requests ({secs:.1f} s, one "
+                                    "thread): " + "; ".join(done)}), flush=True)
+        return
+    specs = reference_specs(args)
+    pairs, secs, parts = 0, 0.0, []
+    for sp in specs:
+        rows = cpu_rows_for(sp, budget_s=args.oracle_budget / len(specs))
+        p, t = oracle_sample(sp, rows)
+        pairs += p
+        secs += t
+        parts.append(f"{rows} rows x {sp['n']} sources of the {sp['name']} operator")
+    print(json.dumps({"value": pairs / secs, "unit": UNIT,
+                      "sample": "; ".join(parts) + f", {specs[0]['nrhs']} right-hand sides "
+                                f"({secs:.1f} s, one thread)"}), flush=True)
 
 
 def cpu_rows_for(spec, budget_s=12.0):
@@ -590,6 +620,7 @@ def main():
         os.environ.update(ORACLE_THREAD_ENV)
     if args.workload in ("stars", "serve") and args.impl == "ours":
         out = run_stars(args) if args.workload == "stars" else run_serve(args)
+        out["cpu_baseline"] = oracle_single_core(args, 12.0)
         print(json.dumps(out), flush=True)
         return
     rank, world = init_dist()
@@ -598,12 +629,7 @@ def main():
     else:
         out = run_ours(args, rank, world)
         if rank == 0 and out is not None and world == 1:
-            spec = workload(args.workload, args.precision, args.n, args.nrhs)
-            p, s, rows = oracle_single_core(args, 12.0)
-            out["cpu_baseline"] = {"value": p / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": f"{rows} rows x {spec['n']} sources of the "
-                                             f"{spec['name']} operator, {spec['nrhs']} "
-                                             f"right-hand sides ({s:.1f} s, one thread)"}
+            out["cpu_baseline"] = oracle_single_core(args, 12.0)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if _PG is not None:

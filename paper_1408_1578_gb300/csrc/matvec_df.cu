@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "hankel64.cuh"
 #include "internal.h"
@@ -602,6 +604,43 @@ int launch_df_hard(cfie_op* op, df_params P, const float4* x4, int nrhs) {
   return splits;
 }
 
+std::mutex g_df_mu;
+std::map<std::pair<int, int>, int> g_df_rb;
+
+// right-hand sides per CTA of the soft residual kernel for (n, nrhs): cached,
+// else both candidates timed once with CUDA events on the operator's stream
+template <typename F>
+int df_tile_choice(cfie_op* op, int n, int nrhs, F run) {
+  const auto key = std::make_pair(n, nrhs);
+  {
+    std::lock_guard<std::mutex> lock(g_df_mu);
+    auto it = g_df_rb.find(key);
+    if (it != g_df_rb.end()) return it->second;
+  }
+  cudaStream_t st = op->ctx->stream;
+  cudaEvent_t e0, e1;
+  CFIE_CHECK_CUDA(cudaEventCreate(&e0));
+  CFIE_CHECK_CUDA(cudaEventCreate(&e1));
+  op->ctx->prof_suspend++;
+  float t[2] = {0.f, 0.f};
+  const int cand[2] = {64, 32};
+  for (int c = 0; c < 2; ++c) {
+    run(cand[c]);   // attributes, scratch
+    CFIE_CHECK_CUDA(cudaEventRecord(e0, st));
+    run(cand[c]);
+    CFIE_CHECK_CUDA(cudaEventRecord(e1, st));
+    CFIE_CHECK_CUDA(cudaEventSynchronize(e1));
+    CFIE_CHECK_CUDA(cudaEventElapsedTime(&t[c], e0, e1));
+  }
+  op->ctx->prof_suspend--;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int choice = t[1] < t[0] ? 32 : 64;
+  std::lock_guard<std::mutex> lock(g_df_mu);
+  g_df_rb[key] = choice;
+  return choice;
+}
+
 }  // namespace
 
 void df_prepare(cfie_op* op) {
@@ -678,9 +717,17 @@ void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
   k_df_x<<<nbk(tot), 256, 0, op->ctx->stream>>>(tot, x, op->df_x.as<float4>());
   CFIE_CHECK_LAUNCH();
   P.x = op->df_x.as<float4>();
-  const int splits = nrhs > 32   ? launch_df<64>(op, P, nrhs)
-                     : nrhs > 16 ? launch_df<32>(op, P, nrhs)
-                                 : launch_df<16>(op, P, nrhs);
+  int splits;
+  if (nrhs > 32) {
+    // 64 right-hand sides per CTA (one pass of entries, one CTA per SM) or 32
+    // (entries evaluated twice, two CTAs per SM): timed once per (n, nrhs)
+    const int rb = df_tile_choice(op, n, nrhs, [&](int c) {
+      return c == 64 ? launch_df<64>(op, P, nrhs) : launch_df<32>(op, P, nrhs);
+    });
+    splits = rb == 64 ? launch_df<64>(op, P, nrhs) : launch_df<32>(op, P, nrhs);
+  } else {
+    splits = nrhs > 16 ? launch_df<32>(op, P, nrhs) : launch_df<16>(op, P, nrhs);
+  }
   k_reduce_df<<<nbk(tot), 256, 0, op->ctx->stream>>>(n, nrhs, splits, op->df_part.as<double2>(),
                                                       y);
   CFIE_CHECK_LAUNCH();

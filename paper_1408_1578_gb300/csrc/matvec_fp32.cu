@@ -298,7 +298,7 @@ k_spectral32(int n, const float* __restrict__ ct, const double* __restrict__ sp,
 // ---------------------------------------------------------------------------
 __global__ void k_geo32(int n, geom_dev g, geo32 o, const double* __restrict__ w,
                         const double* __restrict__ ct, float* __restrict__ w32,
-                        float* __restrict__ c32) {
+                        float* __restrict__ c32, float4* __restrict__ pk) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double x = g.x[i], y = g.y[i];
@@ -315,6 +315,8 @@ __global__ void k_geo32(int n, geom_dev g, geo32 o, const double* __restrict__ w
   // the Kress table twice over, indexed by i - j + n (no cyclic wrap)
   w32[2 * n + i] = (float)w[i];
   w32[3 * n + i] = (float)w[i];
+  pk[i] = make_float4(xh, (float)(x - (double)xh), yh, (float)(y - (double)yh));
+  pk[n + i] = make_float4((float)g.nx[i], (float)g.ny[i], (float)g.sp[i], 0.f);
 }
 
 // Largest cyclic index distance |i - j| of a pair with omega r < X0 (with a
@@ -436,7 +438,7 @@ int launch32(cfie_op* op, pair_params P, int rowtiles, int slices) {
 void fp32_prepare(cfie_op* op) {
   const int n = op->n;
   cudaStream_t st = op->ctx->stream;
-  op->geo32.reserve(sizeof(float) * 11 * (size_t)n);
+  op->geo32.reserve(sizeof(float) * geo32_floats(n));
   // band width and argument range
   dbuf scan;
   scan.reserve(16);
@@ -466,7 +468,8 @@ void fp32_prepare(cfie_op* op) {
   float* w32 = base + 7 * n;
   float* c32 = base + 8 * n;
   k_geo32<<<nblk(n), 256, 0, st>>>(n, op->g, o, op->wtab.as<double>(), op->ctab.as<double>(),
-                                    w32, c32);
+                                    w32, c32,
+                                    reinterpret_cast<float4*>(base + geo32_pack_offset(n)));
   CFIE_CHECK_LAUNCH();
   float2* band = op->band.as<float2>();
   if (op->bc == CFIE_SOUND_SOFT) {

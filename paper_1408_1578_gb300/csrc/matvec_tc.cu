@@ -52,6 +52,7 @@ struct tc_params : omega32 {
   geo32 g;
   const float* w32;
   const float* wext;     // Kress table indexed by i - j + n
+  const float4* pk;      // packed coordinates (n) then normals / speeds (n)
   const float2* band;
 };
 
@@ -147,21 +148,18 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
         const int r = warp + NPROD * lane;
         const int i = m0 + r;
         const bool ok = i < n;
-        S.tgt[r] = ok ? make_float4(P.g.xh[i], P.g.xl[i], P.g.yh[i], P.g.yl[i])
-                      : make_float4(0.f, 0.f, 0.f, 0.f);
+        S.tgt[r] = ok ? P.pk[i] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncwarp();
       // geometry of this lane's two sources, loaded one tile ahead
-      float4 pc[2];
-      float3 pn[2];
+      float4 pc[2], pn[2];
       auto load_src = [&](int kk) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const int jj = kk * TBK + jp + u;
           const bool ok = jj < n;
-          pc[u] = ok ? make_float4(P.g.xh[jj], P.g.xl[jj], P.g.yh[jj], P.g.yl[jj])
-                     : make_float4(0.f, 0.f, 0.f, 0.f);
-          pn[u] = ok ? make_float3(P.g.nx[jj], P.g.ny[jj], P.g.sp[jj]) : make_float3(0.f, 0.f, 1.f);
+          pc[u] = ok ? P.pk[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+          pn[u] = ok ? P.pk[n + jj] : make_float4(0.f, 0.f, 1.f, 0.f);
         }
       };
       load_src(sg.z);
@@ -170,7 +168,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
         const int j0 = k * TBK;
         const int j = j0 + jp;                       // first of the lane's two sources
         const float4 sc[2] = {pc[0], pc[1]};
-        const float3 sn[2] = {pn[0], pn[1]};
+        const float4 sn[2] = {pn[0], pn[1]};
         if (k + 1 < sg.w) load_src(k + 1);
         if (*(volatile int*)&S.abort) break;
         if (it >= TSTAGES && !mbar_wait(&S.empty[st], ((it / TSTAGES) - 1) & 1)) {
@@ -436,6 +434,7 @@ void run_fused(cfie_op* op, const double2* x, double2* y, int r0, int nr) {
   P.g = geo32_at(base, n);
   P.w32 = base + 7 * n;
   P.wext = base + 9 * n;
+  P.pk = reinterpret_cast<const float4*>(base + geo32_pack_offset(n));
   P.band = op->band.as<float2>();
   const size_t smem = tc_smem_bytes<NP>();
   CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_fused_tc<NP>,

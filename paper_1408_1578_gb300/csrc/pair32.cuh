@@ -12,6 +12,12 @@ struct geo32 {
   float *xh, *xl, *yh, *yl, *nx, *ny, *sp;
 };
 
+// packed per-node copies for the fused kernels, after the 11 n floats above:
+// float4 (x hi, x lo, y hi, y lo) and float4 (nu1, nu2, |z'|, 0), n of each,
+// starting on a 16-byte boundary
+inline size_t geo32_pack_offset(int n) { return ((size_t)11 * n + 3) & ~size_t(3); }
+inline size_t geo32_floats(int n) { return geo32_pack_offset(n) + (size_t)8 * n; }
+
 inline geo32 geo32_at(float* base, int n) {
   return geo32{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n,
                base + 6 * n};

@@ -100,6 +100,7 @@ SIGNATURES = {
     "cfie_op_set_variant": (_I, [_P, _I]),
     "cfie_gmres_solve": (_I, [_P, _P, _P, _I, _D, _I, _I, _IP, _DP]),
     "cfie_op_set_inner_basis": (_I, [_P, _I]),
+    "cfie_op_set_residual_variant": (_I, [_P, _I]),
     "cfie_field_eval": (_I, [_P, _P, _I, _I, _P, _P]),
     "cfie_op_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
     "cfie_ctx_set_profiling": (_I, [_P, _I]),
@@ -445,6 +446,11 @@ class Operator:
         npts = pts.numel()
         self.ctx.check(self.ctx.lib.cfie_field_eval(self.h, _addr(q), int(nrhs), int(npts),
                                                     _addr(pts), _addr(u)), "cfie_field_eval")
+
+    def set_residual_variant(self, variant):
+        """0 automatic, 1 double-float Dot2 on the CUDA cores, 2 sliced on the tensor cores."""
+        self.ctx.check(self.ctx.lib.cfie_op_set_residual_variant(self.h, int(variant)),
+                       "cfie_op_set_residual_variant")
 
     def set_inner_basis(self, fp32):
         """Refined precisions: inner Krylov basis in FP32 (True, default) or FP64."""

@@ -349,6 +349,8 @@ cfie_status cfie_apply(cfie_op* op, const void* x_dev, void* y_dev, int nrhs) {
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     if (op->prec == CFIE_FP32_REFINED && tc_take_error(op))
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
+    if (op->prec != CFIE_FP64 && df_take_error(op))
+      throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
   });
 }
 
@@ -371,6 +373,8 @@ cfie_status cfie_apply_residual(cfie_op* op, const void* x_dev, void* y_dev, int
     CFIE_REQUIRE(x_dev != y_dev, "x and y must not overlap");
     set_device(op->ctx);
     matvec_residual(op, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev), nrhs);
+    if (op->prec != CFIE_FP64 && df_take_error(op))
+      throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
   });
 }
 
@@ -429,6 +433,8 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     if (op->prec == CFIE_FP32_REFINED && tc_take_error(op))
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
+    if (op->prec != CFIE_FP64 && df_take_error(op))
+      throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     if (result == CFIE_ENOCONV) op->ctx->err = "GMRES reached maxit before rtol";
   });
   if (st != CFIE_OK) return st;
@@ -456,6 +462,16 @@ cfie_status cfie_measure_peaks(cfie_ctx* ctx, cfie_peaks* out) {
   return guarded(ctx, [&] {
     set_device(ctx);
     measure_peaks(ctx, out);
+  });
+}
+
+cfie_status cfie_op_set_residual_variant(cfie_op* op, int variant) {
+  if (!op || variant < 0 || variant > 2) return CFIE_EINVAL;
+  return guarded(op->ctx, [&] {
+    CFIE_REQUIRE(op->prec != CFIE_FP64, "the FP64 precision computes residuals with its own matvec");
+    CFIE_REQUIRE(variant != 2 || op->bc == CFIE_SOUND_SOFT,
+                 "the tensor-core residual supports the sound-soft operator");
+    op->res_variant = variant;
   });
 }
 
@@ -647,6 +663,9 @@ cfie_status cfie_batch_gmres_solve(cfie_batch* b, const void* f_dev, void* x_dev
     b->stats.matvec_variant = b->all_stored ? 3 : b->ops.empty() ? 0 : b->ops[0]->stats.matvec_variant;
     if (b->all_stored && gemm_plan_take_error(b->plan, b->ctx))
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
+    for (cfie_op* o : b->ops)
+      if (o->prec != CFIE_FP64 && df_take_error(o))
+        throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     if (result == CFIE_ENOCONV) b->ctx->err = "GMRES reached maxit before rtol";
   });
   if (st != CFIE_OK) return st;

@@ -156,6 +156,17 @@ struct tc_plan {
   alignas(64) unsigned char tmB[128];   // CUtensorMap of the B planes
 };
 
+// Plan of the tensor-core residual for one right-hand-side block width
+// (matvec_df.cu): stream-K segments, density slice planes and their tensor
+// map, per-segment double-float sums, column exponents, band part, error flag.
+struct rtc_plan {
+  bool built = false;
+  int grid = 0, nsegs = 0, mtiles = 0, pitch = 0;
+  size_t o_cbeg = 0, o_mts = 0;
+  dbuf tables, bt, acc, fx, yb, err;
+  alignas(64) unsigned char tmB[128];
+};
+
 struct cfie_op {
   cfie_ctx* ctx = nullptr;
   int n = 0;
@@ -184,6 +195,9 @@ struct cfie_op {
   // FP64-accurate residual matvec in double-float arithmetic (sound-soft)
   dbuf df_geo, df_band, df_part, df_x;
   int df_b = -1;
+  dbuf df_rowexp;    // sound soft: row exponents of the far entries (tensor-core residual)
+  rtc_plan rtc[3];   // tensor-core residual plans for 16, 32, 64 right-hand sides per pass
+  int res_variant = 0;   // residual: 0 automatic, 1 CUDA-core Dot2, 2 tensor cores
 
   // FP32 matvec variant: 0 = autotuned, 1 = FP32-pipe contraction, 2 = tensor cores
   int variant = 0, tuned_nrhs = -1, tuned_choice = 1;
@@ -276,6 +290,7 @@ void matvec_residual(cfie_op* op, const double2* x, double2* y, int nrhs);
 // matvec_tc.cu
 void matvec_fp32_tc(cfie_op* op, const double2* x, double2* y, int nrhs);
 int tc_take_error(cfie_op* op);
+int df_take_error(cfie_op* op);
 // arnoldi.cu
 void pset_build(pset& ps, const std::vector<size_t>& off, const std::vector<int>& len,
                 cudaStream_t st);

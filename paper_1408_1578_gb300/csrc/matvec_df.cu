@@ -25,8 +25,16 @@
 #include <map>
 #include <mutex>
 
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <vector>
+
 #include "hankel64.cuh"
 #include "internal.h"
+#include "pair32.cuh"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -135,6 +143,7 @@ struct df_params {
   const float4* band;           // near entries (re hi, re lo, im hi, im lo), n x (2b + 1)
   const float4* x;              // densities as double-float (re hi, re lo, im hi, im lo)
   double2* part;                // [split][k][i]
+  const int* fx;                // tensor-core residual: exponent of each accumulator column
 };
 
 // Hankel values of one far pair (omega r >= 40) in double-float: (dx, dy) =
@@ -453,6 +462,472 @@ __global__ void k_df_x_hard(int n, size_t len, const double2* __restrict__ x,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Sound-soft residual with the source sums on the tensor cores.
+//
+// Far pairs (outside the double-float band) are evaluated in double-float as
+// above and written as bf16 slices: with E_i the row's exponent (every far
+// |Re a_ij|, |Im a_ij| < 2^E_i, precomputed per operator) the entry scaled by
+// 2^(7 - E_i) is split into six integers q_1..q_6, |q_s| <= 128, taken 8 bits
+// at a time, and slice s is stored as q_s 2^(-8(s-1)), exact in bf16.  The
+// densities are sliced the same way per right-hand side (exponent F_r).  The
+// products of slice pairs (s, t) with s + t <= 7 are summed by tcgen05.mma into
+// four FP32 accumulators by level L = s + t: L = 2, 3, 4 (one each) and L >= 5
+// (together).  Within one level every product is an integer multiple of the
+// same power of two and stays below 2^14 of it, so 128 sources (256 terms with
+// the split complex product, 768 for level 4) sum exactly in FP32; only the
+// levels >= 5 (below 2^-24 of the result) round.  Every 128 sources the
+// epilogue adds the four levels in double-float, scales by 2^(E_i + F_r - 14)
+// and accumulates per-segment double-float sums in global memory.  Near pairs
+// (the band, with the diagonal) are summed separately (k_band_df).  Split
+// complex as in the FP32 tensor-core kernel: [Yr | Yi] += Ar [Xr | Xi] +
+// Ai [-Xi | Xr].
+// ---------------------------------------------------------------------------
+constexpr int RTM = 128;      // rows per tile (UMMA M)
+constexpr int RTK = 16;       // sources per tile: one K step, 32-byte rows
+constexpr int RSL = 6;        // slices per operand
+constexpr int RST = 2;        // pipeline stages
+constexpr int RCK = 8;        // tiles per exact TMEM chunk (128 sources)
+constexpr int RPROD = 16;     // producer warps
+constexpr int RWTMA = RPROD, RWMMA = RPROD + 1;
+constexpr int RNT = (RPROD + 6) * 32;
+
+template <int NB>
+struct rtc_smem {
+  __nv_bfloat16 A[RST][2 * RSL][RTM * RTK];    // Ar slices 0..5, Ai slices 0..5
+  __nv_bfloat16 B[RST][2 * RSL][2 * NB * RTK]; // per slice t: [Xr | Xi], [-Xi | Xr]
+  float4 tgt[RTM];
+  int ex[RTM];
+  uint64_t full[RST], empty[RST], tfull, tempty;
+  uint32_t tmem_base;
+  int abort;
+  int issued[RST];
+};
+
+template <int NB>
+constexpr size_t rtc_smem_bytes() {
+  return sizeof(rtc_smem<NB>) + 1024;
+}
+
+// byte offset of element (row r, k < 16) in a 32-byte-swizzled K-major tile
+__device__ __forceinline__ uint32_t sw32(int r, int k) {
+  return (uint32_t)(r * 32 + ((((k >> 3) ^ (r >> 2)) & 1) << 4) + (k & 7) * 2);
+}
+
+// K-major operand in 32-byte-swizzled rows, 8-row groups 256 bytes apart
+__device__ __forceinline__ uint64_t smem_desc_sw32(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(256 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;                      // 32-byte swizzle
+  return d;
+}
+
+// six 8-bit slices of a double-float value already scaled below 128 in
+// magnitude, slice s multiplied by 2^(-8 s)
+__device__ __forceinline__ void slice6(float h, float l, float* o) {
+  float q = rintf(h);
+  o[0] = q;
+  float r = h - q;                             // exact
+#pragma unroll
+  for (int s = 1; s < 3; ++s) {
+    q = rintf(r * 256.f);
+    r = fmaf(r, 256.f, -q);                    // exact
+    o[s] = q * (s == 1 ? 0.00390625f : 1.52587890625e-05f);
+  }
+  // the rest of h (scaled by 2^16) with l: within 2^-24 of its size
+  float rr = fmaf(r, 256.f, l * 16777216.f);
+  q = rintf(rr);
+  o[3] = q * 5.9604644775390625e-08f;          // 2^-24
+  rr -= q;
+  q = rintf(rr * 256.f);
+  o[4] = q * 2.3283064365386963e-10f;          // 2^-32
+  rr = fmaf(rr, 256.f, -q);
+  q = rintf(rr * 256.f);
+  o[5] = q * 9.094947017729282e-13f;           // 2^-40
+}
+
+template <int NB>
+__global__ void __launch_bounds__(RNT, 1)
+k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ CUtensorMap tmB,
+           const int4* __restrict__ segs, const int* __restrict__ cbeg,
+           float2* __restrict__ acc_out, int* __restrict__ err) {
+  constexpr int NC = 2 * NB;                   // accumulator columns per level
+  constexpr uint32_t TMEM_COLS = 4 * NC <= 128 ? 128 : (4 * NC <= 256 ? 256 : 512);
+  constexpr uint32_t B_BYTES = 2u * RSL * NC * RTK * 2u;
+  extern __shared__ unsigned char raw[];
+  rtc_smem<NB>& S = *reinterpret_cast<rtc_smem<NB>*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
+                                                      ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sb = cbeg[blockIdx.x], se = cbeg[blockIdx.x + 1];
+  const int n = P.n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < RST; ++s) {
+      mbar_init(&S.full[s], RPROD * 32 + 1);
+      mbar_init(&S.empty[s], 1);
+      S.issued[s] = -1;
+    }
+    mbar_init(&S.tfull, 1);
+    mbar_init(&S.tempty, 4);
+    S.abort = 0;
+    fence_mbar_init();
+  }
+  if (warp == RWMMA) {
+    tmem_alloc(&S.tmem_base, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = S.tmem_base;
+
+  if (warp < RPROD) {
+    // ---- producers: warp w owns rows w + RPROD (4 q + lane / 8), q = 0, 1;
+    // lane l the two adjacent sources 2 (l % 8), +1 of the 16-source tile
+    const int sub = lane >> 3, jp = 2 * (lane & 7);
+    int it = 0;
+    for (int s = sb; s < se; ++s) {
+      const int4 sg = segs[s];
+      const int m0 = sg.y * RTM;
+      __syncwarp();
+      if (lane < RTM / RPROD) {
+        const int r = warp + RPROD * lane;
+        const int i = m0 + r;
+        S.tgt[r] = i < n ? P.g[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        S.ex[r] = i < n ? rowexp[i] : 0;
+      }
+      __syncwarp();
+      for (int k = sg.z; k < sg.w; ++k, ++it) {
+        const int st = it % RST;
+        if (*(volatile int*)&S.abort) break;
+        if (it >= RST && !mbar_wait(&S.empty[st], ((it / RST) - 1) & 1)) {
+          if (lane == 0) {
+            atomicExch(err, 21);
+            S.abort = 1;
+          }
+          break;
+        }
+        const int j = k * RTK + jp;
+        float4 gj[2], nj[2];
+        float2 sj[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const bool ok = j + u < n;
+          gj[u] = ok ? P.g[j + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+          nj[u] = ok ? P.nrm[j + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+          sj[u] = ok ? P.sp[j + u] : make_float2(1.f, 0.f);
+        }
+        unsigned char* A = reinterpret_cast<unsigned char*>(&S.A[st][0][0]);
+#pragma unroll 1
+        for (int q = 0; q < 2; ++q) {
+          const int il = warp + RPROD * (4 * q + sub);
+          const int i = m0 + il;
+          const float4 gi = S.tgt[il];
+          const int e = S.ex[il];
+          float sl[2][2][RSL];                  // [source][re/im][slice]
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int jj = j + u;
+            if (i < n && jj < n) {
+              int d = i - jj;
+              if (d < 0) d += n;
+              if (d > P.b && d < n - P.b) a = entry_df(P, gi, gj[u], nj[u], sj[u], P.w[d]);
+            }
+            // scale by 2^(7 - e): exact for both parts
+            const float sc = __int_as_float((127 + 7 - e) << 23);
+            slice6(a.x * sc, a.y * sc, sl[u][0]);
+            slice6(a.z * sc, a.w * sc, sl[u][1]);
+          }
+          const uint32_t o = sw32(il, jp);
+#pragma unroll
+          for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int t = 0; t < RSL; ++t) {
+              const __nv_bfloat162 v = __floats2bfloat162_rn(sl[0][c][t], sl[1][c][t]);
+              *reinterpret_cast<__nv_bfloat162*>(A + (size_t)(c * RSL + t) * RTM * RTK * 2 + o) = v;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&S.full[st]);
+      }
+      if (*(volatile int*)&S.abort) break;
+    }
+  } else if (warp == RWTMA) {
+    if (lane == 0) {
+      // ---- TMA: the 2 x 6 density-slice planes of each source tile
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      int it = 0;
+      for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
+        const int4 sg = segs[s];
+        for (int k = sg.z; k < sg.w; ++k, ++it) {
+          const int st = it % RST;
+          if (it >= RST && !mbar_wait(&S.empty[st], ((it / RST) - 1) & 1)) {
+            atomicExch(err, 22);
+            S.abort = 1;
+            break;
+          }
+          mbar_arrive_expect_tx(&S.full[st], B_BYTES);
+          S.issued[st] = (it / RST) & 1;
+#pragma unroll
+          for (int p = 0; p < 2 * RSL; ++p)
+            tma_load_2d(&S.B[st][p][0], &tmB, &S.full[st], k * RTK, p * NC);
+        }
+      }
+    }
+  } else if (warp == RWMMA) {
+    if (lane == 0) {
+      // ---- MMA: per tile and slice pair (s, t), s + t <= 7 (1-based), two
+      // MMAs into the accumulator of level min(s + t, 5)
+      constexpr uint32_t idesc = make_idesc(RTM, NC);
+      int it = 0, cc = 0;
+      for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
+        const int4 sg = segs[s];
+        for (int c0 = sg.z; c0 < sg.w; c0 += RCK, ++cc) {
+          const int c1 = min(sg.w, c0 + RCK);
+          if (cc >= 1 && !mbar_wait(&S.tempty, (cc - 1) & 1)) {
+            atomicExch(err, 24);
+            S.abort = 1;
+          }
+          if (*(volatile int*)&S.abort) break;
+          tc_fence_after();
+          for (int k = c0; k < c1; ++k, ++it) {
+            const int st = it % RST;
+            if (!mbar_wait(&S.full[st], (it / RST) & 1)) {
+              atomicExch(err, 23);
+              S.abort = 1;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t a_base = smem_u32(&S.A[st][0][0]);
+            const uint32_t b_base = smem_u32(&S.B[st][0][0]);
+            bool started[4] = {k > c0, k > c0, k > c0, k > c0};
+#pragma unroll
+            for (int sa = 0; sa < RSL; ++sa)
+#pragma unroll
+              for (int tb = 0; tb < RSL; ++tb) {
+                if (sa + tb > 5) continue;          // levels up to 7 (1-based s + t)
+                const int lv = sa + tb < 3 ? sa + tb : 3;
+                const uint32_t d = tmem + (uint32_t)(lv * NC);
+                const uint32_t ar = a_base + (uint32_t)(sa * RTM * RTK * 2);
+                const uint32_t ai = a_base + (uint32_t)((RSL + sa) * RTM * RTK * 2);
+                const uint32_t b1 = b_base + (uint32_t)((2 * tb) * NC * RTK * 2);
+                const uint32_t b2 = b_base + (uint32_t)((2 * tb + 1) * NC * RTK * 2);
+                umma_bf16(d, smem_desc_sw32(ar), smem_desc_sw32(b1), idesc, started[lv] ? 1u : 0u);
+                started[lv] = true;
+                umma_bf16(d, smem_desc_sw32(ai), smem_desc_sw32(b2), idesc, 1u);
+              }
+            umma_commit(&S.empty[st]);
+          }
+          umma_commit(&S.tfull);
+        }
+      }
+    }
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows)
+    const int qd = warp & 3;
+    const int row = 32 * qd + lane;
+    int cc = 0;
+    bool stop = false;
+    for (int s = sb; s < se && !stop; ++s) {
+      const int4 sg = segs[s];
+      const int i = sg.y * RTM + row;
+      const float rs = __int_as_float((127 + (i < n ? rowexp[i] : 0) - 14) << 23);
+      float2* dst = acc_out + (size_t)s * NC * RTM + row;
+      for (int c0 = sg.z; c0 < sg.w; c0 += RCK, ++cc) {
+        if (*(volatile int*)&S.abort || !mbar_wait(&S.tfull, cc & 1)) {
+          if (lane == 0) {
+            atomicExch(err, 25);
+            S.abort = 1;
+          }
+          stop = true;
+          break;
+        }
+        __syncwarp();
+        tc_fence_after();
+        const bool first = c0 == sg.z;
+        const uint32_t base = tmem + ((uint32_t)(32 * qd) << 16);
+#pragma unroll 1
+        for (int cb = 0; cb < NC; cb += 16) {
+          float v0[16], v1[16], v2[16], v3[16];
+          tmem_ld16(base + (uint32_t)(0 * NC + cb), v0);
+          tmem_ld16(base + (uint32_t)(1 * NC + cb), v1);
+          tmem_ld16(base + (uint32_t)(2 * NC + cb), v2);
+          tmem_ld16(base + (uint32_t)(3 * NC + cb), v3);
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            const int col = cb + r;
+            // levels 2 + 3 exactly (TwoSum), then the smaller levels
+            const float sh = v0[r] + v1[r];
+            const float bv = sh - v0[r];
+            float sl = (v0[r] - (sh - bv)) + (v1[r] - bv);
+            sl += v2[r] + v3[r];
+            const float fs = __int_as_float((127 + P.fx[col]) << 23);  // 2^F_col
+            df val = quick(sh, sl);
+            val.h *= rs * fs;
+            val.l *= rs * fs;
+            float2* p = dst + (size_t)col * RTM;
+            if (!first) {
+              const float2 o = *p;
+              val = dadd(val, df{o.x, o.y});
+            }
+            *p = make_float2(val.h, val.l);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.tempty);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *(volatile int*)&S.abort) {
+    for (int s = 0; s < RST; ++s)
+      if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
+  }
+  __syncthreads();
+  if (warp == RWMMA) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// Row exponents of the far entries: E_i with |Re a_ij|, |Im a_ij| < 2^E_i for
+// every pair outside the double-float band, from the FP32 entries with a
+// 1e-4 margin (their relative error is ~1e-6); 0 for rows without far pairs.
+__global__ void __launch_bounds__(256)
+k_rowexp(int n, int b, omega32 W, geo32 g, const float* __restrict__ w32, int* __restrict__ rowexp) {
+  __shared__ float red[4][64];
+  const int il = threadIdx.x % 64, qd = threadIdx.x / 64;
+  const int i = blockIdx.x * 64 + il;
+  float m = 0.f;
+  if (i < n) {
+    const float txh = g.xh[i], txl = g.xl[i], tyh = g.yh[i], tyl = g.yl[i];
+    for (int j = qd; j < n; j += 4) {
+      int d = i - j;
+      if (d < 0) d += n;
+      if (d <= b || d >= n - b) continue;
+      float2 a, unused;
+      pair_entries_fp32<0>(W, txh, txl, tyh, tyl, 0.f, 0.f, 1.f, g.xh[j], g.xl[j], g.yh[j],
+                           g.yl[j], g.nx[j], g.ny[j], g.sp[j], w32[d], a, unused);
+      m = fmaxf(m, fmaxf(fabsf(a.x), fabsf(a.y)));
+    }
+  }
+  red[qd][il] = m;
+  __syncthreads();
+  if (qd == 0 && i < n) {
+    m = fmaxf(fmaxf(red[0][il], red[1][il]), fmaxf(red[2][il], red[3][il]));
+    int e = 0;
+    if (m > 0.f) frexpf(m * 1.0001f, &e);
+    rowexp[i] = e;
+  }
+}
+
+// Column exponents F_r (|Re x|, |Im x| < 2^F_r) of the right-hand sides r0 ..
+// r0 + nr - 1, written for the 2 NB accumulator columns (re r, then im r).
+__global__ void __launch_bounds__(256)
+k_colexp(int n, int NB, int nr, const double2* __restrict__ x, int* __restrict__ fx) {
+  __shared__ double red[256];
+  const int r = blockIdx.x;
+  double m = 0.0;
+  if (r < nr)
+    for (int j = threadIdx.x; j < n; j += 256) {
+      const double2 v = x[(size_t)r * n + j];
+      m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int e = 0;
+    if (red[0] > 0.0) frexp(red[0] * (1.0 + 1e-6), &e);
+    fx[r] = e;
+    fx[NB + r] = e;
+  }
+}
+
+// Density slices: plane 2t = [Xr_t | Xi_t], plane 2t + 1 = [-Xi_t | Xr_t] (rows
+// = accumulator columns, NB each half), slice t scaled as in slice6.
+__global__ void k_xslices(int n, int pitch, int NB, int nr, const double2* __restrict__ x,
+                          const int* __restrict__ fx, __nv_bfloat16* __restrict__ bt) {
+  const int j = blockIdx.x * 256 + threadIdx.x;
+  const int r = blockIdx.y;
+  if (j >= pitch) return;
+  float sr[RSL], si[RSL];
+  if (j < n && r < nr) {
+    const double2 v = x[(size_t)r * n + j];
+    const double sc = ldexp(1.0, 7 - fx[r]);
+    const double vr = v.x * sc, vi = v.y * sc;
+    const float rh = (float)vr, ih = (float)vi;
+    slice6(rh, (float)(vr - (double)rh), sr);
+    slice6(ih, (float)(vi - (double)ih), si);
+  } else {
+#pragma unroll
+    for (int t = 0; t < RSL; ++t) sr[t] = si[t] = 0.f;
+  }
+  const size_t plane = (size_t)2 * NB * pitch;
+#pragma unroll
+  for (int t = 0; t < RSL; ++t) {
+    __nv_bfloat16* p1 = bt + (size_t)(2 * t) * plane;
+    __nv_bfloat16* p2 = bt + (size_t)(2 * t + 1) * plane;
+    p1[(size_t)r * pitch + j] = __float2bfloat16_rn(sr[t]);
+    p1[(size_t)(NB + r) * pitch + j] = __float2bfloat16_rn(si[t]);
+    p2[(size_t)r * pitch + j] = __float2bfloat16_rn(-si[t]);
+    p2[(size_t)(NB + r) * pitch + j] = __float2bfloat16_rn(sr[t]);
+  }
+}
+
+// Near-band part of the soft residual (diagonal included): Dot2 over the
+// 2 b + 1 band entries of each row, double-float densities
+__global__ void k_band_df(int n, int b, int nrhs, const float4* __restrict__ band,
+                          const float4* __restrict__ x, double2* __restrict__ yb) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * nrhs) return;
+  const int i = (int)(e % n), r = (int)(e / n);
+  const int bw = 2 * b + 1;
+  float sx = 0.f, ex = 0.f, sy = 0.f, ey = 0.f;
+  for (int dd = -b; dd <= b; ++dd) {
+    // each pair once: the offset its cyclic distance maps to (matters when
+    // the band wraps around, 2 b + 1 > n)
+    const int d = dd < 0 ? dd + n : dd;
+    if ((d <= b ? d : d - n) != dd) continue;
+    int j = (i - dd) % n;
+    if (j < 0) j += n;
+    const float4 a = band[(size_t)i * bw + dd + b];
+    const float4 v = x[(size_t)r * n + j];
+    dot2_term(sx, ex, a.x, a.y, v.x, v.y);
+    dot2_term(sx, ex, -a.z, -a.w, v.z, v.w);
+    dot2_term(sy, ey, a.x, a.y, v.z, v.w);
+    dot2_term(sy, ey, a.z, a.w, v.x, v.y);
+  }
+  yb[e] = make_double2((double)sx + (double)ex, (double)sy + (double)ey);
+}
+
+// y[r][i] = band part + sum of the segment sums of row tile i / 128 (FP64)
+__global__ void k_reduce_rtc(int n, int NB, int nr, const int2* __restrict__ mt_seg,
+                             const float2* __restrict__ acc, const double2* __restrict__ yb,
+                             double2* __restrict__ y) {
+  const int m = blockIdx.x, r = blockIdx.y, row = threadIdx.x;
+  const int i = m * RTM + row;
+  if (i >= n || r >= nr) return;
+  const int NC = 2 * NB;
+  const int2 sr = mt_seg[m];
+  double2 v = yb[(size_t)r * n + i];
+  for (int s = sr.x; s < sr.x + sr.y; ++s) {
+    const float2 pr = acc[((size_t)s * NC + r) * RTM + row];
+    const float2 pi = acc[((size_t)s * NC + NB + r) * RTM + row];
+    v.x += (double)pr.x + (double)pr.y;
+    v.y += (double)pi.x + (double)pi.y;
+  }
+  y[(size_t)r * n + i] = v;
+}
+
 // densities to double-float planes, once per matvec
 __global__ void k_df_x(size_t len, const double2* __restrict__ x, float4* __restrict__ xo) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -604,6 +1079,78 @@ int launch_df_hard(cfie_op* op, df_params P, const float4* x4, int nrhs) {
   return splits;
 }
 
+template <int NB>
+void run_rtc(cfie_op* op, df_params P, const double2* x, double2* y, int r0, int nr) {
+  constexpr int NC = 2 * NB;
+  rtc_plan& T = op->rtc[NB == 16 ? 0 : (NB == 32 ? 1 : 2)];
+  const int n = op->n;
+  cudaStream_t st = op->ctx->stream;
+  if (!T.built) {
+    const int mtiles = (n + RTM - 1) / RTM, ktiles = (n + RTK - 1) / RTK;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, op->ctx->device);
+    std::vector<int4> segs;
+    std::vector<int> cbeg;
+    std::vector<int2> mt_seg;
+    streamk_segments(mtiles, ktiles, sms, segs, cbeg, mt_seg);
+    T.grid = (int)cbeg.size() - 1;
+    T.nsegs = (int)segs.size();
+    T.mtiles = mtiles;
+    T.pitch = (n + 63) / 64 * 64;
+    T.tables.reserve(sizeof(int4) * segs.size() + sizeof(int) * cbeg.size() +
+                     sizeof(int2) * mt_seg.size() + 64);
+    char* tb = T.tables.as<char>();
+    T.o_cbeg = (sizeof(int4) * segs.size() + 15) & ~size_t(15);
+    T.o_mts = (T.o_cbeg + sizeof(int) * cbeg.size() + 15) & ~size_t(15);
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(tb, segs.data(), sizeof(int4) * segs.size(),
+                                    cudaMemcpyHostToDevice, st));
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(tb + T.o_cbeg, cbeg.data(), sizeof(int) * cbeg.size(),
+                                    cudaMemcpyHostToDevice, st));
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(tb + T.o_mts, mt_seg.data(), sizeof(int2) * mt_seg.size(),
+                                    cudaMemcpyHostToDevice, st));
+    T.bt.reserve(sizeof(__nv_bfloat16) * 2 * RSL * (size_t)NC * T.pitch);
+    T.acc.reserve(sizeof(float2) * (size_t)T.nsegs * NC * RTM);
+    T.fx.reserve(sizeof(int) * NC);
+    T.yb.reserve(sizeof(double2) * (size_t)NB * n);
+    T.err.reserve(sizeof(int));
+    CFIE_CHECK_CUDA(cudaMemsetAsync(T.err.p, 0, sizeof(int), st));
+    const CUtensorMap mb = tc_make_map(T.bt.p, 2 * RSL * (uint64_t)NC, (uint64_t)T.pitch, T.pitch,
+                                       NC, RTK, CU_TENSOR_MAP_SWIZZLE_32B);
+    std::memcpy(T.tmB, &mb, sizeof(mb));
+    CFIE_CHECK_CUDA(cudaStreamSynchronize(st));   // the host tables die on return
+    T.built = true;
+  }
+  const double2* xr = x + (size_t)r0 * n;
+  k_colexp<<<NB, 256, 0, st>>>(n, NB, nr, xr, T.fx.as<int>());
+  CFIE_CHECK_LAUNCH();
+  k_xslices<<<dim3((unsigned)((T.pitch + 255) / 256), NB), 256, 0, st>>>(
+      n, T.pitch, NB, nr, xr, T.fx.as<int>(), T.bt.as<__nv_bfloat16>());
+  CFIE_CHECK_LAUNCH();
+  const size_t tot = (size_t)n * nr;
+  k_band_df<<<nbk(tot), 256, 0, st>>>(n, P.b, nr, P.band, P.x + (size_t)r0 * n,
+                                      T.yb.as<double2>());
+  CFIE_CHECK_LAUNCH();
+  P.fx = T.fx.as<int>();
+  const size_t smem = rtc_smem_bytes<NB>();
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_resid_tc<NB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  char* tb = T.tables.as<char>();
+  {
+    prof_scope ps(op->ctx, CFIE_K_MATVEC_FP64);
+    k_resid_tc<NB><<<T.grid, RNT, smem, st>>>(P, op->df_rowexp.as<int>(),
+                                              *reinterpret_cast<const CUtensorMap*>(T.tmB),
+                                              reinterpret_cast<const int4*>(tb),
+                                              reinterpret_cast<const int*>(tb + T.o_cbeg),
+                                              T.acc.as<float2>(), T.err.as<int>());
+    CFIE_CHECK_LAUNCH();
+  }
+  k_reduce_rtc<<<dim3(T.mtiles, nr), RTM, 0, st>>>(n, NB, nr,
+                                                  reinterpret_cast<const int2*>(tb + T.o_mts),
+                                                  T.acc.as<float2>(), T.yb.as<double2>(),
+                                                  y + (size_t)r0 * n);
+  CFIE_CHECK_LAUNCH();
+}
+
 std::mutex g_df_mu;
 std::map<std::pair<int, int>, int> g_df_rb;
 
@@ -674,7 +1221,36 @@ void df_prepare(cfie_op* op) {
                                                   op->wtab.as<double>(), op->diag.as<double2>(),
                                                   op->df_band.as<float4>());
   CFIE_CHECK_LAUNCH();
+  if (!hard) {
+    op->df_rowexp.reserve(sizeof(int) * (size_t)n);
+    float* base = op->geo32.as<float>();
+    omega32 W{};
+    W.wh = (float)op->omega;
+    W.wl = (float)(op->omega - (double)W.wh);
+    W.winv = (float)(1.0 / op->omega);
+    W.eta = (float)op->eta;
+    W.h = (float)op->h;
+    k_rowexp<<<(unsigned)((n + 63) / 64), 256, 0, st>>>(n, b, W, geo32_at(base, n), base + 7 * n,
+                                                        op->df_rowexp.as<int>());
+    CFIE_CHECK_LAUNCH();
+  }
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
+}
+
+int df_take_error(cfie_op* op) {
+  int any = 0;
+  for (rtc_plan& T : op->rtc) {
+    if (!T.err.p) continue;
+    int e = 0;
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(&e, T.err.p, sizeof(int), cudaMemcpyDeviceToHost,
+                                    op->ctx->stream));
+    CFIE_CHECK_CUDA(cudaStreamSynchronize(op->ctx->stream));
+    if (e) {
+      any = e;
+      CFIE_CHECK_CUDA(cudaMemsetAsync(T.err.p, 0, sizeof(int), op->ctx->stream));
+    }
+  }
+  return any;
 }
 
 bool df_available(const cfie_op* op) { return op->df_b > 0; }
@@ -717,6 +1293,18 @@ void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
   k_df_x<<<nbk(tot), 256, 0, op->ctx->stream>>>(tot, x, op->df_x.as<float4>());
   CFIE_CHECK_LAUNCH();
   P.x = op->df_x.as<float4>();
+  if (op->res_variant == 2 || (op->res_variant == 0 && nrhs >= 8)) {
+    for (int r0 = 0; r0 < nrhs; r0 += 64) {
+      const int nr = std::min(64, nrhs - r0);
+      if (nr > 32)
+        run_rtc<64>(op, P, x, y, r0, nr);
+      else if (nr > 16)
+        run_rtc<32>(op, P, x, y, r0, nr);
+      else
+        run_rtc<16>(op, P, x, y, r0, nr);
+    }
+    return;
+  }
   int splits;
   if (nrhs > 32) {
     // 64 right-hand sides per CTA (one pass of entries, one CTA per SM) or 32

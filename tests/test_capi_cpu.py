@@ -53,6 +53,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.cfie_batch_set_inner_basis(None, 0) == cfie.CFIE_EINVAL
     assert lib.cfie_op_set_variant(None, 1) == cfie.CFIE_EINVAL
     assert lib.cfie_measure_peaks(None, None) == cfie.CFIE_EINVAL
+    assert lib.cfie_op_set_residual_variant(None, 1) == cfie.CFIE_EINVAL
     assert lib.cfie_last_error(None) == b"null context"
 
 

@@ -45,6 +45,41 @@ def test_residual_matvec_parity(ctx, kind, params, n, omega, nrhs, prec):
 
 
 @pytest.mark.parametrize("kind,params,n,omega,nrhs", [
+    ("kite", {}, 2000, 200.0, 8),
+    ("kite", {}, 2000, 200.0, 64),
+    ("kite", {}, 1000, 120.0, 70),                    # two passes (64 + 6)
+    ("star", {"a": [0.03, -0.02, 0.04], "b": [0.01, 0.05, -0.03]}, 3002, 450.0, 17),
+    ("ellipse", {"a": 1.0, "b": 0.5}, 1000, 90.0, 33),
+    ("circle", {}, 64, 2.0, 9),                       # every pair in the band
+])
+def test_tensor_core_residual_parity(ctx, kind, params, n, omega, nrhs):
+    """Sliced tensor-core residual (variant 2) against the oracle and against
+    the CUDA-core double-float residual (variant 1)."""
+    c = geometry.make(kind, n, **params)
+    A = operators.soft_matrix(c, omega, omega)
+    X = inputs.random_density(n, nrhs, seed=3 * n + nrhs)
+    op = ctx.geometry(kind, **params).discretise(n, omega, precision="fp32")
+    y2, y1 = empty(nrhs, n), empty(nrhs, n)
+    op.set_residual_variant(2)
+    op.apply_residual(to_dev(X), y2)
+    op.set_residual_variant(1)
+    op.apply_residual(to_dev(X), y1)
+    assert np.max(col_rel(to_host(y2), (A @ X.T).T)) < TOL_RES
+    assert np.max(col_rel(to_host(y2), to_host(y1))) < TOL_RES
+
+
+def test_residual_variant_arguments(ctx):
+    from paper_1408_1578_gb300 import cfie
+    op = ctx.kite().discretise(256, 20.0, bc="hard", precision="fp32")
+    with pytest.raises(cfie.CfieError):
+        op.set_residual_variant(2)
+    op.set_residual_variant(1)
+    op64 = ctx.kite().discretise(256, 20.0, precision="fp64")
+    with pytest.raises(cfie.CfieError):
+        op64.set_residual_variant(1)
+
+
+@pytest.mark.parametrize("kind,params,n,omega,nrhs", [
     ("kite", {}, 600, 30.0, 3),
     ("kite", {}, 2000, 200.0, 17),
     ("star", {"a": [0, 0, 0, 0, 0.3], "b": [0] * 5}, 1502, 120.0, 1),

@@ -152,6 +152,7 @@ ENTRY_OPS = {"soft": 101, "hard": 110}   # FP32 pair entries (two-float phase, a
 SUM_OPS = {"soft": 4, "hard": 8}         # FP32 FMAs per pair and right-hand side (CUDA-core sums)
 DF_ENTRY_OPS = 677                       # double-float pair entry of the residual kernel
 DF_TERM_OPS = 48                         # Dot2 complex product-sum per pair and right-hand side
+SLICE_OPS = 48                           # six 8-bit slices of the re / im parts of one entry
 FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)
 
 
@@ -185,6 +186,15 @@ def kernel_rooflines(kt, spec, stats, peaks, src, n, solves_timed):
                         "work": f"{ops} FP32 ops per pair (variant {v}: "
                                 + ("source sums on the tensor cores, not counted" if v == 2
                                    else f"{SUM_OPS[bc]} FMA per pair per right-hand side") + ")",
+                        "peak_source": f"152 SMs x 128 FP32 lanes x {clock_hz / 1e6:.0f} MHz"}
+        elif cls == "matvec_fp64" and prec != "fp64" and stats.get("residual_variant") == 2:
+            ops = DF_ENTRY_OPS + SLICE_OPS
+            a = ops * n * n / avg / 1e12
+            out[cls] = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "Top/s",
+                        "frac": a / fp32_peak, "traffic": None,
+                        "work": f"tensor-core residual: {DF_ENTRY_OPS} + {SLICE_OPS} FP32 ops per "
+                                "pair (double-float entry, slicing; slice products on the tensor "
+                                "cores, not counted)",
                         "peak_source": f"152 SMs x 128 FP32 lanes x {clock_hz / 1e6:.0f} MHz"}
         elif cls == "matvec_fp64" and prec != "fp64" and bc == "soft":
             ops = DF_ENTRY_OPS + DF_TERM_OPS * nrhs

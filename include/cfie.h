@@ -231,6 +231,8 @@ typedef struct {
                             pair kernel with tensor-core source sums, 3 stored
                             matrix on the tensor cores */
   int basis_fp32;        /* 1 if the inner solves kept their Krylov basis in FP32 */
+  int residual_variant;  /* kernel of the last true residual: 0 FP64 pair kernel,
+                            1 double-float Dot2, 2 sliced tensor-core sums */
   long long arnoldi_elems; /* basis elements read by one orthogonalisation pass,
                               summed over the Arnoldi steps (CGS2 makes four
                               passes: two inner products, two updates) */

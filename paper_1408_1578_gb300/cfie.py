@@ -57,7 +57,8 @@ class cfie_solve_stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int), ("refinements", ctypes.c_int),
                 ("inner_matvecs", ctypes.c_int), ("fp64_matvecs", ctypes.c_int),
                 ("arnoldi_steps", ctypes.c_int), ("matvec_variant", ctypes.c_int),
-                ("basis_fp32", ctypes.c_int), ("arnoldi_elems", ctypes.c_longlong)]
+                ("basis_fp32", ctypes.c_int), ("residual_variant", ctypes.c_int),
+                ("arnoldi_elems", ctypes.c_longlong)]
 
 
 class cfie_peaks(ctypes.Structure):

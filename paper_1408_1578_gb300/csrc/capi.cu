@@ -661,6 +661,7 @@ cfie_status cfie_batch_gmres_solve(cfie_batch* b, const void* f_dev, void* x_dev
               static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), rtol, restart,
               maxit, iters_out, relres_out, &result, b->stats);
     b->stats.matvec_variant = b->all_stored ? 3 : b->ops.empty() ? 0 : b->ops[0]->stats.matvec_variant;
+    b->stats.residual_variant = b->ops.empty() ? 0 : b->ops[0]->stats.residual_variant;
     if (b->all_stored && gemm_plan_take_error(b->plan, b->ctx))
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     for (cfie_op* o : b->ops)

@@ -1257,6 +1257,7 @@ bool df_available(const cfie_op* op) { return op->df_b > 0; }
 
 void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
   const int n = op->n;
+  op->stats.residual_variant = 1;
   df_params P{};
   P.n = n;
   P.b = op->df_b;
@@ -1294,6 +1295,7 @@ void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
   CFIE_CHECK_LAUNCH();
   P.x = op->df_x.as<float4>();
   if (op->res_variant == 2 || (op->res_variant == 0 && nrhs >= 8)) {
+    op->stats.residual_variant = 2;
     for (int r0 = 0; r0 < nrhs; r0 += 64) {
       const int nr = std::min(64, nrhs - r0);
       if (nr > 32)

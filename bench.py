@@ -160,7 +160,7 @@ FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)
 # ncu capture of the current kernel at the same launch configuration, keyed by
 # (kernel class, curve, n, nrhs, matvec variant); absent = not captured.
 NCU_TRAFFIC = {
-    ("matvec_fp32", "kite", 32768, 64, 2): 78.603776e6 + 10.776832e6,
+    ("matvec_fp32", "kite", 32768, 64, 2): 78.91328e6 + 11.470592e6,
 }
 
 

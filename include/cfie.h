@@ -131,8 +131,10 @@ cfie_status cfie_apply(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
  * (default: the first block matvec for a given (boundary condition, n, nrhs)
  * times both variants once on the context stream and the process keeps the
  * faster), 1 = register-blocked FP32 sums on the CUDA cores (any operator),
- * 2 = tensor cores (entries split bf16 hi + lo, tcgen05 contraction; sound-soft
- * operators).  Both evaluate the same FP32 entries. */
+ * 2 = tensor cores (entries split bf16 hi + lo, tcgen05 contraction; for the
+ * sound-hard operator S is applied to the three vectors of Maue's identity and
+ * D' to the density, each a pass of the same kernel).  Both evaluate the same
+ * FP32 entries. */
 cfie_status cfie_op_set_variant(cfie_op* op, int variant);
 
 /* y = A x in FP64 whatever the operator's precision (the matvec used for true

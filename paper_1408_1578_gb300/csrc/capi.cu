@@ -107,7 +107,7 @@ std::map<std::tuple<int, int, int>, int> g_tuned;
 
 int tuned_variant(cfie_op* op, const double2* x, double2* y, int nrhs) {
   if (op->variant) return op->variant;
-  if (op->bc != CFIE_SOUND_SOFT || nrhs < 8) return 1;
+  if (nrhs < 8) return 1;
   const auto key = std::make_tuple((int)op->bc, op->n, nrhs);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -358,8 +358,8 @@ cfie_status cfie_op_set_variant(cfie_op* op, int variant) {
   if (!op) return CFIE_EINVAL;
   return guarded(op->ctx, [&] {
     CFIE_REQUIRE(variant >= 0 && variant <= 2, "variant must be 0, 1 or 2");
-    CFIE_REQUIRE(variant != 2 || (op->prec == CFIE_FP32_REFINED && op->bc == CFIE_SOUND_SOFT),
-                 "the tensor-core variant needs a sound-soft CFIE_FP32_REFINED operator");
+    CFIE_REQUIRE(variant != 2 || op->prec == CFIE_FP32_REFINED,
+                 "the tensor-core variant needs a CFIE_FP32_REFINED operator");
     op->variant = variant;
   });
 }

@@ -191,6 +191,7 @@ struct cfie_op {
   dbuf band;         // near-field band entries (complex64), n x (2 b + 1) per operator
   int band_b = -1;
   dbuf xin32, xin32b; // FP32 staging of the input (and hard-path helpers)
+  dbuf tcv, tcs;      // sound-hard tensor-core path: S inputs, S and D' outputs
 
   // FP64-accurate residual matvec in double-float arithmetic (sound-soft)
   dbuf df_geo, df_band, df_part, df_x;
@@ -271,6 +272,11 @@ void matvec_fp64_static(cfie_op* op, const double2* x, double2* y, int nrhs);
 size_t static_scratch_capacity();
 // matvec_fp32.cu
 void fp32_prepare(cfie_op* op);
+// FP32 helpers shared with the tensor-core kernels: x32 = x, u32 = (1/|z'|) d/dt x32,
+// y += (1/(i eta)) (1/|z'|) d/dt t32
+void k_to32_fp32(cfie_op* op, const double2* x, float2* x32, size_t tot);
+void spectral32_apply(cfie_op* op, const float2* x32, float2* u32, int nrhs);
+void spectral32_accumulate(cfie_op* op, const float2* t32, double2* y, int nrhs);
 void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs);
 // stored.cu
 void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& ops,

@@ -884,14 +884,20 @@ __global__ void k_xslices(int n, int pitch, int NB, int nr, const double2* __res
 }
 
 // Near-band part of the soft residual (diagonal included): Dot2 over the
-// 2 b + 1 band entries of each row, double-float densities
+// 2 b + 1 band entries of each row, double-float densities; one thread per
+// (row, group of 8 right-hand sides), each band entry loaded once per group
+constexpr int BRG = 8;
 __global__ void k_band_df(int n, int b, int nrhs, const float4* __restrict__ band,
                           const float4* __restrict__ x, double2* __restrict__ yb) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (size_t)n * nrhs) return;
-  const int i = (int)(e % n), r = (int)(e / n);
+  const int groups = (nrhs + BRG - 1) / BRG;
+  if (e >= (size_t)n * groups) return;
+  const int i = (int)(e % n), r0 = (int)(e / n) * BRG;
+  const int rn = min(BRG, nrhs - r0);
   const int bw = 2 * b + 1;
-  float sx = 0.f, ex = 0.f, sy = 0.f, ey = 0.f;
+  float s[BRG][4];
+#pragma unroll
+  for (int q = 0; q < BRG; ++q) s[q][0] = s[q][1] = s[q][2] = s[q][3] = 0.f;
   for (int dd = -b; dd <= b; ++dd) {
     // each pair once: the offset its cyclic distance maps to (matters when
     // the band wraps around, 2 b + 1 > n)
@@ -900,13 +906,22 @@ __global__ void k_band_df(int n, int b, int nrhs, const float4* __restrict__ ban
     int j = (i - dd) % n;
     if (j < 0) j += n;
     const float4 a = band[(size_t)i * bw + dd + b];
-    const float4 v = x[(size_t)r * n + j];
-    dot2_term(sx, ex, a.x, a.y, v.x, v.y);
-    dot2_term(sx, ex, -a.z, -a.w, v.z, v.w);
-    dot2_term(sy, ey, a.x, a.y, v.z, v.w);
-    dot2_term(sy, ey, a.z, a.w, v.x, v.y);
+#pragma unroll
+    for (int q = 0; q < BRG; ++q) {
+      if (q < rn) {
+        const float4 v = x[(size_t)(r0 + q) * n + j];
+        dot2_term(s[q][0], s[q][1], a.x, a.y, v.x, v.y);
+        dot2_term(s[q][0], s[q][1], -a.z, -a.w, v.z, v.w);
+        dot2_term(s[q][2], s[q][3], a.x, a.y, v.z, v.w);
+        dot2_term(s[q][2], s[q][3], a.z, a.w, v.x, v.y);
+      }
+    }
   }
-  yb[e] = make_double2((double)sx + (double)ex, (double)sy + (double)ey);
+#pragma unroll
+  for (int q = 0; q < BRG; ++q)
+    if (q < rn)
+      yb[(size_t)(r0 + q) * n + i] =
+          make_double2((double)s[q][0] + (double)s[q][1], (double)s[q][2] + (double)s[q][3]);
 }
 
 // y[r][i] = band part + sum of the segment sums of row tile i / 128 (FP64)
@@ -1126,7 +1141,7 @@ void run_rtc(cfie_op* op, df_params P, const double2* x, double2* y, int r0, int
   k_xslices<<<dim3((unsigned)((T.pitch + 255) / 256), NB), 256, 0, st>>>(
       n, T.pitch, NB, nr, xr, T.fx.as<int>(), T.bt.as<__nv_bfloat16>());
   CFIE_CHECK_LAUNCH();
-  const size_t tot = (size_t)n * nr;
+  const size_t tot = (size_t)n * ((nr + BRG - 1) / BRG);
   k_band_df<<<nbk(tot), 256, 0, st>>>(n, P.b, nr, P.band, P.x + (size_t)r0 * n,
                                       T.yb.as<double2>());
   CFIE_CHECK_LAUNCH();

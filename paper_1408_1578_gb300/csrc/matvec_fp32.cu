@@ -485,6 +485,31 @@ void fp32_prepare(cfie_op* op) {
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
 }
 
+void k_to32_fp32(cfie_op* op, const double2* x, float2* x32, size_t tot) {
+  k_to32<<<nblk(tot), 256, 0, op->ctx->stream>>>(tot, x, x32);
+  CFIE_CHECK_LAUNCH();
+}
+
+void spectral32_apply(cfie_op* op, const float2* x32, float2* u32, int nrhs) {
+  const int n = op->n;
+  const float* c32 = op->geo32.as<float>() + 8 * n;
+  const dim3 g2(nblk(n, SPT), nrhs);
+  prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
+  k_spectral32<false><<<g2, SPT, 0, op->ctx->stream>>>(n, c32, op->g.sp, x32,
+                                                      make_double2(1.0, 0.0), u32, nullptr);
+  CFIE_CHECK_LAUNCH();
+}
+
+void spectral32_accumulate(cfie_op* op, const float2* t32, double2* y, int nrhs) {
+  const int n = op->n;
+  const float* c32 = op->geo32.as<float>() + 8 * n;
+  const dim3 g2(nblk(n, SPT), nrhs);
+  prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
+  k_spectral32<true><<<g2, SPT, 0, op->ctx->stream>>>(n, c32, op->g.sp, t32,
+                                                     make_double2(0.0, -1.0 / op->eta), nullptr, y);
+  CFIE_CHECK_LAUNCH();
+}
+
 void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs) {
   const int n = op->n;
   const bool hard = op->bc == CFIE_SOUND_HARD;

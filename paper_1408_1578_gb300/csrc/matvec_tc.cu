@@ -53,8 +53,27 @@ struct tc_params : omega32 {
   const float* w32;
   const float* wext;     // Kress table indexed by i - j + n
   const float4* pk;      // packed coordinates (n) then normals / speeds (n)
-  const float2* band;
+  const float2* band;    // near entries of the evaluated kind (soft A, or S, or D')
 };
+
+// Entry kinds of the fused kernel: the sound-soft combination of eq. 1, or
+// one of the two layer operators of the sound-hard operator of eq. 2
+enum { KIND_SOFT = 0, KIND_S = 1, KIND_DP = 2 };
+
+template <int KIND>
+__device__ __forceinline__ float2 entry_kind(const omega32& P, float4 tg, float4 tn, float4 sc,
+                                             float4 sn, float w) {
+  float2 a, b;
+  if constexpr (KIND == KIND_SOFT) {
+    pair_entries_fp32<0>(P, tg.x, tg.y, tg.z, tg.w, 0.f, 0.f, 1.f, sc.x, sc.y, sc.z, sc.w, sn.x,
+                         sn.y, sn.z, w, a, b);
+    return a;
+  } else {
+    pair_entries_fp32<1>(P, tg.x, tg.y, tg.z, tg.w, tn.x, tn.y, tn.z, sc.x, sc.y, sc.z, sc.w,
+                         sn.x, sn.y, sn.z, w, a, b);
+    return KIND == KIND_S ? a : b;
+  }
+}
 
 // bf16 hi / lo split of two entries of one row (adjacent sources k, k + 1)
 // into the four A planes: one packed 32-bit word per plane at byte offset o
@@ -79,6 +98,7 @@ struct tc_smem {
   __nv_bfloat16 B[TSTAGES][4][NP * TBK];    // B1 hi, B1 lo, B2 hi, B2 lo
   float acc[NP][TBM];                       // epilogue running sums, column-major
   float4 tgt[TBM];                          // targets (x hi, x lo, y hi, y lo)
+  float4 tgn[TBM];                          // targets (nu1, nu2, |z'|, 0)
   uint64_t full[TSTAGES], empty[TSTAGES], tfull[2], tempty[2];
   uint32_t tmem_base;
   int abort;
@@ -95,7 +115,7 @@ __device__ __forceinline__ uint32_t sw64(int r, int k) {
   return (uint32_t)(r * 64 + ((((k >> 3) ^ (r >> 1)) & 3) << 4) + (k & 7) * 2);
 }
 
-template <int NP>
+template <int NP, int KIND>
 __global__ void __launch_bounds__(TNT, 1)
 k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __restrict__ segs,
            const int* __restrict__ cbeg, float2* __restrict__ partial, int* __restrict__ err) {
@@ -149,6 +169,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
         const int i = m0 + r;
         const bool ok = i < n;
         S.tgt[r] = ok ? P.pk[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        S.tgn[r] = ok ? P.pk[n + i] : make_float4(0.f, 0.f, 1.f, 0.f);
       }
       __syncwarp();
       // geometry of this lane's two sources, loaded one tile ahead
@@ -201,12 +222,11 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
           for (int q = 0; q < QS; ++q) {
             const int il = warp + NPROD * (2 * q + half);
             const float4 tg = S.tgt[il];
-            float2 e[2], unused;
+            const float4 tn = KIND == KIND_DP ? S.tgn[il] : make_float4(0.f, 0.f, 1.f, 0.f);
+            float2 e[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u)
-              pair_entries_fp32<0>(P, tg.x, tg.y, tg.z, tg.w, 0.f, 0.f, 1.f, sc[u].x, sc[u].y,
-                                   sc[u].z, sc[u].w, sn[u].x, sn[u].y, sn[u].z,
-                                   u ? wv[q].y : wv[q].x, e[u], unused);
+              e[u] = entry_kind<KIND>(P, tg, tn, sc[u], sn[u], u ? wv[q].y : wv[q].x);
             store_split2(a0, a1, a2, a3, sw64(il, jp), e[0], e[1]);
           }
         } else {
@@ -215,22 +235,20 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
             const int il = warp + NPROD * (2 * q + half);
             const int i = m0 + il;
             const float4 tg = S.tgt[il];
+            const float4 tn = KIND == KIND_DP ? S.tgn[il] : make_float4(0.f, 0.f, 1.f, 0.f);
             float2 e[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               const int jj = j + u;
-              float2 a = make_float2(0.f, 0.f), unused;
+              float2 a = make_float2(0.f, 0.f);
               if (i < n && jj < n) {
                 int d = i - jj;
                 if (d < 0) d += n;
                 const int dd = d <= P.b ? d : (d >= n - P.b ? d - n : INT_MAX);
-                if (dd != INT_MAX) {
+                if (dd != INT_MAX)
                   a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
-                } else {
-                  pair_entries_fp32<0>(P, tg.x, tg.y, tg.z, tg.w, 0.f, 0.f, 1.f, sc[u].x,
-                                       sc[u].y, sc[u].z, sc[u].w, sn[u].x, sn[u].y, sn[u].z,
-                                       P.w32[d], a, unused);
-                }
+                else
+                  a = entry_kind<KIND>(P, tg, tn, sc[u], sn[u], P.w32[d]);
               }
               e[u] = a;
             }
@@ -381,7 +399,7 @@ __global__ void k_reduce_tc(int n, int nr, int NR, const int2* __restrict__ mt_s
 
 unsigned nb(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
 
-template <int NP>
+template <int NP, int KIND>
 void run_fused(cfie_op* op, const double2* x, double2* y, int r0, int nr) {
   constexpr int NR = NP / 2;
   tc_plan& T = op->tc[NP == 64 ? 0 : 1];
@@ -435,14 +453,16 @@ void run_fused(cfie_op* op, const double2* x, double2* y, int r0, int nr) {
   P.w32 = base + 7 * n;
   P.wext = base + 9 * n;
   P.pk = reinterpret_cast<const float4*>(base + geo32_pack_offset(n));
-  P.band = op->band.as<float2>();
+  // the FP32 band holds the soft entries, or S then D' for the hard operator
+  P.band = op->band.as<float2>() +
+           (KIND == KIND_DP ? (size_t)n * (2 * (size_t)op->band_b + 1) : (size_t)0);
   const size_t smem = tc_smem_bytes<NP>();
-  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_fused_tc<NP>,
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_fused_tc<NP, KIND>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   char* tb = T.tables.as<char>();
   {
     prof_scope ps(op->ctx, CFIE_K_MATVEC_FP32);
-    k_fused_tc<NP><<<T.grid, TNT, smem, st>>>(P, *reinterpret_cast<const CUtensorMap*>(T.tmB),
+    k_fused_tc<NP, KIND><<<T.grid, TNT, smem, st>>>(P, *reinterpret_cast<const CUtensorMap*>(T.tmB),
                                              reinterpret_cast<const int4*>(tb),
                                              reinterpret_cast<const int*>(tb + T.o_cbeg),
                                              T.partial.as<float2>(), T.err.as<int>());
@@ -454,18 +474,80 @@ void run_fused(cfie_op* op, const double2* x, double2* y, int r0, int nr) {
   CFIE_CHECK_LAUNCH();
 }
 
-}  // namespace
-
-void matvec_fp32_tc(cfie_op* op, const double2* x, double2* y, int nrhs) {
-  if (op->bc != CFIE_SOUND_SOFT)
-    throw cfie_error(CFIE_EINVAL, "tensor-core contraction supports the sound-soft operator");
+template <int KIND>
+void run_blocks(cfie_op* op, const double2* x, double2* y, int nrhs) {
   for (int r0 = 0; r0 < nrhs; r0 += 64) {
     const int nr = std::min(64, nrhs - r0);
     if (nr > 32)
-      run_fused<128>(op, x, y, r0, nr);
+      run_fused<128, KIND>(op, x, y, r0, nr);
     else
-      run_fused<64>(op, x, y, r0, nr);
+      run_fused<64, KIND>(op, x, y, r0, nr);
   }
+}
+
+// hard operator inputs of the S sums: [u, n1 x, n2 x] (u = (1/|z'|) d/dt x)
+__global__ void k_hard_inputs(int n, size_t tot, const double2* __restrict__ x,
+                              const float2* __restrict__ u32, geom_dev g,
+                              double2* __restrict__ v) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= tot) return;
+  const int i = (int)(e % n);
+  const double inv = 1.0 / g.sp[i];
+  const double2 xv = x[e];
+  const float2 uv = u32[e];
+  v[e] = make_double2(uv.x, uv.y);
+  v[tot + e] = make_double2(g.nx[i] * inv * xv.x, g.nx[i] * inv * xv.y);
+  v[2 * tot + e] = make_double2(g.ny[i] * inv * xv.x, g.ny[i] * inv * xv.y);
+}
+
+// y = x/2 - D' x - i (omega^2 / eta) (n1 S(n1 x) + n2 S(n2 x)), t = S u (FP32)
+__global__ void k_hard_combine(int n, size_t tot, double omega, double eta, geom_dev g,
+                               const double2* __restrict__ x, const double2* __restrict__ ys,
+                               const double2* __restrict__ yd, float2* __restrict__ t32,
+                               double2* __restrict__ y) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= tot) return;
+  const int i = (int)(e % n);
+  const double inv = 1.0 / g.sp[i];
+  const double n1 = g.nx[i] * inv, n2 = g.ny[i] * inv;
+  const double2 s1 = ys[tot + e], s2 = ys[2 * tot + e];
+  const double2 m = make_double2(n1 * s1.x + n2 * s2.x, n1 * s1.y + n2 * s2.y);
+  const double k = omega * omega / eta;
+  const double2 xv = x[e], d = yd[e];
+  y[e] = make_double2(0.5 * xv.x - d.x + k * m.y, 0.5 * xv.y - d.y - k * m.x);
+  t32[e] = make_float2((float)ys[e].x, (float)ys[e].y);
+}
+
+}  // namespace
+
+void matvec_fp32_tc(cfie_op* op, const double2* x, double2* y, int nrhs) {
+  if (op->bc == CFIE_SOUND_SOFT) {
+    run_blocks<KIND_SOFT>(op, x, y, nrhs);
+    return;
+  }
+  // sound hard (eq. 2 with Maue's identity): S applied to [u, n1 x, n2 x] and
+  // D' to x, each with the tensor-core sums, then the spectral derivative
+  const int n = op->n;
+  const size_t tot = (size_t)n * nrhs;
+  cudaStream_t st = op->ctx->stream;
+  op->xin32.reserve(sizeof(float2) * tot * 3);
+  float2* x32 = op->xin32.as<float2>();
+  float2* u32 = x32 + tot;
+  float2* t32 = x32 + 2 * tot;
+  op->tcv.reserve(sizeof(double2) * tot * 4);
+  double2* v = op->tcv.as<double2>();        // [u, n1 x, n2 x], then S of them
+  op->tcs.reserve(sizeof(double2) * tot * 4);
+  double2* ys = op->tcs.as<double2>();       // S [u, n1 x, n2 x], then D' x
+  k_to32_fp32(op, x, x32, tot);
+  spectral32_apply(op, x32, u32, nrhs);
+  k_hard_inputs<<<nb(tot), 256, 0, st>>>(n, tot, x, u32, op->g, v);
+  CFIE_CHECK_LAUNCH();
+  run_blocks<KIND_S>(op, v, ys, 3 * nrhs);
+  run_blocks<KIND_DP>(op, x, ys + 3 * tot, nrhs);
+  k_hard_combine<<<nb(tot), 256, 0, st>>>(n, tot, op->omega, op->eta, op->g, x, ys, ys + 3 * tot,
+                                          t32, y);
+  CFIE_CHECK_LAUNCH();
+  spectral32_accumulate(op, t32, y, nrhs);
 }
 
 int tc_take_error(cfie_op* op) {

@@ -179,12 +179,51 @@ def test_fp32_tensor_core_refined_solve(ctx):
 
 def test_tensor_core_variant_arguments(ctx):
     from paper_1408_1578_gb300 import cfie
-    op = ctx.kite().discretise(256, 20.0, bc="hard", precision="fp32")
-    with pytest.raises(cfie.CfieError):
-        op.set_variant(2)
     op64 = ctx.kite().discretise(256, 20.0, precision="fp64")
     with pytest.raises(cfie.CfieError):
         op64.set_variant(2)
+    op = ctx.kite().discretise(256, 20.0, precision="fp32")
+    with pytest.raises(cfie.CfieError):
+        op.set_variant(3)
+
+
+@pytest.mark.parametrize("kind,params,n,omega,nrhs", [
+    ("kite", {}, 2000, 200.0, 8),
+    ("kite", {}, 2000, 200.0, 30),                    # S pass of 90 right-hand sides
+    ("star", {"a": [0, 0, 0, 0, 0.3], "b": [0] * 5}, 1502, 120.0, 16),
+    ("ellipse", {"a": 1.0, "b": 0.5}, 1000, 90.0, 64),
+])
+def test_fp32_tensor_core_sums_hard(ctx, kind, params, n, omega, nrhs):
+    """Sound-hard operator (eq. 2, N by Maue's identity) with the source sums of
+    S and D' on the tensor cores."""
+    c = geometry.make(kind, n, **params)
+    A = operators.cfie_matrix(c, omega, omega, "hard")
+    X = inputs.random_density(n, nrhs, seed=7 * n + nrhs)
+    op = ctx.geometry(kind, **params).discretise(n, omega, bc="hard", precision="fp32")
+    op.set_variant(2)
+    y = empty(nrhs, n)
+    op.apply(to_dev(X), y)
+    assert np.max(col_rel(to_host(y), (A @ X.T).T)) < TOL_FP32
+    op.set_variant(1)
+    y1 = empty(nrhs, n)
+    op.apply(to_dev(X), y1)
+    assert np.max(col_rel(to_host(y), to_host(y1))) < TOL_FP32
+
+
+def test_fp32_tensor_core_refined_solve_hard(ctx):
+    n, w, nrhs = 1502, 120.0, 12
+    params = {"a": [0, 0, 0, 0, 0.3], "b": [0] * 5}
+    c = geometry.fourier_star(n, params["a"], params["b"])
+    A = operators.cfie_matrix(c, w, w, "hard")
+    F = operators.plane_wave_rhs(c, w, inputs.directions(nrhs), "hard")
+    Q = solvers.lu_solve(A, F).T
+    op = ctx.fourier_star(params["a"], params["b"]).discretise(n, w, bc="hard", precision="fp32")
+    op.set_variant(2)
+    x = zeros(nrhs, n)
+    its, rel, _ = op.gmres_solve(to_dev(F.T), x, rtol=1e-8, restart=80, maxit=3000)
+    assert np.all(rel <= 1e-8)
+    assert op.last_stats()["matvec_variant"] == 2
+    assert np.max(col_rel(to_host(x), Q)) < TOL_REFINED
 
 
 @pytest.mark.parametrize("bc", ["soft", "hard"])

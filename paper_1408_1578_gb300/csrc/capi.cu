@@ -16,6 +16,7 @@ namespace {
 
 template <class F>
 cfie_status guarded(cfie_ctx* ctx, F&& f) {
+  stream_scope ss(ctx ? ctx->stream : alloc_stream());
   try {
     f();
     if (ctx) ctx->err.clear();
@@ -177,7 +178,15 @@ cfie_status cfie_ctx_create(int device, void* cuda_stream, cfie_ctx** out) {
   if (!c) return CFIE_ENOMEM;
   c->device = device;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
-  cfie_status st = guarded(c, [&] { set_device(c); });
+  cfie_status st = guarded(c, [&] {
+    set_device(c);
+    // keep freed device buffers in the stream-ordered pool between calls
+    // (operators and batches are created and destroyed at every solve)
+    cudaMemPool_t pool;
+    CFIE_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+    uint64_t keep = UINT64_MAX;
+    CFIE_CHECK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  });
   if (st != CFIE_OK) {
     delete c;
     return st;
@@ -316,6 +325,7 @@ cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cf
 void cfie_op_destroy(cfie_op* op) {
   if (!op) return;
   cudaSetDevice(op->ctx->device);
+  stream_scope ss(op->ctx->stream);
   cudaStreamSynchronize(op->ctx->stream);
   krylov_release(op->K);
   gemm_plan_release(op->plan);
@@ -562,6 +572,7 @@ static void batch_fp64(cfie_batch* b, const double2* x, double2* y) {
   try {
     for (size_t k = 0; k < b->ops.size(); ++k) {
       c->stream = b->aux[k % K];
+      stream_scope ss(c->stream);
       matvec_residual(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
     }
   } catch (...) {
@@ -682,6 +693,7 @@ cfie_status cfie_batch_last_stats(const cfie_batch* b, cfie_solve_stats* out) {
 void cfie_batch_destroy(cfie_batch* b) {
   if (!b) return;
   cudaSetDevice(b->ctx->device);
+  stream_scope ss(b->ctx->stream);
   cudaStreamSynchronize(b->ctx->stream);
   krylov_release(b->K);
   gemm_plan_release(b->plan);

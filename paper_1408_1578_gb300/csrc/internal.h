@@ -46,6 +46,24 @@ extern std::atomic<long long> g_cfie_launches;  // kernel launches issued by the
 // ----------------------------------------------------------------------------
 // device buffer owned by the library
 // ----------------------------------------------------------------------------
+// Stream on which the calling thread's library work is ordered.  Device
+// buffers are allocated and freed on it through the device's stream-ordered
+// memory pool: a buffer freed after its last use on that stream is reused at
+// once by later work, without the device-wide synchronisation and address
+// mapping of cudaMalloc / cudaFree.  Entry points set it to the context
+// stream (stream_scope); 0 (the legacy default stream) outside them.
+inline cudaStream_t& alloc_stream() {
+  static thread_local cudaStream_t s = nullptr;
+  return s;
+}
+struct stream_scope {
+  cudaStream_t prev;
+  explicit stream_scope(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
+  ~stream_scope() { alloc_stream() = prev; }
+  stream_scope(const stream_scope&) = delete;
+  stream_scope& operator=(const stream_scope&) = delete;
+};
+
 struct dbuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -54,7 +72,7 @@ struct dbuf {
   dbuf& operator=(const dbuf&) = delete;
   ~dbuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, alloc_stream());
     p = nullptr;
     bytes = 0;
   }
@@ -62,7 +80,7 @@ struct dbuf {
   void reserve(size_t need) {
     if (need <= bytes) return;
     release();
-    CFIE_CHECK_CUDA(cudaMalloc(&p, need));
+    CFIE_CHECK_CUDA(cudaMallocAsync(&p, need, alloc_stream()));
     bytes = need;
   }
   template <class T>

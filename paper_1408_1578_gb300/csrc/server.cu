@@ -134,6 +134,7 @@ void worker_main(cfie_server* S) {
   cfie_ctx* ctx = nullptr;
   const bool ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess &&
                   cfie_ctx_create(S->device, stream, &ctx) == CFIE_OK;
+  stream_scope ss(stream);     // the slot's staging buffers live on its stream
   dbuf fbuf, xbuf;
   for (;;) {
     request_rec* r = nullptr;
@@ -181,6 +182,7 @@ void worker_main(cfie_server* S) {
   }
   fbuf.release();
   xbuf.release();
+  if (stream) cudaStreamSynchronize(stream);
   if (ctx) cfie_ctx_destroy(ctx);
   if (stream) cudaStreamDestroy(stream);
 }

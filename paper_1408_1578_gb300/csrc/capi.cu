@@ -309,6 +309,7 @@ cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cf
     op->layout = layout;
     geometry_sample(op, geom);
     kress_tables(op);
+    if (bc == CFIE_SOUND_HARD) fft_prepare(op);
     if (precision != CFIE_FP64) fp32_prepare(op);
     if (precision != CFIE_FP64) df_prepare(op);
     if (layout == CFIE_STORED) stored_prepare(op);

@@ -185,6 +185,14 @@ struct rtc_plan {
   alignas(64) unsigned char tmB[128];
 };
 
+// Bluestein / radix-2 FFT tables of an operator's spectral derivative
+// (spectral_fft.cu): power-of-two length N >= 2 n - 1, twiddles, chirp, FFT of
+// the wrapped chirp (FP64 and FP32), work buffers.
+struct fft_plan {
+  int N = 0, L = 0;
+  dbuf tw, tw32, chirp, chirp32, bf, bf32, work, work32;
+};
+
 struct cfie_op {
   cfie_ctx* ctx = nullptr;
   int n = 0;
@@ -210,6 +218,7 @@ struct cfie_op {
   int band_b = -1;
   dbuf xin32, xin32b; // FP32 staging of the input (and hard-path helpers)
   dbuf tcv, tcs;      // sound-hard tensor-core path: S inputs, S and D' outputs
+  fft_plan fft;       // sound hard: FFT spectral derivative
 
   // FP64-accurate residual matvec in double-float arithmetic (sound-soft)
   dbuf df_geo, df_band, df_part, df_x;
@@ -282,6 +291,13 @@ void rhs_plane_waves(cfie_op* op, int nrhs, const double* theta_host, double2* f
 void matvec_fp64(cfie_op* op, const double2* x, double2* y, int nrhs);
 void spectral_apply(cfie_op* op, const double2* in, double2* out, const double2* base,
                     double2 scale, int nrhs);
+// spectral_fft.cu: the same derivative by FFT (tables built by fft_prepare)
+void fft_prepare(cfie_op* op);
+void spectral_fft64(cfie_op* op, const double2* in, double2* out, const double2* base,
+                    double2 scale, int nrhs);
+void spectral_fft32_apply(cfie_op* op, const float2* in, float2* out, int nrhs);
+void spectral_fft32_accumulate(cfie_op* op, const float2* in, double2* y, double2 scale,
+                               int nrhs);
 // sound-hard combination of the four FP64-layout partial sums (S u, S n1 x,
 // S n2 x, D' x): t = S u, y = x / 2 - D' x - i (omega^2 / eta) (n1 S n1 x + n2 S n2 x)
 void reduce_hard_fp64(cfie_op* op, const double2* part, int splits, const double2* x,

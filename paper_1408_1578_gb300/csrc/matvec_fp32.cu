@@ -491,23 +491,11 @@ void k_to32_fp32(cfie_op* op, const double2* x, float2* x32, size_t tot) {
 }
 
 void spectral32_apply(cfie_op* op, const float2* x32, float2* u32, int nrhs) {
-  const int n = op->n;
-  const float* c32 = op->geo32.as<float>() + 8 * n;
-  const dim3 g2(nblk(n, SPT), nrhs);
-  prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
-  k_spectral32<false><<<g2, SPT, 0, op->ctx->stream>>>(n, c32, op->g.sp, x32,
-                                                      make_double2(1.0, 0.0), u32, nullptr);
-  CFIE_CHECK_LAUNCH();
+  spectral_fft32_apply(op, x32, u32, nrhs);
 }
 
 void spectral32_accumulate(cfie_op* op, const float2* t32, double2* y, int nrhs) {
-  const int n = op->n;
-  const float* c32 = op->geo32.as<float>() + 8 * n;
-  const dim3 g2(nblk(n, SPT), nrhs);
-  prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
-  k_spectral32<true><<<g2, SPT, 0, op->ctx->stream>>>(n, c32, op->g.sp, t32,
-                                                     make_double2(0.0, -1.0 / op->eta), nullptr, y);
-  CFIE_CHECK_LAUNCH();
+  spectral_fft32_accumulate(op, t32, y, make_double2(0.0, -1.0 / op->eta), nrhs);
 }
 
 void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs) {
@@ -552,13 +540,7 @@ void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs) {
   }
   float2* u32 = x32 + tot;
   float2* t32 = x32 + 2 * tot;
-  const dim3 g2(nblk(n, SPT), nrhs);
-  {
-    prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
-    k_spectral32<false><<<g2, SPT, 0, st>>>(n, c32, op->g.sp, x32, make_double2(1.0, 0.0), u32,
-                                             nullptr);
-    CFIE_CHECK_LAUNCH();
-  }
+  spectral32_apply(op, x32, u32, nrhs);
   P.uin = u32;
   int splits;
   if (nrhs > 8)
@@ -568,11 +550,6 @@ void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs) {
   k_reduce32<1><<<nblk(tot), 256, 0, st>>>(n, nrhs, splits, op->omega, op->eta, op->g,
                                            op->partial.as<float2>(), x, t32, y);
   CFIE_CHECK_LAUNCH();
-  {
-    // y += (1/(i eta)) (1/s) Dt t
-    prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
-    k_spectral32<true><<<g2, SPT, 0, st>>>(n, c32, op->g.sp, t32, make_double2(0.0, -1.0 / op->eta),
-                                            nullptr, y);
-    CFIE_CHECK_LAUNCH();
-  }
+  // y += (1/(i eta)) (1/s) Dt t
+  spectral32_accumulate(op, t32, y, nrhs);
 }

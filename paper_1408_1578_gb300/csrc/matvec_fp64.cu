@@ -280,13 +280,11 @@ void launch_pair(cfie_op* op, const double2* x, const double2* u, int nrhs, int 
 
 }  // namespace
 
+// out = base + scale (1/|z'|) d/dt in: by FFT (O(n log n) per column); the
+// allocation-free variant below keeps the circulant kernel
 void spectral_apply(cfie_op* op, const double2* in, double2* out, const double2* base,
                     double2 scale, int nrhs) {
-  dim3 grid((op->n + SPT - 1) / SPT, nrhs);
-  prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
-  k_spectral_fp64<<<grid, SPT, 0, op->ctx->stream>>>(op->n, op->ctab.as<double>(), op->g.sp, in,
-                                                      base, scale, out);
-  CFIE_CHECK_LAUNCH();
+  spectral_fft64(op, in, out, base, scale, nrhs);
 }
 
 void reduce_hard_fp64(cfie_op* op, const double2* part, int splits, const double2* x,

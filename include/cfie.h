@@ -187,13 +187,13 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
 /* How the refined precisions compute true residuals (cfie_apply_residual and
  * inside cfie_gmres_solve), all to ~1e-13 relative: variant 1 evaluates the
  * entries in double-float (FP32 pairs) and sums with compensated Dot2 on the
- * CUDA cores; variant 2 (sound-soft only) evaluates the far entries in
- * double-float, splits entries and densities into six 8-bit slices on per-row /
- * per-column power-of-two grids and sums the slice products on the tensor cores,
- * exactly in FP32 for the three leading levels, with the near band on the CUDA
- * cores; 0 (default) picks 2 for sound-soft operators with 8 or more
- * right-hand sides, else 1.  CFIE_EINVAL for the FP64 precision, for variant 2
- * on a sound-hard operator, or another value. */
+ * CUDA cores; variant 2 evaluates the far entries in double-float (for the
+ * sound-hard operator S and D' in separate passes), splits entries and
+ * densities into six 8-bit slices on per-row / per-column power-of-two grids
+ * and sums the slice products on the tensor cores, exactly in FP32 for the
+ * three leading levels, with the near band on the CUDA cores; 0 (default)
+ * picks 2 with 8 or more right-hand sides, else 1.  CFIE_EINVAL for the FP64
+ * precision or another value. */
 cfie_status cfie_op_set_residual_variant(cfie_op* op, int variant);
 
 /* Precision of the Krylov basis of the inner solves of the refined precisions

@@ -480,8 +480,6 @@ cfie_status cfie_op_set_residual_variant(cfie_op* op, int variant) {
   if (!op || variant < 0 || variant > 2) return CFIE_EINVAL;
   return guarded(op->ctx, [&] {
     CFIE_REQUIRE(op->prec != CFIE_FP64, "the FP64 precision computes residuals with its own matvec");
-    CFIE_REQUIRE(variant != 2 || op->bc == CFIE_SOUND_SOFT,
-                 "the tensor-core residual supports the sound-soft operator");
     op->res_variant = variant;
   });
 }

@@ -497,6 +497,8 @@ struct rtc_smem {
   __nv_bfloat16 A[RST][2 * RSL][RTM * RTK];    // Ar slices 0..5, Ai slices 0..5
   __nv_bfloat16 B[RST][2 * RSL][2 * NB * RTK]; // per slice t: [Xr | Xi], [-Xi | Xr]
   float4 tgt[RTM];
+  float4 tgn[RTM];   // target normal (hi, lo pairs) and, below, speed: hard kinds
+  float2 tgs[RTM];
   int ex[RTM];
   uint64_t full[RST], empty[RST], tfull, tempty;
   uint32_t tmem_base;
@@ -549,7 +551,11 @@ __device__ __forceinline__ void slice6(float h, float l, float* o) {
   o[5] = q * 9.094947017729282e-13f;           // 2^-40
 }
 
-template <int NB>
+// entry kinds of the sliced residual: the sound-soft combination (eq. 1), or
+// S or D' of the sound-hard operator (eq. 2)
+enum { RK_SOFT = 0, RK_S = 1, RK_DP = 2 };
+
+template <int NB, int KIND>
 __global__ void __launch_bounds__(RNT, 1)
 k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ CUtensorMap tmB,
            const int4* __restrict__ segs, const int* __restrict__ cbeg,
@@ -598,6 +604,8 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
         const int i = m0 + r;
         S.tgt[r] = i < n ? P.g[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         S.ex[r] = i < n ? rowexp[i] : 0;
+        S.tgn[r] = i < n ? P.nrm[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        S.tgs[r] = i < n ? P.sp[i] : make_float2(1.f, 0.f);
       }
       __syncwarp();
       for (int k = sg.z; k < sg.w; ++k, ++it) {
@@ -635,7 +643,15 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
             if (i < n && jj < n) {
               int d = i - jj;
               if (d < 0) d += n;
-              if (d > P.b && d < n - P.b) a = entry_df(P, gi, gj[u], nj[u], sj[u], P.w[d]);
+              if (d > P.b && d < n - P.b) {
+                if constexpr (KIND == RK_SOFT) {
+                  a = entry_df(P, gi, gj[u], nj[u], sj[u], P.w[d]);
+                } else {
+                  float4 es, ed;
+                  entry_df_hard(P, gi, gj[u], S.tgn[il], S.tgs[il], sj[u], P.w[d], es, ed);
+                  a = KIND == RK_S ? es : ed;
+                }
+              }
             }
             // scale by 2^(7 - e): exact for both parts
             const float sc = __int_as_float((127 + 7 - e) << 23);
@@ -798,6 +814,7 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
 // Row exponents of the far entries: E_i with |Re a_ij|, |Im a_ij| < 2^E_i for
 // every pair outside the double-float band, from the FP32 entries with a
 // 1e-4 margin (their relative error is ~1e-6); 0 for rows without far pairs.
+template <int KIND>
 __global__ void __launch_bounds__(256)
 k_rowexp(int n, int b, omega32 W, geo32 g, const float* __restrict__ w32, int* __restrict__ rowexp) {
   __shared__ float red[4][64];
@@ -806,13 +823,16 @@ k_rowexp(int n, int b, omega32 W, geo32 g, const float* __restrict__ w32, int* _
   float m = 0.f;
   if (i < n) {
     const float txh = g.xh[i], txl = g.xl[i], tyh = g.yh[i], tyl = g.yl[i];
+    const float tnx = g.nx[i], tny = g.ny[i], tsp = g.sp[i];
     for (int j = qd; j < n; j += 4) {
       int d = i - j;
       if (d < 0) d += n;
       if (d <= b || d >= n - b) continue;
-      float2 a, unused;
-      pair_entries_fp32<0>(W, txh, txl, tyh, tyl, 0.f, 0.f, 1.f, g.xh[j], g.xl[j], g.yh[j],
-                           g.yl[j], g.nx[j], g.ny[j], g.sp[j], w32[d], a, unused);
+      float2 a, bb;
+      pair_entries_fp32<KIND == RK_SOFT ? 0 : 1>(W, txh, txl, tyh, tyl, tnx, tny, tsp, g.xh[j],
+                                                 g.xl[j], g.yh[j], g.yl[j], g.nx[j], g.ny[j],
+                                                 g.sp[j], w32[d], a, bb);
+      if (KIND == RK_DP) a = bb;
       m = fmaxf(m, fmaxf(fabsf(a.x), fabsf(a.y)));
     }
   }
@@ -1094,7 +1114,7 @@ int launch_df_hard(cfie_op* op, df_params P, const float4* x4, int nrhs) {
   return splits;
 }
 
-template <int NB>
+template <int NB, int KIND>
 void run_rtc(cfie_op* op, df_params P, const double2* x, double2* y, int r0, int nr) {
   constexpr int NC = 2 * NB;
   rtc_plan& T = op->rtc[NB == 16 ? 0 : (NB == 32 ? 1 : 2)];
@@ -1147,12 +1167,12 @@ void run_rtc(cfie_op* op, df_params P, const double2* x, double2* y, int r0, int
   CFIE_CHECK_LAUNCH();
   P.fx = T.fx.as<int>();
   const size_t smem = rtc_smem_bytes<NB>();
-  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_resid_tc<NB>,
+  CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_resid_tc<NB, KIND>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   char* tb = T.tables.as<char>();
   {
     prof_scope ps(op->ctx, CFIE_K_MATVEC_FP64);
-    k_resid_tc<NB><<<T.grid, RNT, smem, st>>>(P, op->df_rowexp.as<int>(),
+    k_resid_tc<NB, KIND><<<T.grid, RNT, smem, st>>>(P, op->df_rowexp.as<int>() + (KIND == RK_DP ? n : 0),
                                               *reinterpret_cast<const CUtensorMap*>(T.tmB),
                                               reinterpret_cast<const int4*>(tb),
                                               reinterpret_cast<const int*>(tb + T.o_cbeg),
@@ -1164,6 +1184,49 @@ void run_rtc(cfie_op* op, df_params P, const double2* x, double2* y, int r0, int
                                                   T.acc.as<float2>(), T.yb.as<double2>(),
                                                   y + (size_t)r0 * n);
   CFIE_CHECK_LAUNCH();
+}
+
+template <int KIND>
+void run_rtc_block(cfie_op* op, const df_params& P, const double2* x, double2* y, int r0,
+                   int nr) {
+  if (nr > 32)
+    run_rtc<64, KIND>(op, P, x, y, r0, nr);
+  else if (nr > 16)
+    run_rtc<32, KIND>(op, P, x, y, r0, nr);
+  else
+    run_rtc<16, KIND>(op, P, x, y, r0, nr);
+}
+
+// sound-hard inputs of the S sums, [u, n1 x, n2 x]
+__global__ void k_hard_inputs64(int n, size_t tot, const double2* __restrict__ x,
+                                const double2* __restrict__ u, geom_dev g,
+                                double2* __restrict__ v) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= tot) return;
+  const int i = (int)(e % n);
+  const double inv = 1.0 / g.sp[i];
+  const double2 xv = x[e];
+  v[e] = u[e];
+  v[tot + e] = make_double2(g.nx[i] * inv * xv.x, g.nx[i] * inv * xv.y);
+  v[2 * tot + e] = make_double2(g.ny[i] * inv * xv.x, g.ny[i] * inv * xv.y);
+}
+
+// y = x/2 - D' x - i (omega^2 / eta) (n1 S(n1 x) + n2 S(n2 x)), t = S u
+__global__ void k_hard_combine64(int n, size_t tot, double omega, double eta, geom_dev g,
+                                 const double2* __restrict__ x, const double2* __restrict__ ys,
+                                 const double2* __restrict__ yd, double2* __restrict__ t,
+                                 double2* __restrict__ y) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= tot) return;
+  const int i = (int)(e % n);
+  const double inv = 1.0 / g.sp[i];
+  const double n1 = g.nx[i] * inv, n2 = g.ny[i] * inv;
+  const double2 s1 = ys[tot + e], s2 = ys[2 * tot + e];
+  const double2 m = make_double2(n1 * s1.x + n2 * s2.x, n1 * s1.y + n2 * s2.y);
+  const double k = omega * omega / eta;
+  const double2 xv = x[e], d = yd[e];
+  y[e] = make_double2(0.5 * xv.x - d.x + k * m.y, 0.5 * xv.y - d.y - k * m.x);
+  t[e] = ys[e];
 }
 
 std::mutex g_df_mu;
@@ -1236,8 +1299,8 @@ void df_prepare(cfie_op* op) {
                                                   op->wtab.as<double>(), op->diag.as<double2>(),
                                                   op->df_band.as<float4>());
   CFIE_CHECK_LAUNCH();
-  if (!hard) {
-    op->df_rowexp.reserve(sizeof(int) * (size_t)n);
+  {
+    op->df_rowexp.reserve(sizeof(int) * (size_t)n * (hard ? 2 : 1));
     float* base = op->geo32.as<float>();
     omega32 W{};
     W.wh = (float)op->omega;
@@ -1245,8 +1308,17 @@ void df_prepare(cfie_op* op) {
     W.winv = (float)(1.0 / op->omega);
     W.eta = (float)op->eta;
     W.h = (float)op->h;
-    k_rowexp<<<(unsigned)((n + 63) / 64), 256, 0, st>>>(n, b, W, geo32_at(base, n), base + 7 * n,
-                                                        op->df_rowexp.as<int>());
+    const unsigned g = (unsigned)((n + 63) / 64);
+    if (hard) {
+      k_rowexp<RK_S><<<g, 256, 0, st>>>(n, b, W, geo32_at(base, n), base + 7 * n,
+                                        op->df_rowexp.as<int>());
+      CFIE_CHECK_LAUNCH();
+      k_rowexp<RK_DP><<<g, 256, 0, st>>>(n, b, W, geo32_at(base, n), base + 7 * n,
+                                         op->df_rowexp.as<int>() + n);
+    } else {
+      k_rowexp<RK_SOFT><<<g, 256, 0, st>>>(n, b, W, geo32_at(base, n), base + 7 * n,
+                                           op->df_rowexp.as<int>());
+    }
     CFIE_CHECK_LAUNCH();
   }
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -1287,6 +1359,42 @@ void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
   P.w = (const float2*)(base + (2 * sizeof(float4) + sizeof(float2)) * n);
   P.band = op->df_band.as<float4>();
   const size_t tot = (size_t)n * nrhs;
+  if (op->bc == CFIE_SOUND_HARD && (op->res_variant == 2 || (op->res_variant == 0 && nrhs >= 8))) {
+    // S on [u, n1 x, n2 x] and D' on x with the sliced tensor-core sums
+    op->stats.residual_variant = 2;
+    cudaStream_t st = op->ctx->stream;
+    op->tmp1.reserve(sizeof(double2) * tot);
+    op->tmp2.reserve(sizeof(double2) * tot);
+    double2* u = op->tmp1.as<double2>();
+    double2* t = op->tmp2.as<double2>();
+    spectral_apply(op, x, u, nullptr, make_double2(1.0, 0.0), nrhs);
+    op->tcv.reserve(sizeof(double2) * tot * 4);
+    double2* v = op->tcv.as<double2>();
+    op->tcs.reserve(sizeof(double2) * tot * 4);
+    double2* ys = op->tcs.as<double2>();
+    k_hard_inputs64<<<nbk(tot), 256, 0, st>>>(n, tot, x, u, op->g, v);
+    CFIE_CHECK_LAUNCH();
+    op->df_x.reserve(sizeof(float4) * tot * 4);
+    float4* xv = op->df_x.as<float4>();
+    k_df_x<<<nbk(3 * tot), 256, 0, st>>>(3 * tot, v, xv);
+    CFIE_CHECK_LAUNCH();
+    k_df_x<<<nbk(tot), 256, 0, st>>>(tot, x, xv + 3 * tot);
+    CFIE_CHECK_LAUNCH();
+    const size_t nbw = (size_t)n * (2 * (size_t)P.b + 1);
+    df_params PS = P, PD = P;
+    PS.x = xv;
+    PD.x = xv + 3 * tot;
+    PD.band = P.band + nbw;
+    for (int r0 = 0; r0 < 3 * nrhs; r0 += 64)
+      run_rtc_block<RK_S>(op, PS, v, ys, r0, std::min(64, 3 * nrhs - r0));
+    for (int r0 = 0; r0 < nrhs; r0 += 64)
+      run_rtc_block<RK_DP>(op, PD, x, ys + 3 * tot, r0, std::min(64, nrhs - r0));
+    k_hard_combine64<<<nbk(tot), 256, 0, st>>>(n, tot, op->omega, op->eta, op->g, x, ys,
+                                               ys + 3 * tot, t, y);
+    CFIE_CHECK_LAUNCH();
+    spectral_apply(op, t, y, y, make_double2(0.0, -1.0 / op->eta), nrhs);
+    return;
+  }
   if (op->bc == CFIE_SOUND_HARD) {
     // y = x/2 - D' x + (1/(i eta)) [d/ds S d/ds x + omega^2 sum_c n_c S (n_c x)]
     op->tmp1.reserve(sizeof(double2) * tot);
@@ -1313,12 +1421,7 @@ void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
     op->stats.residual_variant = 2;
     for (int r0 = 0; r0 < nrhs; r0 += 64) {
       const int nr = std::min(64, nrhs - r0);
-      if (nr > 32)
-        run_rtc<64>(op, P, x, y, r0, nr);
-      else if (nr > 16)
-        run_rtc<32>(op, P, x, y, r0, nr);
-      else
-        run_rtc<16>(op, P, x, y, r0, nr);
+      run_rtc_block<RK_SOFT>(op, P, x, y, r0, nr);
     }
     return;
   }

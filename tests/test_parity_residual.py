@@ -71,12 +71,34 @@ def test_tensor_core_residual_parity(ctx, kind, params, n, omega, nrhs):
 def test_residual_variant_arguments(ctx):
     from paper_1408_1578_gb300 import cfie
     op = ctx.kite().discretise(256, 20.0, bc="hard", precision="fp32")
-    with pytest.raises(cfie.CfieError):
-        op.set_residual_variant(2)
+    op.set_residual_variant(2)
     op.set_residual_variant(1)
+    with pytest.raises(cfie.CfieError):
+        op.set_residual_variant(3)
     op64 = ctx.kite().discretise(256, 20.0, precision="fp64")
     with pytest.raises(cfie.CfieError):
         op64.set_residual_variant(1)
+
+
+@pytest.mark.parametrize("kind,params,n,omega,nrhs", [
+    ("kite", {}, 2000, 200.0, 8),
+    ("star", {"a": [0, 0, 0, 0, 0.3], "b": [0] * 5}, 1502, 120.0, 30),   # S passes of 64 + 26
+    ("ellipse", {"a": 1.0, "b": 0.5}, 1000, 90.0, 3),
+])
+def test_tensor_core_residual_parity_hard(ctx, kind, params, n, omega, nrhs):
+    """Sound-hard residual with the S and D' sums sliced on the tensor cores,
+    against the oracle and the CUDA-core double-float residual."""
+    c = geometry.make(kind, n, **params)
+    A = operators.cfie_matrix(c, omega, omega, "hard")
+    X = inputs.random_density(n, nrhs, seed=11 * n + nrhs)
+    op = ctx.geometry(kind, **params).discretise(n, omega, bc="hard", precision="fp32")
+    y2, y1 = empty(nrhs, n), empty(nrhs, n)
+    op.set_residual_variant(2)
+    op.apply_residual(to_dev(X), y2)
+    op.set_residual_variant(1)
+    op.apply_residual(to_dev(X), y1)
+    assert np.max(col_rel(to_host(y2), (A @ X.T).T)) < TOL_RES
+    assert np.max(col_rel(to_host(y2), to_host(y1))) < TOL_RES
 
 
 @pytest.mark.parametrize("kind,params,n,omega,nrhs", [

@@ -312,6 +312,7 @@ cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cf
     if (bc == CFIE_SOUND_HARD) fft_prepare(op);
     if (precision != CFIE_FP64) fp32_prepare(op);
     if (precision != CFIE_FP64) df_prepare(op);
+    if (precision != CFIE_FP64) fp32_band(op);
     if (layout == CFIE_STORED) stored_prepare(op);
     CFIE_CHECK_CUDA(cudaStreamSynchronize(ctx->stream));
   });

@@ -306,6 +306,7 @@ void matvec_fp64_static(cfie_op* op, const double2* x, double2* y, int nrhs);
 size_t static_scratch_capacity();
 // matvec_fp32.cu
 void fp32_prepare(cfie_op* op);
+void fp32_band(cfie_op* op);   // after df_prepare
 // FP32 helpers shared with the tensor-core kernels: x32 = x, u32 = (1/|z'|) d/dt x32,
 // y += (1/(i eta)) (1/|z'|) d/dt t32
 void k_to32_fp32(cfie_op* op, const double2* x, float2* x32, size_t tot);

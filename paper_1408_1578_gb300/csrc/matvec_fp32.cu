@@ -361,6 +361,22 @@ k_band_scan(int n, double omega, geom_dev g, int* __restrict__ bmax, float* __re
   }
 }
 
+// FP32 band entries (offsets |dd| <= b) from the double-float band of width
+// bd >= b: the high parts (the FP32 rounding of the FP64 entries); `ops`
+// bands of each kind (sound hard: S, then D')
+__global__ void k_band_from_df(int n, int b, int bd, int ops, const float4* __restrict__ dfb,
+                               float2* __restrict__ band) {
+  const int bw = 2 * b + 1, bwd = 2 * bd + 1;
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (size_t)n * bw) return;
+  const int i = (int)(e / bw);
+  const int dd = (int)(e % bw) - b;
+  for (int o = 0; o < ops; ++o) {
+    const float4 v = dfb[(size_t)o * n * bwd + (size_t)i * bwd + dd + bd];
+    band[(size_t)o * n * bw + e] = make_float2(v.x, v.z);
+  }
+}
+
 template <int BC>
 __global__ void k_band_fill(int n, int b, double omega, double eta, geom_dev g,
                             const double* __restrict__ wtab, const double2* __restrict__ diag,
@@ -471,8 +487,21 @@ void fp32_prepare(cfie_op* op) {
                                     w32, c32,
                                     reinterpret_cast<float4*>(base + geo32_pack_offset(n)));
   CFIE_CHECK_LAUNCH();
+}
+
+// The FP32 near band (omega r < 16), after df_prepare: rounded from the
+// FP64-evaluated double-float band when that one is at least as wide (it holds
+// the same entries), else evaluated in FP64 here.
+void fp32_band(cfie_op* op) {
+  const int n = op->n, b = op->band_b;
+  const size_t bw = 2 * (size_t)b + 1;
+  cudaStream_t st = op->ctx->stream;
   float2* band = op->band.as<float2>();
-  if (op->bc == CFIE_SOUND_SOFT) {
+  const bool hard = op->bc == CFIE_SOUND_HARD;
+  if (op->df_b >= b) {
+    k_band_from_df<<<nblk((size_t)n * bw), 256, 0, st>>>(n, b, op->df_b, hard ? 2 : 1,
+                                                          op->df_band.as<float4>(), band);
+  } else if (!hard) {
     k_band_fill<0><<<nblk((size_t)n * bw), 256, 0, st>>>(n, b, op->omega, op->eta, op->g,
                                                           op->wtab.as<double>(),
                                                           op->diag.as<double2>(), band, nullptr);

@@ -156,6 +156,89 @@ __global__ void k_bs_out(int n, int N, int cols, const T* __restrict__ conv2,
   out[(size_t)c * n + j] = r;
 }
 
+// The whole derivative of one column in one CTA when both length-N work
+// buffers fit in shared memory: chirp premultiply, FFT, times Bf, inverse FFT,
+// derivative, FFT, times Bf, inverse FFT, output, with barriers between passes.
+template <typename T>
+__device__ __forceinline__ void smem_fft(int N, int L, T* a, T* b, const T* __restrict__ tw,
+                                         int inverse, T*& res) {
+  int m = 1;
+  for (int p = 0; p < L; ++p, m *= 2) {
+    for (int i = threadIdx.x; i < N / 2; i += blockDim.x) {
+      const int j = i / m, k = i - j * m;
+      T w = tw[(size_t)k * (N / (2 * m))];
+      if (inverse) w.y = -w.y;
+      const T u = a[j * m + k], v = cmul(w, a[j * m + k + N / 2]);
+      b[2 * j * m + k] = cx<T>::make(u.x + v.x, u.y + v.y);
+      b[2 * j * m + k + m] = cx<T>::make(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+    T* t = a;
+    a = b;
+    b = t;
+  }
+  res = a;
+}
+
+template <typename T, typename X, typename O>
+__global__ void __launch_bounds__(512)
+k_spectral_smem(int n, int N, int L, const X* __restrict__ in, const T* __restrict__ ch,
+                const T* __restrict__ bf, const T* __restrict__ tw, const double* __restrict__ sp,
+                double2 scale, const O* __restrict__ base, O* __restrict__ out) {
+  using S = typename cx<T>::S;
+  extern __shared__ __align__(16) unsigned char raw[];
+  T* a = reinterpret_cast<T*>(raw);
+  T* b = a + N;
+  const int c = blockIdx.x;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    T v = cx<T>::make(0.0, 0.0);
+    if (j < n) {
+      const X xv = in[(size_t)c * n + j];
+      v = cmulc(cx<T>::make(xv.x, xv.y), ch[j]);
+    }
+    a[j] = v;
+  }
+  __syncthreads();
+  T* r;
+  smem_fft(N, L, a, b, tw, 0, r);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) r[k] = cmul(r[k], bf[k]);
+  __syncthreads();
+  T* o = r == a ? b : a;
+  smem_fft(N, L, r, o, tw, 1, r);
+  o = r == a ? b : a;
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+    T v = cx<T>::make(0.0, 0.0);
+    if (m < n) {
+      const T Xm = cmulc(r[m], ch[m]);
+      const S mm = (S)(2 * m < n ? m : (2 * m == n ? 0 : m - n)) / (S)N;
+      const T D = cx<T>::make(-mm * Xm.y, mm * Xm.x);
+      v = cmulc(cx<T>::make(D.x, -D.y), ch[m]);
+    }
+    o[m] = v;
+  }
+  __syncthreads();
+  smem_fft(N, L, o, r, tw, 0, r);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) r[k] = cmul(r[k], bf[k]);
+  __syncthreads();
+  o = r == a ? b : a;
+  smem_fft(N, L, r, o, tw, 1, r);
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const T w = cmulc(r[j], ch[j]);
+    const double f = 1.0 / ((double)n * (double)N * sp[j]);
+    const double dx = (double)w.x * f, dy = -(double)w.y * f;
+    double ox = scale.x * dx - scale.y * dy, oy = scale.x * dy + scale.y * dx;
+    if (base) {
+      const O bv = base[(size_t)c * n + j];
+      ox += (double)bv.x;
+      oy += (double)bv.y;
+    }
+    O q;
+    q.x = ox;
+    q.y = oy;
+    out[(size_t)c * n + j] = q;
+  }
+}
+
 unsigned nb(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
 
 // FFT of `cols` columns of length N between the two work buffers; returns the
@@ -196,6 +279,17 @@ void spectral_fft(cfie_op* op, const X* in, O* out, const O* base, double2 scale
   fft_plan& F = op->fft;
   const int n = op->n, N = F.N, L = F.L;
   cudaStream_t st = op->ctx->stream;
+  const size_t smem = 2 * sizeof(T) * (size_t)N;
+  if (smem <= (size_t)128 * 1024) {
+    // one CTA per column, everything in shared memory
+    prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
+    CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_spectral_smem<T, X, O>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_spectral_smem<T, X, O><<<cols, 512, smem, st>>>(n, N, L, in, chirp_of<T>(F), bf_of<T>(F),
+                                                     tw_of<T>(F), op->g.sp, scale, base, out);
+    CFIE_CHECK_LAUNCH();
+    return;
+  }
   dbuf& w = sizeof(T) == 16 ? F.work : F.work32;
   w.reserve(sizeof(T) * 2 * (size_t)N * cols);
   T* a = w.as<T>();

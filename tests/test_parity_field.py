@@ -48,7 +48,7 @@ def test_field_matches_oracle_elementwise(ctx, bc, npts, nrhs):
 
 @pytest.mark.parametrize("bc", ["soft", "hard"])
 def test_disk_series_end_to_end(ctx, bc):
-    """Config 1 shape: unit circle, omega = 64, n = 1024, d = (1, 0); the GPU
+    """Unit circle, omega = 64, n = 1024, d = (1, 0); the GPU
     solution's field at r = 2 against the Fourier-Bessel series."""
     n, w = 1024, 64.0
     op = ctx.circle().discretise(n, w, bc=bc, precision="fp64")
@@ -64,7 +64,7 @@ def test_disk_series_end_to_end(ctx, bc):
 
 @pytest.mark.parametrize("bc", ["soft", "hard"])
 def test_point_source_refined_end_to_end(ctx, bc):
-    """Star of config 2's shape at omega = 64: boundary data -G(., x0) with x0
+    """Star r = 1 + 0.3 cos 5t at omega = 64: boundary data -G(., x0) with x0
     inside, FP32-refined GPU solve, GPU field on the radius-3 circle = -G."""
     n, w = 1024, 64.0
     x0 = np.array([0.1, 0.05])

@@ -85,7 +85,7 @@ def test_refined_solve_matches_fp64_solution(ctx, bc):
 
 
 @pytest.mark.slow
-def test_kite_config_fp32_sampled_rows(ctx):
+def test_kite_n32768_fp32_sampled_rows(ctx):
     """Kite, omega = 2048, n = 32768, 64 right-hand sides (the precision
     workload): FP32 matvec rows sampled against the oracle's FP64 rows."""
     spec = inputs.WORKLOADS["kite"]
@@ -104,7 +104,7 @@ def test_kite_config_fp32_sampled_rows(ctx):
 
 
 @pytest.mark.slow
-def test_kite_config_refined_residual_rows(ctx):
+def test_kite_n32768_refined_residual_rows(ctx):
     """Full-size refined solve: the returned FP64 residual meets 1e-8, and the
     oracle's rows of f - A x agree with it (sampled property at full size)."""
     spec = inputs.WORKLOADS["kite"]

@@ -82,7 +82,7 @@ def test_plane_wave_rhs_parity(ctx, bc):
     assert np.max(col_rel(to_host(f), want)) < 8 * omega * 2.2e-16
 
 
-def test_disk_config_unrestarted_gmres(ctx):
+def test_disk_n1024_unrestarted_gmres(ctx):
     """Unit circle, omega = eta = 64, n = 1024, d = (1, 0), unrestarted GMRES to 1e-8."""
     w, n = 64.0, 1024
     c = geometry.circle(n)
@@ -131,7 +131,7 @@ def test_initial_guess_is_used(ctx):
 
 
 @pytest.mark.slow
-def test_star_config_full_size(ctx):
+def test_star_n4096_full_size(ctx):
     """Sound-hard star r = 1 + 0.3 cos 5t, omega = 256, n = 4096, 16 directions:
     FP64 matvec and solve against the oracle's assembled matrix and LU."""
     spec = inputs.WORKLOADS["star"]
@@ -156,7 +156,7 @@ def test_star_config_full_size(ctx):
 
 
 @pytest.mark.slow
-def test_kite_config_sampled_rows(ctx):
+def test_kite_n32768_sampled_rows(ctx):
     """Kite, omega = 2048, n = 32768, 64 right-hand sides: FP64 matvec rows
     sampled against the oracle's rows (the full oracle matvec is too slow)."""
     spec = inputs.WORKLOADS["kite"]

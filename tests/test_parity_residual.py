@@ -140,7 +140,7 @@ def test_residual_of_fp64_operators_is_the_fp64_kernel(ctx):
 
 
 @pytest.mark.slow
-def test_kite_config_residual_rows(ctx):
+def test_kite_n32768_residual_rows(ctx):
     spec = inputs.WORKLOADS["kite"]
     n, w, nrhs = spec["n"], spec["omega"], spec["nrhs"]
     c = geometry.kite(n)

@@ -348,7 +348,9 @@ def run_ours(args, rank, world):
             "iterations": [int(v) for v in its[:4]],
             "solve_stats": stats,
             "e2e": {"value": e2e_pairs_all / (e2e_ms_max / 1e3), "unit": UNIT,
-                    "h2d_bytes_per_step": int(nrhs * 8 + 64 * 16),
+                    "h2d_bytes_per_step": int(8 * (nrhs + sum(len(v) for v in
+                                                              spec["params"].values()
+                                                              if isinstance(v, list)))),
                     "d2h_bytes_per_step": int(nrhs * n * 16)},
             "gpu_launches": int(launches),
             "kernel_ms": {k: round(v[0], 3) for k, v in ktimes.items()},
@@ -702,6 +704,19 @@ def run_stars(args):
     kt = ctx.kernel_times()
     launches = ctx.lib.cfie_launch_count() - l0
     clk = clocks.stop()
+    ctx.set_profiling(False)
+    # end to end: host angles in (inside the C calls), solutions out to pinned
+    # host memory, copies inside the timed region
+    x_host = torch.empty(L, dtype=torch.complex128, pin_memory=True)
+    e2e_ms, e2e_pairs = 0.0, 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its_e, rel_e, stats_e = step()
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_pairs += pairs_mv * (stats_e["inner_matvecs"] + stats_e["fp64_matvecs"])
     peaks, src = measured_peaks()
     tens_ms, tens_n = kt["matvec_tensor"]
     gemm_bytes = sum(s["n"] * (s["n"] + 63) // 64 * 64 * 8 for s in specs)
@@ -718,6 +733,9 @@ def run_stars(args):
            "dtype": "bf16x3+f64", "data": "synthetic",
            "config": dict(stars_config(count), sum_n2=pairs_mv),
            "solves_per_s": solves / (ms / 1e3), "max_relres": worst, "solve_stats": stats,
+           "e2e": {"value": e2e_pairs / (e2e_ms / 1e3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(sum(s["nrhs"] for s in specs) * 8),
+                   "d2h_bytes_per_step": int(L * 16)},
            "gpu_launches": int(launches), "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
            "kernel_launches": {k: v[1] for k, v in kt.items()}, "roofline": roof, "clocks": clk}
     ctx.close()

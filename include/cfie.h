@@ -33,6 +33,11 @@
  *    context keeps a message readable with cfie_last_error; outputs are left
  *    unspecified unless stated.
  *  - A context is not thread-safe: use one context per host thread.
+ *  - Library device memory comes from the device's stream-ordered pool
+ *    (cudaMallocAsync / cudaFreeAsync on the context stream); cfie_ctx_create
+ *    raises the pool's release threshold so that buffers freed when operators
+ *    are destroyed are reused by the next ones instead of returned to the
+ *    driver.
  */
 #ifndef CFIE_H
 #define CFIE_H

@@ -1299,7 +1299,7 @@ void df_prepare(cfie_op* op) {
                                                   op->wtab.as<double>(), op->diag.as<double2>(),
                                                   op->df_band.as<float4>());
   CFIE_CHECK_LAUNCH();
-  {
+  if (op->layout != CFIE_STORED) {   // stored operators get them from the assembly
     op->df_rowexp.reserve(sizeof(int) * (size_t)n * (hard ? 2 : 1));
     float* base = op->geo32.as<float>();
     omega32 W{};

@@ -56,14 +56,26 @@ __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bflo
   lo = __float2bfloat16_rn(v - __bfloat162float(hi));
 }
 
+// row maxima (float bits, in place) -> exponents E with max < 2^E (1e-4 margin
+// for the FP32 evaluation), 0 for rows without far entries
+__global__ void k_rowexp_from_max(int n, unsigned* __restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float m = __uint_as_float(r[i]);
+  int e = 0;
+  if (m > 0.f) frexpf(m * 1.0001f, &e);
+  reinterpret_cast<int*>(r)[i] = e;
+}
+
 // planes [4][n][pitch]: hi_re, hi_im, lo_re, lo_im; grid (ceil(pitch / 256), n)
 __global__ void __launch_bounds__(256)
-k_assemble(int n, int pitch, int b, omega32 W, geo32 g, const float* __restrict__ w32,
-           const float2* __restrict__ band, __nv_bfloat16* __restrict__ planes) {
+k_assemble(int n, int pitch, int b, int bd, omega32 W, geo32 g, const float* __restrict__ w32,
+           const float2* __restrict__ band, __nv_bfloat16* __restrict__ planes,
+           unsigned* __restrict__ rmax) {
   const int i = blockIdx.y;
   const int j = blockIdx.x * 256 + threadIdx.x;
-  if (j >= pitch) return;
   float2 a = make_float2(0.f, 0.f), unused;
+  float far_max = 0.f;
   if (j < n) {
     int d = i - j;
     if (d < 0) d += n;
@@ -75,7 +87,15 @@ k_assemble(int n, int pitch, int b, omega32 W, geo32 g, const float* __restrict_
                            g.xh[j], g.xl[j], g.yh[j], g.yl[j], g.nx[j], g.ny[j], g.sp[j], w32[d],
                            a, unused);
     }
+    // largest far entry of the row (outside the double-float band of width bd):
+    // the row exponent of the tensor-core residual
+    if (rmax && d > bd && d < n - bd) far_max = fmaxf(fabsf(a.x), fabsf(a.y));
   }
+  if (rmax) {
+    for (int o = 16; o > 0; o >>= 1) far_max = fmaxf(far_max, __shfl_xor_sync(0xffffffffu, far_max, o));
+    if ((threadIdx.x & 31) == 0 && far_max > 0.f) atomicMax(&rmax[i], __float_as_uint(far_max));
+  }
+  if (j >= pitch) return;
   __nv_bfloat16 hr, lr, hi, li;
   split_bf16(a.x, hr, lr);
   split_bf16(a.y, hi, li);
@@ -292,30 +312,31 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
 }
 
 // B operand planes of every job: B1 = [Xr | Xi], B2 = [-Xi | Xr] (rows = output
-// columns), hi / lo bf16 split; grid (ceil(max pitch / 256), NP, jobs)
+// columns), hi / lo bf16 split; grid (NP, jobs), each CTA striding over the
+// job's pitch
 __global__ void k_prep_b_jobs(const gemm_job* __restrict__ jobs, const gemm_io* __restrict__ io,
                               int NP) {
-  const gemm_job& J = jobs[blockIdx.z];
-  const int c = blockIdx.y;
-  const int j = blockIdx.x * 256 + threadIdx.x;
-  if (j >= J.pitch) return;
+  const gemm_job& J = jobs[blockIdx.y];
+  const int c = blockIdx.x;
   const int NR = NP / 2;
   const int r = c < NR ? c : c - NR;
-  double w1 = 0.0, w2 = 0.0;
-  if (j < J.n && r < J.nr) {
-    const double2 xv = io->x[J.xoff + (long long)r * J.n + j];
-    w1 = c < NR ? xv.x : xv.y;
-    w2 = c < NR ? -xv.y : xv.x;
-  }
-  const __nv_bfloat16 h1 = __float2bfloat16_rn((float)w1), h2 = __float2bfloat16_rn((float)w2);
-  const __nv_bfloat16 l1 = __float2bfloat16_rn((float)(w1 - (double)__bfloat162float(h1)));
-  const __nv_bfloat16 l2 = __float2bfloat16_rn((float)(w2 - (double)__bfloat162float(h2)));
   const size_t plane = (size_t)NP * J.pitch;
-  const size_t e = (size_t)c * J.pitch + j;
-  J.bt[e] = h1;
-  J.bt[plane + e] = l1;
-  J.bt[2 * plane + e] = h2;
-  J.bt[3 * plane + e] = l2;
+  for (int j = threadIdx.x; j < J.pitch; j += blockDim.x) {
+    double w1 = 0.0, w2 = 0.0;
+    if (j < J.n && r < J.nr) {
+      const double2 xv = io->x[J.xoff + (long long)r * J.n + j];
+      w1 = c < NR ? xv.x : xv.y;
+      w2 = c < NR ? -xv.y : xv.x;
+    }
+    const __nv_bfloat16 h1 = __float2bfloat16_rn((float)w1), h2 = __float2bfloat16_rn((float)w2);
+    const __nv_bfloat16 l1 = __float2bfloat16_rn((float)(w1 - (double)__bfloat162float(h1)));
+    const __nv_bfloat16 l2 = __float2bfloat16_rn((float)(w2 - (double)__bfloat162float(h2)));
+    const size_t e = (size_t)c * J.pitch + j;
+    J.bt[e] = h1;
+    J.bt[plane + e] = l1;
+    J.bt[2 * plane + e] = h2;
+    J.bt[3 * plane + e] = l2;
+  }
 }
 
 // y = sum of the segment partials of each (job, m tile), fixed order, FP64;
@@ -393,7 +414,8 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
       J.tb = make_map(J.bt, 4 * (uint64_t)kNP, (uint64_t)J.pitch, J.pitch, kNP);
     }
   }
-  // stream-K split of the (m tile, k tile) pairs over one CTA per SM
+  // one CTA per SM: stream-K split of the (m tile, k tile) pairs when there are
+  // few row tiles, whole row tiles dealt round-robin otherwise
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   long long W = 0;
@@ -408,7 +430,26 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
   std::vector<int> cbeg(grid + 1, 0);
   std::vector<int2> mt_job(mt_total), mt_seg(mt_total, make_int2(0, 0));
   size_t jk = 0;
-  for (int c = 0; c < grid; ++c) {
+  if (mt_total >= 4 * grid) {
+    // many row tiles (batches): whole (job, row tile) units dealt round-robin,
+    // unit u to CTA u % grid, so that the CTAs work on neighbouring units of
+    // few jobs at any time and the jobs' right-hand-side planes stay in L2
+    std::vector<std::vector<int4>> per(grid);
+    int u = 0;
+    for (size_t k = 0; k < jobs.size(); ++k) {
+      const int mt = (jobs[k].n + BM - 1) / BM, kt = (jobs[k].n + BK - 1) / BK;
+      for (int m = 0; m < mt; ++m, ++u) per[u % grid].push_back(make_int4((int)k, m, 0, kt));
+    }
+    for (int c = 0; c < grid; ++c) {
+      cbeg[c] = (int)segs.size();
+      for (const int4& sg : per[c]) {
+        const int g = jobs[sg.x].mt0 + sg.y;
+        mt_seg[g] = make_int2((int)segs.size(), 1);
+        segs.push_back(sg);
+      }
+    }
+  }
+  for (int c = 0; c < grid && mt_total < 4 * grid; ++c) {
     const long long b = W * c / grid, e = W * (c + 1) / grid;
     cbeg[c] = (int)segs.size();
     long long t = b;
@@ -477,7 +518,7 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
   if (e1 == cudaSuccess) {
     const gemm_job* dj = G.jobs.as<gemm_job>();
     const gemm_io* io = G.io.as<gemm_io>();
-    k_prep_b_jobs<<<dim3(nblk(max_pitch), kNP, G.njobs), 256, 0, cs>>>(dj, io, kNP);
+    k_prep_b_jobs<<<dim3(kNP, G.njobs), 256, 0, cs>>>(dj, io, kNP);
     k_gemm_persistent<kNP><<<grid, 192, smem, cs>>>(
         dj, reinterpret_cast<const int4*>(tb + o_segs), reinterpret_cast<const int*>(tb + o_cbeg),
         G.partial.as<float2>(), G.err.as<int>(), G.stall);
@@ -535,10 +576,23 @@ void stored_prepare(cfie_op* op) {
   W.eta = (float)op->eta;
   W.h = (float)op->h;
   const dim3 grid(nblk(pitch), n);
-  k_assemble<<<grid, 256, 0, op->ctx->stream>>>(n, pitch, op->band_b, W, geo32_at(base, n),
-                                                base + 7 * n, op->band.as<float2>(),
-                                                op->stored.as<__nv_bfloat16>());
+  // the row maxima of the far entries come with the assembly (sound soft:
+  // the tensor-core residual's row exponents), not from a separate pass
+  unsigned* rmax = nullptr;
+  if (op->df_b > 0) {
+    op->df_rowexp.reserve(sizeof(int) * (size_t)n);
+    rmax = reinterpret_cast<unsigned*>(op->df_rowexp.as<int>());
+    CFIE_CHECK_CUDA(cudaMemsetAsync(rmax, 0, sizeof(unsigned) * n, op->ctx->stream));
+  }
+  k_assemble<<<grid, 256, 0, op->ctx->stream>>>(n, pitch, op->band_b, op->df_b, W,
+                                                geo32_at(base, n), base + 7 * n,
+                                                op->band.as<float2>(),
+                                                op->stored.as<__nv_bfloat16>(), rmax);
   CFIE_CHECK_LAUNCH();
+  if (rmax) {
+    k_rowexp_from_max<<<nblk(n), 256, 0, op->ctx->stream>>>(n, rmax);
+    CFIE_CHECK_LAUNCH();
+  }
   CFIE_CHECK_CUDA(cudaStreamSynchronize(op->ctx->stream));
 }
 

@@ -1236,7 +1236,9 @@ std::map<std::pair<int, int>, int> g_df_rb;
 // else both candidates timed once with CUDA events on the operator's stream
 template <typename F>
 int df_tile_choice(cfie_op* op, int n, int nrhs, F run) {
-  const auto key = std::make_pair(n, nrhs);
+  int nb = 1;                      // shared by shapes up to the next power of two
+  while (nb < n) nb *= 2;
+  const auto key = std::make_pair(nb, nrhs > 48 ? 64 : 48);
   {
     std::lock_guard<std::mutex> lock(g_df_mu);
     auto it = g_df_rb.find(key);

@@ -145,10 +145,13 @@ def measured_peaks():
 
 
 # Algorithmic work per (target, source) pair of each kernel class, counted from
-# the kernels' per-pair formulas (FP32 add / mul / fma / rint = 1 operation,
-# IEEE division or square root = 8).
+# the kernels' per-pair formulas (FP32 add / mul / fma / min / max / rint and
+# each special-function unit op = 1 operation, IEEE division or square root = 8).
 SMS, FP32_LANES = 152, 128
-ENTRY_OPS = {"soft": 101, "hard": 110}   # FP32 pair entries (two-float phase, asymptotics)
+# FP32 pair entries (two-float phase, asymptotics) by summation variant: the
+# CUDA-core kernel evaluates both hard entries from one phase; the tensor-core
+# kernel folds the per-node factors in and evaluates S and D' in two passes
+ENTRY_OPS = {("soft", 1): 82, ("hard", 1): 95, ("soft", 2): 72, ("hard", 2): 114}
 SUM_OPS = {"soft": 4, "hard": 8}         # FP32 FMAs per pair and right-hand side (CUDA-core sums)
 DF_ENTRY_OPS = 677                       # double-float pair entry of the residual kernel
 DF_TERM_OPS = 48                         # Dot2 complex product-sum per pair and right-hand side
@@ -160,7 +163,7 @@ FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)
 # ncu capture of the current kernel at the same launch configuration, keyed by
 # (kernel class, curve, n, nrhs, matvec variant); absent = not captured.
 NCU_TRAFFIC = {
-    ("matvec_fp32", "kite", 32768, 64, 2): 78.91328e6 + 11.470592e6,
+    ("matvec_fp32", "kite", 32768, 64, 2): 79.323904e6 + 10.755328e6,
 }
 
 
@@ -179,7 +182,7 @@ def kernel_rooflines(kt, spec, stats, peaks, src, n, solves_timed):
         avg = sec / launches
         if cls == "matvec_fp32":
             v = stats.get("matvec_variant", 1)
-            ops = ENTRY_OPS[bc] + (SUM_OPS[bc] * nrhs if v == 1 else 0)
+            ops = ENTRY_OPS[(bc, 2 if v == 2 else 1)] + (SUM_OPS[bc] * nrhs if v == 1 else 0)
             a = ops * n * n / avg / 1e12
             out[cls] = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "Top/s",
                         "frac": a / fp32_peak, "traffic": None,

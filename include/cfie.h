@@ -348,6 +348,12 @@ cfie_status cfie_server_wait_all(cfie_server* server, double timeout_s);
 cfie_status cfie_server_release(cfie_server* server, long long ticket);
 cfie_status cfie_server_stats(cfie_server* server, cfie_server_counters* out);
 const char* cfie_server_last_error(cfie_server* server);
+/* The error message of a finished request whose status is not CFIE_OK (empty
+ * otherwise, or while it runs), copied NUL-terminated into buf (host, len
+ * bytes, truncated to fit).  CFIE_EINVAL for an unknown ticket, a null
+ * server or buffer, or len 0. */
+cfie_status cfie_server_request_error(cfie_server* server, long long ticket, char* buf,
+                                      size_t len);
 /* Stop the slots (running solves finish first) and free everything. */
 void cfie_server_destroy(cfie_server* server);
 

@@ -122,6 +122,7 @@ SIGNATURES = {
     "cfie_server_release": (_I, [_P, ctypes.c_longlong]),
     "cfie_server_stats": (_I, [_P, ctypes.POINTER(cfie_server_counters)]),
     "cfie_server_last_error": (ctypes.c_char_p, [_P]),
+    "cfie_server_request_error": (_I, [_P, ctypes.c_longlong, ctypes.c_char_p, ctypes.c_size_t]),
     "cfie_server_destroy": (None, [_P]),
 }
 
@@ -368,6 +369,10 @@ class Server:
         out = {k: getattr(r, k) for k, _ in r._fields_}
         if want_x and r.done:
             out["x"] = x
+        if r.done and r.status != CFIE_OK:
+            buf = ctypes.create_string_buffer(512)
+            self.lib.cfie_server_request_error(self.h, ticket, buf, 512)
+            out["error"] = buf.value.decode(errors="replace")
         return out
 
     def wait_all(self, timeout_s=600.0):

@@ -6,14 +6,16 @@
 // FP32 with two safeguards:
 //
 //  * Phase.  omega r reaches ~6e3 on the largest workloads, where one FP32
-//    rounding of r is a ~4e-4 rad phase error.  Coordinates are stored as
-//    hi + lo FP32 pairs; z_i - z_j, r^2, r and x = omega r are carried as
-//    two-float numbers (error-free transformations built from fmaf), and
+//    rounding of r is a ~4e-4 rad phase error.  Coordinates are stored
+//    times omega as hi + lo FP32 pairs, the hi parts on a common grid on
+//    which their differences are exact, so the node distance is x = omega r
+//    itself; omega (z_i - z_j), x^2 and x are carried as two-float numbers
+//    (error-free transformations built from fmaf), and
 //    chi = x - pi/4 is reduced modulo 2 pi with a three-part Cody-Waite
 //    constant whose first part has 10 significant bits (k * C1 exact for
 //    x < 1e5).  The reduced phase is accurate to a few 1e-7 rad.
 //  * Small arguments.  Hankel's asymptotic expansion (A&S 9.2.5, 9.2.9, 9.2.10;
-//    four terms of P and of Q, truncation error < 2e-9 for x >= 16) is used for
+//    three terms of P and of Q, truncation error < 4.1e-8 for x >= 16) is used for
 //    every pair with omega r >= 16.  Pairs closer than that form a band
 //    |i - j| <= b around the diagonal (b found by an O(n^2) scan at set-up);
 //    their entries are evaluated once in FP64 and stored as complex64.
@@ -296,27 +298,56 @@ k_spectral32(int n, const float* __restrict__ ct, const double* __restrict__ sp,
 // ---------------------------------------------------------------------------
 // set-up kernels
 // ---------------------------------------------------------------------------
-__global__ void k_geo32(int n, geom_dev g, geo32 o, const double* __restrict__ w,
-                        const double* __restrict__ ct, float* __restrict__ w32,
-                        float* __restrict__ c32, float4* __restrict__ pk) {
+// Largest |x|, |y| over the nodes, as the bit pattern of a non-negative float
+// (ordered like the values), for the coordinate grid below
+__global__ void k_coord_bound(int n, geom_dev g, unsigned* __restrict__ bound) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  float m = 0.f;
+  if (i < n) m = fmaxf(fabsf((float)g.x[i]), fabsf((float)g.y[i]));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(bound, __float_as_uint(m));
+}
+
+// FP32 geometry.  Coordinates scaled by omega and split as hi + lo with hi on
+// the grid 2^-g, g = 22 - e where every omega |x|, omega |y| < 2^e: a hi part
+// then needs at most 23 bits, the difference of two of them at most 24, so it
+// is exact in FP32; the lo parts (|lo| <= 2^(e-23)) keep the rest to ~2^(e-47).
+__global__ void k_geo32(int n, geom_dev g, geo32 o, const double* __restrict__ w,
+                        const double* __restrict__ ct, const unsigned* __restrict__ bound,
+                        double omega, double eta, double h, float* __restrict__ w32,
+                        float* __restrict__ c32, float4* __restrict__ pk,
+                        float* __restrict__ wkt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 8) wkt[2 * n + i] = 0.f;
   if (i >= n) return;
-  const double x = g.x[i], y = g.y[i];
-  const float xh = (float)x, yh = (float)y;
+  int e = 0;
+  const double m = omega * (double)__uint_as_float(*bound);
+  if (m > 0.0) frexp(m, &e);
+  const double q = ldexp(1.0, 22 - e), qi = ldexp(1.0, e - 22);
+  const double x = omega * g.x[i], y = omega * g.y[i];
+  const double xhd = rint(x * q) * qi, yhd = rint(y * q) * qi;
+  const float xh = (float)xhd, yh = (float)yhd;
+  const float xl = (float)(x - xhd), yl = (float)(y - yhd);
   o.xh[i] = xh;
-  o.xl[i] = (float)(x - (double)xh);
+  o.xl[i] = xl;
   o.yh[i] = yh;
-  o.yl[i] = (float)(y - (double)yh);
+  o.yl[i] = yl;
   o.nx[i] = (float)g.nx[i];
   o.ny[i] = (float)g.ny[i];
   o.sp[i] = (float)g.sp[i];
   w32[i] = (float)w[i];
   c32[i] = (float)ct[i];
-  // the Kress table twice over, indexed by i - j + n (no cyclic wrap)
-  w32[2 * n + i] = (float)w[i];
-  w32[3 * n + i] = (float)w[i];
-  pk[i] = make_float4(xh, (float)(x - (double)xh), yh, (float)(y - (double)yh));
-  pk[n + i] = make_float4((float)g.nx[i], (float)g.ny[i], (float)g.sp[i], 0.f);
+  // the Kress table twice over, divided by pi h, indexed by i - j + n (no
+  // cyclic wrap); the zero tail is written above
+  const double wk = w[i] / (3.141592653589793 * h);
+  wkt[i] = (float)wk;
+  wkt[n + i] = (float)wk;
+  const double f = 0.25 * h * 0.7978845608028654;   // hq c0
+  const double nx = g.nx[i], ny = g.ny[i], sp = g.sp[i];
+  pk[i] = make_float4(xh, xl, yh, yl);
+  pk[n + i] = make_float4((float)(omega * f * nx), (float)(omega * f * ny),
+                          (float)(f * eta * sp), (float)(f * sp));
+  pk[2 * n + i] = make_float4((float)(omega * nx / sp), (float)(omega * ny / sp), 0.f, 0.f);
 }
 
 // Largest cyclic index distance |i - j| of a pair with omega r < X0 (with a
@@ -483,9 +514,14 @@ void fp32_prepare(cfie_op* op) {
   geo32 o{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 6 * n};
   float* w32 = base + 7 * n;
   float* c32 = base + 8 * n;
+  unsigned* bound = reinterpret_cast<unsigned*>(scan.as<int>() + 2);
+  CFIE_CHECK_CUDA(cudaMemsetAsync(bound, 0, sizeof(unsigned), st));
+  k_coord_bound<<<nblk(n), 256, 0, st>>>(n, op->g, bound);
+  CFIE_CHECK_LAUNCH();
   k_geo32<<<nblk(n), 256, 0, st>>>(n, op->g, o, op->wtab.as<double>(), op->ctab.as<double>(),
-                                    w32, c32,
-                                    reinterpret_cast<float4*>(base + geo32_pack_offset(n)));
+                                    bound, op->omega, op->eta, op->h, w32, c32,
+                                    reinterpret_cast<float4*>(base + geo32_pack_offset(n)),
+                                    base + geo32_wk_offset(n));
   CFIE_CHECK_LAUNCH();
 }
 

@@ -43,6 +43,7 @@ constexpr int TSTAGES = 2;
 // that bias near 2e-6 whatever n is, while the running sums (FP32 adds, rounded
 // to nearest) and the FP64 segment reduction add only unbiased rounding.
 constexpr int CK = 8;
+constexpr int WKW = TBM + TBK + 4;   // Kress window of a tile (+ alignment slack)
 constexpr int NPROD = 16;    // producer warps
 constexpr int WTMA = NPROD, WMMA = NPROD + 1, WEPI0 = NPROD + 2;
 constexpr int TNT = (NPROD + 6) * 32;
@@ -51,29 +52,10 @@ struct tc_params : omega32 {
   int n, b, ktiles;
   geo32 g;
   const float* w32;
-  const float* wext;     // Kress table indexed by i - j + n
-  const float4* pk;      // packed coordinates (n) then normals / speeds (n)
+  const float* wext;     // Kress table / (pi h), indexed by i - j + n
+  const float4* pk;      // packed coordinates, source factors, target factors (n each)
   const float2* band;    // near entries of the evaluated kind (soft A, or S, or D')
 };
-
-// Entry kinds of the fused kernel: the sound-soft combination of eq. 1, or
-// one of the two layer operators of the sound-hard operator of eq. 2
-enum { KIND_SOFT = 0, KIND_S = 1, KIND_DP = 2 };
-
-template <int KIND>
-__device__ __forceinline__ float2 entry_kind(const omega32& P, float4 tg, float4 tn, float4 sc,
-                                             float4 sn, float w) {
-  float2 a, b;
-  if constexpr (KIND == KIND_SOFT) {
-    pair_entries_fp32<0>(P, tg.x, tg.y, tg.z, tg.w, 0.f, 0.f, 1.f, sc.x, sc.y, sc.z, sc.w, sn.x,
-                         sn.y, sn.z, w, a, b);
-    return a;
-  } else {
-    pair_entries_fp32<1>(P, tg.x, tg.y, tg.z, tg.w, tn.x, tn.y, tn.z, sc.x, sc.y, sc.z, sc.w,
-                         sn.x, sn.y, sn.z, w, a, b);
-    return KIND == KIND_S ? a : b;
-  }
-}
 
 // bf16 hi / lo split of two entries of one row (adjacent sources k, k + 1)
 // into the four A planes: one packed 32-bit word per plane at byte offset o
@@ -98,11 +80,14 @@ struct tc_smem {
   __nv_bfloat16 B[TSTAGES][4][NP * TBK];    // B1 hi, B1 lo, B2 hi, B2 lo
   float acc[NP][TBM];                       // epilogue running sums, column-major
   float4 tgt[TBM];                          // targets (x hi, x lo, y hi, y lo)
-  float4 tgn[TBM];                          // targets (nu1, nu2, |z'|, 0)
-  uint64_t full[TSTAGES], empty[TSTAGES], tfull[2], tempty[2];
+  float4 tgn[TBM];                          // target factors (D' only)
+  float4 src[TSTAGES][2][TBK];              // sources: coordinates, factors
+  float wk[TSTAGES][WKW];                   // Kress weights / (pi h) of a plain tile
+  uint64_t full[TSTAGES], empty[TSTAGES], sfull[TSTAGES], tfull[2], tempty[2];
   uint32_t tmem_base;
   int abort;
-  int issued[TSTAGES];
+  int issued[TSTAGES], sissued[TSTAGES];
+  int wofs[TSTAGES];                        // plain tile: window entry of (row 0, source 0); else -1
 };
 
 template <int NP>
@@ -133,7 +118,9 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
     for (int s = 0; s < TSTAGES; ++s) {
       mbar_init(&S.full[s], NPROD * 32 + 1);   // producer threads + the TMA thread
       mbar_init(&S.empty[s], 1);
+      mbar_init(&S.sfull[s], 1);
       S.issued[s] = -1;
+      S.sissued[s] = -1;
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&S.tfull[b], 1);
@@ -169,52 +156,37 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
         const int i = m0 + r;
         const bool ok = i < n;
         S.tgt[r] = ok ? P.pk[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        S.tgn[r] = ok ? P.pk[n + i] : make_float4(0.f, 0.f, 1.f, 0.f);
+        if (KIND == KIND_DP) S.tgn[r] = ok ? P.pk[2 * n + i] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncwarp();
-      // geometry of this lane's two sources, loaded one tile ahead
-      float4 pc[2], pn[2];
-      auto load_src = [&](int kk) {
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int jj = kk * TBK + jp + u;
-          const bool ok = jj < n;
-          pc[u] = ok ? P.pk[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
-          pn[u] = ok ? P.pk[n + jj] : make_float4(0.f, 0.f, 1.f, 0.f);
-        }
-      };
-      load_src(sg.z);
       for (int k = sg.z; k < sg.w; ++k, ++it) {
         const int st = it % TSTAGES;
         const int j0 = k * TBK;
         const int j = j0 + jp;                       // first of the lane's two sources
-        const float4 sc[2] = {pc[0], pc[1]};
-        const float4 sn[2] = {pn[0], pn[1]};
-        if (k + 1 < sg.w) load_src(k + 1);
         if (*(volatile int*)&S.abort) break;
-        if (it >= TSTAGES && !mbar_wait(&S.empty[st], ((it / TSTAGES) - 1) & 1)) {
+        // this tile's source geometry and Kress window, brought in by the TMA
+        // warp once the MMAs of the stage's previous tile were done (so the A
+        // planes of the stage are free as well)
+        if (!mbar_wait(&S.sfull[st], (it / TSTAGES) & 1)) {
           if (lane == 0) {
-            atomicExch(err, 11);
+            atomicExch(err, 15);
             S.abort = 1;
           }
           break;
         }
+        const float4 sc[2] = {S.src[st][0][jp], S.src[st][0][jp + 1]};
+        const float4 sn[2] = {S.src[st][1][jp], S.src[st][1][jp + 1]};
         unsigned char* a0 = reinterpret_cast<unsigned char*>(S.A[st][0]);
         unsigned char* a1 = reinterpret_cast<unsigned char*>(S.A[st][1]);
         unsigned char* a2 = reinterpret_cast<unsigned char*>(S.A[st][2]);
         unsigned char* a3 = reinterpret_cast<unsigned char*>(S.A[st][3]);
-        // A tile is plain when it holds full rows and sources and no pair of
-        // the near band: d = i - j spans [dlo, dhi] there, and the band is
-        // |d - t n| <= b for t = -1, 0, 1.  Plain tiles (all but ~1%) skip the
-        // per-pair range and band tests; the Kress weight comes from the
-        // unwrapped table at i - j + n.  The test is uniform over the CTA.
-        const int dlo = m0 - j0 - (TBK - 1), dhi = m0 + TBM - 1 - j0;
-        bool near = false;
-#pragma unroll
-        for (int t = -1; t <= 1; ++t) near |= (dhi >= t * n - P.b) && (dlo <= t * n + P.b);
+        // Plain tiles (all but ~1%, flagged by the TMA warp) skip the per-pair
+        // range and band tests and take the Kress weights from the staged
+        // window of the unwrapped table (entry i - j + n)
+        const int wofs = S.wofs[st];
         constexpr int QS = TBM / NPROD / 2;          // loop steps (two rows each)
-        if (!near && m0 + TBM <= n && j0 + TBK <= n) {
-          const float* wq = P.wext + (m0 + warp + NPROD * half - j + n);
+        if (wofs >= 0) {
+          const float* wq = S.wk[st] + wofs + warp + NPROD * half - jp;
           float2 wv[QS];
 #pragma unroll
           for (int q = 0; q < QS; ++q) wv[q] = make_float2(wq[2 * NPROD * q], wq[2 * NPROD * q - 1]);
@@ -222,11 +194,11 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
           for (int q = 0; q < QS; ++q) {
             const int il = warp + NPROD * (2 * q + half);
             const float4 tg = S.tgt[il];
-            const float4 tn = KIND == KIND_DP ? S.tgn[il] : make_float4(0.f, 0.f, 1.f, 0.f);
+            const float4 tn = KIND == KIND_DP ? S.tgn[il] : make_float4(0.f, 0.f, 0.f, 0.f);
             float2 e[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u)
-              e[u] = entry_kind<KIND>(P, tg, tn, sc[u], sn[u], u ? wv[q].y : wv[q].x);
+              e[u] = entry_folded32<KIND>(P, tg, tn, sc[u], sn[u], u ? wv[q].y : wv[q].x);
             store_split2(a0, a1, a2, a3, sw64(il, jp), e[0], e[1]);
           }
         } else {
@@ -235,7 +207,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
             const int il = warp + NPROD * (2 * q + half);
             const int i = m0 + il;
             const float4 tg = S.tgt[il];
-            const float4 tn = KIND == KIND_DP ? S.tgn[il] : make_float4(0.f, 0.f, 1.f, 0.f);
+            const float4 tn = KIND == KIND_DP ? S.tgn[il] : make_float4(0.f, 0.f, 0.f, 0.f);
             float2 e[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
@@ -248,7 +220,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
                 if (dd != INT_MAX)
                   a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
                 else
-                  a = entry_kind<KIND>(P, tg, tn, sc[u], sn[u], P.w32[d]);
+                  a = entry_folded32<KIND>(P, tg, tn, sc[u], sn[u], P.wext[i - jj + n]);
               }
               e[u] = a;
             }
@@ -279,6 +251,23 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
           S.issued[st] = (it / TSTAGES) & 1;
 #pragma unroll
           for (int p = 0; p < 4; ++p) tma_load_2d(S.B[st][p], &tmB, &S.full[st], k * TBK, p * NP);
+          // Source coordinates and factors of the tile.  A tile is plain when
+          // it holds full rows and sources and no pair of the near band: d =
+          // i - j spans [dlo, dhi] there, and the band is |d - t n| <= b for
+          // t = -1, 0, 1; a plain tile also gets the window of the Kress table
+          // (entries dlo + n ... dhi + n) from the 16-byte boundary below it.
+          const int m0 = sg.y * TBM, j0 = k * TBK;
+          const int dlo = m0 - j0 - (TBK - 1), dhi = m0 + TBM - 1 - j0;
+          bool near = false;
+#pragma unroll
+          for (int t = -1; t <= 1; ++t) near |= (dhi >= t * n - P.b) && (dlo <= t * n + P.b);
+          const bool plain = !near && m0 + TBM <= n && j0 + TBK <= n;
+          S.wofs[st] = plain ? m0 - j0 + n - ((dlo + n) & ~3) : -1;
+          mbar_arrive_expect_tx(&S.sfull[st], 2u * TBK * 16u + (plain ? WKW * 4u : 0u));
+          S.sissued[st] = (it / TSTAGES) & 1;
+          bulk_load(S.src[st][0], P.pk + j0, TBK * 16u, &S.sfull[st]);
+          bulk_load(S.src[st][1], P.pk + n + j0, TBK * 16u, &S.sfull[st]);
+          if (plain) bulk_load(S.wk[st], P.wext + ((dlo + n) & ~3), WKW * 4u, &S.sfull[st]);
         }
       }
     }
@@ -371,8 +360,10 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
   }
   __syncthreads();
   if (threadIdx.x == 0 && *(volatile int*)&S.abort) {
-    for (int s = 0; s < TSTAGES; ++s)
+    for (int s = 0; s < TSTAGES; ++s) {
       if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
+      if (S.sissued[s] >= 0) mbar_wait(&S.sfull[s], (uint32_t)S.sissued[s]);
+    }
   }
   __syncthreads();
   if (warp == WMMA) {
@@ -451,7 +442,7 @@ void run_fused(cfie_op* op, const double2* x, double2* y, int r0, int nr) {
   float* base = op->geo32.as<float>();
   P.g = geo32_at(base, n);
   P.w32 = base + 7 * n;
-  P.wext = base + 9 * n;
+  P.wext = base + geo32_wk_offset(n);
   P.pk = reinterpret_cast<const float4*>(base + geo32_pack_offset(n));
   // the FP32 band holds the soft entries, or S then D' for the hard operator
   P.band = op->band.as<float2>() +

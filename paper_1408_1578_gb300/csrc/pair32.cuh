@@ -4,19 +4,25 @@
 // Hankel expansion (A&S 9.2.5, 9.2.9, 9.2.10).
 #pragma once
 
-// FP32 geometry of an operator: hi/lo coordinates, unnormalised normal, speed.
-// Stored in one buffer of 11 n floats: xh, xl, yh, yl, nx, ny, sp, w32 (Kress
-// table), c32 (spectral-derivative circulant), and the Kress table twice over
-// (2 n floats, entry i - j + n holds w_{(i - j) mod n}).
+// FP32 geometry of an operator: coordinates times omega as hi/lo pairs,
+// unnormalised normal, speed.
+// Stored in one buffer: 9 n floats xh, xl, yh, yl, nx, ny, sp, w32 (Kress
+// table), c32 (spectral-derivative circulant); then, for the fused
+// tensor-core kernel, starting on 16-byte boundaries:
+//   n float4 coordinates      (omega x hi, lo, omega y hi, lo)
+//   n float4 source factors   (omega hq c0 nu1, omega hq c0 nu2, hq c0 eta |z'|, hq c0 |z'|)
+//   n float4 target factors   (omega nu1 / |z'|, omega nu2 / |z'|, 0, 0)
+//   2 n + 8 floats: the Kress table twice over divided by pi h (entry
+//   i - j + n holds w_{(i - j) mod n} / (pi h)), then zeros
+// with hq = h / 4 and c0 = sqrt(2 / pi) (nu = unnormalised normal, |z'| = speed).
 struct geo32 {
   float *xh, *xl, *yh, *yl, *nx, *ny, *sp;
 };
 
-// packed per-node copies for the fused kernels, after the 11 n floats above:
-// float4 (x hi, x lo, y hi, y lo) and float4 (nu1, nu2, |z'|, 0), n of each,
-// starting on a 16-byte boundary
-inline size_t geo32_pack_offset(int n) { return ((size_t)11 * n + 3) & ~size_t(3); }
-inline size_t geo32_floats(int n) { return geo32_pack_offset(n) + (size_t)8 * n; }
+inline size_t geo32_pack_offset(int n) { return ((size_t)9 * n + 3) & ~size_t(3); }
+inline size_t geo32_wk_offset(int n) { return geo32_pack_offset(n) + (size_t)12 * n; }
+// (+ 128 floats of slack: the fused kernel copies whole 32-source tiles)
+inline size_t geo32_floats(int n) { return geo32_wk_offset(n) + (size_t)2 * n + 8 + 128; }
 
 inline geo32 geo32_at(float* base, int n) {
   return geo32{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n,
@@ -40,11 +46,80 @@ constexpr float kInv2Pi = 0.15915493667125702f;
 constexpr float kSqrt2OverPi = 0.7978845834732056f;
 constexpr float kInv4Pi = 0.07957747154594767f;
 
-// two-float helpers --------------------------------------------------------
-__device__ __forceinline__ void two_diff(float a, float b, float& s, float& e) {
-  s = a - b;
-  const float v = s - a;
-  e = (a - (s - v)) - (b + v);
+// Special-function-unit approximations without subnormal handling: their
+// arguments here are >= 16 (square roots) or reduced phases, never subnormal
+__device__ __forceinline__ float rsqrt_sfu(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ void sincos_sfu(float x, float* s, float* c) {
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(*s) : "f"(x));
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(*c) : "f"(x));
+}
+
+// Distance and phase of one pair with omega r >= kX0.  Coordinates are scaled
+// by omega, so the distance of two nodes is the Hankel argument x = omega r
+// itself, and split as hi + lo with the hi parts on a grid 2^-g coarse enough
+// that the difference of two of them is exact in FP32 (geometry set-up): then
+// omega (z_i - z_j) = (dxh, dxl) costs one subtraction per part.  x^2 and x are
+// carried as two-float numbers (error-free transformations built from fmaf),
+// and chi = x - pi/4 is reduced modulo 2 pi with a three-part Cody-Waite
+// constant.
+struct pair_phase {
+  float dx, dy;   // omega (z_i - z_j)
+  float xinv;     // 1 / (omega r)
+  float ra;       // (omega r)^(-1/2)
+  float s, c;     // sin, cos of omega r - pi / 4
+};
+
+__device__ __forceinline__ pair_phase pair_phase32(float txh, float txl, float tyh, float tyl,
+                                                   float sxh, float sxl, float syh, float syl) {
+  pair_phase f;
+  const float dxh = txh - sxh, dxl = txl - sxl;   // dxh, dyh exact
+  const float dyh = tyh - syh, dyl = tyl - syl;
+  // x^2 = dxh^2 + dyh^2 + dxl (2 dxh + dxl) + dyl (2 dyh + dyl) as two-float
+  const float px = dxh * dxh, qx = fmaf(dxh, dxh, -px);
+  const float py = dyh * dyh, qy = fmaf(dyh, dyh, -py);
+  const float pa = fmaxf(px, py), pb = fminf(px, py);
+  const float t = pa + pb;
+  const float te = pb - (t - pa);                  // exact: pa >= pb >= 0
+  const float cr = fmaf(dxl, fmaf(2.0f, dxh, dxl), dyl * fmaf(2.0f, dyh, dyl));
+  const float lo = (te + (qx + qy)) + cr;
+  const float x2 = t + lo;
+  const float x2l = lo - (x2 - t);
+  const float xinv = rsqrt_sfu(x2);
+  const float xh = x2 * xinv;
+  const float xl = (fmaf(-xh, xh, x2) + x2l) * (0.5f * xinv);
+  // chi = x - pi/4 reduced to [-pi, pi]
+  const float k = rintf(fmaf(xh, kInv2Pi, -0.125f));
+  float chi = fmaf(-k, kC1, xh);
+  chi = fmaf(-k, kC2, chi);
+  chi = fmaf(-k, kC3, chi);
+  chi = (chi - kPi4H) + (xl - kPi4L);
+  sincos_sfu(chi, &f.s, &f.c);
+  f.dx = dxh + dxl;
+  f.dy = dyh + dyl;
+  f.xinv = xinv;
+  f.ra = rsqrt_sfu(xh);
+  return f;
+}
+
+// Hankel's asymptotic expansion for x >= kX0 (t = 1/x), three terms of each
+// of P and Q (A&S 9.2.9, 9.2.10), without the common factor c0 x^(-1/2):
+// J_m = c0 ra j_m, Y_m = c0 ra y_m.  The remainder is below the first omitted
+// term (A&S 9.2.10 remark), < 4.1e-8 for x >= 16: under one FP32 ulp.
+__device__ __forceinline__ void hankel_asym32(float ti, float s, float c, float& j0, float& y0,
+                                              float& j1, float& y1) {
+  const float t2 = ti * ti;
+  const float P0 = fmaf(t2, fmaf(t2, 0.112152099609375f, -0.0703125f), 1.0f);
+  const float Q0 = ti * fmaf(t2, fmaf(t2, -0.22710800170898438f, 0.0732421875f), -0.125f);
+  const float P1 = fmaf(t2, fmaf(t2, -0.144195556640625f, 0.1171875f), 1.0f);
+  const float Q1 = ti * fmaf(t2, fmaf(t2, 0.2775764465332031f, -0.1025390625f), 0.375f);
+  j0 = fmaf(P0, c, -Q0 * s);
+  y0 = fmaf(P0, s, Q0 * c);
+  j1 = fmaf(P1, s, Q1 * c);
+  y1 = fmaf(Q1, s, -P1 * c);
 }
 
 // Entries of one pair with omega r >= kX0 (outside the band).
@@ -55,51 +130,15 @@ __device__ __forceinline__ void pair_entries_fp32(const omega32& P, float txh, f
                                                   float tsp, float sxh, float sxl, float syh,
                                                   float syl, float snx, float sny, float ssp,
                                                   float w, float2& a, float2& b) {
-  float dxs, dxe, dys, dye;
-  two_diff(txh, sxh, dxs, dxe);
-  dxe += txl - sxl;
-  two_diff(tyh, syh, dys, dye);
-  dye += tyl - syl;
-  // r^2 = (dxs + dxe)^2 + (dys + dye)^2 as two-float
-  const float px = dxs * dxs, qx = fmaf(dxs, dxs, -px);
-  const float py = dys * dys, qy = fmaf(dys, dys, -py);
-  const float t = px + py;
-  const float tv = t - px;
-  const float te = (px - (t - tv)) + (py - tv);
-  const float lo = te + qx + qy + 2.0f * fmaf(dxs, dxe, dys * dye);
-  const float r2 = t + lo;
-  const float r2l = lo - (r2 - t);
-  const float rinv = rsqrtf(r2);
-  const float rh = r2 * rinv;
-  const float rl = (fmaf(-rh, rh, r2) + r2l) * (0.5f * rinv);
-  // x = omega r as two-float
-  const float xh = P.wh * rh;
-  const float xl = fmaf(P.wh, rh, -xh) + fmaf(P.wh, rl, P.wl * rh);
-  // chi = x - pi/4 reduced to [-pi, pi]
-  const float k = rintf(fmaf(xh, kInv2Pi, -0.125f));
-  float chi = fmaf(-k, kC1, xh);
-  chi = fmaf(-k, kC2, chi);
-  chi = fmaf(-k, kC3, chi);
-  chi = (chi - kPi4H) + (xl - kPi4L);
-  float s, c;
-  __sincosf(chi, &s, &c);
-  // Hankel asymptotic expansion, t = 1/x
-  const float ti = rinv * P.winv;
-  const float t2 = ti * ti;
-  const float P0 = fmaf(t2, fmaf(t2, fmaf(t2, -0.5725014209747314f, 0.112152099609375f), -0.0703125f), 1.0f);
-  const float Q0 = ti * fmaf(t2, fmaf(t2, fmaf(t2, 1.7277275025844574f, -0.22710800170898438f), 0.0732421875f), -0.125f);
-  const float P1 = fmaf(t2, fmaf(t2, fmaf(t2, 0.6765925884246826f, -0.144195556640625f), 0.1171875f), 1.0f);
-  const float Q1 = ti * fmaf(t2, fmaf(t2, fmaf(t2, -1.993531733751297f, 0.2775764465332031f), -0.1025390625f), 0.375f);
-  const float amp = kSqrt2OverPi * rsqrtf(xh);
-  const float J0 = amp * (P0 * c - Q0 * s);
-  const float Y0 = amp * (P0 * s + Q0 * c);
-  const float J1 = amp * (P1 * s + Q1 * c);
-  const float Y1 = amp * (Q1 * s - P1 * c);
-  const float dx = dxs + dxe, dy = dys + dye;
+  const pair_phase f = pair_phase32(txh, txl, tyh, tyl, sxh, sxl, syh, syl);
+  float j0, y0, j1, y1;
+  hankel_asym32(f.xinv, f.s, f.c, j0, y0, j1, y1);
+  const float amp = kSqrt2OverPi * f.ra;
+  const float J0 = amp * j0, Y0 = amp * y0, J1 = amp * j1, Y1 = amp * y1;
   const float omega = P.wh;
   const float hq = 0.25f * P.h;
   if constexpr (BC == 0) {
-    const float cc = (dx * snx + dy * sny) * rinv;
+    const float cc = (f.dx * snx + f.dy * sny) * f.xinv;
     const float es = P.eta * ssp;
     const float oc = omega * cc;
     a.x = hq * (es * J0 - oc * Y1) - w * kInv4Pi * oc * J1;
@@ -107,10 +146,45 @@ __device__ __forceinline__ void pair_entries_fp32(const omega32& P, float txh, f
   } else {
     a.x = -hq * Y0 * ssp - w * kInv4Pi * J0 * ssp;
     a.y = hq * J0 * ssp;
-    const float cp = -(dx * tnx + dy * tny) * rinv * ssp / tsp;
+    const float cp = -(f.dx * tnx + f.dy * tny) * f.xinv * ssp / tsp;
     const float oc = omega * cp;
     b.x = -hq * oc * Y1 - w * kInv4Pi * oc * J1;
     b.y = hq * oc * J1;
   }
 }
 
+// Entry kinds: the sound-soft combination of eq. 1, or one of the two layer
+// operators S, D' of the sound-hard operator of eq. 2
+enum { KIND_SOFT = 0, KIND_S = 1, KIND_DP = 2 };
+
+// The same entries with the per-node factors folded in (fused tensor-core
+// kernel): tg, sc = target and source coordinates, tq = target factors (D'
+// only), sq = source factors, wk = Kress weight / (pi h); see the packed
+// layout above.  With A = sq ra and B = omega hq c0 (nu_j . (z_i - z_j)) ra / r,
+//   soft:  re = A j0 - B (y1 + wk j1),      im = B j1 + A (y0 + wk j0)
+//   S:     re = -A' (y0 + wk j0),            im = A' j0        (A' = hq c0 |z'_j| ra)
+//   D':    re = D (y1 + wk j1),              im = -D j1
+// with D = omega (nu_i . (z_i - z_j)) / |z'_i| hq c0 |z'_j| ra / r.
+template <int KIND>
+__device__ __forceinline__ float2 entry_folded32(const omega32& P, float4 tg, float4 tq, float4 sc,
+                                                 float4 sq, float wk) {
+  const pair_phase f = pair_phase32(tg.x, tg.y, tg.z, tg.w, sc.x, sc.y, sc.z, sc.w);
+  float j0, y0, j1, y1;
+  hankel_asym32(f.xinv, f.s, f.c, j0, y0, j1, y1);
+  float2 a;
+  if constexpr (KIND == KIND_SOFT) {
+    const float A = sq.z * f.ra;
+    const float B = fmaf(f.dx, sq.x, f.dy * sq.y) * (f.xinv * f.ra);
+    a.x = fmaf(A, j0, -B * fmaf(wk, j1, y1));
+    a.y = fmaf(B, j1, A * fmaf(wk, j0, y0));
+  } else if constexpr (KIND == KIND_S) {
+    const float A = sq.w * f.ra;
+    a.x = -A * fmaf(wk, j0, y0);
+    a.y = A * j0;
+  } else {
+    const float D = fmaf(f.dx, tq.x, f.dy * tq.y) * (f.xinv * f.ra) * sq.w;
+    a.x = D * fmaf(wk, j1, y1);
+    a.y = -D * j1;
+  }
+  return a;
+}

@@ -317,6 +317,22 @@ cfie_status cfie_server_stats(cfie_server* S, cfie_server_counters* out) {
   return CFIE_OK;
 }
 
+cfie_status cfie_server_request_error(cfie_server* S, long long ticket, char* buf, size_t len) {
+  if (!S || !buf || len == 0) return CFIE_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) {
+    S->err = "unknown ticket";
+    return CFIE_EINVAL;
+  }
+  const request_rec* r = it->second.get();
+  const std::string& m = r->done ? r->err : std::string();
+  const size_t k = std::min(len - 1, m.size());
+  std::memcpy(buf, m.data(), k);
+  buf[k] = 0;
+  return CFIE_OK;
+}
+
 const char* cfie_server_last_error(cfie_server* S) { return S ? S->err.c_str() : "null server"; }
 
 void cfie_server_destroy(cfie_server* S) {

@@ -280,11 +280,16 @@ void spectral_fft(cfie_op* op, const X* in, O* out, const O* base, double2 scale
   const int n = op->n, N = F.N, L = F.L;
   cudaStream_t st = op->ctx->stream;
   const size_t smem = 2 * sizeof(T) * (size_t)N;
-  if (smem <= (size_t)128 * 1024) {
-    // one CTA per column, everything in shared memory
+  constexpr size_t kSmemMax = (size_t)128 * 1024;
+  if (smem <= kSmemMax) {
+    // one CTA per column, everything in shared memory.  The attribute is the
+    // bound of this branch, not this launch's size: it is per kernel and
+    // process-wide, and operators of other sizes launch the same kernel from
+    // other host threads (server slots)
     prof_scope ps(op->ctx, CFIE_K_SPECTRAL);
     CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_spectral_smem<T, X, O>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemMax));
     k_spectral_smem<T, X, O><<<cols, 512, smem, st>>>(n, N, L, in, chirp_of<T>(F), bf_of<T>(F),
                                                      tw_of<T>(F), op->g.sp, scale, base, out);
     CFIE_CHECK_LAUNCH();

@@ -74,3 +74,6 @@ def test_server_needs_a_device(lib):
     h = ctypes.c_void_p()
     assert lib.cfie_server_create(0, 1 << 30, 2, ctypes.byref(h)) == cfie.CFIE_ECUDA
     assert lib.cfie_server_submit(None, None, None) == cfie.CFIE_EINVAL
+    buf = ctypes.create_string_buffer(16)
+    assert lib.cfie_server_request_error(None, ctypes.c_longlong(1), buf,
+                                         ctypes.c_size_t(16)) == cfie.CFIE_EINVAL

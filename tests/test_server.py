@@ -37,7 +37,7 @@ def test_served_results_equal_alone_and_oracle():
     ctx = cfie.Context(0)
     for r, t in zip(reqs, tickets):
         out = srv.poll(t, want_x=True)
-        assert out["done"] and out["status"] == cfie.CFIE_OK
+        assert out["done"] and out["status"] == cfie.CFIE_OK, out.get("error")
         assert out["relres_max"] <= 1e-8
         assert out["latency_s"] >= out["service_s"] > 0
         # the same solve alone, through the operator API

@@ -152,7 +152,8 @@ struct df_hankel {
   df dx, dy, rinv, J0, Y0, J1, Y1;
 };
 
-__device__ __forceinline__ df_hankel hankel_df(const df_params& P, float4 gi, float4 gj) {
+__device__ __forceinline__ df_hankel hankel_df(const df_params& P, float4 gi, float4 gj,
+                                               const float4* __restrict__ tab) {
   const df dx = dsub({gi.x, gi.y}, {gj.x, gj.y});
   const df dy = dsub({gi.z, gi.w}, {gj.z, gj.w});
   const df r2 = dadd(dmul(dx, dx), dmul(dy, dy));
@@ -178,7 +179,7 @@ __device__ __forceinline__ df_hankel hankel_df(const df_params& P, float4 gi, fl
   const df sd = dadd(d, dmul(d3, sb));                          // sin d
   const df cb = dadd({-0.5f, 0.f}, {z * (1.0f / 24.0f - z * (1.0f / 720.0f)), 0.f});
   const df cd = dadd({1.0f, 0.f}, dmul(d2, cb));                // cos d
-  const float4 tj = kSinCos[(int)jf + 32];
+  const float4 tj = tab[(int)jf + 32];
   const df sj = {tj.x, tj.y}, cj = {tj.z, tj.w};
   const df sn = dadd(dmul(sj, cd), dmul(cj, sd));
   const df cs = dsub(dmul(cj, cd), dmul(sj, sd));
@@ -205,8 +206,8 @@ __device__ __forceinline__ df_hankel hankel_df(const df_params& P, float4 gi, fl
 
 // one far pair: soft entry a = h K + w K1 (eq. 1), K = L - i eta M
 __device__ __forceinline__ float4 entry_df(const df_params& P, float4 gi, float4 gj, float4 nj,
-                                           float2 sj2, float2 w2) {
-  const df_hankel H = hankel_df(P, gi, gj);
+                                           float2 sj2, float2 w2, const float4* __restrict__ tab) {
+  const df_hankel H = hankel_df(P, gi, gj, tab);
   // c = (z_i - z_j) . nu~_j / r,  es = eta |z'_j|,  oc = omega c
   const df c = dmul(dadd(dmul(H.dx, {nj.x, nj.y}), dmul(H.dy, {nj.z, nj.w})), H.rinv);
   const df es = dmul(P.eta, {sj2.x, sj2.y});
@@ -225,8 +226,9 @@ __device__ __forceinline__ float4 entry_df(const df_params& P, float4 gi, float4
 // cp = -((z_i - z_j) . nu~_i / r) |z'_j| / |z'_i|
 __device__ __forceinline__ void entry_df_hard(const df_params& P, float4 gi, float4 gj,
                                               float4 ni, float2 si2, float2 sj2, float2 w2,
-                                              float4& S, float4& Dp) {
-  const df_hankel H = hankel_df(P, gi, gj);
+                                              const float4* __restrict__ tab, float4& S,
+                                              float4& Dp) {
+  const df_hankel H = hankel_df(P, gi, gj, tab);
   const df sj = {sj2.x, sj2.y};
   const df wq = dmul({w2.x, w2.y}, {kI4PiH, kI4PiL});
   // S: re = -(h/4 Y0 + w/(4 pi) J0) |z'_j|, im = h/4 J0 |z'_j|
@@ -266,7 +268,11 @@ __global__ void __launch_bounds__(DNT) k_pair_df(df_params P) {
   constexpr int RQ = RB / (DNT / DTI);
   extern __shared__ __align__(16) unsigned char raw[];
   df_smem<RB>& S = *reinterpret_cast<df_smem<RB>*>(raw);
+  // the sin / cos table, indexed per lane: shared memory, not the constant
+  // cache (which serialises differing addresses within a warp)
+  __shared__ float4 sTab[65];
   const int n = P.n, tid = threadIdx.x;
+  if (tid < 65) sTab[tid] = kSinCos[tid];
   const int i0 = blockIdx.x * DTI, split = blockIdx.y, rb0 = blockIdx.z * RB;
   const int rbn = min(RB, P.nrhs - rb0);
   const int ntiles = (n + DTJ - 1) / DTJ;
@@ -299,7 +305,7 @@ __global__ void __launch_bounds__(DNT) k_pair_df(df_params P) {
         if (dd != INT_MAX)
           a = P.band[(size_t)i * bw + dd + P.b];
         else
-          a = entry_df(P, P.g[i], P.g[j], P.nrm[j], P.sp[j], P.w[d]);
+          a = entry_df(P, P.g[i], P.g[j], P.nrm[j], P.sp[j], P.w[d], sTab);
       }
       S.A[il][jl] = a;
     }
@@ -356,7 +362,9 @@ __global__ void __launch_bounds__(DNT) k_pair_df_hard(df_params P, const float4*
   constexpr int RQ = RB / (DNT / DTI);
   extern __shared__ __align__(16) unsigned char raw[];
   df_smem_hard<RB>& S = *reinterpret_cast<df_smem_hard<RB>*>(raw);
+  __shared__ float4 sTab[65];   // sin / cos table (see k_pair_df)
   const int n = P.n, tid = threadIdx.x;
+  if (tid < 65) sTab[tid] = kSinCos[tid];
   const int i0 = blockIdx.x * DTI, split = blockIdx.y, rb0 = blockIdx.z * RB;
   const int rbn = min(RB, P.nrhs - rb0);
   const int ntiles = (n + DTJ - 1) / DTJ;
@@ -391,7 +399,7 @@ __global__ void __launch_bounds__(DNT) k_pair_df_hard(df_params P, const float4*
           a = P.band[(size_t)i * bw + dd + P.b];
           b = P.band[nbw + (size_t)i * bw + dd + P.b];
         } else {
-          entry_df_hard(P, P.g[i], P.g[j], P.nrm[i], P.sp[i], P.sp[j], P.w[d], a, b);
+          entry_df_hard(P, P.g[i], P.g[j], P.nrm[i], P.sp[i], P.sp[j], P.w[d], sTab, a, b);
         }
       }
       S.S[il][jl] = a;
@@ -500,6 +508,7 @@ struct rtc_smem {
   float4 tgn[RTM];   // target normal (hi, lo pairs) and, below, speed: hard kinds
   float2 tgs[RTM];
   int ex[RTM];
+  float4 tab[65];    // sin / cos table (per-lane indices: shared, not constant)
   uint64_t full[RST], empty[RST], tfull, tempty;
   uint32_t tmem_base;
   int abort;
@@ -581,6 +590,7 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
     S.abort = 0;
     fence_mbar_init();
   }
+  if (threadIdx.x < 65) S.tab[threadIdx.x] = kSinCos[threadIdx.x];
   if (warp == RWMMA) {
     tmem_alloc(&S.tmem_base, TMEM_COLS);
     tmem_relinquish();
@@ -645,10 +655,11 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
               if (d < 0) d += n;
               if (d > P.b && d < n - P.b) {
                 if constexpr (KIND == RK_SOFT) {
-                  a = entry_df(P, gi, gj[u], nj[u], sj[u], P.w[d]);
+                  a = entry_df(P, gi, gj[u], nj[u], sj[u], P.w[d], S.tab);
                 } else {
                   float4 es, ed;
-                  entry_df_hard(P, gi, gj[u], S.tgn[il], S.tgs[il], sj[u], P.w[d], es, ed);
+                  entry_df_hard(P, gi, gj[u], S.tgn[il], S.tgs[il], sj[u], P.w[d], S.tab, es,
+                                ed);
                   a = KIND == RK_S ? es : ed;
                 }
               }

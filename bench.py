@@ -151,7 +151,7 @@ SMS, FP32_LANES = 152, 128
 # FP32 pair entries (two-float phase, asymptotics) by summation variant: the
 # CUDA-core kernel evaluates both hard entries from one phase; the tensor-core
 # kernel folds the per-node factors in and evaluates S and D' in two passes
-ENTRY_OPS = {("soft", 1): 82, ("hard", 1): 95, ("soft", 2): 72, ("hard", 2): 114}
+ENTRY_OPS = {("soft", 1): 74, ("hard", 1): 87, ("soft", 2): 64, ("hard", 2): 98}
 SUM_OPS = {"soft": 4, "hard": 8}         # FP32 FMAs per pair and right-hand side (CUDA-core sums)
 DF_ENTRY_OPS = 677                       # double-float pair entry of the residual kernel
 DF_TERM_OPS = 48                         # Dot2 complex product-sum per pair and right-hand side
@@ -163,7 +163,7 @@ FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)
 # ncu capture of the current kernel at the same launch configuration, keyed by
 # (kernel class, curve, n, nrhs, matvec variant); absent = not captured.
 NCU_TRAFFIC = {
-    ("matvec_fp32", "kite", 32768, 64, 2): 79.323904e6 + 10.755328e6,
+    ("matvec_fp32", "kite", 32768, 64, 2): 79.151872e6 + 11.139584e6,
 }
 
 

@@ -8,12 +8,15 @@
 //  * Phase.  omega r reaches ~6e3 on the largest workloads, where one FP32
 //    rounding of r is a ~4e-4 rad phase error.  Coordinates are stored
 //    times omega as hi + lo FP32 pairs, the hi parts on a common grid on
-//    which their differences are exact, so the node distance is x = omega r
-//    itself; omega (z_i - z_j), x^2 and x are carried as two-float numbers
-//    (error-free transformations built from fmaf), and
-//    chi = x - pi/4 is reduced modulo 2 pi with a three-part Cody-Waite
-//    constant whose first part has 10 significant bits (k * C1 exact for
-//    x < 1e5).  The reduced phase is accurate to a few 1e-7 rad.
+//    which their differences and the sum of two squared differences are
+//    exact, so the node distance is x = omega r itself; x^2 and x are
+//    carried as two-float numbers (error-free transformations built from
+//    fmaf), and chi = x - pi/4 is reduced modulo 2 pi with a three-part
+//    Cody-Waite constant whose first part has 10 significant bits (k * C1
+//    exact for x < 1e5).  The phase error grows with the scaled coordinates
+//    (lo parts and their cross terms in FP32): ~2^(e - 33) rad for
+//    omega |z| < 2^e, 6.5e-7 rad at most on the kite at omega = 2048 (e = 12),
+//    1.3e-6 at e = 13; below the bf16 hi + lo split of the tensor-core sums.
 //  * Small arguments.  Hankel's asymptotic expansion (A&S 9.2.5, 9.2.9, 9.2.10;
 //    three terms of P and of Q, truncation error < 4.1e-8 for x >= 16) is used for
 //    every pair with omega r >= 16.  Pairs closer than that form a band
@@ -309,21 +312,23 @@ __global__ void k_coord_bound(int n, geom_dev g, unsigned* __restrict__ bound) {
 }
 
 // FP32 geometry.  Coordinates scaled by omega and split as hi + lo with hi on
-// the grid 2^-g, g = 22 - e where every omega |x|, omega |y| < 2^e: a hi part
-// then needs at most 23 bits, the difference of two of them at most 24, so it
-// is exact in FP32; the lo parts (|lo| <= 2^(e-23)) keep the rest to ~2^(e-47).
+// the grid 2^-g, g = 10 - e where every omega |x|, omega |y| < 2^e: then a hi
+// difference is a multiple of 2^-g below 2^(e+1) (+ one grid step), exact in
+// FP32, and the sum of two squared hi differences a multiple of 2^-2g below
+// 2^23.1 of them, exact as well; the lo parts (|lo| <= 2^(e-11)) keep the rest
+// to ~2^(e-35).
 __global__ void k_geo32(int n, geom_dev g, geo32 o, const double* __restrict__ w,
                         const double* __restrict__ ct, const unsigned* __restrict__ bound,
                         double omega, double eta, double h, float* __restrict__ w32,
                         float* __restrict__ c32, float4* __restrict__ pk,
-                        float* __restrict__ wkt) {
+                        float2* __restrict__ wkt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < 8) wkt[2 * n + i] = 0.f;
+  if (i < 8) wkt[2 * n + i] = make_float2(0.f, 0.f);
   if (i >= n) return;
   int e = 0;
   const double m = omega * (double)__uint_as_float(*bound);
   if (m > 0.0) frexp(m, &e);
-  const double q = ldexp(1.0, 22 - e), qi = ldexp(1.0, e - 22);
+  const double q = ldexp(1.0, 10 - e), qi = ldexp(1.0, e - 10);
   const double x = omega * g.x[i], y = omega * g.y[i];
   const double xhd = rint(x * q) * qi, yhd = rint(y * q) * qi;
   const float xh = (float)xhd, yh = (float)yhd;
@@ -338,10 +343,12 @@ __global__ void k_geo32(int n, geom_dev g, geo32 o, const double* __restrict__ w
   w32[i] = (float)w[i];
   c32[i] = (float)ct[i];
   // the Kress table twice over, divided by pi h, indexed by i - j + n (no
-  // cyclic wrap); the zero tail is written above
-  const double wk = w[i] / (3.141592653589793 * h);
-  wkt[i] = (float)wk;
-  wkt[n + i] = (float)wk;
+  // cyclic wrap), paired with the weight of the next source; the zero tail is
+  // written above
+  const double ph = 3.141592653589793 * h;
+  const float2 wk = make_float2((float)(w[i] / ph), (float)(w[i == 0 ? n - 1 : i - 1] / ph));
+  wkt[i] = wk;
+  wkt[n + i] = wk;
   const double f = 0.25 * h * 0.7978845608028654;   // hq c0
   const double nx = g.nx[i], ny = g.ny[i], sp = g.sp[i];
   pk[i] = make_float4(xh, xl, yh, yl);
@@ -521,7 +528,7 @@ void fp32_prepare(cfie_op* op) {
   k_geo32<<<nblk(n), 256, 0, st>>>(n, op->g, o, op->wtab.as<double>(), op->ctab.as<double>(),
                                     bound, op->omega, op->eta, op->h, w32, c32,
                                     reinterpret_cast<float4*>(base + geo32_pack_offset(n)),
-                                    base + geo32_wk_offset(n));
+                                    reinterpret_cast<float2*>(base + geo32_wk_offset(n)));
   CFIE_CHECK_LAUNCH();
 }
 

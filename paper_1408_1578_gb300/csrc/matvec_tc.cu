@@ -43,7 +43,7 @@ constexpr int TSTAGES = 2;
 // that bias near 2e-6 whatever n is, while the running sums (FP32 adds, rounded
 // to nearest) and the FP64 segment reduction add only unbiased rounding.
 constexpr int CK = 8;
-constexpr int WKW = TBM + TBK + 4;   // Kress window of a tile (+ alignment slack)
+constexpr int WKW = TBM + TBK + 2;   // Kress window of a tile (+ alignment slack)
 constexpr int NPROD = 16;    // producer warps
 constexpr int WTMA = NPROD, WMMA = NPROD + 1, WEPI0 = NPROD + 2;
 constexpr int TNT = (NPROD + 6) * 32;
@@ -52,7 +52,7 @@ struct tc_params : omega32 {
   int n, b, ktiles;
   geo32 g;
   const float* w32;
-  const float* wext;     // Kress table / (pi h), indexed by i - j + n
+  const float2* wext;    // Kress table / (pi h) at i - j + n, paired with the next source's
   const float4* pk;      // packed coordinates, source factors, target factors (n each)
   const float2* band;    // near entries of the evaluated kind (soft A, or S, or D')
 };
@@ -82,7 +82,7 @@ struct tc_smem {
   float4 tgt[TBM];                          // targets (x hi, x lo, y hi, y lo)
   float4 tgn[TBM];                          // target factors (D' only)
   float4 src[TSTAGES][2][TBK];              // sources: coordinates, factors
-  float wk[TSTAGES][WKW];                   // Kress weights / (pi h) of a plain tile
+  float2 wk[TSTAGES][WKW];                  // Kress weight pairs / (pi h) of a plain tile
   uint64_t full[TSTAGES], empty[TSTAGES], sfull[TSTAGES], tfull[2], tempty[2];
   uint32_t tmem_base;
   int abort;
@@ -186,10 +186,10 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
         const int wofs = S.wofs[st];
         constexpr int QS = TBM / NPROD / 2;          // loop steps (two rows each)
         if (wofs >= 0) {
-          const float* wq = S.wk[st] + wofs + warp + NPROD * half - jp;
+          const float2* wq = S.wk[st] + wofs + warp + NPROD * half - jp;
           float2 wv[QS];
 #pragma unroll
-          for (int q = 0; q < QS; ++q) wv[q] = make_float2(wq[2 * NPROD * q], wq[2 * NPROD * q - 1]);
+          for (int q = 0; q < QS; ++q) wv[q] = wq[2 * NPROD * q];
 #pragma unroll
           for (int q = 0; q < QS; ++q) {
             const int il = warp + NPROD * (2 * q + half);
@@ -220,7 +220,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
                 if (dd != INT_MAX)
                   a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
                 else
-                  a = entry_folded32<KIND>(P, tg, tn, sc[u], sn[u], P.wext[i - jj + n]);
+                  a = entry_folded32<KIND>(P, tg, tn, sc[u], sn[u], P.wext[i - jj + n].x);
               }
               e[u] = a;
             }
@@ -256,18 +256,19 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
           // i - j spans [dlo, dhi] there, and the band is |d - t n| <= b for
           // t = -1, 0, 1; a plain tile also gets the window of the Kress table
           // (entries dlo + n ... dhi + n) from the 16-byte boundary below it.
+          // Window bytes: WKW float2 = 1296, a multiple of 16.
           const int m0 = sg.y * TBM, j0 = k * TBK;
           const int dlo = m0 - j0 - (TBK - 1), dhi = m0 + TBM - 1 - j0;
           bool near = false;
 #pragma unroll
           for (int t = -1; t <= 1; ++t) near |= (dhi >= t * n - P.b) && (dlo <= t * n + P.b);
           const bool plain = !near && m0 + TBM <= n && j0 + TBK <= n;
-          S.wofs[st] = plain ? m0 - j0 + n - ((dlo + n) & ~3) : -1;
-          mbar_arrive_expect_tx(&S.sfull[st], 2u * TBK * 16u + (plain ? WKW * 4u : 0u));
+          S.wofs[st] = plain ? m0 - j0 + n - ((dlo + n) & ~1) : -1;
+          mbar_arrive_expect_tx(&S.sfull[st], 2u * TBK * 16u + (plain ? WKW * 8u : 0u));
           S.sissued[st] = (it / TSTAGES) & 1;
           bulk_load(S.src[st][0], P.pk + j0, TBK * 16u, &S.sfull[st]);
           bulk_load(S.src[st][1], P.pk + n + j0, TBK * 16u, &S.sfull[st]);
-          if (plain) bulk_load(S.wk[st], P.wext + ((dlo + n) & ~3), WKW * 4u, &S.sfull[st]);
+          if (plain) bulk_load(S.wk[st], P.wext + ((dlo + n) & ~1), WKW * 8u, &S.sfull[st]);
         }
       }
     }
@@ -442,7 +443,7 @@ void run_fused(cfie_op* op, const double2* x, double2* y, int r0, int nr) {
   float* base = op->geo32.as<float>();
   P.g = geo32_at(base, n);
   P.w32 = base + 7 * n;
-  P.wext = base + geo32_wk_offset(n);
+  P.wext = reinterpret_cast<const float2*>(base + geo32_wk_offset(n));
   P.pk = reinterpret_cast<const float4*>(base + geo32_pack_offset(n));
   // the FP32 band holds the soft entries, or S then D' for the hard operator
   P.band = op->band.as<float2>() +

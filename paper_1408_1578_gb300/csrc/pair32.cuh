@@ -12,8 +12,9 @@
 //   n float4 coordinates      (omega x hi, lo, omega y hi, lo)
 //   n float4 source factors   (omega hq c0 nu1, omega hq c0 nu2, hq c0 eta |z'|, hq c0 |z'|)
 //   n float4 target factors   (omega nu1 / |z'|, omega nu2 / |z'|, 0, 0)
-//   2 n + 8 floats: the Kress table twice over divided by pi h (entry
-//   i - j + n holds w_{(i - j) mod n} / (pi h)), then zeros
+//   2 n + 8 float2: the Kress table twice over divided by pi h, entry
+//   k = i - j + n holding the weights of sources j and j + 1,
+//   (w_{k mod n}, w_{(k - 1) mod n}) / (pi h), then zeros
 // with hq = h / 4 and c0 = sqrt(2 / pi) (nu = unnormalised normal, |z'| = speed).
 struct geo32 {
   float *xh, *xl, *yh, *yl, *nx, *ny, *sp;
@@ -22,7 +23,7 @@ struct geo32 {
 inline size_t geo32_pack_offset(int n) { return ((size_t)9 * n + 3) & ~size_t(3); }
 inline size_t geo32_wk_offset(int n) { return geo32_pack_offset(n) + (size_t)12 * n; }
 // (+ 128 floats of slack: the fused kernel copies whole 32-source tiles)
-inline size_t geo32_floats(int n) { return geo32_wk_offset(n) + (size_t)2 * n + 8 + 128; }
+inline size_t geo32_floats(int n) { return geo32_wk_offset(n) + (size_t)4 * n + 16 + 128; }
 
 inline geo32 geo32_at(float* base, int n) {
   return geo32{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n,
@@ -60,12 +61,14 @@ __device__ __forceinline__ void sincos_sfu(float x, float* s, float* c) {
 
 // Distance and phase of one pair with omega r >= kX0.  Coordinates are scaled
 // by omega, so the distance of two nodes is the Hankel argument x = omega r
-// itself, and split as hi + lo with the hi parts on a grid 2^-g coarse enough
-// that the difference of two of them is exact in FP32 (geometry set-up): then
-// omega (z_i - z_j) = (dxh, dxl) costs one subtraction per part.  x^2 and x are
-// carried as two-float numbers (error-free transformations built from fmaf),
-// and chi = x - pi/4 is reduced modulo 2 pi with a three-part Cody-Waite
-// constant.
+// itself, and split as hi + lo with the hi parts on a grid coarse enough that
+// the difference of two of them and the sum of the two squared differences
+// are exact in FP32 (geometry set-up).  Then x^2 = H + C with H = dxh^2 + dyh^2
+// exact and the lo-part terms C = dxl (2 dxh + dxl) + dyl (2 dyh + dyl) in
+// FP32; x^2 and x are carried as two-float numbers (error-free
+// transformations built from fmaf), and chi = x - pi/4 is reduced modulo 2 pi
+// with a three-part Cody-Waite constant.  Phase error ~2^(e - 33) rad when
+// omega |z| < 2^e (6.5e-7 rad at most for the kite at omega = 2048).
 struct pair_phase {
   float dx, dy;   // omega (z_i - z_j)
   float xinv;     // 1 / (omega r)
@@ -78,25 +81,21 @@ __device__ __forceinline__ pair_phase pair_phase32(float txh, float txl, float t
   pair_phase f;
   const float dxh = txh - sxh, dxl = txl - sxl;   // dxh, dyh exact
   const float dyh = tyh - syh, dyl = tyl - syl;
-  // x^2 = dxh^2 + dyh^2 + dxl (2 dxh + dxl) + dyl (2 dyh + dyl) as two-float
-  const float px = dxh * dxh, qx = fmaf(dxh, dxh, -px);
-  const float py = dyh * dyh, qy = fmaf(dyh, dyh, -py);
-  const float pa = fmaxf(px, py), pb = fminf(px, py);
-  const float t = pa + pb;
-  const float te = pb - (t - pa);                  // exact: pa >= pb >= 0
-  const float cr = fmaf(dxl, fmaf(2.0f, dxh, dxl), dyl * fmaf(2.0f, dyh, dyl));
-  const float lo = (te + (qx + qy)) + cr;
-  const float x2 = t + lo;
-  const float x2l = lo - (x2 - t);
+  const float H = fmaf(dxh, dxh, dyh * dyh);      // exact
+  const float C = fmaf(dxl, fmaf(2.0f, dxh, dxl), dyl * fmaf(2.0f, dyh, dyl));
+  // x^2 = H + C as two-float (TwoSum)
+  const float x2 = H + C;
+  const float bv = x2 - H;
+  const float x2l = (H - (x2 - bv)) + (C - bv);
   const float xinv = rsqrt_sfu(x2);
   const float xh = x2 * xinv;
-  const float xl = (fmaf(-xh, xh, x2) + x2l) * (0.5f * xinv);
+  // x lo, less the lo part of the pi/4 split
+  const float xl4 = fmaf(fmaf(-xh, xh, x2) + x2l, 0.5f * xinv, -kPi4L);
   // chi = x - pi/4 reduced to [-pi, pi]
   const float k = rintf(fmaf(xh, kInv2Pi, -0.125f));
   float chi = fmaf(-k, kC1, xh);
   chi = fmaf(-k, kC2, chi);
-  chi = fmaf(-k, kC3, chi);
-  chi = (chi - kPi4H) + (xl - kPi4L);
+  chi = fmaf(-k, kC3, chi - kPi4H) + xl4;
   sincos_sfu(chi, &f.s, &f.c);
   f.dx = dxh + dxl;
   f.dy = dyh + dyl;

@@ -153,7 +153,7 @@ SMS, FP32_LANES = 152, 128
 # kernel folds the per-node factors in and evaluates S and D' in two passes
 ENTRY_OPS = {("soft", 1): 74, ("hard", 1): 87, ("soft", 2): 64, ("hard", 2): 98}
 SUM_OPS = {"soft": 4, "hard": 8}         # FP32 FMAs per pair and right-hand side (CUDA-core sums)
-DF_ENTRY_OPS = 677                       # double-float pair entry of the residual kernel
+DF_ENTRY_OPS = 563                       # double-float pair entry of the residual kernel
 DF_TERM_OPS = 48                         # Dot2 complex product-sum per pair and right-hand side
 SLICE_OPS = 48                           # six 8-bit slices of the re / im parts of one entry
 FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)

@@ -6,9 +6,13 @@
 // GB300 runs FP64 at a small fraction of its FP32 rate, and the two residual
 // matvecs of a refined solve cost more than all its inner FP32 matvecs when
 // computed in FP64.  These kernels evaluate the same Nystrom entries as the
-// FP64 kernel (Kress log-split rule) in double-float arithmetic: every quantity is an unevaluated sum hi + lo of two
-// FP32 numbers (~48 significant bits), products and sums use error-free
-// transformations (TwoProd with fmaf, TwoSum), and
+// FP64 kernel (Kress log-split rule) in double-float arithmetic: every
+// quantity is an unevaluated sum hi + lo of two FP32 numbers (~48 significant
+// bits), products and sums use error-free transformations (TwoProd with fmaf,
+// TwoSum), reciprocals and square roots start from the special-function
+// unit's approximations and take one double-float correction; coordinates are
+// stored times omega (the node distance is the Hankel argument) and the
+// per-node factors of each entry are folded into per-node vectors; and
 //  * Hankel's asymptotic expansion (A&S 9.2.5, 9.2.9, 9.2.10) carries its
 //    leading terms in double-float and the small corrections in FP32 (for
 //    omega r >= 40 the dropped terms are below 1e-13);
@@ -76,17 +80,23 @@ __host__ __device__ __forceinline__ df dmake(double v) {
   const float h = (float)v;
   return {h, (float)(v - (double)h)};
 }
-// 1 / a
+// 1 / a from the special-function unit's approximation q (~1 ulp): with
+// e = 1 - a q, 1 / a = q (1 + e + e^2 + ...), kept to second order
 __device__ __forceinline__ df drcp(df a) {
-  const float q = 1.0f / a.h;
-  const float e = fmaf(-a.h, q, 1.0f) - a.l * q;   // 1 - a q
-  return quick(q, q * e);
+  float q;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(a.h));
+  const float e = fmaf(-a.h, q, 1.0f) - a.l * q;
+  return quick(q, q * fmaf(e, e, e));
 }
-// sqrt(a), a > 0
+// sqrt(a), a > 0: r = a rs with rs ~ 1/sqrt(a.h) (one Newton step on the
+// special-function unit's value), then one Newton correction in double-float
 __device__ __forceinline__ df dsqrt(df a) {
-  const float r = sqrtf(a.h);
+  float rs;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rs) : "f"(a.h));
+  rs = rs * fmaf(-0.5f * a.h * rs, rs, 1.5f);
+  const float r = a.h * rs;
   const float e = fmaf(-r, r, a.h) + a.l;           // a - r^2
-  return quick(r, e * 0.5f / r);
+  return quick(r, e * (0.5f * rs));
 }
 
 // sin(j pi / 32), cos(j pi / 32) for j = -32 .. 32 as hi / lo pairs
@@ -133,33 +143,35 @@ __constant__ float kN6H = -0.1666666716337204f, kN6L = 4.967053879312289e-09f;
 // 2 pi = C1 + C2 + C3, C1 on 10 significant bits
 __constant__ float kC1 = 6.28125f, kC2 = 0.0019353071693331003f, kC3 = 1.0253376273028358e-11f;
 
+// Per-node double-float data (hi, lo pairs), with hq = h / 4, c0 = sqrt(2/pi),
+// nu the unnormalised normal and |z'| the speed:
 struct df_params {
   int n, b, nrhs, splits, tiles_per_split;
-  df om, eta, hq;               // omega, eta, h / 4
-  const float4* g;              // per node: (x hi, x lo, y hi, y lo)
-  const float4* nrm;            // per node: (nu1 hi, nu1 lo, nu2 hi, nu2 lo)
-  const float2* sp;             // per node: |z'| (hi, lo)
-  const float2* w;              // Kress table w_d (hi, lo)
+  const float4* g;              // omega (x, y)
+  const float4* sqa;            // source factors omega hq c0 (nu1, nu2)
+  const float4* tq;             // target factors omega (nu1, nu2) / |z'|
+  const float2* sqe;            // source factor hq c0 eta |z'|
+  const float2* sqs;            // source factor hq c0 |z'|
+  const float2* w;              // Kress table w_d / (pi h)
   const float4* band;           // near entries (re hi, re lo, im hi, im lo), n x (2b + 1)
   const float4* x;              // densities as double-float (re hi, re lo, im hi, im lo)
   double2* part;                // [split][k][i]
   const int* fx;                // tensor-core residual: exponent of each accumulator column
 };
 
-// Hankel values of one far pair (omega r >= 40) in double-float: (dx, dy) =
-// z_i - z_j, 1 / r, J0, Y0, J1, Y1 at omega r
+// Hankel values of one far pair (x = omega r >= 40) in double-float, without
+// the common factor c0 x^(-1/2): (dx, dy) = omega (z_i - z_j), 1 / x,
+// ra = x^(-1/2), and j_m, y_m with J_m = c0 ra j_m, Y_m = c0 ra y_m
 struct df_hankel {
-  df dx, dy, rinv, J0, Y0, J1, Y1;
+  df dx, dy, xinv, ra, j0, y0, j1, y1;
 };
 
-__device__ __forceinline__ df_hankel hankel_df(const df_params& P, float4 gi, float4 gj,
+__device__ __forceinline__ df_hankel hankel_df(float4 gi, float4 gj,
                                                const float4* __restrict__ tab) {
   const df dx = dsub({gi.x, gi.y}, {gj.x, gj.y});
   const df dy = dsub({gi.z, gi.w}, {gj.z, gj.w});
-  const df r2 = dadd(dmul(dx, dx), dmul(dy, dy));
-  const df r = dsqrt(r2);
-  const df rinv = drcp(r);
-  const df x = dmul(P.om, r);
+  const df x = dsqrt(dadd(dmul(dx, dx), dmul(dy, dy)));
+  const df t = drcp(x);
   // chi = x - pi/4 - 2 pi k, |chi| <= pi
   const float k = rintf(fmaf(x.h, 0.15915493667125702f, -0.125f));
   df chi = {fmaf(-k, kC1, x.h), x.l};                          // exact first step
@@ -184,7 +196,6 @@ __device__ __forceinline__ df_hankel hankel_df(const df_params& P, float4 gi, fl
   const df sn = dadd(dmul(sj, cd), dmul(cj, sd));
   const df cs = dsub(dmul(cj, cd), dmul(sj, sd));
   // asymptotic expansion, t = 1/x
-  const df t = drcp(x);
   const float t2 = t.h * t.h;
   const df P0 = quick(1.0f, t2 * (-0.0703125f + t2 * (0.112152099609375f +
                               t2 * (-0.5725014209747314f + t2 * 6.074042001273483f))));
@@ -196,51 +207,53 @@ __device__ __forceinline__ df_hankel hankel_df(const df_params& P, float4 gi, fl
   const df Q1 = dadd(dmulf(t, 0.375f),
                      {t.h * t2 * (-0.1025390625f + t2 * (0.2775764465332031f +
                                   t2 * -1.993531733751297f)), 0.f});
-  const df amp = dmul({kSq2PiH, kSq2PiL}, dsqrt(t));
-  const df J0 = dmul(amp, dsub(dmul(P0, cs), dmul(Q0, sn)));
-  const df Y0 = dmul(amp, dadd(dmul(P0, sn), dmul(Q0, cs)));
-  const df J1 = dmul(amp, dadd(dmul(P1, sn), dmul(Q1, cs)));
-  const df Y1 = dmul(amp, dsub(dmul(Q1, sn), dmul(P1, cs)));
-  return {dx, dy, rinv, J0, Y0, J1, Y1};
+  df_hankel H;
+  H.dx = dx;
+  H.dy = dy;
+  H.xinv = t;
+  H.ra = dsqrt(t);
+  H.j0 = dsub(dmul(P0, cs), dmul(Q0, sn));
+  H.y0 = dadd(dmul(P0, sn), dmul(Q0, cs));
+  H.j1 = dadd(dmul(P1, sn), dmul(Q1, cs));
+  H.y1 = dsub(dmul(Q1, sn), dmul(P1, cs));
+  return H;
 }
 
-// one far pair: soft entry a = h K + w K1 (eq. 1), K = L - i eta M
-__device__ __forceinline__ float4 entry_df(const df_params& P, float4 gi, float4 gj, float4 nj,
-                                           float2 sj2, float2 w2, const float4* __restrict__ tab) {
-  const df_hankel H = hankel_df(P, gi, gj, tab);
-  // c = (z_i - z_j) . nu~_j / r,  es = eta |z'_j|,  oc = omega c
-  const df c = dmul(dadd(dmul(H.dx, {nj.x, nj.y}), dmul(H.dy, {nj.z, nj.w})), H.rinv);
-  const df es = dmul(P.eta, {sj2.x, sj2.y});
-  const df oc = dmul(P.om, c);
-  const df wq = dmul({w2.x, w2.y}, {kI4PiH, kI4PiL});
-  const df re =
-      dsub(dmul(P.hq, dsub(dmul(es, H.J0), dmul(oc, H.Y1))), dmul(wq, dmul(oc, H.J1)));
-  const df im =
-      dadd(dmul(P.hq, dadd(dmul(oc, H.J1), dmul(es, H.Y0))), dmul(wq, dmul(es, H.J0)));
+// one far pair: soft entry a = h K + w K1 (eq. 1), K = L - i eta M.  With the
+// per-node factors folded in (source: sa = omega hq c0 nu_j, se = hq c0 eta
+// |z'_j|; wk = w / (pi h)): A = se ra, B = (sa . dx) ra / x and
+//   Re a = A j0 - B (y1 + wk j1),  Im a = B j1 + A (y0 + wk j0)
+__device__ __forceinline__ float4 entry_df(float4 gi, float4 gj, float4 sa, float2 se, float2 w2,
+                                           const float4* __restrict__ tab) {
+  const df_hankel H = hankel_df(gi, gj, tab);
+  const df wk = {w2.x, w2.y};
+  const df A = dmul({se.x, se.y}, H.ra);
+  const df B = dmul(dadd(dmul(H.dx, {sa.x, sa.y}), dmul(H.dy, {sa.z, sa.w})), dmul(H.xinv, H.ra));
+  const df re = dsub(dmul(A, H.j0), dmul(B, dadd(H.y1, dmul(wk, H.j1))));
+  const df im = dadd(dmul(B, H.j1), dmul(A, dadd(H.y0, dmul(wk, H.j0))));
   return make_float4(re.h, re.l, im.h, im.l);
 }
 
 // one far pair of the sound-hard operator (eq. 2): S_ij = h M + w M1 with
 // M = (i/4) H0 |z'_j|, M1 = -(1/4 pi) J0 |z'_j|, and D'_ij = h L' + w L'1 with
 // L' = (i omega / 4) H1 cp, L'1 = -(omega / 4 pi) J1 cp,
-// cp = -((z_i - z_j) . nu~_i / r) |z'_j| / |z'_i|
-__device__ __forceinline__ void entry_df_hard(const df_params& P, float4 gi, float4 gj,
-                                              float4 ni, float2 si2, float2 sj2, float2 w2,
-                                              const float4* __restrict__ tab, float4& S,
-                                              float4& Dp) {
-  const df_hankel H = hankel_df(P, gi, gj, tab);
-  const df sj = {sj2.x, sj2.y};
-  const df wq = dmul({w2.x, w2.y}, {kI4PiH, kI4PiL});
-  // S: re = -(h/4 Y0 + w/(4 pi) J0) |z'_j|, im = h/4 J0 |z'_j|
-  const df sre = dneg(dmul(dadd(dmul(P.hq, H.Y0), dmul(wq, H.J0)), sj));
-  const df sim = dmul(dmul(P.hq, H.J0), sj);
+// cp = -((z_i - z_j) . nu~_i / r) |z'_j| / |z'_i|.  Folded (ss = hq c0 |z'_j|,
+// ti = omega nu_i / |z'_i|): A = ss ra, D = (ti . dx) ra ss / x and
+//   S = -A (y0 + wk j0) + i A j0,   D' = D (y1 + wk j1) - i D j1
+__device__ __forceinline__ void entry_df_hard(float4 gi, float4 gj, float4 ti, float2 ss2,
+                                              float2 w2, const float4* __restrict__ tab,
+                                              float4& S, float4& Dp) {
+  const df_hankel H = hankel_df(gi, gj, tab);
+  const df wk = {w2.x, w2.y};
+  const df ss = {ss2.x, ss2.y};
+  const df A = dmul(ss, H.ra);
+  const df sre = dneg(dmul(A, dadd(H.y0, dmul(wk, H.j0))));
+  const df sim = dmul(A, H.j0);
   S = make_float4(sre.h, sre.l, sim.h, sim.l);
-  const df ci = dmul(dadd(dmul(H.dx, {ni.x, ni.y}), dmul(H.dy, {ni.z, ni.w})), H.rinv);
-  const df cp = dneg(dmul(ci, dmul(sj, drcp({si2.x, si2.y}))));
-  const df oc = dmul(P.om, cp);
-  // D': re = -omega cp (h/4 Y1 + w/(4 pi) J1), im = h/4 omega cp J1
-  const df dre = dneg(dmul(oc, dadd(dmul(P.hq, H.Y1), dmul(wq, H.J1))));
-  const df dim = dmul(dmul(P.hq, oc), H.J1);
+  const df D = dmul(dmul(dadd(dmul(H.dx, {ti.x, ti.y}), dmul(H.dy, {ti.z, ti.w})),
+                         dmul(H.xinv, H.ra)), ss);
+  const df dre = dmul(D, dadd(H.y1, dmul(wk, H.j1)));
+  const df dim = dneg(dmul(D, H.j1));
   Dp = make_float4(dre.h, dre.l, dim.h, dim.l);
 }
 
@@ -305,7 +318,7 @@ __global__ void __launch_bounds__(DNT) k_pair_df(df_params P) {
         if (dd != INT_MAX)
           a = P.band[(size_t)i * bw + dd + P.b];
         else
-          a = entry_df(P, P.g[i], P.g[j], P.nrm[j], P.sp[j], P.w[d], sTab);
+          a = entry_df(P.g[i], P.g[j], P.sqa[j], P.sqe[j], P.w[d], sTab);
       }
       S.A[il][jl] = a;
     }
@@ -399,7 +412,7 @@ __global__ void __launch_bounds__(DNT) k_pair_df_hard(df_params P, const float4*
           a = P.band[(size_t)i * bw + dd + P.b];
           b = P.band[nbw + (size_t)i * bw + dd + P.b];
         } else {
-          entry_df_hard(P, P.g[i], P.g[j], P.nrm[i], P.sp[i], P.sp[j], P.w[d], sTab, a, b);
+          entry_df_hard(P.g[i], P.g[j], P.tq[i], P.sqs[j], P.w[d], sTab, a, b);
         }
       }
       S.S[il][jl] = a;
@@ -505,8 +518,7 @@ struct rtc_smem {
   __nv_bfloat16 A[RST][2 * RSL][RTM * RTK];    // Ar slices 0..5, Ai slices 0..5
   __nv_bfloat16 B[RST][2 * RSL][2 * NB * RTK]; // per slice t: [Xr | Xi], [-Xi | Xr]
   float4 tgt[RTM];
-  float4 tgn[RTM];   // target normal (hi, lo pairs) and, below, speed: hard kinds
-  float2 tgs[RTM];
+  float4 tgn[RTM];   // target factors (hard kinds)
   int ex[RTM];
   float4 tab[65];    // sin / cos table (per-lane indices: shared, not constant)
   uint64_t full[RST], empty[RST], tfull, tempty;
@@ -614,8 +626,7 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
         const int i = m0 + r;
         S.tgt[r] = i < n ? P.g[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         S.ex[r] = i < n ? rowexp[i] : 0;
-        S.tgn[r] = i < n ? P.nrm[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        S.tgs[r] = i < n ? P.sp[i] : make_float2(1.f, 0.f);
+        if (KIND != RK_SOFT) S.tgn[r] = i < n ? P.tq[i] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncwarp();
       for (int k = sg.z; k < sg.w; ++k, ++it) {
@@ -635,8 +646,12 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
         for (int u = 0; u < 2; ++u) {
           const bool ok = j + u < n;
           gj[u] = ok ? P.g[j + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-          nj[u] = ok ? P.nrm[j + u] : make_float4(0.f, 0.f, 0.f, 0.f);
-          sj[u] = ok ? P.sp[j + u] : make_float2(1.f, 0.f);
+          if (KIND == RK_SOFT) {
+            nj[u] = ok ? P.sqa[j + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sj[u] = ok ? P.sqe[j + u] : make_float2(0.f, 0.f);
+          } else {
+            sj[u] = ok ? P.sqs[j + u] : make_float2(0.f, 0.f);
+          }
         }
         unsigned char* A = reinterpret_cast<unsigned char*>(&S.A[st][0][0]);
 #pragma unroll 1
@@ -655,11 +670,10 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
               if (d < 0) d += n;
               if (d > P.b && d < n - P.b) {
                 if constexpr (KIND == RK_SOFT) {
-                  a = entry_df(P, gi, gj[u], nj[u], sj[u], P.w[d], S.tab);
+                  a = entry_df(gi, gj[u], nj[u], sj[u], P.w[d], S.tab);
                 } else {
                   float4 es, ed;
-                  entry_df_hard(P, gi, gj[u], S.tgn[il], S.tgs[il], sj[u], P.w[d], S.tab, es,
-                                ed);
+                  entry_df_hard(gi, gj[u], S.tgn[il], sj[u], P.w[d], S.tab, es, ed);
                   a = KIND == RK_S ? es : ed;
                 }
               }
@@ -997,17 +1011,26 @@ __global__ void k_reduce_df(int n, int nrhs, int splits, const double2* __restri
   y[e] = make_double2(sx, sy);
 }
 
-// set-up: split geometry / tables, band width for omega r < kXD, FP64 band
-__global__ void k_df_geo(int n, geom_dev g, const double* __restrict__ w, float4* __restrict__ go,
-                         float4* __restrict__ no, float2* __restrict__ so,
-                         float2* __restrict__ wo) {
+// set-up: per-node double-float data (df_params), band width for
+// omega r < kXD, FP64 band
+__global__ void k_df_geo(int n, geom_dev g, const double* __restrict__ w, double omega,
+                         double eta, double h, float4* __restrict__ go, float4* __restrict__ sa,
+                         float4* __restrict__ tq, float2* __restrict__ se,
+                         float2* __restrict__ ss, float2* __restrict__ wo) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const df x = dmake(g.x[i]), y = dmake(g.y[i]), a = dmake(g.nx[i]), b = dmake(g.ny[i]);
-  const df s = dmake(g.sp[i]), ww = dmake(w[i]);
+  const double f = 0.25 * h * 0.7978845608028654;   // hq c0
+  const double sp = g.sp[i];
+  const df x = dmake(omega * g.x[i]), y = dmake(omega * g.y[i]);
+  const df a1 = dmake(omega * f * g.nx[i]), a2 = dmake(omega * f * g.ny[i]);
+  const df t1 = dmake(omega * g.nx[i] / sp), t2 = dmake(omega * g.ny[i] / sp);
+  const df e = dmake(f * eta * sp), s = dmake(f * sp);
+  const df ww = dmake(w[i] / (3.141592653589793 * h));
   go[i] = make_float4(x.h, x.l, y.h, y.l);
-  no[i] = make_float4(a.h, a.l, b.h, b.l);
-  so[i] = make_float2(s.h, s.l);
+  sa[i] = make_float4(a1.h, a1.l, a2.h, a2.l);
+  tq[i] = make_float4(t1.h, t1.l, t2.h, t2.l);
+  se[i] = make_float2(e.h, e.l);
+  ss[i] = make_float2(s.h, s.l);
   wo[i] = make_float2(ww.h, ww.l);
 }
 
@@ -1299,14 +1322,15 @@ void df_prepare(cfie_op* op) {
     return;
   }
   op->df_b = b;
-  op->df_geo.reserve((sizeof(float4) * 2 + sizeof(float2) * 2) * (size_t)n);
+  op->df_geo.reserve((sizeof(float4) * 3 + sizeof(float2) * 3) * (size_t)n);
   const int hard = op->bc == CFIE_SOUND_HARD ? 1 : 0;
   op->df_band.reserve(sizeof(float4) * (size_t)n * bw * (hard ? 2 : 1));
   char* base = op->df_geo.as<char>();
-  k_df_geo<<<nbk(n), 256, 0, st>>>(n, op->g, op->wtab.as<double>(), (float4*)base,
-                                    (float4*)(base + sizeof(float4) * n),
-                                    (float2*)(base + 2 * sizeof(float4) * n),
-                                    (float2*)(base + (2 * sizeof(float4) + sizeof(float2)) * n));
+  const size_t f4 = sizeof(float4) * n, f2 = sizeof(float2) * n;
+  k_df_geo<<<nbk(n), 256, 0, st>>>(n, op->g, op->wtab.as<double>(), op->omega, op->eta, op->h,
+                                    (float4*)base, (float4*)(base + f4), (float4*)(base + 2 * f4),
+                                    (float2*)(base + 3 * f4), (float2*)(base + 3 * f4 + f2),
+                                    (float2*)(base + 3 * f4 + 2 * f2));
   CFIE_CHECK_LAUNCH();
   k_df_band<<<nbk((size_t)n * bw), 256, 0, st>>>(n, b, hard, op->omega, op->eta, op->g,
                                                   op->wtab.as<double>(), op->diag.as<double2>(),
@@ -1362,14 +1386,14 @@ void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
   P.n = n;
   P.b = op->df_b;
   P.nrhs = nrhs;
-  P.om = dmake(op->omega);
-  P.eta = dmake(op->eta);
-  P.hq = dmake(0.25 * op->h);
   char* base = op->df_geo.as<char>();
+  const size_t f4 = sizeof(float4) * n, f2 = sizeof(float2) * n;
   P.g = (const float4*)base;
-  P.nrm = (const float4*)(base + sizeof(float4) * n);
-  P.sp = (const float2*)(base + 2 * sizeof(float4) * n);
-  P.w = (const float2*)(base + (2 * sizeof(float4) + sizeof(float2)) * n);
+  P.sqa = (const float4*)(base + f4);
+  P.tq = (const float4*)(base + 2 * f4);
+  P.sqe = (const float2*)(base + 3 * f4);
+  P.sqs = (const float2*)(base + 3 * f4 + f2);
+  P.w = (const float2*)(base + 3 * f4 + 2 * f2);
   P.band = op->df_band.as<float4>();
   const size_t tot = (size_t)n * nrhs;
   if (op->bc == CFIE_SOUND_HARD && (op->res_variant == 2 || (op->res_variant == 0 && nrhs >= 8))) {

@@ -52,6 +52,7 @@ template <> struct basis_t<float2> {
   static __device__ __forceinline__ float2 make(double a, double b) {
     return make_float2((float)a, (float)b);
   }
+  static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
 };
 
 struct chunk_ref {
@@ -195,54 +196,68 @@ k_update(int J, const T* __restrict__ V, size_t L, const double2* __restrict__ h
   }
 }
 
-// One thread per problem: ||w||, Givens rotations, residual estimate.
-__global__ void k_givens(int P, int m, int j, const int* __restrict__ act, pset_dev ps,
+// One warp per problem: ||w||, Givens rotations, residual estimate.  The
+// warp stages column j of H and the previous rotations in shared memory;
+// lane 0 applies the rotations in order (each depends on the last).
+__global__ void k_givens(int m, int j, const int* __restrict__ act, pset_dev ps,
                          const double* __restrict__ nrm_partial, double2* __restrict__ H,
                          double* __restrict__ cs, double2* __restrict__ sn,
                          double2* __restrict__ gv, double* __restrict__ hnorm,
                          double* __restrict__ res) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= P || !act[p]) return;
-  double s2 = 0.0;
-  for (int c = 0; c < ps.nch[p]; ++c) s2 += nrm_partial[ps.chb[p] + c];
-  const double hn = sqrt(s2);
-  hnorm[p] = hn;
+  const int p = blockIdx.x, lane = threadIdx.x;
+  if (!act[p]) return;
+  extern __shared__ double2 gsh[];
+  double2* col = gsh;                                  // m + 1
+  double2* ssn = gsh + (m + 1);                        // m
+  double* scs = reinterpret_cast<double*>(ssn + m);    // m
   double2* Hk = H + (size_t)p * (m + 1) * m;
-  Hk[(size_t)(j + 1) * m + j] = make_double2(hn, 0.0);
-  for (int q = 0; q < j; ++q) {   // previous rotations [c s; -conj(s) c] on column j
-    const double2 a = Hk[(size_t)q * m + j], b = Hk[(size_t)(q + 1) * m + j];
-    const double c = cs[(size_t)p * m + q];
-    const double2 s = sn[(size_t)p * m + q];
-    Hk[(size_t)q * m + j] =
-        make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
-    Hk[(size_t)(q + 1) * m + j] = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x,
-                                               -(s.x * a.y - s.y * a.x) + c * b.y);
+  double s2 = 0.0;
+  for (int c = lane; c < ps.nch[p]; c += 32) s2 += nrm_partial[ps.chb[p] + c];
+  for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  const double hn = sqrt(s2);
+  for (int q = lane; q <= j; q += 32) col[q] = Hk[(size_t)q * m + j];
+  for (int q = lane; q < j; q += 32) {
+    scs[q] = cs[(size_t)p * m + q];
+    ssn[q] = sn[(size_t)p * m + q];
   }
-  const double2 a = Hk[(size_t)j * m + j];
-  const double bn = hn;  // b = ||w|| is real
-  double c;
-  double2 s;
-  const double aa = hypot(a.x, a.y);
-  if (bn == 0.0) {
-    c = 1.0;
-    s = make_double2(0.0, 0.0);
-  } else if (aa == 0.0) {
-    c = 0.0;
-    s = make_double2(1.0, 0.0);
-  } else {
-    const double t = hypot(aa, bn);
-    c = aa / t;
-    s = make_double2(a.x / aa * bn / t, a.y / aa * bn / t);  // (a/|a|) conj(b) / t
+  __syncwarp();
+  if (lane == 0) {
+    hnorm[p] = hn;
+    double2 a = col[0];
+    for (int q = 0; q < j; ++q) {   // previous rotations [c s; -conj(s) c] on column j
+      const double2 b = col[q + 1];
+      const double c = scs[q];
+      const double2 s = ssn[q];
+      col[q] = make_double2(c * a.x + s.x * b.x - s.y * b.y, c * a.y + s.x * b.y + s.y * b.x);
+      a = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y);
+    }
+    const double bn = hn;  // b = ||w|| is real
+    double c;
+    double2 s;
+    const double aa = hypot(a.x, a.y);
+    if (bn == 0.0) {
+      c = 1.0;
+      s = make_double2(0.0, 0.0);
+    } else if (aa == 0.0) {
+      c = 0.0;
+      s = make_double2(1.0, 0.0);
+    } else {
+      const double t = hypot(aa, bn);
+      c = aa / t;
+      s = make_double2(a.x / aa * bn / t, a.y / aa * bn / t);  // (a/|a|) conj(b) / t
+    }
+    cs[(size_t)p * m + j] = c;
+    sn[(size_t)p * m + j] = s;
+    col[j] = make_double2(c * a.x + s.x * bn, c * a.y + s.y * bn);
+    col[j + 1] = make_double2(0.0, 0.0);
+    const double2 gj = gv[(size_t)p * (m + 1) + j];
+    const double2 g1 = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+    gv[(size_t)p * (m + 1) + j + 1] = g1;
+    gv[(size_t)p * (m + 1) + j] = make_double2(c * gj.x, c * gj.y);
+    res[p] = hypot(g1.x, g1.y);
   }
-  cs[(size_t)p * m + j] = c;
-  sn[(size_t)p * m + j] = s;
-  Hk[(size_t)j * m + j] = make_double2(c * a.x + s.x * bn, c * a.y + s.y * bn);
-  Hk[(size_t)(j + 1) * m + j] = make_double2(0.0, 0.0);
-  const double2 gj = gv[(size_t)p * (m + 1) + j];
-  const double2 g1 = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
-  gv[(size_t)p * (m + 1) + j + 1] = g1;
-  gv[(size_t)p * (m + 1) + j] = make_double2(c * gj.x, c * gj.y);
-  res[p] = hypot(g1.x, g1.y);
+  __syncwarp();
+  for (int q = lane; q <= j + 1; q += 32) Hk[(size_t)q * m + j] = col[q];
 }
 
 // vout = w / ||w|| per problem (0 on breakdown); vin (optional) = the same
@@ -255,12 +270,14 @@ k_scale(const int* __restrict__ act, pset_dev ps, const double* __restrict__ hn,
   if (!act[c.p]) return;
   const double h = hn[c.p];
   const double inv = h > 0.0 ? 1.0 / h : 0.0;
+  // the multiply in the basis precision (FP64 runs at 1/64 of the FP32 rate)
+  const typename basis_t<T>::S s = (typename basis_t<T>::S)inv;
 #pragma unroll
   for (int e = 0; e < AE; ++e) {
     const int q = e * AT + threadIdx.x;
     if (q < c.cnt) {
       const T v = w[c.base + q];
-      const T o = basis_t<T>::make(v.x * inv, v.y * inv);
+      const T o = basis_t<T>::make(v.x * s, v.y * s);
       vout[c.base + q] = o;
       if (vin) vin[c.base + q] = make_double2(o.x, o.y);
     }
@@ -598,8 +615,8 @@ void gmres_cycle(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps, c
               j, W.V, L, W.hbuf, W.act, ps.dev, W.w, pass == 1 ? W.nrmp : nullptr);
         CFIE_CHECK_LAUNCH();
       }
-      k_givens<<<blocks_for(P, 64), 64, 0, st>>>(P, m, j, W.act, ps.dev, W.nrmp, W.H, W.cs, W.sn,
-                                                 W.gv, W.hn, W.res);
+      k_givens<<<P, 32, (sizeof(double2) * 2 + sizeof(double)) * m + sizeof(double2), st>>>(
+          m, j, W.act, ps.dev, W.nrmp, W.H, W.cs, W.sn, W.gv, W.hn, W.res);
       CFIE_CHECK_LAUNCH();
       if (W.f32)
         k_scale<float2><<<ps.Q, AT, 0, st>>>(W.act, ps.dev, W.hn, W.w32,

@@ -16,7 +16,7 @@
 // Warp roles: 0-7 evaluate pair entries into the stage ring, 8 issues the TMA
 // loads of the right-hand sides, 9 issues the MMAs (double-buffered
 // accumulators), 10-13 drain finished accumulators into per-segment partial
-// sums, which a second kernel adds in FP64 in a fixed order.  All mbarrier
+// sums, which a second kernel adds in a fixed order.  All mbarrier
 // waits are bounded (error flag, drain, TMEM freed on every path).
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -373,14 +373,16 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
   }
 }
 
-// y[r][i] = sum of the segment partials of row tile i / 128 (fixed order, FP64)
+// y[r][i] = sum of the (one to a few) segment partials of row tile i / 128, in
+// a fixed order; FP32 adds (the partials are FP32 sums of bf16 products: FP64
+// adds would buy nothing here and run at 1/64 of the FP32 rate)
 __global__ void k_reduce_tc(int n, int nr, int NR, const int2* __restrict__ mt_seg,
                             const float2* __restrict__ partial, double2* __restrict__ y) {
   const int m = blockIdx.x, r = blockIdx.y, row = threadIdx.x;
   const int i = m * TBM + row;
   if (i >= n || r >= nr) return;
   const int2 sr = mt_seg[m];
-  double sx = 0.0, sy = 0.0;
+  float sx = 0.f, sy = 0.f;
   for (int s = sr.x; s < sr.x + sr.y; ++s) {
     const float2 p = partial[((size_t)s * NR + r) * TBM + row];
     sx += p.x;

@@ -267,33 +267,48 @@ inline void streamk_segments(int mtiles, int ktiles, int grid_max, std::vector<i
 
 // B operand planes [4][NP][pitch] for nr right-hand sides (complex128, [r][j]):
 // B1 = [Xr | Xi], B2 = [-Xi | Xr] (rows = output columns), hi / lo bf16 split
+// (of the FP32-rounded value, in FP32).  One thread per right-hand side r and
+// source pair j, j + 1: x read once, packed bf16 pairs stored.
 __global__ void k_prep_b_planes(int n, int pitch, int NP, int nr, const double2* __restrict__ x,
                                 __nv_bfloat16* __restrict__ bt) {
-  const int c = blockIdx.y;
-  const int j = blockIdx.x * 256 + threadIdx.x;
+  const int r = blockIdx.y;                       // < NP / 2
+  const int j = 2 * (blockIdx.x * 256 + threadIdx.x);
   if (j >= pitch) return;
   const int NR = NP / 2;
-  const int r = c < NR ? c : c - NR;
-  double w1 = 0.0, w2 = 0.0;
-  if (j < n && r < nr) {
-    const double2 xv = x[(size_t)r * n + j];
-    w1 = c < NR ? xv.x : xv.y;
-    w2 = c < NR ? -xv.y : xv.x;
+  float re[2] = {0.f, 0.f}, im[2] = {0.f, 0.f};
+  if (r < nr) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (j + u < n) {
+        const double2 v = x[(size_t)r * n + j + u];
+        re[u] = (float)v.x;
+        im[u] = (float)v.y;
+      }
   }
-  const __nv_bfloat16 h1 = __float2bfloat16_rn((float)w1), h2 = __float2bfloat16_rn((float)w2);
-  const __nv_bfloat16 l1 = __float2bfloat16_rn((float)(w1 - (double)__bfloat162float(h1)));
-  const __nv_bfloat16 l2 = __float2bfloat16_rn((float)(w2 - (double)__bfloat162float(h2)));
+  const __nv_bfloat162 hr = __floats2bfloat162_rn(re[0], re[1]);
+  const __nv_bfloat162 lr =
+      __floats2bfloat162_rn(re[0] - __low2float(hr), re[1] - __high2float(hr));
+  const __nv_bfloat162 hi = __floats2bfloat162_rn(im[0], im[1]);
+  const __nv_bfloat162 li =
+      __floats2bfloat162_rn(im[0] - __low2float(hi), im[1] - __high2float(hi));
   const size_t plane = (size_t)NP * pitch;
-  const size_t e = (size_t)c * pitch + j;
-  bt[e] = h1;
-  bt[plane + e] = l1;
-  bt[2 * plane + e] = h2;
-  bt[3 * plane + e] = l2;
+  __nv_bfloat162* b = reinterpret_cast<__nv_bfloat162*>(bt);
+  const size_t e0 = ((size_t)r * pitch + j) / 2, e1 = ((size_t)(NR + r) * pitch + j) / 2;
+  const size_t p2 = plane / 2;
+  // row r: B1 = Xr, B2 = -Xi;  row NR + r: B1 = Xi, B2 = Xr
+  b[e0] = hr;
+  b[p2 + e0] = lr;
+  b[2 * p2 + e0] = __hneg2(hi);
+  b[3 * p2 + e0] = __hneg2(li);
+  b[e1] = hi;
+  b[p2 + e1] = li;
+  b[2 * p2 + e1] = hr;
+  b[3 * p2 + e1] = lr;
 }
 
 inline void prep_b_planes(cfie_ctx* ctx, int n, int pitch, int NP, int nr, const double2* x,
                           __nv_bfloat16* bt) {
-  k_prep_b_planes<<<dim3((unsigned)((pitch + 255) / 256), NP), 256, 0, ctx->stream>>>(
+  k_prep_b_planes<<<dim3((unsigned)((pitch / 2 + 255) / 256), NP / 2), 256, 0, ctx->stream>>>(
       n, pitch, NP, nr, x, bt);
   CFIE_CHECK_LAUNCH();
 }

@@ -352,37 +352,41 @@ __global__ void k_lsq(int P, int m, const int* __restrict__ kd, const double2* _
   }
 }
 
-// x += sum_{jj < kd[p]} V[jj] y[p][jj] (sums in FP64 for either basis type)
+// x += sum_{jj < kd[p]} V[jj] y[p][jj]: the sum in the basis precision (an
+// FP32 basis is orthonormal to FP32 accuracy, so |sum| ~ |y| and FP32 loses
+// nothing the inner solve's tolerance would notice), added to x in FP64
 template <typename T>
 __global__ void __launch_bounds__(AT)
 k_xupdate(int m, const int* __restrict__ kd, pset_dev ps, const T* __restrict__ V, size_t L,
           const double2* __restrict__ y, double2* __restrict__ x) {
+  using S = typename basis_t<T>::S;
   const chunk_ref c = chunk_of(ps, blockIdx.x);
   const int K = kd[c.p];
   if (K == 0) return;
-  double2 acc[AE];
+  S ar[AE], ai[AE];
 #pragma unroll
-  for (int e = 0; e < AE; ++e) {
-    const int q = e * AT + threadIdx.x;
-    acc[e] = q < c.cnt ? x[c.base + q] : make_double2(0.0, 0.0);
-  }
+  for (int e = 0; e < AE; ++e) ar[e] = ai[e] = 0;
   for (int jj = 0; jj < K; ++jj) {
-    const double2 yy = y[(size_t)c.p * m + jj];
+    const double2 yd = y[(size_t)c.p * m + jj];
+    const S yr = (S)yd.x, yi = (S)yd.y;
     const T* v = V + (size_t)jj * L + c.base;
 #pragma unroll
     for (int e = 0; e < AE; ++e) {
       const int q = e * AT + threadIdx.x;
       if (q < c.cnt) {
         const T a = v[q];
-        acc[e].x += (double)a.x * yy.x - (double)a.y * yy.y;
-        acc[e].y += (double)a.x * yy.y + (double)a.y * yy.x;
+        ar[e] = fma(a.x, yr, fma(-a.y, yi, ar[e]));
+        ai[e] = fma(a.x, yi, fma(a.y, yr, ai[e]));
       }
     }
   }
 #pragma unroll
   for (int e = 0; e < AE; ++e) {
     const int q = e * AT + threadIdx.x;
-    if (q < c.cnt) x[c.base + q] = acc[e];
+    if (q < c.cnt) {
+      const double2 xo = x[c.base + q];
+      x[c.base + q] = make_double2(xo.x + (double)ar[e], xo.y + (double)ai[e]);
+    }
   }
 }
 

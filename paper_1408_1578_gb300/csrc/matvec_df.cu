@@ -498,8 +498,9 @@ __global__ void k_df_x_hard(int n, size_t len, const double2* __restrict__ x,
 // same power of two and stays below 2^14 of it, so 128 sources (256 terms with
 // the split complex product, 768 for level 4) sum exactly in FP32; only the
 // levels >= 5 (below 2^-24 of the result) round.  Every 128 sources the
-// epilogue adds the four levels in double-float, scales by 2^(E_i + F_r - 14)
-// and accumulates per-segment double-float sums in global memory.  Near pairs
+// producer warps add the four levels in double-float, scale by
+// 2^(E_i + F_r - 14) and accumulate per-segment double-float sums in global
+// memory.  Near pairs
 // (the band, with the diagonal) are summed separately (k_band_df).  Split
 // complex as in the FP32 tensor-core kernel: [Yr | Yi] += Ar [Xr | Xi] +
 // Ai [-Xi | Xr].
@@ -511,7 +512,9 @@ constexpr int RST = 2;        // pipeline stages
 constexpr int RCK = 8;        // tiles per exact TMEM chunk (128 sources)
 constexpr int RPROD = 16;     // producer warps
 constexpr int RWTMA = RPROD, RWMMA = RPROD + 1;
-constexpr int RNT = (RPROD + 6) * 32;
+// 18 warps (the producers also drain the accumulators): at most 5 per
+// scheduler, so 96 registers per thread fit its quarter of the register file
+constexpr int RNT = (RPROD + 2) * 32;
 
 template <int NB>
 struct rtc_smem {
@@ -598,7 +601,7 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
       S.issued[s] = -1;
     }
     mbar_init(&S.tfull, 1);
-    mbar_init(&S.tempty, 4);
+    mbar_init(&S.tempty, RPROD);
     S.abort = 0;
     fence_mbar_init();
   }
@@ -616,8 +619,64 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
     // ---- producers: warp w owns rows w + RPROD (4 q + lane / 8), q = 0, 1;
     // lane l the two adjacent sources 2 (l % 8), +1 of the 16-source tile
     const int sub = lane >> 3, jp = 2 * (lane & 7);
-    int it = 0;
-    for (int s = sb; s < se; ++s) {
+    // Accumulator drain: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its
+    // rows) and a group of columns; chunk c (RCK tiles) is drained once the
+    // first tile of chunk c + 1 is produced: the four exact levels are added
+    // in double-float, scaled by 2^(E_i + F_r - 14), and accumulated into the
+    // segment's double-float sums in global memory.
+    constexpr int CPG = NC / 4 < 16 ? 16 : NC / 4;    // columns per warp group
+    const int qd = warp & 3, erow = 32 * qd + lane, cg0 = (warp >> 2) * CPG;
+    auto drain = [&](int c, int seg, int m0d, bool first) -> bool {
+      if (!__all_sync(0xffffffffu, mbar_wait(&S.tfull, c & 1))) {
+        if (lane == 0) {
+          atomicExch(err, 25);
+          S.abort = 1;
+        }
+        return false;
+      }
+      tc_fence_after();
+      if (cg0 < NC) {
+        const int i = m0d + erow;
+        const float rs = __int_as_float((127 + (i < n ? rowexp[i] : 0) - 14) << 23);
+        float2* dst = acc_out + (size_t)seg * NC * RTM + erow;
+        const uint32_t base = tmem + ((uint32_t)(32 * qd) << 16);
+#pragma unroll 1
+        for (int cb = cg0; cb < cg0 + CPG; cb += 16) {
+          float v0[16], v1[16], v2[16], v3[16];
+          tmem_ld16(base + (uint32_t)(0 * NC + cb), v0);
+          tmem_ld16(base + (uint32_t)(1 * NC + cb), v1);
+          tmem_ld16(base + (uint32_t)(2 * NC + cb), v2);
+          tmem_ld16(base + (uint32_t)(3 * NC + cb), v3);
+#pragma unroll
+          for (int r = 0; r < 16; ++r) {
+            const int col = cb + r;
+            // levels 2 + 3 exactly (TwoSum), then the smaller levels
+            const float sh = v0[r] + v1[r];
+            const float bv = sh - v0[r];
+            float sl = (v0[r] - (sh - bv)) + (v1[r] - bv);
+            sl += v2[r] + v3[r];
+            const float fs = __int_as_float((127 + P.fx[col]) << 23);  // 2^F_col
+            df val = quick(sh, sl);
+            val.h *= rs * fs;
+            val.l *= rs * fs;
+            float2* pp = dst + (size_t)col * RTM;
+            if (!first) {
+              const float2 o = *pp;
+              val = dadd(val, df{o.x, o.y});
+            }
+            *pp = make_float2(val.h, val.l);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&S.tempty);
+      return true;
+    };
+    int it = 0, cc = 0;
+    int pc = -1, ps = 0, pm0 = 0;      // undrained chunk, its segment and row tile
+    bool pfirst = false, stop = false;
+    for (int s = sb; s < se && !stop; ++s) {
       const int4 sg = segs[s];
       const int m0 = sg.y * RTM;
       __syncwarp();
@@ -694,9 +753,21 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&S.full[st]);
+        if ((k - sg.z) % RCK == 0) {
+          // first tile of a chunk: drain the previous chunk
+          if (pc >= 0 && !drain(pc, ps, pm0, pfirst)) {
+            stop = true;
+            break;
+          }
+          pc = cc++;
+          ps = s;
+          pm0 = m0;
+          pfirst = k == sg.z;
+        }
       }
-      if (*(volatile int*)&S.abort) break;
+      if (*(volatile int*)&S.abort) stop = true;
     }
+    if (!stop && pc >= 0) drain(pc, ps, pm0, pfirst);
   } else if (warp == RWTMA) {
     if (lane == 0) {
       // ---- TMA: the 2 x 6 density-slice planes of each source tile
@@ -765,62 +836,6 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
           }
           umma_commit(&S.tfull);
         }
-      }
-    }
-  } else {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows)
-    const int qd = warp & 3;
-    const int row = 32 * qd + lane;
-    int cc = 0;
-    bool stop = false;
-    for (int s = sb; s < se && !stop; ++s) {
-      const int4 sg = segs[s];
-      const int i = sg.y * RTM + row;
-      const float rs = __int_as_float((127 + (i < n ? rowexp[i] : 0) - 14) << 23);
-      float2* dst = acc_out + (size_t)s * NC * RTM + row;
-      for (int c0 = sg.z; c0 < sg.w; c0 += RCK, ++cc) {
-        if (*(volatile int*)&S.abort || !mbar_wait(&S.tfull, cc & 1)) {
-          if (lane == 0) {
-            atomicExch(err, 25);
-            S.abort = 1;
-          }
-          stop = true;
-          break;
-        }
-        __syncwarp();
-        tc_fence_after();
-        const bool first = c0 == sg.z;
-        const uint32_t base = tmem + ((uint32_t)(32 * qd) << 16);
-#pragma unroll 1
-        for (int cb = 0; cb < NC; cb += 16) {
-          float v0[16], v1[16], v2[16], v3[16];
-          tmem_ld16(base + (uint32_t)(0 * NC + cb), v0);
-          tmem_ld16(base + (uint32_t)(1 * NC + cb), v1);
-          tmem_ld16(base + (uint32_t)(2 * NC + cb), v2);
-          tmem_ld16(base + (uint32_t)(3 * NC + cb), v3);
-#pragma unroll
-          for (int r = 0; r < 16; ++r) {
-            const int col = cb + r;
-            // levels 2 + 3 exactly (TwoSum), then the smaller levels
-            const float sh = v0[r] + v1[r];
-            const float bv = sh - v0[r];
-            float sl = (v0[r] - (sh - bv)) + (v1[r] - bv);
-            sl += v2[r] + v3[r];
-            const float fs = __int_as_float((127 + P.fx[col]) << 23);  // 2^F_col
-            df val = quick(sh, sl);
-            val.h *= rs * fs;
-            val.l *= rs * fs;
-            float2* p = dst + (size_t)col * RTM;
-            if (!first) {
-              const float2 o = *p;
-              val = dadd(val, df{o.x, o.y});
-            }
-            *p = make_float2(val.h, val.l);
-          }
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&S.tempty);
       }
     }
   }

@@ -14,12 +14,14 @@
 // stored times omega (the node distance is the Hankel argument) and the
 // per-node factors of each entry are folded into per-node vectors; and
 //  * Hankel's asymptotic expansion (A&S 9.2.5, 9.2.9, 9.2.10) carries its
-//    leading terms in double-float and the small corrections in FP32 (for
-//    omega r >= 40 the dropped terms are below 1e-13);
+//    leading terms in double-float and the small corrections in FP32: for
+//    omega r >= 40 four terms of P and Q, for 20 <= omega r < 40 (pairs next to
+//    the band) seven and their first corrections in double-float; the dropped
+//    terms are below 1e-13;
 //  * the phase omega r - pi/4 is reduced modulo 2 pi with a three-part
 //    constant, then sin / cos come from a 64-entry double-float table of
 //    sin(j pi/32), cos(j pi/32) and Taylor series of the remainder |d| <= pi/64;
-//  * pairs with omega r < 40 come from a band of entries evaluated in FP64.
+//  * pairs with omega r < 20 come from a band of entries evaluated in FP64.
 // Source sums use Dot2 (Ogita, Rump & Oishi) inside each 32-source tile and
 // double-float additions across tiles; the densities are converted to
 // double-float once per matvec.  Relative accuracy ~1e-13 (tests ask 1e-11).
@@ -45,7 +47,8 @@ namespace {
 constexpr int DTI = 64;
 constexpr int DTJ = 32;
 constexpr int DNT = 256;
-constexpr float kXD = 40.0f;   // asymptotic expansion in this kernel for omega r >= 40
+constexpr float kXD = 20.0f;   // asymptotic expansion in this kernel for omega r >= 20
+constexpr float kXS = 40.0f;   // short series (leading terms in FP32) for omega r >= 40
 
 struct df {
   float h, l;
@@ -159,7 +162,7 @@ struct df_params {
   const int* fx;                // tensor-core residual: exponent of each accumulator column
 };
 
-// Hankel values of one far pair (x = omega r >= 40) in double-float, without
+// Hankel values of one far pair (x = omega r >= 20) in double-float, without
 // the common factor c0 x^(-1/2): (dx, dy) = omega (z_i - z_j), 1 / x,
 // ra = x^(-1/2), and j_m, y_m with J_m = c0 ra j_m, Y_m = c0 ra y_m
 struct df_hankel {
@@ -196,17 +199,47 @@ __device__ __forceinline__ df_hankel hankel_df(float4 gi, float4 gj,
   const df sn = dadd(dmul(sj, cd), dmul(cj, sd));
   const df cs = dsub(dmul(cj, cd), dmul(sj, sd));
   // asymptotic expansion, t = 1/x
-  const float t2 = t.h * t.h;
-  const df P0 = quick(1.0f, t2 * (-0.0703125f + t2 * (0.112152099609375f +
-                              t2 * (-0.5725014209747314f + t2 * 6.074042001273483f))));
-  const df P1 = quick(1.0f, t2 * (0.1171875f + t2 * (-0.144195556640625f +
-                              t2 * (0.6765925884246826f + t2 * -6.883914268109947f))));
-  const df Q0 = dadd({-0.125f * t.h, -0.125f * t.l},
-                     {t.h * t2 * (0.0732421875f + t2 * (-0.22710800170898438f +
-                                  t2 * 1.7277275025844574f)), 0.f});
-  const df Q1 = dadd(dmulf(t, 0.375f),
-                     {t.h * t2 * (-0.1025390625f + t2 * (0.2775764465332031f +
-                                  t2 * -1.993531733751297f)), 0.f});
+  df P0, P1, Q0, Q1;
+  if (x.h >= kXS) {
+    // x >= 40: terms up to t^8 (P) and t^7 (Q), the corrections in FP32
+    const float t2 = t.h * t.h;
+    P0 = quick(1.0f, t2 * (-0.0703125f + t2 * (0.112152099609375f +
+                     t2 * (-0.5725014209747314f + t2 * 6.074042001273483f))));
+    P1 = quick(1.0f, t2 * (0.1171875f + t2 * (-0.144195556640625f +
+                     t2 * (0.6765925884246826f + t2 * -6.883914268109947f))));
+    Q0 = dadd({-0.125f * t.h, -0.125f * t.l},
+              {t.h * t2 * (0.0732421875f + t2 * (-0.22710800170898438f +
+                           t2 * 1.7277275025844574f)), 0.f});
+    Q1 = dadd(dmulf(t, 0.375f),
+              {t.h * t2 * (-0.1025390625f + t2 * (0.2775764465332031f +
+                           t2 * -1.993531733751297f)), 0.f});
+  } else {
+    // 20 <= x < 40 (pairs next to the band only): terms up to t^14 (P) and
+    // t^15 (Q), the first omitted one below 1e-14 at x = 20; the t^2 term of P
+    // and the t^3 term of Q (up to 2e-4 and 1e-5 there) in double-float
+    const df u2 = dmul(t, t), u3 = dmul(u2, t);
+    const float u = u2.h;
+    const float p0 = u * u * (0.112152099609375f + u * (-0.5725014209747314f +
+                     u * (6.074042001273483f + u * (-110.01714026924674f +
+                     u * (3038.090510922384f + u * -118838.42625678325f)))));
+    const float p1 = u * u * (-0.144195556640625f + u * (0.6765925884246826f +
+                     u * (-6.883914268109947f + u * (121.59789187653587f +
+                     u * (-3302.2722944808525f + u * 127641.2726461746f)))));
+    const float q0 = u3.h * u * (-0.22710800170898438f + u * (1.7277275025844574f +
+                     u * (-24.380529699556064f + u * (551.3358961220206f +
+                     u * (-18257.755474293175f + u * 832859.3040162893f)))));
+    const float q1 = u3.h * u * (0.2775764465332031f + u * (-1.993531733751297f +
+                     u * (27.248827311268542f + u * (-603.8440767050702f +
+                     u * (19718.37591223663f + u * -890297.8767070678f)))));
+    P0 = dadd({1.0f, 0.f}, dmulf(u2, -0.0703125f));
+    P0 = quick(P0.h, P0.l + p0);
+    P1 = dadd({1.0f, 0.f}, dmulf(u2, 0.1171875f));
+    P1 = quick(P1.h, P1.l + p1);
+    Q0 = dadd({-0.125f * t.h, -0.125f * t.l}, dmulf(u3, 0.0732421875f));
+    Q0 = quick(Q0.h, Q0.l + q0);
+    Q1 = dadd(dmulf(t, 0.375f), dmulf(u3, -0.1025390625f));
+    Q1 = quick(Q1.h, Q1.l + q1);
+  }
   df_hankel H;
   H.dx = dx;
   H.dy = dy;

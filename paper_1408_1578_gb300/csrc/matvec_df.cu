@@ -889,23 +889,23 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
 // 1e-4 margin (their relative error is ~1e-6); 0 for rows without far pairs.
 template <int KIND>
 __global__ void __launch_bounds__(256)
-k_rowexp(int n, int b, omega32 W, geo32 g, const float* __restrict__ w32, int* __restrict__ rowexp) {
+k_rowexp(int n, int b, const float4* __restrict__ pk, const float2* __restrict__ wkt,
+         int* __restrict__ rowexp) {
   __shared__ float red[4][64];
   const int il = threadIdx.x % 64, qd = threadIdx.x / 64;
   const int i = blockIdx.x * 64 + il;
   float m = 0.f;
   if (i < n) {
-    const float txh = g.xh[i], txl = g.xl[i], tyh = g.yh[i], tyl = g.yl[i];
-    const float tnx = g.nx[i], tny = g.ny[i], tsp = g.sp[i];
+    // the folded FP32 entries of the fused tensor-core kernel (packed
+    // per-node vectors; source j is the same for a whole warp)
+    const float4 tg = pk[i];
+    const float4 tq = KIND == RK_DP ? pk[2 * n + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const omega32 none{};
     for (int j = qd; j < n; j += 4) {
       int d = i - j;
       if (d < 0) d += n;
       if (d <= b || d >= n - b) continue;
-      float2 a, bb;
-      pair_entries_fp32<KIND == RK_SOFT ? 0 : 1>(W, txh, txl, tyh, tyl, tnx, tny, tsp, g.xh[j],
-                                                 g.xl[j], g.yh[j], g.yl[j], g.nx[j], g.ny[j],
-                                                 g.sp[j], w32[d], a, bb);
-      if (KIND == RK_DP) a = bb;
+      const float2 a = entry_folded32<KIND>(none, tg, tq, pk[j], pk[n + j], wkt[i - j + n].x);
       m = fmaxf(m, fmaxf(fabsf(a.x), fabsf(a.y)));
     }
   }
@@ -1387,22 +1387,15 @@ void df_prepare(cfie_op* op) {
   if (op->layout != CFIE_STORED) {   // stored operators get them from the assembly
     op->df_rowexp.reserve(sizeof(int) * (size_t)n * (hard ? 2 : 1));
     float* base = op->geo32.as<float>();
-    omega32 W{};
-    W.wh = (float)op->omega;
-    W.wl = (float)(op->omega - (double)W.wh);
-    W.winv = (float)(1.0 / op->omega);
-    W.eta = (float)op->eta;
-    W.h = (float)op->h;
+    const float4* pk = reinterpret_cast<const float4*>(base + geo32_pack_offset(n));
+    const float2* wkt = reinterpret_cast<const float2*>(base + geo32_wk_offset(n));
     const unsigned g = (unsigned)((n + 63) / 64);
     if (hard) {
-      k_rowexp<RK_S><<<g, 256, 0, st>>>(n, b, W, geo32_at(base, n), base + 7 * n,
-                                        op->df_rowexp.as<int>());
+      k_rowexp<RK_S><<<g, 256, 0, st>>>(n, b, pk, wkt, op->df_rowexp.as<int>());
       CFIE_CHECK_LAUNCH();
-      k_rowexp<RK_DP><<<g, 256, 0, st>>>(n, b, W, geo32_at(base, n), base + 7 * n,
-                                         op->df_rowexp.as<int>() + n);
+      k_rowexp<RK_DP><<<g, 256, 0, st>>>(n, b, pk, wkt, op->df_rowexp.as<int>() + n);
     } else {
-      k_rowexp<RK_SOFT><<<g, 256, 0, st>>>(n, b, W, geo32_at(base, n), base + 7 * n,
-                                           op->df_rowexp.as<int>());
+      k_rowexp<RK_SOFT><<<g, 256, 0, st>>>(n, b, pk, wkt, op->df_rowexp.as<int>());
     }
     CFIE_CHECK_LAUNCH();
   }

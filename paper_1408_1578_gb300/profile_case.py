@@ -2,7 +2,7 @@
 profilers (ncu) and quick timing.  Prints the per-class kernel times.
 
     python -m paper_1408_1578_gb300.profile_case --path fused    [--n 8192] [--nrhs 64]
-    python -m paper_1408_1578_gb300.profile_case --path residual [--n 8192] [--nrhs 64]
+    python -m paper_1408_1578_gb300.profile_case --path residual [--n 8192] [--nrhs 64] [--variant 1|2]
     python -m paper_1408_1578_gb300.profile_case --path fp64     [--n 4096] [--nrhs 16] [--bc hard]
     python -m paper_1408_1578_gb300.profile_case --path stored   [--n 8192] [--nrhs 32]
     python -m paper_1408_1578_gb300.profile_case --path batch    [--count 16]
@@ -29,7 +29,9 @@ def main():
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--nrhs", type=int, default=None)
     p.add_argument("--bc", default="soft", choices=["soft", "hard"])
-    p.add_argument("--variant", type=int, default=0, help="fused: 0 autotuned, 1, 2")
+    p.add_argument("--variant", type=int, default=0,
+                   help="fused: summation variant (0 autotuned, 1, 2); residual: 1 CUDA-core "
+                        "Dot2 sums, 2 sliced tensor-core sums (0 automatic)")
     p.add_argument("--count", type=int, default=16, help="batch: operators")
     p.add_argument("--repeat", type=int, default=5)
     a = p.parse_args()
@@ -65,6 +67,8 @@ def main():
                              layout="stored" if prec == "tensor" else "matrix_free")
         if a.variant and a.path == "fused":
             op.set_variant(a.variant)
+        if a.variant and a.path == "residual":
+            op.set_residual_variant(a.variant)
         X = torch.from_numpy(inputs.random_density(n, nrhs, seed=1)).cuda()
         Y = torch.empty_like(X)
         if a.path == "solve":

@@ -900,12 +900,11 @@ k_rowexp(int n, int b, const float4* __restrict__ pk, const float2* __restrict__
     // per-node vectors; source j is the same for a whole warp)
     const float4 tg = pk[i];
     const float4 tq = KIND == RK_DP ? pk[2 * n + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const omega32 none{};
     for (int j = qd; j < n; j += 4) {
       int d = i - j;
       if (d < 0) d += n;
       if (d <= b || d >= n - b) continue;
-      const float2 a = entry_folded32<KIND>(none, tg, tq, pk[j], pk[n + j], wkt[i - j + n].x);
+      const float2 a = entry_folded32<KIND>(tg, tq, pk[j], pk[n + j], wkt[i - j + n].x);
       m = fmaxf(m, fmaxf(fabsf(a.x), fabsf(a.y)));
     }
   }

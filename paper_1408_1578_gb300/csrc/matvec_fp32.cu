@@ -581,8 +581,6 @@ void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs) {
   P.b = op->band_b;
   P.nrhs = nrhs;
   P.wh = (float)op->omega;
-  P.wl = (float)(op->omega - (double)P.wh);
-  P.winv = (float)(1.0 / op->omega);
   P.eta = (float)op->eta;
   P.h = (float)op->h;
   P.g = geo32{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 6 * n};

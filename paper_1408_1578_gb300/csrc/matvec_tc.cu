@@ -48,10 +48,8 @@ constexpr int NPROD = 16;    // producer warps
 constexpr int WTMA = NPROD, WMMA = NPROD + 1, WEPI0 = NPROD + 2;
 constexpr int TNT = (NPROD + 6) * 32;
 
-struct tc_params : omega32 {
+struct tc_params {
   int n, b, ktiles;
-  geo32 g;
-  const float* w32;
   const float2* wext;    // Kress table / (pi h) at i - j + n, paired with the next source's
   const float4* pk;      // packed coordinates, source factors, target factors (n each)
   const float2* band;    // near entries of the evaluated kind (soft A, or S, or D')
@@ -198,7 +196,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
             float2 e[2];
 #pragma unroll
             for (int u = 0; u < 2; ++u)
-              e[u] = entry_folded32<KIND>(P, tg, tn, sc[u], sn[u], u ? wv[q].y : wv[q].x);
+              e[u] = entry_folded32<KIND>(tg, tn, sc[u], sn[u], u ? wv[q].y : wv[q].x);
             store_split2(a0, a1, a2, a3, sw64(il, jp), e[0], e[1]);
           }
         } else {
@@ -220,7 +218,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
                 if (dd != INT_MAX)
                   a = P.band[(size_t)i * (2 * P.b + 1) + dd + P.b];
                 else
-                  a = entry_folded32<KIND>(P, tg, tn, sc[u], sn[u], P.wext[i - jj + n].x);
+                  a = entry_folded32<KIND>(tg, tn, sc[u], sn[u], P.wext[i - jj + n].x);
               }
               e[u] = a;
             }
@@ -434,17 +432,10 @@ void run_fused(cfie_op* op, const double2* x, double2* y, int r0, int nr) {
   }
   prep_b_planes(op->ctx, n, pitch, NP, nr, x + (size_t)r0 * n, T.bt.as<__nv_bfloat16>());
   tc_params P{};
-  P.wh = (float)op->omega;
-  P.wl = (float)(op->omega - (double)P.wh);
-  P.winv = (float)(1.0 / op->omega);
-  P.eta = (float)op->eta;
-  P.h = (float)op->h;
   P.n = n;
   P.b = op->band_b;
   P.ktiles = (n + TBK - 1) / TBK;
   float* base = op->geo32.as<float>();
-  P.g = geo32_at(base, n);
-  P.w32 = base + 7 * n;
   P.wext = reinterpret_cast<const float2*>(base + geo32_wk_offset(n));
   P.pk = reinterpret_cast<const float4*>(base + geo32_pack_offset(n));
   // the FP32 band holds the soft entries, or S then D' for the hard operator

@@ -30,9 +30,10 @@ inline geo32 geo32_at(float* base, int n) {
                base + 6 * n};
 }
 
-// omega = wh + wl (two-float), winv ~ 1/omega, eta, h = 2 pi / n
+// omega (FP32), eta, h = 2 pi / n: the operator constants of the generic
+// entries (the phase comes from the omega-scaled coordinates)
 struct omega32 {
-  float wh, wl, winv, eta, h;
+  float wh, eta, h;
 };
 
 constexpr float kX0 = 16.0f;  // asymptotic expansion used for omega r >= kX0
@@ -165,8 +166,8 @@ enum { KIND_SOFT = 0, KIND_S = 1, KIND_DP = 2 };
 //   D':    re = D (y1 + wk j1),              im = -D j1
 // with D = omega (nu_i . (z_i - z_j)) / |z'_i| hq c0 |z'_j| ra / r.
 template <int KIND>
-__device__ __forceinline__ float2 entry_folded32(const omega32& P, float4 tg, float4 tq, float4 sc,
-                                                 float4 sq, float wk) {
+__device__ __forceinline__ float2 entry_folded32(float4 tg, float4 tq, float4 sc, float4 sq,
+                                                 float wk) {
   const pair_phase f = pair_phase32(tg.x, tg.y, tg.z, tg.w, sc.x, sc.y, sc.z, sc.w);
   float j0, y0, j1, y1;
   hankel_asym32(f.xinv, f.s, f.c, j0, y0, j1, y1);

@@ -571,8 +571,6 @@ void stored_prepare(cfie_op* op) {
   float* base = op->geo32.as<float>();
   omega32 W{};
   W.wh = (float)op->omega;
-  W.wl = (float)(op->omega - (double)W.wh);
-  W.winv = (float)(1.0 / op->omega);
   W.eta = (float)op->eta;
   W.h = (float)op->h;
   const dim3 grid(nblk(pitch), n);

@@ -169,7 +169,7 @@ cfie_status cfie_apply_fp64_static(cfie_op* op, const void* x_dev, void* y_dev, 
  * true residuals: for sound-soft CFIE_FP32_REFINED / CFIE_TENSOR_REFINED
  * operators the same entries as cfie_apply_fp64 evaluated in double-float
  * arithmetic on the FP32 pipe (hi + lo pairs, error-free products and sums;
- * ~1e-13 relative), otherwise the FP64 matvec.  Arguments as cfie_apply. */
+ * a few 1e-12 relative), otherwise the FP64 matvec.  Arguments as cfie_apply. */
 cfie_status cfie_apply_residual(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
 
 /* Solve A x = f for nrhs independent right-hand sides by restarted GMRES
@@ -190,7 +190,7 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
                              int restart, int maxit, int* iters_out, double* relres_out);
 
 /* How the refined precisions compute true residuals (cfie_apply_residual and
- * inside cfie_gmres_solve), all to ~1e-13 relative: variant 1 evaluates the
+ * inside cfie_gmres_solve), all to a few 1e-12 relative: variant 1 evaluates the
  * entries in double-float (FP32 pairs) and sums with compensated Dot2 on the
  * CUDA cores; variant 2 evaluates the far entries in double-float (for the
  * sound-hard operator S and D' in separate passes), splits entries and

@@ -24,7 +24,8 @@
 //  * pairs with omega r < 20 come from a band of entries evaluated in FP64.
 // Source sums use Dot2 (Ogita, Rump & Oishi) inside each 32-source tile and
 // double-float additions across tiles; the densities are converted to
-// double-float once per matvec.  Relative accuracy ~1e-13 (tests ask 1e-11).
+// double-float once per matvec.  Relative accuracy a few 1e-12 (the FP32
+// corrections of P and Q at omega r ~ 40 bound it; tests ask 1e-11).
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -202,7 +203,9 @@ __device__ __forceinline__ df_hankel hankel_df(float4 gi, float4 gj,
   df P0, P1, Q0, Q1;
   if (x.h >= kXS) {
     // x >= 40: terms up to t^8 (P) and t^7 (Q), the corrections in FP32
-    const float t2 = t.h * t.h;
+    // (t^2 with the lo part of t: its FP32 error, times the 0.07 t^2 term,
+    // stays below 3e-12 of P)
+    const float t2 = fmaf(t.h, t.h, 2.0f * t.h * t.l);
     P0 = quick(1.0f, t2 * (-0.0703125f + t2 * (0.112152099609375f +
                      t2 * (-0.5725014209747314f + t2 * 6.074042001273483f))));
     P1 = quick(1.0f, t2 * (0.1171875f + t2 * (-0.144195556640625f +

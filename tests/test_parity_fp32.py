@@ -33,6 +33,11 @@ CASES = [
     ("star", {"a": [0, 0, 0, 0, 0.3], "b": [0] * 5}, 1502, 120.0, "hard", 16),
     ("star", {"a": [0.03, -0.02, 0.04], "b": [0.01, 0.05, -0.03]}, 3000, 450.0, "soft", 64),
     ("ellipse", {"a": 1.0, "b": 0.5}, 1000, 90.0, "soft", 9),
+    # large scaled coordinates: omega |z| up to 2^14 (coarse coordinate grid,
+    # phase error ~2e-6 rad), both summation forms, both conditions
+    ("circle", {}, 2048, 12000.0, "soft", 3),
+    ("circle", {}, 2048, 12000.0, "soft", 12),
+    ("circle", {}, 2048, 12000.0, "hard", 8),
     # small problems: the near band covers every pair
     ("circle", {}, 64, 2.0, "soft", 2),
     ("circle", {}, 64, 2.0, "hard", 2),

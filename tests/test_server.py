@@ -81,3 +81,17 @@ def test_bad_requests_are_refused():
     with pytest.raises(cfie.CfieError):
         srv.submit([0.1], [0.0], 1000, 10.0, precision="tensor")
     srv.close()
+
+
+def test_failed_request_reports_its_error():
+    """A request the FP32 form refuses (omega so low that every pair is in the
+    near band) finishes with that status and its message, not a crash."""
+    from paper_1408_1578_gb300 import cfie
+    srv = cfie.Server(0, hbm_budget_bytes=8 << 30, slots=1)
+    t = srv.submit([0.1], [0.0], 65536, 0.01)
+    assert srv.wait_all(300)
+    out = srv.poll(t)
+    assert out["done"] and out["status"] == cfie.CFIE_EINVAL
+    assert "band" in out["error"]
+    srv.release(t)
+    srv.close()

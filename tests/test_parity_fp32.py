@@ -54,10 +54,15 @@ def test_fp32_matvec_parity(ctx, kind, params, n, omega, bc, nrhs):
     op.apply(to_dev(X), y)
     err = np.max(col_rel(to_host(y), (A @ X.T).T))
     assert err < TOL_FP32, err
-    # the same operator's FP64 matvec (used for true residuals) stays FP64-exact
+    # the same operator's FP64 matvec (used for true residuals) stays FP64-exact:
+    # 1e-12, or the FP64 resolution of the phase omega r when that is coarser
+    # (a few roundings of 2^-53 relative on omega r up to omega x diameter:
+    # ~1e-11 for the omega = 12000 circle)
     y64 = empty(nrhs, n)
     op.apply_fp64(to_dev(X), y64)
-    assert np.max(col_rel(to_host(y64), (A @ X.T).T)) < 1e-12
+    diam = np.hypot(*np.ptp(c.z, axis=0))      # bounding-box diagonal >= diameter
+    tol64 = max(1e-12, 4e-16 * omega * diam)
+    assert np.max(col_rel(to_host(y64), (A @ X.T).T)) < tol64
 
 
 def test_fp32_matvec_plane_wave_data(ctx):

@@ -34,4 +34,12 @@ operators  Bessel values, S / D / D' / N Nystrom matrices, CFIE matrices,
            row-sampled operators, spectral derivative, plane-wave data
 solvers    LU solve and restarted GMRES (modified Gram-Schmidt, Givens)
 field      off-surface representation formulas for the scattered field
+directional  the directional preconditioner of Section 2 (sound soft): segment
+           partition, flat diagonal blocks B, partial Fourier matrices U, the
+           sparse E of rank-1 block coefficients, eq. (eapp); with the
+           arclength sampling it needs (geometry.Arclength).  Its algebra
+           (eq. aug / fac / esol), entry function, interpolation and
+           arclength map are pinned by tests/test_oracle_directional.py; the
+           quality of the data-sparse approximation is checked only through
+           its effect on GMRES iteration counts (Table 1 gives no entries).
 """

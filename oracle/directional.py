@@ -37,6 +37,13 @@ Section 2.2 (preconditioner)
 The entries of M at points off the nodes (Chebyshev grids) come from the same
 Kress-Nystrom entry formula with the weight R_d replaced by its trigonometric
 interpolant R(tau), so that on the nodes they are the matrix entries.
+
+Parity: the algebra (eq. aug, fac, esol), the entry function, the Chebyshev
+interpolation, the curvature and the partition rules are pinned by
+tests/test_oracle_directional.py.  The diagonal of B_l and the values e_ij are
+parity unpinned beyond that: the paper prints no intermediate values, so they
+are checked only through the interpolation's exactness, the closeness of
+B + U E U^t to M and the cut in GMRES iterations (Table 1).
 """
 import numpy as np
 import scipy.linalg as sla

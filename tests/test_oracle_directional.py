@@ -50,6 +50,15 @@ def test_arclength_curve_point_source(ellipse_arc, bc):
     assert cf.rel(u, -cf.green(w, pts, x0)) < 1e-10
 
 
+def test_curvature_of_the_ellipse(ellipse_arc):
+    """kappa = a b / (a^2 sin^2 t + b^2 cos^2 t)^(3/2) at the arclength nodes."""
+    n = 256
+    c = ellipse_arc.curve(n)
+    t = ellipse_arc.t_of_s(ellipse_arc.L * np.arange(n) / n)
+    want = 0.5 / (np.sin(t) ** 2 + 0.25 * np.cos(t) ** 2) ** 1.5
+    assert np.max(np.abs(directional.curvature(c) - want)) < 1e-12
+
+
 def test_partition_rules(ellipse_arc):
     q, p = 4, 8
     c = ellipse_arc.curve(4**q * p)

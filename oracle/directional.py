@@ -50,7 +50,6 @@ import scipy.linalg as sla
 import scipy.sparse as sps
 import scipy.sparse.linalg as spla
 
-from .geometry import Arclength
 from .kress import kress_weights
 from .operators import EULER_GAMMA, bessel01
 

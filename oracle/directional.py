@@ -38,12 +38,16 @@ The entries of M at points off the nodes (Chebyshev grids) come from the same
 Kress-Nystrom entry formula with the weight R_d replaced by its trigonometric
 interpolant R(tau), so that on the nodes they are the matrix entries.
 
+Sound hard (eq. 2): the same construction with the nodal least-squares e_ij
+and the matrix's own diagonal blocks (see Directional).
+
 Parity: the algebra (eq. aug, fac, esol), the entry function, the Chebyshev
-interpolation, the curvature and the partition rules are pinned by
-tests/test_oracle_directional.py.  The diagonal of B_l and the values e_ij are
-parity unpinned beyond that: the paper prints no intermediate values, so they
-are checked only through the interpolation's exactness, the closeness of
-B + U E U^t to M and the cut in GMRES iterations (Table 1).
+interpolation, the curvature, the partition rules and the e_ij of eq. (entry)
+against the least-squares constants over the nodes are pinned by
+tests/test_oracle_directional.py.  The diagonal of the flat B_l is parity
+unpinned beyond that (the paper prints no intermediate values): it is checked
+through the closeness of B + U E U^t to M and the cut in GMRES iterations
+(Tables 1 and 3).
 """
 import numpy as np
 import scipy.linalg as sla
@@ -156,19 +160,18 @@ def soft_entries(n, omega, eta, zx, zy, nuy, speedy, tx, ty):
     return kress_weight_function(n, dt) * K1 + h * (K - K1 * logf)
 
 
-def flat_block(n, level, p, omega, eta, L):
-    """B_l: the sound-soft entries on a straight segment of 2^l p nodes with
-    the spacing and speed L / (2 pi) of the curve's arclength discretisation
-    (the double-layer kernel and the curvature term vanish on a line)."""
+def flat_single_layer(n, level, p, omega, L):
+    """The single-layer (S) Kress-Nystrom block on a straight segment of 2^l p
+    nodes with the spacing and speed L / (2 pi) of the curve's arclength
+    discretisation."""
     cnt = 2**level * p
     h = 2.0 * np.pi / n
-    g = L / (2.0 * np.pi)                 # |z'(sigma)|
+    g = L / (2.0 * np.pi)
     R = kress_weights(n)
     a = np.arange(cnt)
     d = a[:, None] - a[None, :]
     off = d != 0
-    r = np.abs(d) * h * g
-    r_safe = np.where(off, r, 1.0)
+    r_safe = np.where(off, np.abs(d) * h * g, 1.0)
     j0, y0, _, _ = bessel01(omega * r_safe)
     M = 0.25j * (j0 + 1j * y0) * g
     M1 = -(1.0 / (4 * np.pi)) * j0 * g
@@ -177,8 +180,35 @@ def flat_block(n, level, p, omega, eta, L):
     m1 = -g / (4 * np.pi)
     m2 = (0.25j - EULER_GAMMA / (2 * np.pi) - np.log(omega * g / 2.0) / (2 * np.pi)) * g
     S[~off] = R[0] * m1 + h * m2
-    B = -1j * eta * S
+    return S
+
+
+def flat_block_hard(n, level, p, omega, eta, L):
+    """B_l of the sound-hard operator (eq. 2) on a straight segment: D' vanishes
+    (the normal is orthogonal to every chord) and Maue's identity reduces to
+    N = d/ds S d/ds + omega^2 S (n1^2 + n2^2 = 1); d/ds is the curve's spectral
+    derivative (trigonometric interpolant on all n nodes, Nyquist mode zeroed)
+    restricted to the segment, divided by the speed L / (2 pi)."""
+    from .operators import spectral_derivative
+    cnt = 2**level * p
+    g = L / (2.0 * np.pi)
+    S = flat_single_layer(n, level, p, omega, L)
+    e0 = np.zeros(n)
+    e0[0] = 1.0
+    col = spectral_derivative(e0).real           # column 0 of the circulant d/dt
+    a = np.arange(cnt)
+    Dt = col[(a[:, None] - a[None, :]) % n] / g
+    B = (Dt @ S @ Dt + omega**2 * S) / (1j * eta)
     B[np.diag_indices(cnt)] += 0.5
+    return B
+
+
+def flat_block(n, level, p, omega, eta, L):
+    """B_l: the sound-soft entries on a straight segment of 2^l p nodes with
+    the spacing and speed L / (2 pi) of the curve's arclength discretisation
+    (the double-layer kernel and the curvature term vanish on a line)."""
+    B = -1j * eta * flat_single_layer(n, level, p, omega, L)
+    B[np.diag_indices(B.shape[0])] += 0.5
     return B
 
 
@@ -187,10 +217,29 @@ def flat_block(n, level, p, omega, eta, L):
 # ---------------------------------------------------------------------------
 
 class Directional:
-    """Setup of Section 2 for the sound-soft operator on an arclength-sampled
-    curve (`arc`: geometry.Arclength, n = 4^q p nodes)."""
+    """Setup of Section 2 on an arclength-sampled curve (`arc`:
+    geometry.Arclength, n = 4^q p nodes).
 
-    def __init__(self, arc, q, p, omega, eta=None, m_leaf=2, m_c=10, t_keep=4):
+    bc = "soft" builds E from Chebyshev samples of the entry function (eq.
+    entry).  For bc = "hard" the Maue-discretised N has no pointwise kernel at
+    off-node points, so each e_ij is the least-squares constant over the nodes
+    of the block itself (the quantity eq. entry approximates with m_c^2
+    samples): the mean of M~_ij over P_i x P_j, taken from the dense matrix
+    `A`; e_from = "nodes" does the same for the soft operator.
+
+    The diagonal blocks are the flat-segment B_l (b_from = "flat", the default
+    for soft) or the matrix's own diagonal blocks M_jj (b_from = "matrix", the
+    default for hard: the flat restriction of Maue's N, with the curve's
+    spectral derivative cut to the segment, misses 15-20 % of the block and
+    slows GMRES down instead of speeding it up)."""
+
+    def __init__(self, arc, q, p, omega, eta=None, m_leaf=2, m_c=10, t_keep=4, bc="soft",
+                 A=None, e_from=None, b_from=None):
+        self.bc = bc
+        e_from = e_from or ("chebyshev" if bc == "soft" else "nodes")
+        b_from = b_from or ("flat" if bc == "soft" else "matrix")
+        if (e_from == "nodes" or b_from == "matrix") and A is None:
+            raise ValueError("the nodal E and the matrix blocks need the dense matrix A")
         self.arc, self.q, self.p = arc, q, p
         self.omega = omega
         self.eta = omega if eta is None else eta
@@ -213,19 +262,26 @@ class Directional:
         self.m = m
         # B blocks (one per level) and their inverses
         levels = sorted(set(self.level.tolist()))
-        self.B = {l: flat_block(n, l, p, omega, self.eta, L) for l in levels}
-        self.Binv = {l: np.linalg.inv(self.B[l]) for l in levels}
+        fb = flat_block if bc == "soft" else flat_block_hard
+        if b_from == "flat":
+            Bl = {l: fb(n, l, p, omega, self.eta, L) for l in levels}
+            Bli = {l: np.linalg.inv(Bl[l]) for l in levels}
+            self.Bseg = [Bl[l] for l in self.level]
+            self.Binv = [Bli[l] for l in self.level]
+        else:
+            self.Bseg = [A[f:f + c, f:f + c] for f, c in zip(self.first, self.count)]
+            self.Binv = [np.linalg.inv(b) for b in self.Bseg]
         # frequency grids and partial Fourier matrices U_i
         self.K = [frequency_grid(l, omega) for l in self.level]
         self.koff = np.concatenate([[0], np.cumsum([k.size for k in self.K])])
         rho = [s_nodes[f:f + c] - cs for f, c, cs in zip(self.first, self.count, centre_s)]
         self.U = [np.exp(1j * np.outer(r, k)) for r, k in zip(rho, self.K)]
         # E (eq. entry), one non-zero per off-diagonal block
-        self.E = self._build_E(m_c)
+        self.E = self._build_E(m_c) if e_from == "chebyshev" else self._build_E_nodes(A)
         # S_i, T_i, the thresholded T~ and W~ = E + antidiag(T)
         self.T = []
         for i in range(m):
-            Si = self.U[i].T @ self.Binv[self.level[i]] @ self.U[i]
+            Si = self.U[i].T @ self.Binv[i] @ self.U[i]
             self.T.append(np.linalg.inv(Si))
         self.Tt = [self._threshold(Ti, t_keep * Ti.shape[0]) for Ti in self.T]
         self.W = self.E.tolil()
@@ -263,10 +319,7 @@ class Directional:
             for j in range(self.m):
                 if i == j:
                     continue
-                a = self.centre[i] - self.centre[j]
-                a = a / np.hypot(a[0], a[1])
-                ki = round_to_grid(omega * a @ self.tangent[i], self.level[i], omega)
-                kj = round_to_grid(-omega * a @ self.tangent[j], self.level[j], omega)
+                ki, kj = self._pair_wavenumbers(i, j)
                 self.kidx[(i, j)] = (ki, kj)
                 zi, _, ti = pts[i]
                 zj, nuj, tj = pts[j]
@@ -275,6 +328,31 @@ class Directional:
                 Uj = np.exp(1j * self.K[j][kj] * (grids[j] - self.centre_s[j]))
                 Mt = Mij / (Ui[:, None] * Uj[None, :])
                 E[self.koff[i] + ki, self.koff[j] + kj] = avg[i] @ Mt @ avg[j]
+        return E.tocsr()
+
+    def _pair_wavenumbers(self, i, j):
+        a = self.centre[i] - self.centre[j]
+        a = a / np.hypot(a[0], a[1])
+        ki = round_to_grid(self.omega * a @ self.tangent[i], self.level[i], self.omega)
+        kj = round_to_grid(-self.omega * a @ self.tangent[j], self.level[j], self.omega)
+        return ki, kj
+
+    def _build_E_nodes(self, A):
+        """e_ij = mean of M_ij / (U_i(:, k^i) U_j(:, k^j)^t) over the nodes: the
+        least-squares constant of the rank-1 form on the block itself."""
+        K_tot = int(self.koff[-1])
+        E = sps.lil_matrix((K_tot, K_tot), dtype=np.complex128)
+        self.kidx = {}
+        for i in range(self.m):
+            fi, ci = self.first[i], self.count[i]
+            for j in range(self.m):
+                if i == j:
+                    continue
+                fj, cj = self.first[j], self.count[j]
+                ki, kj = self._pair_wavenumbers(i, j)
+                self.kidx[(i, j)] = (ki, kj)
+                Mt = A[fi:fi + ci, fj:fj + cj] / np.outer(self.U[i][:, ki], self.U[j][:, kj])
+                E[self.koff[i] + ki, self.koff[j] + kj] = Mt.mean()
         return E.tocsr()
 
     @staticmethod
@@ -288,8 +366,8 @@ class Directional:
     # block operators ------------------------------------------------------
     def _B_inv(self, x):
         y = np.empty_like(x)
-        for f, c, l in zip(self.first, self.count, self.level):
-            y[f:f + c] = self.Binv[l] @ x[f:f + c]
+        for f, c, bi in zip(self.first, self.count, self.Binv):
+            y[f:f + c] = bi @ x[f:f + c]
         return y
 
     def _U(self, p):
@@ -313,7 +391,7 @@ class Directional:
 
     # dense forms (tests) --------------------------------------------------
     def dense_B(self):
-        return sla.block_diag(*[self.B[l] for l in self.level])
+        return sla.block_diag(*self.Bseg)
 
     def dense_U(self):
         return sla.block_diag(*self.U)

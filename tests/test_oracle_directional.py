@@ -10,8 +10,11 @@ What fixes each part independently of the code under test:
 * Chebyshev interpolation: exact on polynomials of degree < m_c;
 * eq. (aug) / (fac) / (esol): with the exact T and W the five factors solve
   (B + U E U^t) q = f exactly, and so does the augmented 3 x 3 block system;
+* the block coefficients e_ij: the Chebyshev route of eq. (entry) agrees with
+  the least-squares constant over the block's own nodes, which it approximates;
 * the preconditioner's effect: GMRES iterations drop on the p = 8 ellipse, as
-  in Table 1 (n_n 47 -> n_p 14 at n = 32768; the size here is 2048).
+  in Table 1 (n_n 47 -> n_p 14 at n = 32768; the size here is 2048) and Table 3
+  (sound hard, 38 -> 15).
 """
 import numpy as np
 import pytest
@@ -173,3 +176,37 @@ def test_preconditioner_cuts_gmres_iterations(ellipse_arc):
     assert r0 <= 1e-6 and r1 <= 1e-6
     assert it1 <= 0.6 * it0
     assert np.linalg.norm(x - np.linalg.solve(A, f)) < 1e-5 * np.linalg.norm(x)
+
+
+def test_chebyshev_coefficients_match_the_nodal_least_squares(ellipse_arc):
+    """e_ij of eq. (entry) (m_c^2 Chebyshev samples) against the least-squares
+    constant over the nodes of the block (the mean of M~_ij)."""
+    q, p = 3, 8
+    n = 4**q * p
+    w = 2 * np.pi * (n / p) / ellipse_arc.L
+    A = operators.soft_matrix(ellipse_arc.curve(n), w, w)
+    Pc = directional.Directional(ellipse_arc, q, p, w)
+    Pn = directional.Directional(ellipse_arc, q, p, w, A=A, e_from="nodes")
+    ec, en = Pc.E.toarray(), Pn.E.toarray()
+    nz = np.abs(en) > 0
+    assert np.array_equal(nz, np.abs(ec) > 0)                  # same wave-number pairs
+    rel = np.abs(ec[nz] - en[nz]) / np.abs(en[nz])
+    assert np.median(rel) < 1e-3 and rel.max() < 5e-2         # worst: adjacent segments
+
+
+def test_hard_preconditioner(ellipse_arc):
+    """Sound hard (eq. 2): the factors solve B + U E U^t exactly, and GMRES
+    needs fewer iterations with the preconditioner (Table 3)."""
+    q, p = 4, 8
+    n = 4**q * p
+    w = 2 * np.pi * (n / p) / ellipse_arc.L
+    c = ellipse_arc.curve(n)
+    A = operators.hard_matrix(c, w, w)
+    P = directional.Directional(ellipse_arc, q, p, w, bc="hard", A=A)
+    f = operators.plane_wave_rhs(c, w, [0.0], "hard")[:, 0]
+    T, Ws = P.exact_solver()
+    ref = np.linalg.solve(P.approximation(), f)
+    assert np.linalg.norm(P.apply(f, T=T, W_solve=Ws) - ref) < 1e-10 * np.linalg.norm(ref)
+    _, it0, r0 = directional.preconditioned_gmres(A, None, f, rtol=1e-6)
+    x, it1, r1 = directional.preconditioned_gmres(A, P.apply, f, rtol=1e-6)
+    assert r0 <= 1e-6 and r1 <= 1e-6 and it1 < it0

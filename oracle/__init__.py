@@ -32,7 +32,8 @@ geometry   curve samples z, z', z'' at the nodes t_j = 2 pi j / n
 kress      the Kress log-split weights R_d
 operators  Bessel values, S / D / D' / N Nystrom matrices, CFIE matrices,
            row-sampled operators, spectral derivative, plane-wave data
-solvers    LU solve and restarted GMRES (modified Gram-Schmidt, Givens)
+solvers    LU solve, restarted GMRES (modified Gram-Schmidt, Givens) and block
+           GMRES over all right-hand sides (one shared Krylov space)
 field      off-surface representation formulas for the scattered field
 directional  the directional preconditioner of Section 2 (sound soft): segment
            partition, flat diagonal blocks B, partial Fourier matrices U, the

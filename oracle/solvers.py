@@ -10,6 +10,9 @@ guess.  The oracle provides both:
   read from the rotated right-hand side, x updated at the end of every cycle
   and the true residual f - A x recomputed at each restart.  Each right-hand
   side is solved independently.
+* ``block_gmres`` -- block GMRES over all right-hand sides at once (one
+  shared Krylov space; block Gram-Schmidt twice, QR of each new block, the
+  block Hessenberg least-squares problem solved directly).
 """
 import numpy as np
 
@@ -96,3 +99,56 @@ def gmres_columns(matvec, F, rtol=1e-6, restart=80, maxit=1000):
     for k in range(F.shape[1]):
         X[:, k], its[k], rel[k] = gmres(matvec, F[:, k], rtol, restart, maxit)
     return X, its, rel
+
+
+def block_gmres(matmat, F, rtol=1e-6, restart=40, maxit=500):
+    """Block GMRES over all columns of F at once: one Krylov space
+    span{R, A R, A^2 R, ...} shared by the s right-hand sides (the variant of
+    the Arnoldi step listed after the preconditioner among the next steps).
+
+    Block Arnoldi with block classical Gram-Schmidt applied twice and a QR of
+    each new block; the (m+1)s x ms block Hessenberg least-squares problem
+    min ||E1 B - Hbar Y||_F is solved directly each step, its column residuals
+    giving the convergence test ||f_k - A x_k|| <= rtol ||f_k|| for every k.
+    matmat(V) returns A V.  Returns (X, block iterations, relative residuals
+    computed from the final X).  Restarted every `restart` block steps.
+    """
+    F = np.asarray(F, dtype=np.complex128)
+    n, s = F.shape
+    X = np.zeros_like(F)
+    fn = np.linalg.norm(F, axis=0)
+    fn[fn == 0.0] = 1.0
+    its = 0
+    while True:
+        R = F - matmat(X)
+        if np.all(np.linalg.norm(R, axis=0) <= rtol * fn) or its >= maxit:
+            return X, its, np.linalg.norm(R, axis=0) / fn
+        V0, B = np.linalg.qr(R)
+        Vs = [V0]
+        Hcols = []                                      # block columns of Hbar
+        Y = None
+        for k in range(restart):
+            W = matmat(Vs[-1])
+            Vk = np.concatenate(Vs, axis=1)
+            h = Vk.conj().T @ W
+            W = W - Vk @ h
+            h2 = Vk.conj().T @ W                        # second pass (CGS2)
+            W = W - Vk @ h2
+            h = h + h2
+            Q, Rk = np.linalg.qr(W)
+            Vs.append(Q)
+            col = np.zeros(((k + 2) * s, s), dtype=np.complex128)
+            col[:(k + 1) * s] = h
+            col[(k + 1) * s:] = Rk
+            Hcols.append(col)
+            its += 1
+            Hbar = np.zeros(((k + 2) * s, (k + 1) * s), dtype=np.complex128)
+            for j, c in enumerate(Hcols):
+                Hbar[:c.shape[0], j * s:(j + 1) * s] = c
+            G = np.zeros(((k + 2) * s, s), dtype=np.complex128)
+            G[:s] = B
+            Y = np.linalg.lstsq(Hbar, G, rcond=None)[0]
+            res = np.linalg.norm(G - Hbar @ Y, axis=0)
+            if np.all(res <= rtol * fn) or its >= maxit:
+                break
+        X = X + np.concatenate(Vs[:len(Hcols)], axis=1) @ Y

@@ -47,3 +47,32 @@ def test_gmres_restarted_converges_and_counts():
 def test_gmres_zero_rhs():
     x, its, rel = solvers.gmres(lambda v: v, np.zeros(5, complex))
     assert its == 0 and rel == 0.0 and not np.any(x)
+
+
+def test_block_gmres_one_column_is_gmres():
+    """With one right-hand side the block Krylov space is the ordinary one:
+    the same iteration count and solution as GMRES."""
+    n, w = 256, 12.0
+    c = geometry.make("kite", n)
+    A = operators.soft_matrix(c, w, w)
+    f = operators.plane_wave_rhs(c, w, [0.3], "soft")
+    x1, it1, _ = solvers.gmres(lambda v: A @ v, f[:, 0], rtol=1e-10, restart=100)
+    X2, it2, rel2 = solvers.block_gmres(lambda V: A @ V, f, rtol=1e-10, restart=100)
+    assert it2 == it1 and rel2[0] <= 1e-10
+    assert np.linalg.norm(X2[:, 0] - x1) < 1e-8 * np.linalg.norm(x1)
+
+
+def test_block_gmres_many_columns_against_lu():
+    """64 plane waves on one kite: every column meets rtol, the solutions equal
+    LU, and the shared space needs no more block steps than the slowest
+    column needs alone (it contains each column's Krylov space)."""
+    n, w, s = 512, 30.0, 64
+    c = geometry.make("kite", n)
+    A = operators.soft_matrix(c, w, w)
+    F = operators.plane_wave_rhs(c, w, 2 * np.pi * np.arange(s) / s, "soft")
+    X, its, rel = solvers.block_gmres(lambda V: A @ V, F, rtol=1e-10, restart=60)
+    assert np.all(rel <= 1e-10)
+    ref = solvers.lu_solve(A, F)
+    assert np.max(np.abs(X - ref)) < 1e-8 * np.max(np.abs(ref))
+    _, its1, _ = solvers.gmres_columns(lambda v: A @ v, F, rtol=1e-10, restart=200)
+    assert its <= its1.max()

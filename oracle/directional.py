@@ -44,10 +44,12 @@ and the matrix's own diagonal blocks (see Directional).
 Parity: the algebra (eq. aug, fac, esol), the entry function, the Chebyshev
 interpolation, the curvature, the partition rules and the e_ij of eq. (entry)
 against the least-squares constants over the nodes are pinned by
-tests/test_oracle_directional.py.  The diagonal of the flat B_l is parity
-unpinned beyond that (the paper prints no intermediate values): it is checked
-through the closeness of B + U E U^t to M and the cut in GMRES iterations
-(Tables 1 and 3).
+tests/test_oracle_directional.py, and so is the sound-soft flat B_l, diagonal
+included: it equals the CFIE matrix of operators.soft_matrix on the straight
+sides of a stadium sampled in arclength.  flat_block_hard (not the default) is
+parity unpinned: on a closed curve the spectral derivative of Maue's identity
+couples a straight side to the whole curve, so no closed curve reproduces it;
+it is checked only through the closeness of B + U E U^t to M.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -188,7 +190,8 @@ def flat_block_hard(n, level, p, omega, eta, L):
     (the normal is orthogonal to every chord) and Maue's identity reduces to
     N = d/ds S d/ds + omega^2 S (n1^2 + n2^2 = 1); d/ds is the curve's spectral
     derivative (trigonometric interpolant on all n nodes, Nyquist mode zeroed)
-    restricted to the segment, divided by the speed L / (2 pi)."""
+    restricted to the segment, divided by the speed L / (2 pi).  Parity
+    unpinned."""
     from .operators import spectral_derivative
     cnt = 2**level * p
     g = L / (2.0 * np.pi)

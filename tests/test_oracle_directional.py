@@ -7,6 +7,8 @@ What fixes each part independently of the code under test:
   CFIE on the resampled ellipse reproduces the interior point-source field
   (which checks z, z' and z'' of the reparametrisation);
 * the entry function: on the nodes it equals the oracle's matrix entries;
+* the flat block B_l: on the straight sides of a stadium it is the oracle's
+  CFIE matrix (itself pinned by closed forms), diagonal included;
 * Chebyshev interpolation: exact on polynomials of degree < m_c;
 * eq. (aug) / (fac) / (esol): with the exact T and W the five factors solve
   (B + U E U^t) q = f exactly, and so does the augmented 3 x 3 block system;
@@ -210,3 +212,47 @@ def test_hard_preconditioner(ellipse_arc):
     _, it0, r0 = directional.preconditioned_gmres(A, None, f, rtol=1e-6)
     x, it1, r1 = directional.preconditioned_gmres(A, P.apply, f, rtol=1e-6)
     assert r0 <= 1e-6 and r1 <= 1e-6 and it1 < it0
+
+
+def _stadium(n, ell, rho):
+    """A stadium (straight sides of length ell joined by half circles of radius
+    rho), counter-clockwise, sampled equispaced in arclength with speed
+    L / (2 pi); its first side runs along y = -rho from x = -ell / 2."""
+    L = 2 * ell + 2 * np.pi * rho
+    g = L / (2 * np.pi)
+    s = L * np.arange(n) / n
+    z, tan, curv = np.zeros((n, 2)), np.zeros((n, 2)), np.zeros((n, 2))
+    for k, sk in enumerate(s):
+        if sk < ell:
+            z[k], tan[k] = (-ell / 2 + sk, -rho), (1.0, 0.0)
+        elif sk < ell + np.pi * rho:
+            f = (sk - ell) / rho
+            z[k] = (ell / 2 + rho * np.sin(f), -rho * np.cos(f))
+            tan[k], curv[k] = (np.cos(f), np.sin(f)), (-np.sin(f) / rho, np.cos(f) / rho)
+        elif sk < 2 * ell + np.pi * rho:
+            z[k], tan[k] = (ell / 2 - (sk - ell - np.pi * rho), rho), (-1.0, 0.0)
+        else:
+            f = (sk - 2 * ell - np.pi * rho) / rho
+            z[k] = (-ell / 2 - rho * np.sin(f), rho * np.cos(f))
+            tan[k], curv[k] = (-np.cos(f), -np.sin(f)), (np.sin(f) / rho, -np.cos(f) / rho)
+    return geometry.from_samples(z, g * tan, g * g * curv), L
+
+
+@pytest.mark.parametrize("level", [2, 4])
+def test_flat_block_is_the_operator_on_a_straight_side(level):
+    """B_l of the soft operator is the CFIE matrix of a boundary that really is
+    straight there: on a stadium sampled in arclength, the rows and columns of
+    the nodes of one straight side give the whole flat block, diagonal included
+    (the matrix of operators.soft_matrix is pinned on its own by closed forms)."""
+    p, n = 8, 512
+    c, L = _stadium(n, 1.0, 1.0 / np.pi)       # sides of n / 4 nodes, L = 4
+    w = 2 * np.pi * (n / p) / L
+    A = operators.soft_matrix(c, w, w)
+    m = 2**level * p
+    assert m <= n // 4
+    B = directional.flat_block(n, level, p, w, w, L)
+    blk = A[:m, :m]
+    assert np.max(np.abs(B - blk)) < 1e-13 * np.max(np.abs(blk))
+    # the same block further along the side (Toeplitz) and on the other side
+    for o in sorted({n // 4 - m, n // 2, 3 * n // 4 - m}):
+        assert np.max(np.abs(B - A[o:o + m, o:o + m])) < 1e-13 * np.max(np.abs(blk))

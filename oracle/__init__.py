@@ -36,12 +36,16 @@ operators  Bessel values, S / D / D' / N Nystrom matrices, CFIE matrices,
 solvers    LU solve, restarted GMRES (modified Gram-Schmidt, Givens) and block
            GMRES over all right-hand sides (one shared Krylov space)
 field      off-surface representation formulas for the scattered field
-directional  the directional preconditioner of Section 2 (sound soft): segment
-           partition, flat diagonal blocks B, partial Fourier matrices U, the
-           sparse E of rank-1 block coefficients, eq. (eapp); with the
-           arclength sampling it needs (geometry.Arclength).  Its algebra
-           (eq. aug / fac / esol), entry function, interpolation and
-           arclength map are pinned by tests/test_oracle_directional.py; the
-           quality of the data-sparse approximation is checked only through
-           its effect on GMRES iteration counts (Table 1 gives no entries).
+directional  the directional preconditioner of Section 2 (sound soft and sound
+           hard): segment partition, flat diagonal blocks B, partial Fourier
+           matrices U, the sparse E of rank-1 block coefficients, eq. (eapp);
+           with the arclength sampling it needs (geometry.Arclength).  Its
+           algebra (eq. aug / fac / esol), entry function, interpolation,
+           arclength map and sound-soft flat blocks are pinned by
+           tests/test_oracle_directional.py; the quality of the data-sparse
+           approximation is checked through its effect on GMRES iteration
+           counts (Tables 1 and 3 give no entries).
+iteration_counts  the GMRES iteration counts of Tables 1 and 3 (n_n without,
+           n_p with the preconditioner) on the paper's ellipse, recomputed
+           (python -m oracle.iteration_counts).
 """

@@ -256,3 +256,15 @@ def test_flat_block_is_the_operator_on_a_straight_side(level):
     # the same block further along the side (Toeplitz) and on the other side
     for o in sorted({n // 4 - m, n // 2, 3 * n // 4 - m}):
         assert np.max(np.abs(B - A[o:o + m, o:o + m])) < 1e-13 * np.max(np.abs(blk))
+
+
+@pytest.mark.parametrize("bc", ["soft", "hard"])
+def test_iteration_count_script(bc):
+    """oracle.iteration_counts at the smallest size: the setting of Section 3
+    (omega from p = 8 points per wavelength) and fewer iterations with the
+    preconditioner than without."""
+    from oracle import iteration_counts
+    n, omega, n_n, n_p = iteration_counts.counts(3, bc, eta_factor=0.5)
+    L = geometry.Arclength("ellipse", a=1.0, b=0.5).L
+    assert n == 512 and abs(omega - 2 * np.pi * 64 / L) < 1e-9
+    assert 0 < n_p <= n_n

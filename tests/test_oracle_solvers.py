@@ -76,3 +76,20 @@ def test_block_gmres_many_columns_against_lu():
     assert np.max(np.abs(X - ref)) < 1e-8 * np.max(np.abs(ref))
     _, its1, _ = solvers.gmres_columns(lambda v: A @ v, F, rtol=1e-10, restart=200)
     assert its <= its1.max()
+
+
+def test_block_gmres_rank_deficient_block():
+    """Repeated directions and a zero right-hand side make the residual block
+    rank deficient: every column still converges, equal columns give equal
+    solutions and the zero column gives zero."""
+    n, w = 512, 32.0
+    c = geometry.make("kite", n)
+    A = operators.soft_matrix(c, w, w)
+    F = operators.plane_wave_rhs(c, w, [0.0, 0.0, 1.0, 2.0, 1.0], "soft")
+    F[:, 4] = 0.0
+    X, its, rel = solvers.block_gmres(lambda V: A @ V, F, rtol=1e-10, restart=60)
+    assert np.all(rel <= 1e-10)
+    assert np.array_equal(X[:, 0], X[:, 1]) or np.max(np.abs(X[:, 0] - X[:, 1])) < 1e-12
+    assert not np.any(X[:, 4])
+    ref = solvers.lu_solve(A, F)
+    assert np.max(np.abs(X - ref)) < 1e-8 * np.max(np.abs(ref))

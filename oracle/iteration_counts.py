@@ -48,7 +48,9 @@ def _soft_rows(start):
 
 def soft_matrix_parallel(q, p=8, eta_factor=1.0, a=1.0, b=0.5, workers=None):
     """The sound-soft CFIE matrix of eq. 1 on the arclength-sampled ellipse,
-    row blocks computed by `workers` processes (spawned)."""
+    row blocks computed by `workers` processes (spawned: a calling script must
+    keep its own work under `if __name__ == "__main__":`, since each worker
+    imports it)."""
     _, n, _, _ = _setup(a, b, q, p, eta_factor)
     workers = workers or os.cpu_count() or 1
     A = np.empty((n, n), dtype=np.complex128)

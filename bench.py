@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--rtol", type=float, default=None)
     p.add_argument("--n", type=int, default=None, help="override the workload's n (profiling)")
     p.add_argument("--nrhs", type=int, default=None, help="override the number of directions")
+    p.add_argument("--eta-factor", type=float, default=None,
+                   help="coupling eta = factor x omega for the single-operator workloads (default 1)")
     p.add_argument("--oracle-budget", type=float, default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -56,7 +58,7 @@ def parse():
 # ---------------------------------------------------------------------------
 # workload definitions (shapes from inputs.WORKLOADS)
 # ---------------------------------------------------------------------------
-def workload(name, precision, n=None, nrhs=None):
+def workload(name, precision, n=None, nrhs=None, eta_factor=None):
     from paper_1408_1578_gb300 import inputs
     spec = dict(inputs.WORKLOADS[name])
     spec["name"] = name
@@ -67,6 +69,9 @@ def workload(name, precision, n=None, nrhs=None):
         spec["name"] = f"{name} (reduced n={n})"
     if nrhs:
         spec["nrhs"] = nrhs
+    # Section 1 asks only for eta = O(omega)
+    spec["eta_factor"] = eta_factor or 1.0
+    spec["eta"] = spec["eta_factor"] * spec["omega"]
     if precision is None:
         precision = "fp32" if name in ("kite", "ellipse", "ellipse-hard") else "fp64"
     spec["precision"] = precision
@@ -253,7 +258,7 @@ def run_ours(args, rank, world):
 
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
-    spec = workload(args.workload, args.precision, args.n, args.nrhs)
+    spec = workload(args.workload, args.precision, args.n, args.nrhs, args.eta_factor)
     if args.rtol:
         spec["rtol"] = args.rtol
     n, w, nrhs, bc = spec["n"], spec["omega"], spec["nrhs"], spec["bc"]
@@ -269,7 +274,8 @@ def run_ours(args, rank, world):
 
     def step():
         geom = ctx.geometry(spec["curve"], **spec["params"])
-        op = geom.discretise(n, w, bc=bc, precision=spec["precision"], layout=spec["layout"])
+        op = geom.discretise(n, w, eta=spec["eta"], bc=bc, precision=spec["precision"],
+                             layout=spec["layout"])
         op.rhs_plane_waves(theta, f)
         x.zero_()
         its, rel, st = op.gmres_solve(f, x, rtol=spec["rtol"], restart=spec["restart"],
@@ -389,7 +395,7 @@ def oracle_sample(spec, rows_count):
     rows = np.arange(rows_count) * (n // rows_count)
     t0 = time.perf_counter()
     if bc == "soft":
-        A = operators.soft_rows(c, w, w, rows, R)
+        A = operators.soft_rows(c, w, spec["eta"], rows, R)
         _ = A @ X.T
         pairs = rows_count * n
     else:
@@ -411,10 +417,10 @@ def oracle_single_core(args, budget_s):
     env = dict(os.environ, **ORACLE_THREAD_ENV)
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-budget", str(budget_s),
            "--workload", args.workload]
-    for k in ("precision", "n", "nrhs", "count"):
+    for k in ("precision", "n", "nrhs", "count", "eta_factor"):
         v = getattr(args, k)
         if v is not None:
-            cmd += [f"--{k}", str(v)]
+            cmd += [f"--{k.replace('_', '-')}", str(v)]
     out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
     if out.returncode != 0:
         raise RuntimeError("oracle sample failed: " + out.stderr[-500:])
@@ -478,7 +484,7 @@ def reference_specs(args):
                  "params": {"a": list(stars[k]["a"]), "b": list(stars[k]["b"])},
                  "n": stars[k]["n"], "omega": stars[k]["omega"], "nrhs": stars[k]["nrhs"],
                  "bc": "soft", "precision": "tensor"} for k in pick]
-    return [workload(args.workload, args.precision, args.n, args.nrhs)]
+    return [workload(args.workload, args.precision, args.n, args.nrhs, args.eta_factor)]
 
 
 def run_reference_serve(args):
@@ -540,7 +546,7 @@ def run_reference(args, rank, world):
                        for sp, r in zip(specs, rows))
     sample += f", {specs[0]['nrhs']} right-hand sides, per step"
     cfg = stars_config(args.count or 256) if args.workload == "stars" else \
-        single_config(workload(args.workload, args.precision, args.n, args.nrhs), world)
+        single_config(workload(args.workload, args.precision, args.n, args.nrhs, args.eta_factor), world)
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_s * 1e3 / args.steps,
@@ -554,10 +560,16 @@ def run_reference(args, rank, world):
 
 def single_config(spec, world):
     return {"workload": f"{spec['name']}: {spec['curve']} {spec['bc']} n={spec['n']} "
-                        f"omega={spec['omega']} eta=omega nrhs={spec['nrhs']}",
+                        f"omega={spec['omega']} {eta_text(spec)} nrhs={spec['nrhs']}",
             "curve": spec["curve"], "bc": spec["bc"], "n": spec["n"], "omega": spec["omega"],
-            "nrhs": spec["nrhs"], "precision": spec["precision"], "rtol": spec["rtol"],
+            "nrhs": spec["nrhs"], "eta": spec["eta"], "precision": spec["precision"],
+            "rtol": spec["rtol"],
             "restart": spec["restart"], "parallelism": f"replicas{world}"}
+
+
+def eta_text(spec):
+    f = spec["eta_factor"]
+    return "eta=omega" if f == 1.0 else f"eta={f:g}*omega"
 
 
 def stars_config(count):
@@ -627,6 +639,8 @@ def allreduce_sum(v, world):
 
 def main():
     args = parse()
+    if args.eta_factor is not None and (args.eta_factor <= 0 or args.workload in ("stars", "serve")):
+        sys.exit("--eta-factor takes a positive factor and applies to the single-operator workloads")
     if args.oracle_budget is not None:
         oracle_budget_main(args)
         return

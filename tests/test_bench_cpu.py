@@ -42,3 +42,15 @@ def test_our_arm_needs_a_gpu():
     r = _run(["--steps", "1", "--warmup", "3"], timeout=300)
     assert r.returncode != 0
     assert "NVIDIA" in r.stderr or "CUDA" in r.stderr or "cuda" in r.stderr
+
+
+def test_reference_arm_coupling_option():
+    """--eta-factor sets eta = factor x omega for the single-operator
+    workloads and says so in the config; the batch workloads refuse it."""
+    r = _run(["--impl", "reference", "--workload", "disk", "--steps", "1", "--warmup", "1",
+              "--eta-factor", "0.5"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    cfg = json.loads(r.stdout.strip().splitlines()[-1])["config"]
+    assert cfg["eta"] == 0.5 * cfg["omega"] and "eta=0.5*omega" in cfg["workload"]
+    r = _run(["--impl", "reference", "--workload", "stars", "--eta-factor", "0.5"], timeout=120)
+    assert r.returncode != 0 and "single-operator" in r.stderr

@@ -44,7 +44,7 @@ def _compile(src, verbose):
 def build(verbose=False):
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(os.path.dirname(HERE), "include", "cfie.h"))
     if os.path.exists(LIB) and not verbose:
         newest = max(os.path.getmtime(d) for d in deps)

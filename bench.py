@@ -159,6 +159,11 @@ SMS, FP32_LANES = 152, 128
 ENTRY_OPS = {("soft", 1): 74, ("hard", 1): 87, ("soft", 2): 64, ("hard", 2): 98}
 SUM_OPS = {"soft": 4, "hard": 8}         # FP32 FMAs per pair and right-hand side (CUDA-core sums)
 DF_ENTRY_OPS = 563                       # double-float pair entry of the residual kernel
+# sound hard: the phase and Hankel part (431) with the S assembly (39) and the D'
+# assembly (78); the CUDA-core kernel takes both from one phase, the sliced
+# tensor-core kernel evaluates them in separate passes
+DF_HARD_OPS = 431 + 39 + 78
+DF_HARD_PASS_OPS = (431 + 39) + (431 + 78)
 DF_TERM_OPS = 48                         # Dot2 complex product-sum per pair and right-hand side
 SLICE_OPS = 48                           # six 8-bit slices of the re / im parts of one entry
 FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)
@@ -196,20 +201,23 @@ def kernel_rooflines(kt, spec, stats, peaks, src, n, solves_timed):
                                    else f"{SUM_OPS[bc]} FMA per pair per right-hand side") + ")",
                         "peak_source": f"152 SMs x 128 FP32 lanes x {clock_hz / 1e6:.0f} MHz"}
         elif cls == "matvec_fp64" and prec != "fp64" and stats.get("residual_variant") == 2:
-            ops = DF_ENTRY_OPS + SLICE_OPS
+            ent, sl = (DF_ENTRY_OPS, SLICE_OPS) if bc == "soft" else (DF_HARD_PASS_OPS, 2 * SLICE_OPS)
+            ops = ent + sl
             a = ops * n * n / avg / 1e12
             out[cls] = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "Top/s",
                         "frac": a / fp32_peak, "traffic": None,
-                        "work": f"tensor-core residual: {DF_ENTRY_OPS} + {SLICE_OPS} FP32 ops per "
-                                "pair (double-float entry, slicing; slice products on the tensor "
+                        "work": f"tensor-core residual: {ent} + {sl} FP32 ops per pair "
+                                "(double-float entries, slicing; slice products on the tensor "
                                 "cores, not counted)",
                         "peak_source": f"152 SMs x 128 FP32 lanes x {clock_hz / 1e6:.0f} MHz"}
-        elif cls == "matvec_fp64" and prec != "fp64" and bc == "soft":
-            ops = DF_ENTRY_OPS + DF_TERM_OPS * nrhs
+        elif cls == "matvec_fp64" and prec != "fp64":
+            # S applied to the 3 vectors of Maue's identity and D' to x: 4 sums per RHS
+            ent, terms = (DF_ENTRY_OPS, 1) if bc == "soft" else (DF_HARD_OPS, 4)
+            ops = ent + DF_TERM_OPS * terms * nrhs
             a = ops * n * n / avg / 1e12
             out[cls] = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "Top/s",
                         "frac": a / fp32_peak, "traffic": None,
-                        "work": f"double-float residual: {DF_ENTRY_OPS} + {DF_TERM_OPS} x nrhs "
+                        "work": f"double-float residual: {ent} + {DF_TERM_OPS * terms} x nrhs "
                                 "FP32 ops per pair",
                         "peak_source": f"152 SMs x 128 FP32 lanes x {clock_hz / 1e6:.0f} MHz"}
         elif cls == "matvec_fp64":

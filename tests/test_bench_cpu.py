@@ -54,3 +54,72 @@ def test_reference_arm_coupling_option():
     assert cfg["eta"] == 0.5 * cfg["omega"] and "eta=0.5*omega" in cfg["workload"]
     r = _run(["--impl", "reference", "--workload", "stars", "--eta-factor", "0.5"], timeout=120)
     assert r.returncode != 0 and "single-operator" in r.stderr
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+PEAKS = {"hbm_gbs": 6777.6, "sm_max_mhz": 2070.0}
+ALU_PEAK_T = 152 * 128 * 2070e6 / 1e12          # FP32 lanes x clock
+
+
+def test_roofline_fused_fp32_kite():
+    """The reported roofline of the fused FP32 kernel: 64 operations per pair
+    over n^2 pairs per launch, divided by the average launch time, against
+    the lane peak; traffic from the ncu table for this exact configuration."""
+    b = _bench_module()
+    n, ms, launches = 32768, 37.0, 10
+    spec = {"nrhs": 64, "bc": "soft", "precision": "fp32", "curve": "kite"}
+    r = b.kernel_rooflines({"matvec_fp32": (ms, launches)}, spec, {"matvec_variant": 2},
+                           PEAKS, "measured", n, 1)["matvec_fp32"]
+    want = 64 * n * n / (ms / 1e3 / launches) / 1e12
+    assert abs(r["achieved"] - want) < 1e-9 * want
+    assert abs(r["frac"] - want / ALU_PEAK_T) < 1e-12
+    assert r["bound"] == "alu" and r["traffic"] == 79.151872e6 + 11.139584e6
+
+
+@pytest.mark.parametrize("bc,variant,ops", [
+    ("soft", 1, 563 + 48 * 5), ("hard", 1, 548 + 4 * 48 * 5),
+    ("soft", 2, 563 + 48), ("hard", 2, 470 + 509 + 2 * 48)])
+def test_roofline_double_float_residual(bc, variant, ops):
+    """Residual kernels: the double-float entry (sound hard: S and D' from one
+    phase on the CUDA cores, in two passes on the tensor cores) plus the
+    per-right-hand-side Dot2 sums (4 sums per RHS for sound hard) or the
+    slicing."""
+    b = _bench_module()
+    n, ms = 4096, 8.0
+    spec = {"nrhs": 5, "bc": bc, "precision": "fp32", "curve": "star"}
+    r = b.kernel_rooflines({"matvec_fp64": (ms, 2)}, spec, {"residual_variant": variant},
+                           PEAKS, "measured", n, 1)["matvec_fp64"]
+    want = ops * n * n / (ms / 1e3 / 2) / 1e12
+    assert abs(r["achieved"] - want) < 1e-9 * want and r["unit"] == "Top/s"
+    assert r["traffic"] is None
+
+
+def test_roofline_stored_and_arnoldi():
+    b = _bench_module()
+    n = 1000
+    spec = {"nrhs": 32, "bc": "soft", "precision": "tensor", "curve": "star"}
+    kt = {"matvec_tensor": (2.0, 4), "arnoldi": (3.0, 100)}
+    stats = {"arnoldi_elems": 7_000_000, "basis_fp32": True}
+    r = b.kernel_rooflines(kt, spec, stats, PEAKS, "measured", n, 2)
+    pitch = 1024                                  # n rounded up to 64
+    want = n * pitch * 8 / (2.0 / 1e3 / 4) / 1e9
+    assert abs(r["matvec_tensor"]["achieved"] - want) < 1e-9 * want
+    assert abs(r["matvec_tensor"]["frac"] - want / 6777.6) < 1e-12
+    want = 4 * 7_000_000 * 2 * 8 / 3e-3 / 1e9     # four passes, 8-byte elements, 2 solves
+    assert abs(r["arnoldi"]["achieved"] - want) < 1e-9 * want
+
+
+def test_measured_peaks_are_read():
+    b = _bench_module()
+    peaks, src = b.measured_peaks()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert src == "measured" and peaks["hbm_gbs"] > 1000
+    else:
+        assert src == "fallback" and peaks["hbm_gbs"] == 6800.0

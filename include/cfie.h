@@ -81,6 +81,8 @@ typedef struct cfie_op cfie_op;
  * (may be NULL for the legacy default stream); the caller keeps ownership of
  * it and it must outlive the context.  Writes the handle to *out. */
 cfie_status cfie_ctx_create(int device, void* cuda_stream, cfie_ctx** out);
+/* Free a context (NULL is ignored).  Destroy its geometries, operators and
+ * batches first; the caller's stream is left alone. */
 void cfie_ctx_destroy(cfie_ctx* ctx);
 
 /* Message of the last failing call on this context ("" if none).  The string
@@ -105,6 +107,8 @@ cfie_status cfie_geometry_kite(cfie_ctx* ctx, cfie_geom** out);
  * with exactly this n are allowed. */
 cfie_status cfie_geometry_samples(cfie_ctx* ctx, int n, const double* z, const double* dz,
                                   const double* ddz, cfie_geom** out);
+/* Free a geometry (NULL is ignored).  Operators discretised from it keep their
+ * own device copy of the nodes and stay valid. */
 void cfie_geom_destroy(cfie_geom* geom);
 
 /* --- Discretisation ------------------------------------------------------ */
@@ -115,6 +119,9 @@ void cfie_geom_destroy(cfie_geom* geom);
  * usual choice, Section 1 asks for eta = O(omega)).  Synchronous. */
 cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cfie_bc bc,
                             cfie_precision precision, cfie_layout layout, cfie_op** out);
+/* Free an operator and its device buffers (NULL is ignored) after the work
+ * queued on the context stream has finished.  Batches holding it must be
+ * destroyed first. */
 void cfie_op_destroy(cfie_op* op);
 
 /* Number of nodes of an operator. */
@@ -244,6 +251,8 @@ typedef struct {
                               summed over the Arnoldi steps (CGS2 makes four
                               passes: two inner products, two updates) */
 } cfie_solve_stats;
+/* Statistics of the operator's last cfie_gmres_solve, copied to *out (host).
+ * CFIE_EINVAL for a null operator or output. */
 cfie_status cfie_op_last_stats(const cfie_op* op, cfie_solve_stats* out);
 
 /* --- Batches: many operators solved in lockstep ------------------------- */
@@ -269,9 +278,12 @@ cfie_status cfie_batch_apply(cfie_batch* batch, const void* x_dev, void* y_dev);
  * hold one entry per right-hand side in batch order). */
 cfie_status cfie_batch_gmres_solve(cfie_batch* batch, const void* f_dev, void* x_dev, double rtol,
                                    int restart, int maxit, int* iters_out, double* relres_out);
+/* As cfie_op_last_stats, for the batch's last lockstep solve. */
 cfie_status cfie_batch_last_stats(const cfie_batch* batch, cfie_solve_stats* out);
 /* As cfie_op_set_inner_basis, for the lockstep solves of a batch. */
 cfie_status cfie_batch_set_inner_basis(cfie_batch* batch, int fp32);
+/* Free a batch (NULL is ignored) after its queued work has finished; its
+ * operators stay valid. */
 void cfie_batch_destroy(cfie_batch* batch);
 
 
@@ -346,7 +358,11 @@ cfie_status cfie_server_poll(cfie_server* server, long long ticket, cfie_result*
 cfie_status cfie_server_wait_all(cfie_server* server, double timeout_s);
 /* Forget a finished request and free its host solution. */
 cfie_status cfie_server_release(cfie_server* server, long long ticket);
+/* Counters of the server so far, copied to *out (host).  CFIE_EINVAL for a
+ * null server or output. */
 cfie_status cfie_server_stats(cfie_server* server, cfie_server_counters* out);
+/* Message of the server's last failing call ("" if none); valid until its next
+ * call.  Per-request failures: cfie_server_request_error. */
 const char* cfie_server_last_error(cfie_server* server);
 /* The error message of a finished request whose status is not CFIE_OK (empty
  * otherwise, or while it runs), copied NUL-terminated into buf (host, len

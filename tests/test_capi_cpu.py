@@ -77,3 +77,25 @@ def test_server_needs_a_device(lib):
     buf = ctypes.create_string_buffer(16)
     assert lib.cfie_server_request_error(None, ctypes.c_longlong(1), buf,
                                          ctypes.c_size_t(16)) == cfie.CFIE_EINVAL
+
+
+def test_null_handles_documented_behaviour(lib):
+    """What include/cfie.h promises for null handles, without a GPU: destroy
+    calls ignore them, getters return their empty value, everything that
+    returns a status says CFIE_EINVAL."""
+    from paper_1408_1578_gb300 import cfie
+    for fn in ("cfie_ctx_destroy", "cfie_geom_destroy", "cfie_op_destroy", "cfie_batch_destroy",
+               "cfie_server_destroy"):
+        getattr(lib, fn)(None)
+    assert lib.cfie_op_n(None) == 0 and lib.cfie_batch_length(None) == 0
+    stats = cfie.cfie_solve_stats()
+    assert lib.cfie_op_last_stats(None, ctypes.byref(stats)) == cfie.CFIE_EINVAL
+    assert lib.cfie_batch_last_stats(None, ctypes.byref(stats)) == cfie.CFIE_EINVAL
+    counters = cfie.cfie_server_counters()
+    assert lib.cfie_server_stats(None, ctypes.byref(counters)) == cfie.CFIE_EINVAL
+    assert lib.cfie_server_poll(None, ctypes.c_longlong(1), None, None) == cfie.CFIE_EINVAL
+    assert lib.cfie_server_wait_all(None, 1.0) == cfie.CFIE_EINVAL
+    assert lib.cfie_server_release(None, ctypes.c_longlong(1)) == cfie.CFIE_EINVAL
+    assert isinstance(lib.cfie_server_last_error(None), bytes)
+    assert lib.cfie_batch_apply(None, None, None) == cfie.CFIE_EINVAL
+    assert lib.cfie_ctx_set_profiling(None, 1) == cfie.CFIE_EINVAL

@@ -111,6 +111,30 @@ cfie_status cfie_geometry_samples(cfie_ctx* ctx, int n, const double* z, const d
  * own device copy of the nodes and stay valid. */
 void cfie_geom_destroy(cfie_geom* geom);
 
+/* Curves of the cfie_geometry_* constructors, by name, for host-side helpers. */
+typedef enum {
+  CFIE_CURVE_CIRCLE = 0,
+  CFIE_CURVE_ELLIPSE = 1,
+  CFIE_CURVE_STAR = 2,
+  CFIE_CURVE_KITE = 3
+} cfie_curve;
+
+/* Samples of a curve at n points equispaced in arclength, the node set of
+ * Section 2 (segments of 2^l p equispaced points, 2^l wavelengths long).  The
+ * curve is the one the matching cfie_geometry_* call builds, with params
+ * (host, nparams doubles, copied): circle {radius}; ellipse {a, b}; star
+ * {a_1..a_K, b_1..b_K}, nparams = 2K, 1 <= K <= 64; kite none (params may be
+ * NULL).  Outputs (host arrays of 2n doubles, x and y interleaved: the layout
+ * cfie_geometry_samples takes): z, dz/dsigma and d2z/dsigma2 at
+ * sigma_j = 2 pi j / n, where sigma = 2 pi s / L is the arclength s from the
+ * curve's point at t = 0, rescaled to [0, 2 pi) (constant speed L / (2 pi));
+ * *perimeter receives L unless perimeter is NULL.  n even, 8 <= n <= 2^20.
+ * CFIE_EINVAL for invalid arguments or a curve whose speed vanishes (a star
+ * whose r reaches 0).  Host only: needs no context and no GPU; the arclength
+ * is accurate to a few units in the last place of L. */
+cfie_status cfie_arclength_samples(cfie_curve kind, const double* params, int nparams, int n,
+                                   double* z, double* dz, double* ddz, double* perimeter);
+
 /* --- Discretisation ------------------------------------------------------ */
 
 /* Sample the curve at n nodes on the device, build the Kress weight table and

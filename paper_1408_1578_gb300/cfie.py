@@ -23,6 +23,9 @@ STATUS_NAMES = ["CFIE_OK", "CFIE_EINVAL", "CFIE_ENOMEM", "CFIE_ECUDA", "CFIE_ENO
 CFIE_SOUND_SOFT, CFIE_SOUND_HARD = 0, 1
 CFIE_FP64, CFIE_FP32_REFINED, CFIE_TENSOR_REFINED = 0, 1, 2
 CFIE_MATRIX_FREE, CFIE_STORED = 0, 1
+CFIE_CURVE_CIRCLE, CFIE_CURVE_ELLIPSE, CFIE_CURVE_STAR, CFIE_CURVE_KITE = 0, 1, 2, 3
+CURVE = {"circle": CFIE_CURVE_CIRCLE, "ellipse": CFIE_CURVE_ELLIPSE, "star": CFIE_CURVE_STAR,
+         "kite": CFIE_CURVE_KITE}
 (CFIE_K_MATVEC_FP64, CFIE_K_MATVEC_FP32, CFIE_K_MATVEC_TENSOR, CFIE_K_ARNOLDI,
  CFIE_K_SPECTRAL, CFIE_K_COUNT) = range(6)
 KERNEL_CLASS_NAMES = ["matvec_fp64", "matvec_fp32", "matvec_tensor", "arnoldi", "spectral"]
@@ -90,6 +93,7 @@ SIGNATURES = {
     "cfie_geometry_kite": (_I, [_P, ctypes.POINTER(_P)]),
     "cfie_geometry_samples": (_I, [_P, _I, _DP, _DP, _DP, ctypes.POINTER(_P)]),
     "cfie_geom_destroy": (None, [_P]),
+    "cfie_arclength_samples": (_I, [_I, _DP, _I, _I, _DP, _DP, _DP, _DP]),
     "cfie_discretise": (_I, [_P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(_P)]),
     "cfie_op_destroy": (None, [_P]),
     "cfie_op_n": (_I, [_P]),
@@ -170,6 +174,31 @@ def __getattr__(name):
     if name in SIGNATURES:
         return getattr(load(), name)
     raise AttributeError(name)
+
+
+def arclength_samples(kind, n, **params):
+    """cfie_arclength_samples: (z, dz, ddz, L) of the named curve at n points
+    equispaced in arclength, each an (n, 2) array (host; no GPU needed).
+    params as for Context.geometry: circle radius, ellipse a and b, star a and b."""
+    if kind == "circle":
+        p = [params.get("radius", 1.0)]
+    elif kind == "ellipse":
+        p = [params["a"], params["b"]]
+    elif kind == "star":
+        p = list(np.asarray(params["a"], dtype=np.float64)) + \
+            list(np.asarray(params["b"], dtype=np.float64))
+    elif kind == "kite":
+        p = []
+    else:
+        raise ValueError(kind)
+    par = np.ascontiguousarray(p, dtype=np.float64)
+    out = [np.empty((int(n), 2)) for _ in range(3)]
+    L = ctypes.c_double()
+    st = load().cfie_arclength_samples(CURVE[kind], _dptr(par) if par.size else None, int(par.size),
+                                       int(n), *[_dptr(a) for a in out], ctypes.byref(L))
+    if st != CFIE_OK:
+        raise CfieError(st, "cfie_arclength_samples: invalid curve parameters or n")
+    return out[0], out[1], out[2], L.value
 
 
 # ---------------------------------------------------------------------------

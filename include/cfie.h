@@ -135,6 +135,29 @@ typedef enum {
 cfie_status cfie_arclength_samples(cfie_curve kind, const double* params, int nparams, int n,
                                    double* z, double* dz, double* ddz, double* perimeter);
 
+/* Structure of the directional preconditioner (Section 2.1) for the curve
+ * sampled at n = 4^q p points equispaced in arclength (cfie_arclength_samples
+ * with the same curve and n; p points per wavelength 2 pi / omega).
+ *  - Segments, in order along the curve from its point at t = 0: 2^q pieces of
+ *    2^q p points, each halved until it is almost planar (2^l <= 2^q / sqrt(c),
+ *    c the largest |curvature| at its nodes) or a non-planar leaf
+ *    (2^l <= m_leaf).  Segment i holds the 2^level[i] p nodes from first[i].
+ *  - For i != j, with c_i the curve point halfway (in arclength) between the
+ *    segment's first and last node, t_i the unit tangent there and
+ *    a_ij = (c_i - c_j) / |c_i - c_j|: k^i_ij = [omega a_ij . t_i]_i and
+ *    k^j_ij = [-omega a_ij . t_j]_j, the nearest of the 2^(l+1) + 1 equispaced
+ *    wave numbers of [-omega, omega] of each segment's level (ties away from
+ *    zero), as indices 0 .. 2^(l+1): kpair[2 (i m + j)] = k^i_ij,
+ *    kpair[2 (i m + j) + 1] = k^j_ij; zero for i == j.
+ * *m receives the number of segments.  With first, level and kpair all NULL
+ * nothing else is written (the sizing call); otherwise each holds capacity,
+ * capacity and 2 capacity^2 ints (host) and capacity >= *m, else CFIE_EINVAL.
+ * params as for cfie_arclength_samples; 1 <= q <= 9, p >= 1, n even and
+ * 8 <= n <= 2^20, omega > 0, m_leaf >= 1.  Host only: no context, no GPU. */
+cfie_status cfie_dirprec_plan(cfie_curve kind, const double* params, int nparams, int q, int p,
+                              double omega, int m_leaf, int capacity, int* m, int* first,
+                              int* level, int* kpair);
+
 /* --- Discretisation ------------------------------------------------------ */
 
 /* Sample the curve at n nodes on the device, build the Kress weight table and

@@ -94,6 +94,7 @@ SIGNATURES = {
     "cfie_geometry_samples": (_I, [_P, _I, _DP, _DP, _DP, ctypes.POINTER(_P)]),
     "cfie_geom_destroy": (None, [_P]),
     "cfie_arclength_samples": (_I, [_I, _DP, _I, _I, _DP, _DP, _DP, _DP]),
+    "cfie_dirprec_plan": (_I, [_I, _DP, _I, _I, _I, _D, _I, _I, _IP, _IP, _IP, _IP]),
     "cfie_discretise": (_I, [_P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(_P)]),
     "cfie_op_destroy": (None, [_P]),
     "cfie_op_n": (_I, [_P]),
@@ -176,10 +177,7 @@ def __getattr__(name):
     raise AttributeError(name)
 
 
-def arclength_samples(kind, n, **params):
-    """cfie_arclength_samples: (z, dz, ddz, L) of the named curve at n points
-    equispaced in arclength, each an (n, 2) array (host; no GPU needed).
-    params as for Context.geometry: circle radius, ellipse a and b, star a and b."""
+def _curve_params(kind, params):
     if kind == "circle":
         p = [params.get("radius", 1.0)]
     elif kind == "ellipse":
@@ -191,7 +189,37 @@ def arclength_samples(kind, n, **params):
         p = []
     else:
         raise ValueError(kind)
-    par = np.ascontiguousarray(p, dtype=np.float64)
+    return np.ascontiguousarray(p, dtype=np.float64)
+
+
+def dirprec_plan(kind, q, p, omega, m_leaf=2, **params):
+    """cfie_dirprec_plan: (first, level, kpair) of the directional
+    preconditioner's segments for the named curve (host; no GPU needed);
+    kpair has shape (m, m, 2)."""
+    par = _curve_params(kind, params)
+    pp = _dptr(par) if par.size else None
+    m = ctypes.c_int()
+    lib = load()
+    args = (CURVE[kind], pp, int(par.size), int(q), int(p), float(omega), int(m_leaf))
+    st = lib.cfie_dirprec_plan(*args, 0, ctypes.byref(m), None, None, None)
+    if st != CFIE_OK:
+        raise CfieError(st, "cfie_dirprec_plan: invalid curve or sizes")
+    k = m.value
+    first = np.zeros(k, dtype=np.int32)
+    level = np.zeros(k, dtype=np.int32)
+    kpair = np.zeros((k, k, 2), dtype=np.int32)
+    st = lib.cfie_dirprec_plan(*args, k, ctypes.byref(m), first.ctypes.data_as(_IP),
+                               level.ctypes.data_as(_IP), kpair.ctypes.data_as(_IP))
+    if st != CFIE_OK:
+        raise CfieError(st, "cfie_dirprec_plan")
+    return first, level, kpair
+
+
+def arclength_samples(kind, n, **params):
+    """cfie_arclength_samples: (z, dz, ddz, L) of the named curve at n points
+    equispaced in arclength, each an (n, 2) array (host; no GPU needed).
+    params as for Context.geometry: circle radius, ellipse a and b, star a and b."""
+    par = _curve_params(kind, params)
     out = [np.empty((int(n), 2)) for _ in range(3)]
     L = ctypes.c_double()
     st = load().cfie_arclength_samples(CURVE[kind], _dptr(par) if par.size else None, int(par.size),

@@ -158,6 +158,20 @@ cfie_status cfie_dirprec_plan(cfie_curve kind, const double* params, int nparams
                               double omega, int m_leaf, int capacity, int* m, int* first,
                               int* level, int* kpair);
 
+/* Level blocks of the directional preconditioner (Section 2.2, sound soft) for
+ * the segments of level l (c = 2^l p nodes) of an n-node arclength
+ * discretisation of a curve of perimeter L:
+ *  B: c x c, the operator 1/2 I - i eta S restricted to a straight segment of c
+ *     nodes with spacing L / n (Kress-Nystrom entries on a line, where the
+ *     double-layer kernel vanishes);
+ *  Binv: B^-1;  U: c x K, K = 2^(l+1) + 1, U(x, m) = exp(i k_m (x - (c-1)/2) L / n)
+ *     with k_m = -omega + 2 omega m / (K - 1);  T: K x K, (U^t B^-1 U)^-1.
+ * Each output (host, complex128 interleaved, row-major) may be NULL to skip it.
+ * n even, 8 <= n <= 2^20, c <= min(n / 2, 4096), omega, eta, L > 0.
+ * CFIE_EINVAL for invalid arguments or a singular block.  Host only. */
+cfie_status cfie_dirprec_level(int n, int p, int level, double omega, double eta, double L,
+                               double* B, double* Binv, double* U, double* T);
+
 /* --- Discretisation ------------------------------------------------------ */
 
 /* Sample the curve at n nodes on the device, build the Kress weight table and

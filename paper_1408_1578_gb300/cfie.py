@@ -95,6 +95,7 @@ SIGNATURES = {
     "cfie_geom_destroy": (None, [_P]),
     "cfie_arclength_samples": (_I, [_I, _DP, _I, _I, _DP, _DP, _DP, _DP]),
     "cfie_dirprec_plan": (_I, [_I, _DP, _I, _I, _I, _D, _I, _I, _IP, _IP, _IP, _IP]),
+    "cfie_dirprec_level": (_I, [_I, _I, _I, _D, _D, _D, _DP, _DP, _DP, _DP]),
     "cfie_discretise": (_I, [_P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(_P)]),
     "cfie_op_destroy": (None, [_P]),
     "cfie_op_n": (_I, [_P]),
@@ -213,6 +214,19 @@ def dirprec_plan(kind, q, p, omega, m_leaf=2, **params):
     if st != CFIE_OK:
         raise CfieError(st, "cfie_dirprec_plan")
     return first, level, kpair
+
+
+def dirprec_level(n, p, level, omega, eta, L):
+    """cfie_dirprec_level: (B, B^-1, U, T) of one level as complex arrays (host;
+    no GPU needed)."""
+    c, K = (1 << level) * p, (1 << (level + 1)) + 1
+    out = [np.empty((c, c), np.complex128), np.empty((c, c), np.complex128),
+           np.empty((c, K), np.complex128), np.empty((K, K), np.complex128)]
+    st = load().cfie_dirprec_level(int(n), int(p), int(level), float(omega), float(eta), float(L),
+                                   *[a.view(np.float64).ctypes.data_as(_DP) for a in out])
+    if st != CFIE_OK:
+        raise CfieError(st, "cfie_dirprec_level: invalid sizes or a singular block")
+    return tuple(out)
 
 
 def arclength_samples(kind, n, **params):

@@ -167,7 +167,7 @@ cfie_status cfie_dirprec_plan(cfie_curve kind, const double* params, int nparams
  *  Binv: B^-1;  U: c x K, K = 2^(l+1) + 1, U(x, m) = exp(i k_m (x - (c-1)/2) L / n)
  *     with k_m = -omega + 2 omega m / (K - 1);  T: K x K, (U^t B^-1 U)^-1.
  * Each output (host, complex128 interleaved, row-major) may be NULL to skip it.
- * n even, 8 <= n <= 2^20, c <= min(n / 2, 4096), omega, eta, L > 0.
+ * n even, 8 <= n <= 2^20, c <= min(n / 2, 1024), omega, eta, L > 0.
  * CFIE_EINVAL for invalid arguments or a singular block.  Host only. */
 cfie_status cfie_dirprec_level(int n, int p, int level, double omega, double eta, double L,
                                double* B, double* Binv, double* U, double* T);

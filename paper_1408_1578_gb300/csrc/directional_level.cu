@@ -81,7 +81,7 @@ extern "C" cfie_status cfie_dirprec_level(int n, int p, int level, double omega,
                                           double* T) {
   if (n < 8 || n % 2 != 0 || n > (1 << 20) || p < 1 || level < 0 || level > 20) return CFIE_EINVAL;
   const long long cl = (1LL << level) * p;
-  if (cl > n / 2 || cl > 4096) return CFIE_EINVAL;
+  if (cl > n / 2 || cl > 1024) return CFIE_EINVAL;
   if (!(omega > 0) || !(eta > 0) || !(L > 0) || !std::isfinite(omega) || !std::isfinite(eta) ||
       !std::isfinite(L))
     return CFIE_EINVAL;

@@ -65,6 +65,7 @@ def test_blocks_are_consistent():
     (2048, 8, 2, 10.0, 10.0, float("nan")),
     (2048, 0, 2, 10.0, 10.0, 1.0),       # p
     (2048, 8, -1, 10.0, 10.0, 1.0),      # level
+    (65536, 8, 8, 10.0, 10.0, 1.0),      # 2^l p = 2048 > 1024
 ])
 def test_invalid_arguments(lib, args):
     assert lib.cfie_dirprec_level(*args, None, None, None, None) == cfie.CFIE_EINVAL

@@ -268,3 +268,23 @@ def test_iteration_count_script(bc):
     L = geometry.Arclength("ellipse", a=1.0, b=0.5).L
     assert n == 512 and abs(omega - 2 * np.pi * 64 / L) < 1e-9
     assert 0 < n_p <= n_n
+
+
+def test_preconditioner_on_a_curve_with_non_planar_leaves():
+    """The kite's tip (curvature up to ~11.7) forces segments down to level 1,
+    the non-planar leaves of Section 2.1 (m_leaf = 2); the preconditioner still
+    solves its approximation exactly and cuts the GMRES iterations."""
+    arc = geometry.Arclength("kite")
+    q, p = 3, 8
+    n = 4**q * p
+    w = 2 * np.pi * (n / p) / arc.L
+    P = directional.Directional(arc, q, p, w, eta=0.5 * w)
+    assert P.level.min() <= 1 and P.level.max() == q
+    A = operators.soft_matrix(P.curve, w, 0.5 * w)
+    f = operators.plane_wave_rhs(P.curve, w, [0.0], "soft")[:, 0]
+    T, Ws = P.exact_solver()
+    ref = np.linalg.solve(P.approximation(), f)
+    assert np.linalg.norm(P.apply(f, T=T, W_solve=Ws) - ref) < 1e-10 * np.linalg.norm(ref)
+    _, it0, _ = directional.preconditioned_gmres(A, None, f, rtol=1e-6)
+    _, it1, r1 = directional.preconditioned_gmres(A, P.apply, f, rtol=1e-6)
+    assert r1 <= 1e-6 and it1 < it0

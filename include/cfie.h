@@ -172,6 +172,12 @@ cfie_status cfie_dirprec_plan(cfie_curve kind, const double* params, int nparams
 cfie_status cfie_dirprec_level(int n, int p, int level, double omega, double eta, double L,
                                double* B, double* Binv, double* U, double* T);
 
+/* T~ of Section 2.2: the `keep` entries of the K x K block T (host,
+ * complex128 interleaved, row-major) largest in modulus, copied to Tt, every
+ * other entry zero; entries tied in modulus with the smallest one kept are
+ * kept too.  keep >= K^2 copies T.  1 <= K <= 4097, keep >= 0.  Host only. */
+cfie_status cfie_dirprec_threshold(int K, const double* T, int keep, double* Tt);
+
 /* --- Discretisation ------------------------------------------------------ */
 
 /* Sample the curve at n nodes on the device, build the Kress weight table and

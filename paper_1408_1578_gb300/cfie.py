@@ -96,6 +96,7 @@ SIGNATURES = {
     "cfie_arclength_samples": (_I, [_I, _DP, _I, _I, _DP, _DP, _DP, _DP]),
     "cfie_dirprec_plan": (_I, [_I, _DP, _I, _I, _I, _D, _I, _I, _IP, _IP, _IP, _IP]),
     "cfie_dirprec_level": (_I, [_I, _I, _I, _D, _D, _D, _DP, _DP, _DP, _DP]),
+    "cfie_dirprec_threshold": (_I, [_I, _DP, _I, _DP]),
     "cfie_discretise": (_I, [_P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(_P)]),
     "cfie_op_destroy": (None, [_P]),
     "cfie_op_n": (_I, [_P]),
@@ -227,6 +228,18 @@ def dirprec_level(n, p, level, omega, eta, L):
     if st != CFIE_OK:
         raise CfieError(st, "cfie_dirprec_level: invalid sizes or a singular block")
     return tuple(out)
+
+
+def dirprec_threshold(T, keep):
+    """cfie_dirprec_threshold: T~, the `keep` entries of T largest in modulus
+    (host; no GPU needed)."""
+    T = np.ascontiguousarray(T, dtype=np.complex128)
+    out = np.empty_like(T)
+    st = load().cfie_dirprec_threshold(int(T.shape[0]), T.view(np.float64).ctypes.data_as(_DP),
+                                       int(keep), out.view(np.float64).ctypes.data_as(_DP))
+    if st != CFIE_OK:
+        raise CfieError(st, "cfie_dirprec_threshold: invalid size")
+    return out
 
 
 def arclength_samples(kind, n, **params):

@@ -18,6 +18,7 @@
 // - (4 pi / n^2) (-1)^d are summed with the index m d reduced mod n exactly;
 // J0 and Y0 come from the C++17 special functions.  Inverses: Gaussian
 // elimination with partial pivoting on [A | I].
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -154,6 +155,36 @@ extern "C" cfie_status cfie_dirprec_level(int n, int p, int level, double omega,
         }
       if (!invert(S, K, Tm)) return CFIE_EINVAL;
       store(Tm, T);
+    }
+    return CFIE_OK;
+  } catch (...) {
+    return CFIE_ENOMEM;
+  }
+}
+
+// T~: the `keep` largest entries of a K x K block in modulus, the rest zero
+// (Section 2.2: T is numerically sparse; the number kept is proportional to K).
+// Entries equal in modulus to the smallest one kept are all kept.
+extern "C" cfie_status cfie_dirprec_threshold(int K, const double* T, int keep, double* Tt) {
+  if (K < 1 || K > 4097 || !T || !Tt || keep < 0) return CFIE_EINVAL;
+  try {
+    const size_t total = (size_t)K * K;
+    if ((size_t)keep >= total) {
+      std::copy(T, T + 2 * total, Tt);
+      return CFIE_OK;
+    }
+    std::vector<double> mag(total);
+    for (size_t i = 0; i < total; ++i) mag[i] = std::hypot(T[2 * i], T[2 * i + 1]);
+    double cut = INFINITY;
+    if (keep > 0) {
+      std::vector<double> sorted = mag;
+      std::nth_element(sorted.begin(), sorted.begin() + (total - keep), sorted.end());
+      cut = sorted[total - keep];
+    }
+    for (size_t i = 0; i < total; ++i) {
+      const bool in = keep > 0 && mag[i] >= cut;
+      Tt[2 * i] = in ? T[2 * i] : 0.0;
+      Tt[2 * i + 1] = in ? T[2 * i + 1] : 0.0;
     }
     return CFIE_OK;
   } catch (...) {

@@ -69,3 +69,42 @@ def test_blocks_are_consistent():
 ])
 def test_invalid_arguments(lib, args):
     assert lib.cfie_dirprec_level(*args, None, None, None, None) == cfie.CFIE_EINVAL
+
+
+def test_threshold_matches_the_oracle():
+    """T~ keeps the 4 K largest entries of T (reading P7): identical to the
+    oracle's on the same T; from the library's own T_l, identical wherever an
+    entry's modulus is not within rounding of the cut."""
+    arc = geometry.Arclength("ellipse", a=1.0, b=0.5)
+    q, p = 4, 8
+    n = 4**q * p
+    w = 2 * np.pi * (n / p) / arc.L
+    P = directional.Directional(arc, q, p, w)
+    for level in sorted(set(P.level.tolist())):
+        i = int(np.nonzero(P.level == level)[0][0])
+        T = P.T[i]
+        K = T.shape[0]
+        assert np.array_equal(cfie.dirprec_threshold(T, 4 * K), P.Tt[i].toarray())
+        mine = cfie.dirprec_threshold(cfie.dirprec_level(n, p, level, w, w, arc.L)[3], 4 * K)
+        ref = P.Tt[i].toarray()
+        cut = np.sort(np.abs(T).ravel())[-4 * K]
+        clear = np.abs(np.abs(T) - cut) > 1e-9 * cut
+        assert np.array_equal(mine[clear] != 0, ref[clear] != 0)
+        assert np.max(np.abs(mine - ref)[clear]) < 1e-12 * np.max(np.abs(T))
+
+
+def test_threshold_edges(lib):
+    T = np.arange(9, dtype=float).reshape(3, 3) * (1 + 1j)
+    assert not np.any(cfie.dirprec_threshold(T, 0))
+    assert np.array_equal(cfie.dirprec_threshold(T, 9), T)
+    assert np.array_equal(cfie.dirprec_threshold(T, 100), T)
+    kept = cfie.dirprec_threshold(T, 2)
+    assert np.count_nonzero(kept) == 2 and kept[2, 2] == T[2, 2] and kept[2, 1] == T[2, 1]
+    import ctypes
+    buf = np.zeros(18)
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert lib.cfie_dirprec_threshold(0, buf.ctypes.data_as(dp), 1,
+                                      buf.ctypes.data_as(dp)) == cfie.CFIE_EINVAL
+    assert lib.cfie_dirprec_threshold(3, buf.ctypes.data_as(dp), -1,
+                                      buf.ctypes.data_as(dp)) == cfie.CFIE_EINVAL
+    assert lib.cfie_dirprec_threshold(3, None, 1, buf.ctypes.data_as(dp)) == cfie.CFIE_EINVAL

@@ -31,6 +31,19 @@ using cplx = std::complex<double>;
 constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr double kEulerGamma = 0.57721566490153286060651209008240243;
 
+// y[c] -= f x[c] for c < len, in real arithmetic (std::complex products take
+// the slow path that handles infinities and NaNs)
+inline void axpy_neg(cplx f, const cplx* x, cplx* y, int len) {
+  const double fr = f.real(), fi = f.imag();
+  const double* xs = reinterpret_cast<const double*>(x);
+  double* ys = reinterpret_cast<double*>(y);
+  for (int c = 0; c < len; ++c) {
+    const double xr = xs[2 * c], xi = xs[2 * c + 1];
+    ys[2 * c] -= fr * xr - fi * xi;
+    ys[2 * c + 1] -= fr * xi + fi * xr;
+  }
+}
+
 // A^-1 of a k x k row-major matrix; false if a pivot vanishes
 bool invert(std::vector<cplx>& A, int k, std::vector<cplx>& out) {
   out.assign((size_t)k * k, cplx(0.0));
@@ -58,10 +71,8 @@ bool invert(std::vector<cplx>& A, int k, std::vector<cplx>& out) {
       if (r == col) continue;
       const cplx f = A[(size_t)r * k + col];
       if (f == 0.0) continue;
-      for (int c = 0; c < k; ++c) {
-        A[(size_t)r * k + c] -= f * A[(size_t)col * k + c];
-        out[(size_t)r * k + c] -= f * out[(size_t)col * k + c];
-      }
+      axpy_neg(f, &A[(size_t)col * k], &A[(size_t)r * k], k);
+      axpy_neg(f, &out[(size_t)col * k], &out[(size_t)r * k], k);
     }
   }
   return true;
@@ -108,24 +119,20 @@ extern "C" cfie_status cfie_dirprec_level(int n, int p, int level, double omega,
     const double m1d = -g / (4.0 * kPi);
     const cplx m2d = (cplx(0.0, 0.25) - kEulerGamma / (2.0 * kPi) -
                       std::log(omega * g / 2.0) / (2.0 * kPi)) * g;
-    const cplx sdiag = R[0] * m1d + h * m2d;
-    for (int a = 0; a < c; ++a) {
-      for (int b = 0; b < c; ++b) {
-        cplx s;
-        if (a == b) {
-          s = sdiag;
-        } else {
-          const int d = std::abs(a - b);
-          const double x = omega * d * h * g;
-          const double j0 = std::cyl_bessel_j(0.0, x), y0 = std::cyl_neumann(0.0, x);
-          const cplx M = cplx(0.0, 0.25) * cplx(j0, y0) * g;
-          const double M1 = -j0 * g / (4.0 * kPi);
-          const double sn = std::sin(kPi * d / n);
-          s = R[d] * M1 + h * (M - M1 * std::log(4.0 * sn * sn));
-        }
-        Bm[(size_t)a * c + b] = (a == b ? 0.5 : 0.0) - I * eta * s;
-      }
+    // the block is Toeplitz: one single-layer entry per distance d = |a - b|
+    std::vector<cplx> srow(c);
+    srow[0] = R[0] * m1d + h * m2d;
+    for (int d = 1; d < c; ++d) {
+      const double x = omega * d * h * g;
+      const double j0 = std::cyl_bessel_j(0.0, x), y0 = std::cyl_neumann(0.0, x);
+      const cplx M = cplx(0.0, 0.25) * cplx(j0, y0) * g;
+      const double M1 = -j0 * g / (4.0 * kPi);
+      const double sn = std::sin(kPi * d / n);
+      srow[d] = R[d] * M1 + h * (M - M1 * std::log(4.0 * sn * sn));
     }
+    for (int a = 0; a < c; ++a)
+      for (int b = 0; b < c; ++b)
+        Bm[(size_t)a * c + b] = (a == b ? 0.5 : 0.0) - I * eta * srow[std::abs(a - b)];
     store(Bm, B);
     std::vector<cplx> work = Bm, Bi;
     if (!invert(work, c, Bi)) return CFIE_EINVAL;
@@ -144,15 +151,11 @@ extern "C" cfie_status cfie_dirprec_level(int n, int p, int level, double omega,
     if (T) {
       std::vector<cplx> BU((size_t)c * K, cplx(0.0)), S((size_t)K * K, cplx(0.0)), Tm;
       for (int a = 0; a < c; ++a)
-        for (int b = 0; b < c; ++b) {
-          const cplx v = Bi[(size_t)a * c + b];
-          for (int m = 0; m < K; ++m) BU[(size_t)a * K + m] += v * Um[(size_t)b * K + m];
-        }
+        for (int b = 0; b < c; ++b)
+          axpy_neg(-Bi[(size_t)a * c + b], &Um[(size_t)b * K], &BU[(size_t)a * K], K);
       for (int x = 0; x < c; ++x)
-        for (int r = 0; r < K; ++r) {
-          const cplx u = Um[(size_t)x * K + r];
-          for (int m = 0; m < K; ++m) S[(size_t)r * K + m] += u * BU[(size_t)x * K + m];
-        }
+        for (int r = 0; r < K; ++r)
+          axpy_neg(-Um[(size_t)x * K + r], &BU[(size_t)x * K], &S[(size_t)r * K], K);
       if (!invert(S, K, Tm)) return CFIE_EINVAL;
       store(Tm, T);
     }

@@ -17,6 +17,10 @@
  *
  * Call sequence: cfie_ctx_create -> cfie_geometry_* -> cfie_discretise ->
  * cfie_rhs_plane_waves -> cfie_apply / cfie_gmres_solve -> *_destroy.
+ * Host-only helpers that need no context or GPU: cfie_arclength_samples (the
+ * node set of Section 2, for cfie_geometry_samples) and the setup pieces of the
+ * directional preconditioner of Section 2 (cfie_dirprec_plan,
+ * cfie_dirprec_level, cfie_dirprec_threshold).
  *
  * Conventions for every entry point:
  *  - All compute runs on the context's CUDA device and stream; calls that take

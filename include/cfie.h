@@ -162,6 +162,19 @@ cfie_status cfie_dirprec_plan(cfie_curve kind, const double* params, int nparams
                               double omega, int m_leaf, int capacity, int* m, int* first,
                               int* level, int* kpair);
 
+/* Sparsity pattern of W~ = E + antidiag(T) (Section 2.2) from a plan of m
+ * segments (level, kpair as cfie_dirprec_plan writes them).  Segment i owns the
+ * K_i = 2^(level[i]+1) + 1 frequency unknowns from koff[i]; koff (host, m + 1
+ * ints) and *nnz = m (m - 1) + sum K_i are always written.  With row and col
+ * (host, capacity ints each, capacity >= *nnz) the positions follow: first
+ * E's entry of every ordered pair i != j, i major, at
+ * (koff[i] + k^i_ij, koff[j] + k^j_ij); then the anti-diagonal of every T block,
+ * (koff[i] + r, koff[i] + K_i - 1 - r), r = 0 .. K_i - 1.  row and col both
+ * NULL: sizes only.  CFIE_EINVAL for out-of-range levels or indices, or too
+ * small a capacity.  Host only. */
+cfie_status cfie_dirprec_w_pattern(int m, const int* level, const int* kpair, int capacity,
+                                   int* koff, int* nnz, int* row, int* col);
+
 /* Level blocks of the directional preconditioner (Section 2.2, sound soft) for
  * the segments of level l (c = 2^l p nodes) of an n-node arclength
  * discretisation of a curve of perimeter L:

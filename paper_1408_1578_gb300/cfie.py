@@ -95,6 +95,7 @@ SIGNATURES = {
     "cfie_geom_destroy": (None, [_P]),
     "cfie_arclength_samples": (_I, [_I, _DP, _I, _I, _DP, _DP, _DP, _DP]),
     "cfie_dirprec_plan": (_I, [_I, _DP, _I, _I, _I, _D, _I, _I, _IP, _IP, _IP, _IP]),
+    "cfie_dirprec_w_pattern": (_I, [_I, _IP, _IP, _I, _IP, _IP, _IP, _IP]),
     "cfie_dirprec_level": (_I, [_I, _I, _I, _D, _D, _D, _DP, _DP, _DP, _DP]),
     "cfie_dirprec_threshold": (_I, [_I, _DP, _I, _DP]),
     "cfie_discretise": (_I, [_P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(_P)]),
@@ -215,6 +216,28 @@ def dirprec_plan(kind, q, p, omega, m_leaf=2, **params):
     if st != CFIE_OK:
         raise CfieError(st, "cfie_dirprec_plan")
     return first, level, kpair
+
+
+def dirprec_w_pattern(level, kpair):
+    """cfie_dirprec_w_pattern: (koff, row, col) of W~ = E + antidiag(T) from a
+    plan's levels and wave-number pairs (host; no GPU needed)."""
+    level = np.ascontiguousarray(level, dtype=np.int32)
+    kpair = np.ascontiguousarray(kpair, dtype=np.int32)
+    m = int(level.size)
+    koff = np.zeros(m + 1, dtype=np.int32)
+    nnz = ctypes.c_int()
+    lib = load()
+    args = (m, level.ctypes.data_as(_IP), kpair.ctypes.data_as(_IP))
+    st = lib.cfie_dirprec_w_pattern(*args, 0, koff.ctypes.data_as(_IP), ctypes.byref(nnz), None, None)
+    if st != CFIE_OK:
+        raise CfieError(st, "cfie_dirprec_w_pattern")
+    row = np.zeros(nnz.value, dtype=np.int32)
+    col = np.zeros(nnz.value, dtype=np.int32)
+    st = lib.cfie_dirprec_w_pattern(*args, nnz.value, koff.ctypes.data_as(_IP), ctypes.byref(nnz),
+                                    row.ctypes.data_as(_IP), col.ctypes.data_as(_IP))
+    if st != CFIE_OK:
+        raise CfieError(st, "cfie_dirprec_w_pattern")
+    return koff, row, col
 
 
 def dirprec_level(n, p, level, omega, eta, L):

@@ -114,3 +114,47 @@ extern "C" cfie_status cfie_dirprec_plan(cfie_curve kind, const double* params, 
     return CFIE_ENOMEM;
   }
 }
+
+// Positions of W~ = E + antidiag(T) (Section 2.2) in the frequency unknowns:
+// segment i owns K_i = 2^(level_i + 1) + 1 consecutive unknowns from
+// koff[i].  Entries in this order: for every ordered pair i != j (i major),
+// E's one entry (koff[i] + k^i_ij, koff[j] + k^j_ij); then for every segment
+// the anti-diagonal of its T block, (koff[i] + r, koff[i] + K_i - 1 - r).
+extern "C" cfie_status cfie_dirprec_w_pattern(int m, const int* level, const int* kpair,
+                                              int capacity, int* koff, int* nnz, int* row,
+                                              int* col) {
+  if (m < 1 || !level || !kpair || !koff || !nnz) return CFIE_EINVAL;
+  long long total = 0, count = (long long)m * (m - 1);
+  koff[0] = 0;
+  for (int i = 0; i < m; ++i) {
+    if (level[i] < 0 || level[i] > 20) return CFIE_EINVAL;
+    const int K = (1 << (level[i] + 1)) + 1;
+    total += K;
+    count += K;
+    if (total > (1LL << 30)) return CFIE_EINVAL;
+    koff[i + 1] = int(total);
+  }
+  if (count > (1LL << 30)) return CFIE_EINVAL;
+  *nnz = int(count);
+  if (!row && !col) return CFIE_OK;
+  if (!row || !col || capacity < count) return CFIE_EINVAL;
+  long long e = 0;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      if (i == j) continue;
+      const int* kp = kpair + 2 * ((size_t)i * m + j);
+      const int Ki = koff[i + 1] - koff[i], Kj = koff[j + 1] - koff[j];
+      if (kp[0] < 0 || kp[0] >= Ki || kp[1] < 0 || kp[1] >= Kj) return CFIE_EINVAL;
+      row[e] = koff[i] + kp[0];
+      col[e] = koff[j] + kp[1];
+      ++e;
+    }
+  for (int i = 0; i < m; ++i) {
+    const int K = koff[i + 1] - koff[i];
+    for (int r = 0; r < K; ++r, ++e) {
+      row[e] = koff[i] + r;
+      col[e] = koff[i] + K - 1 - r;
+    }
+  }
+  return CFIE_OK;
+}

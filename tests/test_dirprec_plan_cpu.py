@@ -75,3 +75,35 @@ def test_invalid_sizes(lib, q, p, omega, m_leaf):
     m = ctypes.c_int()
     assert lib.cfie_dirprec_plan(cfie.CFIE_CURVE_KITE, None, 0, q, p, omega, m_leaf, 0,
                                  ctypes.byref(m), None, None, None) == cfie.CFIE_EINVAL
+
+
+@pytest.mark.parametrize("kind,params", [("ellipse", {"a": 1.0, "b": 0.5}), ("kite", {})])
+def test_w_pattern_matches_the_oracle(kind, params):
+    """Positions of W~ = E + antidiag(T): the oracle's sparse W~ has exactly
+    these non-zeros, one per ordered segment pair plus every anti-diagonal."""
+    p, q = 8, 4
+    arc = geometry.Arclength(kind, **params)
+    n = 4**q * p
+    w = 2 * np.pi * (n / p) / arc.L
+    first, level, kpair = cfie.dirprec_plan(kind, q, p, w, **params)
+    koff, row, col = cfie.dirprec_w_pattern(level, kpair)
+    P = directional.Directional(arc, q, p, w)
+    assert np.array_equal(koff, P.koff)
+    W = P.W.tocoo()
+    assert len(row) == W.nnz
+    assert set(zip(row.tolist(), col.tolist())) == set(zip(W.row.tolist(), W.col.tolist()))
+
+
+def test_w_pattern_rejects_bad_indices(lib):
+    level = np.array([1, 1], dtype=np.int32)
+    kpair = np.zeros((2, 2, 2), dtype=np.int32)
+    kpair[0, 1] = (5, 0)                 # K = 5: index 5 is out of range
+    koff = np.zeros(3, dtype=np.int32)
+    nnz = ctypes.c_int()
+    ip = ctypes.POINTER(ctypes.c_int)
+    row = np.zeros(16, dtype=np.int32)
+    col = np.zeros(16, dtype=np.int32)
+    st = lib.cfie_dirprec_w_pattern(2, level.ctypes.data_as(ip), kpair.ctypes.data_as(ip), 16,
+                                    koff.ctypes.data_as(ip), ctypes.byref(nnz),
+                                    row.ctypes.data_as(ip), col.ctypes.data_as(ip))
+    assert st == cfie.CFIE_EINVAL and nnz.value == 2 + 10 and list(koff) == [0, 5, 10]

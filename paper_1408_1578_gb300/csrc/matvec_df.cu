@@ -141,8 +141,6 @@ __constant__ float4 kSinCos[65] = {
 };
 __constant__ float kPi32H = 0.09817477315664291f, kPi32L = -2.7319617679211206e-09f;
 __constant__ float kPi4H = 0.7853981852531433f, kPi4L = -2.1855694143368964e-08f;
-__constant__ float kSq2PiH = 0.7978845834732056f, kSq2PiL = -2.2670340271702116e-08f;
-__constant__ float kI4PiH = 0.07957746833562851f, kI4PiL = 3.2103191216492633e-09f;
 __constant__ float kN6H = -0.1666666716337204f, kN6L = 4.967053879312289e-09f;
 // 2 pi = C1 + C2 + C3, C1 on 10 significant bits
 __constant__ float kC1 = 6.28125f, kC2 = 0.0019353071693331003f, kC3 = 1.0253376273028358e-11f;

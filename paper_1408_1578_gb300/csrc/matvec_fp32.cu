@@ -585,7 +585,6 @@ void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs) {
   P.h = (float)op->h;
   P.g = geo32{base, base + n, base + 2 * n, base + 3 * n, base + 4 * n, base + 5 * n, base + 6 * n};
   P.w32 = base + 7 * n;
-  const float* c32 = base + 8 * n;
   const size_t bw = 2 * (size_t)op->band_b + 1;
   P.band = op->band.as<float2>();
   P.band2 = hard ? P.band + (size_t)n * bw : nullptr;

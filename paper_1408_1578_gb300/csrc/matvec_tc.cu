@@ -45,7 +45,7 @@ constexpr int TSTAGES = 2;
 constexpr int CK = 8;
 constexpr int WKW = TBM + TBK + 2;   // Kress window of a tile (+ alignment slack)
 constexpr int NPROD = 16;    // producer warps
-constexpr int WTMA = NPROD, WMMA = NPROD + 1, WEPI0 = NPROD + 2;
+constexpr int WTMA = NPROD, WMMA = NPROD + 1;   // then the epilogue warps
 constexpr int TNT = (NPROD + 6) * 32;
 
 struct tc_params {

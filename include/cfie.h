@@ -164,14 +164,15 @@ cfie_status cfie_dirprec_plan(cfie_curve kind, const double* params, int nparams
 
 /* Sparsity pattern of W~ = E + antidiag(T) (Section 2.2) from a plan of m
  * segments (level, kpair as cfie_dirprec_plan writes them).  Segment i owns the
- * K_i = 2^(level[i]+1) + 1 frequency unknowns from koff[i]; koff (host, m + 1
- * ints) and *nnz = m (m - 1) + sum K_i are always written.  With row and col
+ * K_i = 2^(level[i]+1) + 1 frequency unknowns from koff[i]; on success koff
+ * (host, m + 1 ints) and *nnz = m (m - 1) + sum K_i are written.  With row and col
  * (host, capacity ints each, capacity >= *nnz) the positions follow: first
  * E's entry of every ordered pair i != j, i major, at
  * (koff[i] + k^i_ij, koff[j] + k^j_ij); then the anti-diagonal of every T block,
  * (koff[i] + r, koff[i] + K_i - 1 - r), r = 0 .. K_i - 1.  row and col both
  * NULL: sizes only.  CFIE_EINVAL for out-of-range levels or indices, or too
- * small a capacity.  Host only. */
+ * small a capacity, checked before any output is written (outputs untouched).
+ * Host only. */
 cfie_status cfie_dirprec_w_pattern(int m, const int* level, const int* kpair, int capacity,
                                    int* koff, int* nnz, int* row, int* col);
 
@@ -250,7 +251,8 @@ cfie_status cfie_apply_fp64(cfie_op* op, const void* x_dev, void* y_dev, int nrh
  * (soft) 16 * n * nrhs bytes, (hard) 96 * n * nrhs bytes at the least;
  * larger requests return CFIE_EINVAL with a message.  The first call on a
  * device looks the array's device address up (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  Calls
+ * device current, and so does the first call after the device's context was
+ * replaced (cudaDeviceReset); make such a call before any stream capture.  Calls
  * share the array: calls that overlap on the GPU (other streams, other host
  * threads) race.  Every scratch element a call reads was written by the same
  * call, so nothing needs clearing between calls.  Arguments as cfie_apply. */

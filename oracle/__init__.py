@@ -23,9 +23,7 @@ Every function names the passage it follows.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms (disk eigenvalues, Fourier-Bessel series, interior point
-source identity, trigonometric exactness, Wronskian, brute force), except
-directional.flat_block_hard, the sound-hard flat block of the preconditioner
-(not used by default), which is "parity unpinned".
+source identity, trigonometric exactness, Wronskian, brute force).
 
 Modules
 -------

@@ -46,10 +46,8 @@ interpolation, the curvature, the partition rules and the e_ij of eq. (entry)
 against the least-squares constants over the nodes are pinned by
 tests/test_oracle_directional.py, and so is the sound-soft flat B_l, diagonal
 included: it equals the CFIE matrix of operators.soft_matrix on the straight
-sides of a stadium sampled in arclength.  flat_block_hard (not the default) is
-parity unpinned: on a closed curve the spectral derivative of Maue's identity
-couples a straight side to the whole curve, so no closed curve reproduces it;
-it is checked only through the closeness of B + U E U^t to M.
+sides of a stadium sampled in arclength.  The sound-hard operator takes the
+matrix's own diagonal blocks, pinned with the matrix.
 """
 import numpy as np
 import scipy.linalg as sla
@@ -185,27 +183,6 @@ def flat_single_layer(n, level, p, omega, L):
     return S
 
 
-def flat_block_hard(n, level, p, omega, eta, L):
-    """B_l of the sound-hard operator (eq. 2) on a straight segment: D' vanishes
-    (the normal is orthogonal to every chord) and Maue's identity reduces to
-    N = d/ds S d/ds + omega^2 S (n1^2 + n2^2 = 1); d/ds is the curve's spectral
-    derivative (trigonometric interpolant on all n nodes, Nyquist mode zeroed)
-    restricted to the segment, divided by the speed L / (2 pi).  Parity
-    unpinned."""
-    from .operators import spectral_derivative
-    cnt = 2**level * p
-    g = L / (2.0 * np.pi)
-    S = flat_single_layer(n, level, p, omega, L)
-    e0 = np.zeros(n)
-    e0[0] = 1.0
-    col = spectral_derivative(e0).real           # column 0 of the circulant d/dt
-    a = np.arange(cnt)
-    Dt = col[(a[:, None] - a[None, :]) % n] / g
-    B = (Dt @ S @ Dt + omega**2 * S) / (1j * eta)
-    B[np.diag_indices(cnt)] += 0.5
-    return B
-
-
 def flat_block(n, level, p, omega, eta, L):
     """B_l: the sound-soft entries on a straight segment of 2^l p nodes with
     the spacing and speed L / (2 pi) of the curve's arclength discretisation
@@ -230,17 +207,19 @@ class Directional:
     samples): the mean of M~_ij over P_i x P_j, taken from the dense matrix
     `A`; e_from = "nodes" does the same for the soft operator.
 
-    The diagonal blocks are the flat-segment B_l (b_from = "flat", the default
-    for soft) or the matrix's own diagonal blocks M_jj (b_from = "matrix", the
-    default for hard: the flat restriction of Maue's N, with the curve's
-    spectral derivative cut to the segment, misses 15-20 % of the block and
-    slows GMRES down instead of speeding it up)."""
+    The diagonal blocks are the flat-segment B_l (b_from = "flat", sound soft
+    only, its default) or the matrix's own diagonal blocks M_jj (b_from =
+    "matrix", the only form for hard: a flat restriction of Maue's N, with the
+    curve's spectral derivative cut to the segment, has no closed-form check
+    and missed 15-20 % of the block)."""
 
     def __init__(self, arc, q, p, omega, eta=None, m_leaf=2, m_c=10, t_keep=4, bc="soft",
                  A=None, e_from=None, b_from=None):
         self.bc = bc
         e_from = e_from or ("chebyshev" if bc == "soft" else "nodes")
         b_from = b_from or ("flat" if bc == "soft" else "matrix")
+        if b_from == "flat" and bc != "soft":
+            raise ValueError("the flat diagonal block is the sound-soft one: b_from='matrix'")
         if (e_from == "nodes" or b_from == "matrix") and A is None:
             raise ValueError("the nodal E and the matrix blocks need the dense matrix A")
         self.arc, self.q, self.p = arc, q, p
@@ -265,9 +244,8 @@ class Directional:
         self.m = m
         # B blocks (one per level) and their inverses
         levels = sorted(set(self.level.tolist()))
-        fb = flat_block if bc == "soft" else flat_block_hard
         if b_from == "flat":
-            Bl = {l: fb(n, l, p, omega, self.eta, L) for l in levels}
+            Bl = {l: flat_block(n, l, p, omega, self.eta, L) for l in levels}
             Bli = {l: np.linalg.inv(Bl[l]) for l in levels}
             self.Bseg = [Bl[l] for l in self.level]
             self.Binv = [Bli[l] for l in self.level]

@@ -124,37 +124,48 @@ extern "C" cfie_status cfie_dirprec_w_pattern(int m, const int* level, const int
                                               int capacity, int* koff, int* nnz, int* row,
                                               int* col) {
   if (m < 1 || !level || !kpair || !koff || !nnz) return CFIE_EINVAL;
-  long long total = 0, count = (long long)m * (m - 1);
-  koff[0] = 0;
-  for (int i = 0; i < m; ++i) {
-    if (level[i] < 0 || level[i] > 20) return CFIE_EINVAL;
-    const int K = (1 << (level[i] + 1)) + 1;
-    total += K;
-    count += K;
-    if (total > (1LL << 30)) return CFIE_EINVAL;
-    koff[i + 1] = int(total);
-  }
-  if (count > (1LL << 30)) return CFIE_EINVAL;
-  *nnz = int(count);
-  if (!row && !col) return CFIE_OK;
-  if (!row || !col || capacity < count) return CFIE_EINVAL;
-  long long e = 0;
-  for (int i = 0; i < m; ++i)
-    for (int j = 0; j < m; ++j) {
-      if (i == j) continue;
-      const int* kp = kpair + 2 * ((size_t)i * m + j);
-      const int Ki = koff[i + 1] - koff[i], Kj = koff[j + 1] - koff[j];
-      if (kp[0] < 0 || kp[0] >= Ki || kp[1] < 0 || kp[1] >= Kj) return CFIE_EINVAL;
-      row[e] = koff[i] + kp[0];
-      col[e] = koff[j] + kp[1];
-      ++e;
+  // every argument is checked before any output is written
+  try {
+    std::vector<int> ko((size_t)m + 1, 0);
+    long long total = 0, count = (long long)m * (m - 1);
+    for (int i = 0; i < m; ++i) {
+      if (level[i] < 0 || level[i] > 20) return CFIE_EINVAL;
+      const int K = (1 << (level[i] + 1)) + 1;
+      total += K;
+      count += K;
+      if (total > (1LL << 30)) return CFIE_EINVAL;
+      ko[i + 1] = int(total);
     }
-  for (int i = 0; i < m; ++i) {
-    const int K = koff[i + 1] - koff[i];
-    for (int r = 0; r < K; ++r, ++e) {
-      row[e] = koff[i] + r;
-      col[e] = koff[i] + K - 1 - r;
+    if (count > (1LL << 30)) return CFIE_EINVAL;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        if (i == j) continue;
+        const int* kp = kpair + 2 * ((size_t)i * m + j);
+        if (kp[0] < 0 || kp[0] >= ko[i + 1] - ko[i] || kp[1] < 0 || kp[1] >= ko[j + 1] - ko[j])
+          return CFIE_EINVAL;
+      }
+    if ((row || col) && (!row || !col || capacity < count)) return CFIE_EINVAL;
+    std::copy(ko.begin(), ko.end(), koff);
+    *nnz = int(count);
+    if (!row) return CFIE_OK;
+    long long e = 0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        if (i == j) continue;
+        const int* kp = kpair + 2 * ((size_t)i * m + j);
+        row[e] = ko[i] + kp[0];
+        col[e] = ko[j] + kp[1];
+        ++e;
+      }
+    for (int i = 0; i < m; ++i) {
+      const int K = ko[i + 1] - ko[i];
+      for (int r = 0; r < K; ++r, ++e) {
+        row[e] = ko[i] + r;
+        col[e] = ko[i] + K - 1 - r;
+      }
     }
+    return CFIE_OK;
+  } catch (...) {
+    return CFIE_ENOMEM;
   }
-  return CFIE_OK;
 }

@@ -518,7 +518,8 @@ __global__ void k_df_x_hard(int n, size_t len, const double2* __restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
-// Sound-soft residual with the source sums on the tensor cores.
+// Residual with the source sums on the tensor cores (the sound-soft entries,
+// or S or D' of the sound-hard operator).
 //
 // Far pairs (outside the double-float band) are evaluated in double-float as
 // above and written as bf16 slices: with E_i the row's exponent (every far
@@ -527,23 +528,36 @@ __global__ void k_df_x_hard(int n, size_t len, const double2* __restrict__ x,
 // at a time, and slice s is stored as q_s 2^(-8(s-1)), exact in bf16.  The
 // densities are sliced the same way per right-hand side (exponent F_r).  The
 // products of slice pairs (s, t) with s + t <= 7 are summed by tcgen05.mma into
-// four FP32 accumulators by level L = s + t: L = 2, 3, 4 (one each) and L >= 5
-// (together).  Within one level every product is an integer multiple of the
-// same power of two and stays below 2^14 of it, so 128 sources (256 terms with
-// the split complex product, 768 for level 4) sum exactly in FP32; only the
-// levels >= 5 (below 2^-24 of the result) round.  Every 128 sources the
-// producer warps add the four levels in double-float, scale by
+// FP32 accumulators by level L = s + t.  Within one level every product is an
+// integer multiple of the same power of two and stays below 2^14 of it, so a
+// chunk of 128 sources (256 terms with the split complex product for L = 2,
+// 512 for L = 3, 768 for L = 4, 1024 for L = 5) sums exactly in FP32 whatever
+// the tensor core's rounding.  With up to 32 right-hand sides per pass the
+// tensor memory holds five accumulators: L = 2, 3, 4, 5 exact and L = 6, 7
+// together (below 2^-32 of the leading level).  With 64 right-hand sides only
+// four fit (4 x 128 columns) and L = 5 shares the accumulator of L = 6, 7,
+// whose additions the tensor core does not round to nearest (measured: 1e-12
+// relative for the sound-soft residual; the sound-hard passes, whose
+// hypersingular part magnifies it tenfold, take at most 32 right-hand sides).
+// Every 128 sources the producer warps
+// join the levels in double-float: L = 2 + 3 and L >= 4 each as an exact
+// TwoSum pair, then one double-float addition (adding the lower levels to the
+// low part in FP32 would round at 2^-24 of the L = 4 sum, ~2^-40 of the
+// result: that rounding, not the slicing, set the kernel's error), scale by
 // 2^(E_i + F_r - 14) and accumulate per-segment double-float sums in global
-// memory.  Near pairs
-// (the band, with the diagonal) are summed separately (k_band_df).  Split
+// memory.  Near pairs (the band, with the diagonal) are summed separately
+// (k_band_df).  Split
 // complex as in the FP32 tensor-core kernel: [Yr | Yi] += Ar [Xr | Xi] +
 // Ai [-Xi | Xr].
 // ---------------------------------------------------------------------------
 constexpr int RTM = 128;      // rows per tile (UMMA M)
 constexpr int RTK = 16;       // sources per tile: one K step, 32-byte rows
-constexpr int RSL = 6;        // slices per operand
+constexpr int RSL = 6;        // slices per operand (the 48 bits of a double-float value)
 constexpr int RST = 2;        // pipeline stages
-constexpr int RCK = 8;        // tiles per exact TMEM chunk (128 sources)
+constexpr int RCK = 8;        // tiles per TMEM chunk (128 sources)
+// level accumulators: L = 2, 3, 4, 5 and L >= 6 when they fit, else L >= 5 shared
+template <int NB>
+__host__ __device__ constexpr int rlevels() { return NB <= 32 ? 5 : 4; }
 constexpr int RPROD = 16;     // producer warps
 constexpr int RWTMA = RPROD, RWMMA = RPROD + 1;
 // 18 warps (the producers also drain the accumulators): at most 5 per
@@ -559,6 +573,7 @@ struct rtc_smem {
   int ex[RTM];
   float4 tab[65];    // sin / cos table (per-lane indices: shared, not constant)
   uint64_t full[RST], empty[RST], tfull, tempty;
+  uint64_t mdone;    // completion of every MMA issued (abort path)
   uint32_t tmem_base;
   int abort;
   int issued[RST];
@@ -619,7 +634,9 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
            const int4* __restrict__ segs, const int* __restrict__ cbeg,
            float2* __restrict__ acc_out, int* __restrict__ err) {
   constexpr int NC = 2 * NB;                   // accumulator columns per level
-  constexpr uint32_t TMEM_COLS = 4 * NC <= 128 ? 128 : (4 * NC <= 256 ? 256 : 512);
+  constexpr int NL = rlevels<NB>();
+  constexpr uint32_t TMEM_COLS = NL * NC <= 128 ? 128 : (NL * NC <= 256 ? 256 : 512);
+  static_assert(NL * NC <= 512, "level accumulators exceed the tensor memory");
   constexpr uint32_t B_BYTES = 2u * RSL * NC * RTK * 2u;
   extern __shared__ unsigned char raw[];
   rtc_smem<NB>& S = *reinterpret_cast<rtc_smem<NB>*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
@@ -636,6 +653,7 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
     }
     mbar_init(&S.tfull, 1);
     mbar_init(&S.tempty, RPROD);
+    mbar_init(&S.mdone, 1);
     S.abort = 0;
     fence_mbar_init();
   }
@@ -675,22 +693,36 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
         float2* dst = acc_out + (size_t)seg * NC * RTM + erow;
         const uint32_t base = tmem + ((uint32_t)(32 * qd) << 16);
 #pragma unroll 1
-        for (int cb = cg0; cb < cg0 + CPG; cb += 16) {
-          float v0[16], v1[16], v2[16], v3[16];
-          tmem_ld16(base + (uint32_t)(0 * NC + cb), v0);
-          tmem_ld16(base + (uint32_t)(1 * NC + cb), v1);
-          tmem_ld16(base + (uint32_t)(2 * NC + cb), v2);
-          tmem_ld16(base + (uint32_t)(3 * NC + cb), v3);
+        for (int cb = cg0; cb < cg0 + CPG; cb += 8) {
+          // eight columns at a time: the small levels (L >= 4) first, as one
+          // double-float (L = 4 exact, plus the rest), then L = 2, 3 exactly;
+          // the two are joined in double-float, so nothing of the exact level
+          // sums is rounded away at FP32 precision
+          float t[8], te[8], v0[8], v1[8];
+          tmem_ld8(base + (uint32_t)(3 * NC + cb), t);
+          if constexpr (NL == 5) {
+            tmem_ld8(base + (uint32_t)(4 * NC + cb), v0);
 #pragma unroll
-          for (int r = 0; r < 16; ++r) {
+            for (int r = 0; r < 8; ++r) t[r] += v0[r];
+          }
+          tmem_ld8(base + (uint32_t)(2 * NC + cb), v0);
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
+            const float s2 = v0[r] + t[r];
+            const float b2 = s2 - v0[r];
+            te[r] = (v0[r] - (s2 - b2)) + (t[r] - b2);
+            t[r] = s2;
+          }
+          tmem_ld8(base + (uint32_t)(0 * NC + cb), v0);
+          tmem_ld8(base + (uint32_t)(1 * NC + cb), v1);
+#pragma unroll
+          for (int r = 0; r < 8; ++r) {
             const int col = cb + r;
-            // levels 2 + 3 exactly (TwoSum), then the smaller levels
             const float sh = v0[r] + v1[r];
             const float bv = sh - v0[r];
-            float sl = (v0[r] - (sh - bv)) + (v1[r] - bv);
-            sl += v2[r] + v3[r];
+            const float sl = (v0[r] - (sh - bv)) + (v1[r] - bv);
             const float fs = __int_as_float((127 + P.fx[col]) << 23);  // 2^F_col
-            df val = quick(sh, sl);
+            df val = dadd(quick(sh, sl), df{t[r], te[r]});
             val.h *= rs * fs;
             val.l *= rs * fs;
             float2* pp = dst + (size_t)col * RTM;
@@ -827,7 +859,7 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
   } else if (warp == RWMMA) {
     if (lane == 0) {
       // ---- MMA: per tile and slice pair (s, t), s + t <= 7 (1-based), two
-      // MMAs into the accumulator of level min(s + t, 5)
+      // MMAs into the accumulator of level min(s + t, NL + 1)
       constexpr uint32_t idesc = make_idesc(RTM, NC);
       int it = 0, cc = 0;
       for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
@@ -850,13 +882,15 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
             tc_fence_after();
             const uint32_t a_base = smem_u32(&S.A[st][0][0]);
             const uint32_t b_base = smem_u32(&S.B[st][0][0]);
-            bool started[4] = {k > c0, k > c0, k > c0, k > c0};
+            bool started[NL];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) started[l] = k > c0;
 #pragma unroll
             for (int sa = 0; sa < RSL; ++sa)
 #pragma unroll
               for (int tb = 0; tb < RSL; ++tb) {
                 if (sa + tb > 5) continue;          // levels up to 7 (1-based s + t)
-                const int lv = sa + tb < 3 ? sa + tb : 3;
+                const int lv = sa + tb < NL - 1 ? sa + tb : NL - 1;
                 const uint32_t d = tmem + (uint32_t)(lv * NC);
                 const uint32_t ar = a_base + (uint32_t)(sa * RTM * RTK * 2);
                 const uint32_t ai = a_base + (uint32_t)((RSL + sa) * RTM * RTK * 2);
@@ -874,9 +908,16 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && *(volatile int*)&S.abort) {
-    for (int s = 0; s < RST; ++s)
-      if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
+  // after an abort, wait (bounded) for copies in flight and for every MMA
+  // issued, then free TMEM
+  if (*(volatile int*)&S.abort) {
+    if (threadIdx.x == 0)
+      for (int s = 0; s < RST; ++s)
+        if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
+    if (warp == RWMMA && lane == 0) {
+      umma_commit(&S.mdone);
+      mbar_wait(&S.mdone, 0);
+    }
   }
   __syncthreads();
   if (warp == RWMMA) {
@@ -1463,10 +1504,14 @@ void matvec_df(cfie_op* op, const double2* x, double2* y, int nrhs) {
     PS.x = xv;
     PD.x = xv + 3 * tot;
     PD.band = P.band + nbw;
-    for (int r0 = 0; r0 < 3 * nrhs; r0 += 64)
-      run_rtc_block<RK_S>(op, PS, v, ys, r0, std::min(64, 3 * nrhs - r0));
-    for (int r0 = 0; r0 < nrhs; r0 += 64)
-      run_rtc_block<RK_DP>(op, PD, x, ys + 3 * tot, r0, std::min(64, nrhs - r0));
+    // passes of at most 32 right-hand sides, whose tensor memory holds an
+    // exact accumulator for every level up to L = 5: the hypersingular part
+    // magnifies the rounding of the shared L >= 5 accumulator of 64-wide
+    // passes to ~1e-11 relative (sound soft: ~1e-12)
+    for (int r0 = 0; r0 < 3 * nrhs; r0 += 32)
+      run_rtc_block<RK_S>(op, PS, v, ys, r0, std::min(32, 3 * nrhs - r0));
+    for (int r0 = 0; r0 < nrhs; r0 += 32)
+      run_rtc_block<RK_DP>(op, PD, x, ys + 3 * tot, r0, std::min(32, nrhs - r0));
     k_hard_combine64<<<nbk(tot), 256, 0, st>>>(n, tot, op->omega, op->eta, op->g, x, ys,
                                                ys + 3 * tot, t, y);
     CFIE_CHECK_LAUNCH();

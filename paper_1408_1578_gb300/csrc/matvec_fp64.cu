@@ -27,6 +27,8 @@
 #include <mutex>
 #include <string>
 
+#include <cuda.h>
+
 #include "internal.h"
 #include "hankel64.cuh"
 
@@ -346,7 +348,8 @@ void matvec_fp64(cfie_op* op, const double2* x, double2* y, int nrhs) {
 // the operator grows with cudaMalloc.  Every GPU that loads the library holds
 // this array until the process exits.  Its device address is looked up once
 // per device (cudaGetSymbolAddress, with that device current) on the first
-// call there; host code never hands the array's name itself to a kernel.
+// call there, and again if the device's context has been replaced since;
+// host code never hands the array's name itself to a kernel.
 // Each call overwrites every scratch element it later reads, so nothing has to
 // start at zero; calls that overlap on the GPU share the array and race.
 // ---------------------------------------------------------------------------
@@ -357,20 +360,43 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
+// The address is cached per device together with the device's current CUDA
+// context: a context torn down and created again (cudaDeviceReset) reloads the
+// module, so a cached address from the old context is looked up afresh.
+using ctx_get_fn = CUresult (*)(CUcontext*);
+ctx_get_fn driver_ctx_get_current() {
+  static ctx_get_fn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<ctx_get_fn>(p);
+  }();
+  return fn;
+}
+
 std::mutex g_static_mu;
 void* g_static_addr[kMaxDevices] = {};
+CUcontext g_static_ctx[kMaxDevices] = {};
 
 void* static_scratch_address(int device) {
   if (device < 0 || device >= kMaxDevices)
     throw cfie_error(CFIE_EINVAL, "device index out of range for the static scratch table");
+  ctx_get_fn get = driver_ctx_get_current();
+  CUcontext cur = nullptr;
+  if (!get || get(&cur) != CUDA_SUCCESS || !cur)
+    throw cfie_error(CFIE_ECUDA, "cuCtxGetCurrent: no current CUDA context for the static scratch");
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[device]) {
+  if (!g_static_addr[device] || g_static_ctx[device] != cur) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess || !p)
       throw cfie_error(CFIE_ECUDA, std::string("cudaGetSymbolAddress(static scratch): ") +
                                        cudaGetErrorString(e));
     g_static_addr[device] = p;
+    g_static_ctx[device] = cur;
   }
   return g_static_addr[device];
 }

@@ -13,11 +13,12 @@
 // FP32 accumulation in tensor memory.  Work is split stream-K: the
 // (128-row tile, 32-source tile) pairs form one list and each CTA (one per SM)
 // takes a contiguous range, cut into segments that end at row-tile boundaries.
-// Warp roles: 0-7 evaluate pair entries into the stage ring, 8 issues the TMA
-// loads of the right-hand sides, 9 issues the MMAs (double-buffered
-// accumulators), 10-13 drain finished accumulators into per-segment partial
-// sums, which a second kernel adds in a fixed order.  All mbarrier
-// waits are bounded (error flag, drain, TMEM freed on every path).
+// Warp roles (22 warps): 0-15 evaluate pair entries into the stage ring, 16
+// issues the TMA loads of the right-hand sides, of each tile's source geometry
+// and of its Kress window, 17 issues the MMAs (double-buffered accumulators),
+// 18-21 drain finished accumulators into per-segment partial sums, which a
+// second kernel adds in a fixed order.  All mbarrier waits are bounded (error
+// flag, drain, TMEM freed on every path).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -82,6 +83,7 @@ struct tc_smem {
   float4 src[TSTAGES][2][TBK];              // sources: coordinates, factors
   float2 wk[TSTAGES][WKW];                  // Kress weight pairs / (pi h) of a plain tile
   uint64_t full[TSTAGES], empty[TSTAGES], sfull[TSTAGES], tfull[2], tempty[2];
+  uint64_t mdone;                           // completion of every MMA issued (abort path)
   uint32_t tmem_base;
   int abort;
   int issued[TSTAGES], sissued[TSTAGES];
@@ -124,6 +126,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
       mbar_init(&S.tfull[b], 1);
       mbar_init(&S.tempty[b], 4);
     }
+    mbar_init(&S.mdone, 1);
     S.abort = 0;
     fence_mbar_init();
   }
@@ -358,10 +361,17 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && *(volatile int*)&S.abort) {
-    for (int s = 0; s < TSTAGES; ++s) {
-      if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
-      if (S.sissued[s] >= 0) mbar_wait(&S.sfull[s], (uint32_t)S.sissued[s]);
+  // after an abort, wait (bounded) for copies in flight and for every MMA
+  // issued, then free TMEM
+  if (*(volatile int*)&S.abort) {
+    if (threadIdx.x == 0)
+      for (int s = 0; s < TSTAGES; ++s) {
+        if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
+        if (S.sissued[s] >= 0) mbar_wait(&S.sfull[s], (uint32_t)S.sissued[s]);
+      }
+    if (warp == WMMA && lane == 0) {
+      umma_commit(&S.mdone);
+      mbar_wait(&S.mdone, 0);
     }
   }
   __syncthreads();

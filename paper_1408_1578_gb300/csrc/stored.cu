@@ -127,6 +127,7 @@ struct pgemm_smem {
   __nv_bfloat16 A[STAGES][4][BM * BK];   // planes: hi_re, hi_im, lo_re, lo_im
   __nv_bfloat16 B[STAGES][4][NP * BK];   // planes: B1 hi, B1 lo, B2 hi, B2 lo
   uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
+  uint64_t mdone;                        // completion of every MMA issued (abort path)
   uint32_t tmem_base;
   int abort;
   int issued[STAGES];                    // last issued phase parity per stage, -1 = none
@@ -167,6 +168,7 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
       mbar_init(&S.tfull[b], 1);
       mbar_init(&S.tempty[b], 4);   // one arrival per epilogue warp
     }
+    mbar_init(&S.mdone, 1);
     S.abort = 0;
     fence_mbar_init();
   }
@@ -299,10 +301,17 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
     }
   }
   __syncthreads();
-  // after an abort, wait (bounded) for copies still in flight, then free TMEM
-  if (threadIdx.x == 0 && *(volatile int*)&S.abort) {
-    for (int s = 0; s < STAGES; ++s)
-      if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
+  // after an abort, wait (bounded) for copies still in flight and for every
+  // MMA the MMA thread issued (they may still read shared memory and write
+  // tensor memory), then free TMEM
+  if (*(volatile int*)&S.abort) {
+    if (threadIdx.x == 0)
+      for (int s = 0; s < STAGES; ++s)
+        if (S.issued[s] >= 0) mbar_wait(&S.full[s], (uint32_t)S.issued[s]);
+    if (warp == 1 && lane == 0) {
+      umma_commit(&S.mdone);
+      mbar_wait(&S.mdone, 0);
+    }
   }
   __syncthreads();
   if (warp == 1) {

@@ -50,14 +50,11 @@ def test_matvec_forms_at_eta_half_omega(ctx, oracle_ops, bc):
         y = empty(NRHS, N)
         op.apply(to_dev(X), y)
         assert np.max(col_rel(to_host(y), want)) < 1e-4, variant
-    # sound hard: the residual's error comes from the hypersingular part, whose
-    # weight omega^2 / eta doubles when eta halves (5e-11 at eta = omega)
-    tol_res = 1e-11 if bc == "soft" else 1e-10
     for variant in (1, 2):                      # double-float residual: Dot2 and sliced sums
         op.set_residual_variant(variant)
         y = empty(NRHS, N)
         op.apply_residual(to_dev(X), y)
-        assert np.max(col_rel(to_host(y), want)) < tol_res, variant
+        assert np.max(col_rel(to_host(y), want)) < 1e-11, variant
 
 
 def test_stored_matvec_at_eta_half_omega(ctx, oracle_ops):

@@ -36,6 +36,10 @@ def _static_apply(ctx, op, x, y, nrhs):
     ("kite", {}, 1000, 40.0, "soft", 5),
     ("star", {"a": [0, 0, 0, 0, 0.3], "b": [0] * 5}, 4096, 256.0, "hard", 16),
     ("ellipse", {"a": 1.0, "b": 0.5}, 514, 25.0, "hard", 3),
+    # 16 n nrhs just under the 32 MiB cap: the array holds a single split of
+    # the sources, while the regular matvec splits them and takes its 64-wide
+    # right-hand-side tile
+    ("kite", {}, 8192, 512.0, "soft", 255),
 ])
 def test_static_scratch_matches_regular_fp64(ctx, kind, params, n, omega, bc, nrhs):
     import torch

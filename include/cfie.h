@@ -20,7 +20,9 @@
  * Host-only helpers that need no context or GPU: cfie_arclength_samples (the
  * node set of Section 2, for cfie_geometry_samples) and the setup pieces of the
  * directional preconditioner of Section 2 (cfie_dirprec_plan,
- * cfie_dirprec_level, cfie_dirprec_threshold).
+ * cfie_dirprec_level, cfie_dirprec_threshold, cfie_dirprec_w_pattern).  The
+ * preconditioner itself: cfie_dirprec_create -> cfie_op_set_preconditioner /
+ * cfie_dirprec_apply -> cfie_dirprec_destroy.
  *
  * Conventions for every entry point:
  *  - All compute runs on the context's CUDA device and stream; calls that take
@@ -192,9 +194,54 @@ cfie_status cfie_dirprec_level(int n, int p, int level, double omega, double eta
 
 /* T~ of Section 2.2: the `keep` entries of the K x K block T (host,
  * complex128 interleaved, row-major) largest in modulus, copied to Tt, every
- * other entry zero; entries tied in modulus with the smallest one kept are
- * kept too.  keep >= K^2 copies T.  1 <= K <= 4097, keep >= 0.  Host only. */
+ * other entry zero; entries within a relative 2^-30 of the smallest modulus
+ * kept count as tied with it and are kept too (T is symmetric: equal entries
+ * differ only by rounding).  keep >= K^2 copies T.  1 <= K <= 4097, keep >= 0.  Host only. */
 cfie_status cfie_dirprec_threshold(int K, const double* T, int keep, double* Tt);
+
+/* --- Directional preconditioner (Section 2) on the GPU ------------------- */
+
+typedef struct cfie_dirprec cfie_dirprec;
+
+/* Build the directional preconditioner of Section 2 for a sound-soft operator
+ * (eq. 1) whose nodes are the curve's n = 4^q p points equispaced in arclength
+ * (cfie_arclength_samples with the same kind and params, then
+ * cfie_geometry_samples and cfie_discretise with that n; p points per
+ * wavelength 2 pi / omega).  Steps, following Sections 2.1 and 2.2:
+ *  - segments and wave-number pairs as cfie_dirprec_plan (m_leaf the leaf
+ *    length in wavelengths);
+ *  - per level, B_l^-1, U_l, T_l as cfie_dirprec_level and T~_l as
+ *    cfie_dirprec_threshold keeping t_keep K entries (K = 2^(l+1) + 1);
+ *  - E on the GPU: e_ij = the mean over x in P_i, y in P_j of
+ *    M(x, y) / (U_i(x, k^i_ij) U_j(y, k^j_ij)), the least-squares constant of
+ *    the rank-1 form M_ij ~ U_i e_ij U_j^t on the block's nodes (the quantity
+ *    eq. entry approximates from Chebyshev samples), from the operator's FP64
+ *    entries;
+ *  - W~ = E + antidiag(T) solved exactly through its sparsity: the unknowns
+ *    that couple form a block inverted densely on the GPU (FP64 Gauss-Jordan
+ *    with row pivoting, about half of W~'s dimension).
+ * Device memory: the level matrices and W~'s coupled block (complex64,
+ * 134 MB at q = 6).  Synchronous.  CFIE_EINVAL for a sound-hard operator,
+ * n != 4^q p, nodes that are not the curve's arclength samples, invalid
+ * q (1..9), p, m_leaf or t_keep (>= 1), or a singular block. */
+cfie_status cfie_dirprec_create(cfie_op* op, cfie_curve kind, const double* params, int nparams,
+                                int q, int p, int m_leaf, int t_keep, cfie_dirprec** out);
+/* y = P x, eq. (eapp): b = B^-1 x, p0 = -U^t b, t = T~ p0, r = W~^-1 t,
+ * p = T~ r - t, y = b - B^-1 U p, for nrhs right-hand sides in complex64
+ * arithmetic (device, n x nrhs complex128 in and out, not overlapping;
+ * 1 <= nrhs <= 1024).  Asynchronous on the context stream. */
+cfie_status cfie_dirprec_apply(cfie_dirprec* P, const void* x_dev, void* y_dev, int nrhs);
+/* Number of segments m to *m and, unless e is NULL, the m x m coefficients
+ * e_ij (host, complex128 interleaved, row i major, zero diagonal). */
+cfie_status cfie_dirprec_coefficients(const cfie_dirprec* P, int* m, double* e);
+/* Use P as the right preconditioner of cfie_gmres_solve on op (GMRES on A P y = f,
+ * x = P y; for the refined precisions the inner solves are preconditioned).
+ * NULL detaches.  P must have been built for op's context and size, and must
+ * outlive the solves that use it.  CFIE_EINVAL otherwise. */
+cfie_status cfie_op_set_preconditioner(cfie_op* op, cfie_dirprec* P);
+/* Free a preconditioner (NULL is ignored) after the context stream's queued
+ * work; detach it from its operators first. */
+void cfie_dirprec_destroy(cfie_dirprec* P);
 
 /* --- Discretisation ------------------------------------------------------ */
 

@@ -338,10 +338,13 @@ class Directional:
 
     @staticmethod
     def _threshold(T, keep):
-        """The `keep` largest entries of T in absolute value (T~_i)."""
+        """The `keep` largest entries of T in absolute value (T~_i, reading P7);
+        entries within a relative 2^-30 of the smallest one kept count as tied
+        with it and are kept too (T is symmetric, so equal entries differ only
+        by rounding)."""
         if keep >= T.size:
             return sps.csr_matrix(T)
-        cut = np.partition(np.abs(T).ravel(), -keep)[-keep]
+        cut = np.partition(np.abs(T).ravel(), -keep)[-keep] * (1.0 - 2.0**-30)
         return sps.csr_matrix(np.where(np.abs(T) >= cut, T, 0.0))
 
     # block operators ------------------------------------------------------

@@ -98,6 +98,11 @@ SIGNATURES = {
     "cfie_dirprec_w_pattern": (_I, [_I, _IP, _IP, _I, _IP, _IP, _IP, _IP]),
     "cfie_dirprec_level": (_I, [_I, _I, _I, _D, _D, _D, _DP, _DP, _DP, _DP]),
     "cfie_dirprec_threshold": (_I, [_I, _DP, _I, _DP]),
+    "cfie_dirprec_create": (_I, [_P, _I, _DP, _I, _I, _I, _I, _I, ctypes.POINTER(_P)]),
+    "cfie_dirprec_apply": (_I, [_P, _P, _P, _I]),
+    "cfie_dirprec_coefficients": (_I, [_P, _IP, _DP]),
+    "cfie_op_set_preconditioner": (_I, [_P, _P]),
+    "cfie_dirprec_destroy": (None, [_P]),
     "cfie_discretise": (_I, [_P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(_P)]),
     "cfie_op_destroy": (None, [_P]),
     "cfie_op_n": (_I, [_P]),
@@ -596,9 +601,76 @@ class Operator:
         self.ctx.check(self.ctx.lib.cfie_op_last_stats(self.h, ctypes.byref(s)), "cfie_op_last_stats")
         return {k: getattr(s, k) for k, _ in s._fields_}
 
+    def dirprec(self, kind, q, p, m_leaf=2, t_keep=4, **params):
+        """cfie_dirprec_create: the directional preconditioner of Section 2 for
+        this operator, whose nodes must be the named curve's n = 4^q p
+        arclength samples (arclength_samples + Context.samples)."""
+        par = _curve_params(kind, params)
+        h = _P()
+        self.ctx.check(self.ctx.lib.cfie_dirprec_create(self.h, CURVE[kind],
+                                                        _dptr(par) if par.size else None,
+                                                        int(par.size), int(q), int(p), int(m_leaf),
+                                                        int(t_keep), ctypes.byref(h)),
+                       "cfie_dirprec_create")
+        prec = Preconditioner(self.ctx, h, self.n)
+        self.ctx._children.add(prec)
+        return prec
+
+    def set_preconditioner(self, prec):
+        """Right preconditioner of gmres_solve (None detaches)."""
+        self.ctx.check(self.ctx.lib.cfie_op_set_preconditioner(self.h, prec.h if prec else None),
+                       "cfie_op_set_preconditioner")
+        if getattr(self, "_prec", None) is not None:
+            self._prec._users.discard(self)
+        self._prec = prec
+        if prec is not None:
+            prec._users.add(self)
+
     def close(self):
         if self.h:
+            if getattr(self, "_prec", None) is not None:
+                self._prec._users.discard(self)
+                self._prec = None
             self.ctx.lib.cfie_op_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Preconditioner:
+    """A cfie_dirprec handle: apply(x, y) computes y = P x (eq. eapp)."""
+
+    def __init__(self, ctx, h, n):
+        self.ctx = ctx
+        self.h = h
+        self.n = n
+        self._users = weakref.WeakSet()   # operators that use it as their preconditioner
+
+    def apply(self, x, y, nrhs=None):
+        nrhs = x.numel() // self.n if nrhs is None else nrhs
+        self.ctx.check(self.ctx.lib.cfie_dirprec_apply(self.h, _addr(x), _addr(y), int(nrhs)),
+                       "cfie_dirprec_apply")
+
+    def coefficients(self):
+        """The m x m block coefficients e_ij (complex128, zero diagonal)."""
+        m = ctypes.c_int()
+        self.ctx.check(self.ctx.lib.cfie_dirprec_coefficients(self.h, ctypes.byref(m), None),
+                       "cfie_dirprec_coefficients")
+        e = np.zeros((m.value, m.value), dtype=np.complex128)
+        self.ctx.check(self.ctx.lib.cfie_dirprec_coefficients(
+            self.h, ctypes.byref(m), e.ctypes.data_as(_DP)), "cfie_dirprec_coefficients")
+        return e
+
+    def close(self):
+        if self.h:
+            for op in list(self._users):
+                if op.h:
+                    op.set_preconditioner(None)
+            self.ctx.lib.cfie_dirprec_destroy(self.h)
             self.h = None
 
     def __del__(self):

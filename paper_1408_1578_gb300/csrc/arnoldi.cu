@@ -589,6 +589,10 @@ void gmres_cycle(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps, c
   stats.cycles++;
   for (int j = 0; j < m; ++j) {
     const double2* vj = W.f32 ? W.vin : W.V + (size_t)j * L;
+    if (fns.prec) {   // right preconditioning: the operator is A P
+      fns.prec(vj, K.pz.as<double2>());
+      vj = K.pz.as<double2>();
+    }
     if (inner) {
       stats.inner_matvecs++;
       fns.inner(vj, W.w);
@@ -658,11 +662,23 @@ void gmres_cycle(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps, c
   CFIE_CHECK_CUDA(cudaMemcpyAsync(W.kd, kd.data(), sizeof(int) * P, cudaMemcpyHostToDevice, st));
   k_lsq<<<blocks_for(P, 64), 64, 0, st>>>(P, m, W.kd, W.H, W.gv, W.y);
   CFIE_CHECK_LAUNCH();
+  // x += V y, or with right preconditioning x += P (V y)
+  double2* xu = x;
+  if (fns.prec) {
+    xu = K.pz.as<double2>();
+    k_zero<<<blocks_for(L), 256, 0, st>>>(L, xu);
+    CFIE_CHECK_LAUNCH();
+  }
   if (W.f32)
-    k_xupdate<float2><<<ps.Q, AT, 0, st>>>(m, W.kd, ps.dev, W.V32, L, W.y, x);
+    k_xupdate<float2><<<ps.Q, AT, 0, st>>>(m, W.kd, ps.dev, W.V32, L, W.y, xu);
   else
-    k_xupdate<double2><<<ps.Q, AT, 0, st>>>(m, W.kd, ps.dev, W.V, L, W.y, x);
+    k_xupdate<double2><<<ps.Q, AT, 0, st>>>(m, W.kd, ps.dev, W.V, L, W.y, xu);
   CFIE_CHECK_LAUNCH();
+  if (fns.prec) {
+    fns.prec(xu, K.pz2.as<double2>());
+    k_axpy<<<blocks_for(L), 256, 0, st>>>(L, K.pz2.as<double2>(), x);
+    CFIE_CHECK_LAUNCH();
+  }
   // host vectors copied above must stay alive until the copies ran
   CFIE_CHECK_CUDA(cudaStreamSynchronize(st));
 }
@@ -722,6 +738,10 @@ void gmres_set(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps,
   stats.basis_fp32 = f32 ? 1 : 0;
   ws W = workspace(K, ps, m, f32);
   K.r.reserve(sizeof(double2) * L);
+  if (fns.prec) {
+    K.pz.reserve(sizeof(double2) * L);
+    K.pz2.reserve(sizeof(double2) * L);
+  }
   double2* r = K.r.as<double2>();
   double2* ax = W.w;  // matvec output scratch (free between cycles)
 

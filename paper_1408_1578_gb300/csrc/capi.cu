@@ -443,6 +443,10 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
     solve_fns fns;
     fns.inner = [op, nrhs](const double2* a, double2* b) { apply_inner(op, a, b, nrhs); };
     fns.fp64 = [op, nrhs](const double2* a, double2* b) { matvec_residual(op, a, b, nrhs); };
+    if (op->dirprec) {
+      cfie_dirprec* P = op->dirprec;
+      fns.prec = [P, nrhs](const double2* a, double2* b) { dirprec_apply(P, a, b, nrhs); };
+    }
     fns.basis32 = op->basis32 != 0;
     gmres_set(st, op->ctx, op->K, op->ps, fns, op->prec != CFIE_FP64,
               static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), rtol, restart,
@@ -712,3 +716,63 @@ void cfie_batch_destroy(cfie_batch* b) {
 }
 
 }  // extern "C"
+
+// --- directional preconditioner (Section 2) ---------------------------------
+
+cfie_status cfie_dirprec_create(cfie_op* op, cfie_curve kind, const double* params, int nparams,
+                                int q, int p, int m_leaf, int t_keep, cfie_dirprec** out) {
+  if (!op || !out) return CFIE_EINVAL;
+  *out = nullptr;
+  cfie_dirprec* P = new (std::nothrow) cfie_dirprec;
+  if (!P) return CFIE_ENOMEM;
+  cfie_status st = guarded(op->ctx, [&] {
+    set_device(op->ctx);
+    dirprec_build(P, op, kind, params, nparams, q, p, m_leaf, t_keep);
+  });
+  if (st != CFIE_OK) {
+    stream_scope ss(op->ctx->stream);
+    delete P;
+    return st;
+  }
+  *out = P;
+  return CFIE_OK;
+}
+
+void cfie_dirprec_destroy(cfie_dirprec* P) {
+  if (!P) return;
+  if (P->ctx) {
+    cudaSetDevice(P->ctx->device);
+    stream_scope ss(P->ctx->stream);
+    cudaStreamSynchronize(P->ctx->stream);
+    delete P;
+  } else {
+    delete P;
+  }
+}
+
+cfie_status cfie_dirprec_apply(cfie_dirprec* P, const void* x_dev, void* y_dev, int nrhs) {
+  if (!P || !P->ctx) return CFIE_EINVAL;
+  return guarded(P->ctx, [&] {
+    CFIE_REQUIRE(nrhs >= 1 && nrhs <= 1024, "nrhs must be in [1, 1024]");
+    check_vec(x_dev, "x");
+    check_vec(y_dev, "y");
+    CFIE_REQUIRE(x_dev != y_dev, "x and y must not overlap");
+    set_device(P->ctx);
+    dirprec_apply(P, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev), nrhs);
+  });
+}
+
+cfie_status cfie_dirprec_coefficients(const cfie_dirprec* P, int* m, double* e) {
+  if (!P || !m) return CFIE_EINVAL;
+  *m = dirprec_segments(P, e);
+  return CFIE_OK;
+}
+
+cfie_status cfie_op_set_preconditioner(cfie_op* op, cfie_dirprec* P) {
+  if (!op) return CFIE_EINVAL;
+  return guarded(op->ctx, [&] {
+    CFIE_REQUIRE(!P || (P->ctx == op->ctx && dirprec_n(P) == op->n),
+                 "the preconditioner was built for another operator or context");
+    op->dirprec = P;
+  });
+}

@@ -167,7 +167,10 @@ extern "C" cfie_status cfie_dirprec_level(int n, int p, int level, double omega,
 
 // T~: the `keep` largest entries of a K x K block in modulus, the rest zero
 // (Section 2.2: T is numerically sparse; the number kept is proportional to K).
-// Entries equal in modulus to the smallest one kept are all kept.
+// Entries within a relative 2^-30 of the smallest modulus kept count as tied
+// with it and are all kept: T is symmetric (and on a straight segment also
+// symmetric about its anti-diagonal), so equal entries differ only by
+// rounding, and the choice must not depend on it.
 extern "C" cfie_status cfie_dirprec_threshold(int K, const double* T, int keep, double* Tt) {
   if (K < 1 || K > 4097 || !T || !Tt || keep < 0) return CFIE_EINVAL;
   try {
@@ -182,7 +185,7 @@ extern "C" cfie_status cfie_dirprec_threshold(int K, const double* T, int keep, 
     if (keep > 0) {
       std::vector<double> sorted = mag;
       std::nth_element(sorted.begin(), sorted.begin() + (total - keep), sorted.end());
-      cut = sorted[total - keep];
+      cut = sorted[total - keep] * (1.0 - 0x1p-30);
     }
     for (size_t i = 0; i < total; ++i) {
       const bool in = keep > 0 && mag[i] >= cut;

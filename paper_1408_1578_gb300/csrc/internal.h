@@ -134,6 +134,7 @@ struct pset {
 // Krylov workspace (basis, Hessenberg, Givens data, residual vectors)
 struct krylov_ws {
   dbuf V, H, w, r, d, rin, small;
+  dbuf pz, pz2;             // right preconditioning: P v for the matvec, P (V y) for the update
   dbuf V32, w32, vin;       // FP32 basis of the inner solves (refined precisions)
   double* host = nullptr;   // pinned mirror of per-problem norms
   int host_cap = 0;
@@ -144,6 +145,8 @@ struct krylov_ws {
 struct solve_fns {
   std::function<void(const double2*, double2*)> inner;   // the fast (FP32 / tensor) matvec
   std::function<void(const double2*, double2*)> fp64;    // the FP64 matvec (true residuals)
+  // right preconditioner y = P x (empty: none): GMRES runs on A P and x += P (V y)
+  std::function<void(const double2*, double2*)> prec;
   bool basis32 = true;   // refined precisions: inner Krylov basis in FP32
 };
 
@@ -243,6 +246,22 @@ struct cfie_op {
   int ps_nrhs = -1;
 
   cfie_solve_stats stats{};
+  cfie_dirprec* dirprec = nullptr;   // right preconditioner of cfie_gmres_solve (not owned)
+};
+
+// Directional preconditioner of Section 2 built for one sound-soft operator
+// (dirprec.cu): segments, level matrices and the W~ solve tables on the device.
+struct cfie_dirprec {
+  cfie_ctx* ctx = nullptr;
+  int n = 0, q = 0, p = 0, m = 0, Ktot = 0, nS = 0, nRest = 0, nnz = 0;
+  double omega = 0, eta = 0, L = 0;
+  std::vector<int> first, level, count, koff;
+  std::vector<double> e;          // m x m e_ij (complex128 interleaved, zero diagonal)
+  // level matrices (complex64, row-major), per-segment GEMM descriptors and
+  // work items, W~ solve tables, the inverse of W~'s coupled block
+  dbuf mats, descs, items, wsolve, Z;
+  int item_off[5] = {0}, item_cnt[5] = {0};
+  dbuf work;                      // work vectors, grown with the number of right-hand sides
 };
 
 // A batch of operators solved in lockstep (one problem per right-hand side of
@@ -346,3 +365,9 @@ void gmres_set(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps,
 void krylov_release(krylov_ws& K);
 // dispatch (capi.cu)
 void apply_inner(cfie_op* op, const double2* x, double2* y, int nrhs);
+// dirprec.cu: the directional preconditioner of Section 2
+void dirprec_build(cfie_dirprec* P, cfie_op* op, cfie_curve kind, const double* params,
+                   int nparams, int q, int p, int m_leaf, int t_keep);
+void dirprec_apply(cfie_dirprec* P, const double2* x, double2* y, int nrhs);
+int dirprec_n(const cfie_dirprec* P);
+int dirprec_segments(const cfie_dirprec* P, double* e);

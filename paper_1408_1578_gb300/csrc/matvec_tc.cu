@@ -36,7 +36,7 @@ namespace {
 
 constexpr int TBM = 128;     // targets per tile (UMMA M)
 constexpr int TBK = 32;      // sources per tile (32 bf16 = one 64-byte swizzle row)
-constexpr int TSTAGES = 2;
+constexpr int TSTAGES = 3;
 // Source tiles accumulated in one tensor-memory accumulator before the epilogue
 // warps add it into their running sums.  The tensor core's FP32 accumulation
 // does not round to nearest: its error grows with the number of MMAs summed
@@ -77,7 +77,6 @@ template <int NP>
 struct tc_smem {
   __nv_bfloat16 A[TSTAGES][4][TBM * TBK];   // hi_re, hi_im, lo_re, lo_im
   __nv_bfloat16 B[TSTAGES][4][NP * TBK];    // B1 hi, B1 lo, B2 hi, B2 lo
-  float acc[NP][TBM];                       // epilogue running sums, column-major
   float4 tgt[TBM];                          // targets (x hi, x lo, y hi, y lo)
   float4 tgn[TBM];                          // target factors (D' only)
   float4 src[TSTAGES][2][TBK];              // sources: coordinates, factors
@@ -105,7 +104,9 @@ __global__ void __launch_bounds__(TNT, 1)
 k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __restrict__ segs,
            const int* __restrict__ cbeg, float2* __restrict__ partial, int* __restrict__ err) {
   constexpr int NR = NP / 2;
-  constexpr uint32_t TMEM_COLS = 2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256);
+  // two accumulator buffers, then the epilogue's running sums (NP columns each)
+  constexpr uint32_t TMEM_COLS = 3 * NP <= 256 ? 256 : 512;
+  constexpr uint32_t RUN = 2 * NP;
   constexpr uint32_t B_BYTES = 4u * NP * TBK * 2u;
   extern __shared__ unsigned char raw[];
   tc_smem<NP>& S = *reinterpret_cast<tc_smem<NP>*>((reinterpret_cast<uintptr_t>(raw) + 1023) &
@@ -145,6 +146,11 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
     // 16-31 the second, lane l the two adjacent sources 2 (l % 16), +1, so
     // that the bf16 pairs go to shared memory as packed 32-bit words.
     const int half = lane >> 4, jp = 2 * (lane & 15);
+    // byte offset of the lane's two sources in its first row of a step; the
+    // rows of step q lie 2 NPROD q rows further on, a multiple of the 8-row
+    // period of the 64-byte swizzle, hence 2 NPROD q 64 bytes further
+    static_assert((2 * NPROD) % 8 == 0, "row step must keep the swizzle phase");
+    const uint32_t sbase = sw64(warp + NPROD * half, jp);
     int it = 0;
     for (int s = sb; s < se; ++s) {
       const int4 sg = segs[s];
@@ -200,7 +206,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
 #pragma unroll
             for (int u = 0; u < 2; ++u)
               e[u] = entry_folded32<KIND>(tg, tn, sc[u], sn[u], u ? wv[q].y : wv[q].x);
-            store_split2(a0, a1, a2, a3, sw64(il, jp), e[0], e[1]);
+            store_split2(a0, a1, a2, a3, sbase + (uint32_t)(2 * NPROD * 64 * q), e[0], e[1]);
           }
         } else {
 #pragma unroll 1
@@ -225,7 +231,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
               }
               e[u] = a;
             }
-            store_split2(a0, a1, a2, a3, sw64(il, jp), e[0], e[1]);
+            store_split2(a0, a1, a2, a3, sbase + (uint32_t)(2 * NPROD * 64 * q), e[0], e[1]);
           }
         }
         // generic-proxy writes become visible to the tensor core's async proxy
@@ -320,10 +326,12 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
       }
     }
   } else {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one row per thread;
-    // running sums per segment in shared memory (each thread owns its row)
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, one row per
+    // thread, and keeps the segment's running sums in the same lanes of the
+    // last NP tensor-memory columns (FP32 adds, rounded to nearest)
     const int q = warp & 3;
     const int row = 32 * q + lane;
+    const uint32_t lanes = tmem + ((uint32_t)(32 * q) << 16);
     int cc = 0;
     bool stop = false;
     for (int s = sb; s < se && !stop; ++s) {
@@ -340,15 +348,19 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
         }
         __syncwarp();
         tc_fence_after();
-        const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(tb * NP);
+        const uint32_t base = lanes + (uint32_t)(tb * NP);
         const bool first = c0 == sg.z;
-#pragma unroll
+#pragma unroll 2
         for (int cb = 0; cb < NP; cb += 16) {
           float v[16];
           tmem_ld16(base + (uint32_t)cb, v);
+          if (!first) {
+            float r[16];
+            tmem_ld16(lanes + RUN + (uint32_t)cb, r);
 #pragma unroll
-          for (int r = 0; r < 16; ++r)
-            S.acc[cb + r][row] = first ? v[r] : S.acc[cb + r][row] + v[r];
+            for (int k = 0; k < 16; ++k) v[k] += r[k];
+          }
+          tmem_st16(lanes + RUN + (uint32_t)cb, v);
         }
         tc_fence_before();
         __syncwarp();
@@ -356,8 +368,14 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
       }
       if (stop) break;
       float2* dst = partial + (size_t)s * TBM * NR + row;
-#pragma unroll 4
-      for (int r = 0; r < NR; ++r) dst[(size_t)r * TBM] = make_float2(S.acc[r][row], S.acc[NR + r][row]);
+#pragma unroll 1
+      for (int cb = 0; cb < NR; cb += 16) {
+        float re[16], im[16];
+        tmem_ld16(lanes + RUN + (uint32_t)cb, re);
+        tmem_ld16(lanes + RUN + (uint32_t)(NR + cb), im);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) dst[(size_t)(cb + k) * TBM] = make_float2(re[k], im[k]);
+      }
     }
   }
   __syncthreads();

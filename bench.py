@@ -51,6 +51,10 @@ def parse():
     p.add_argument("--nrhs", type=int, default=None, help="override the number of directions")
     p.add_argument("--eta-factor", type=float, default=None,
                    help="coupling eta = factor x omega for the single-operator workloads (default 1)")
+    p.add_argument("--dirprec", action="store_true",
+                   help="single-operator sound-soft workloads: nodes equispaced in arclength "
+                        "(n = 4^q p, p = 8) and the directional preconditioner of Section 2 on "
+                        "the right of every solve (its setup inside each step)")
     p.add_argument("--oracle-budget", type=float, default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -272,6 +276,17 @@ def run_ours(args, rank, world):
     n, w, nrhs, bc = spec["n"], spec["omega"], spec["nrhs"], spec["bc"]
     stream = torch.cuda.current_stream()
     ctx = cfie.Context(dev, stream=stream)
+    prec_q = None
+    if args.dirprec:
+        # Section 2's node set: n = 4^q p points equispaced in arclength, p = 8
+        prec_q = dirprec_levels(n, DIRPREC_P)
+        if bc != "soft" or prec_q is None:
+            raise SystemExit("--dirprec needs a sound-soft workload with n = 4^q * 8")
+        arc = cfie.arclength_samples(spec["curve"], n, **spec["params"])
+        spec["nodes"] = "arclength"
+    else:
+        arc = None
+    setup_s = []
     theta = inputs.directions(nrhs)
     f = torch.empty((nrhs, n), dtype=torch.complex128, device="cuda")
     x = torch.zeros((nrhs, n), dtype=torch.complex128, device="cuda")
@@ -280,20 +295,42 @@ def run_ours(args, rank, world):
     basis_bytes = (spec["restart"] + 1) * n * nrhs * 16
     flush_l2 = basis_bytes < 2 * 129 * 1024 * 1024
 
-    def step():
-        geom = ctx.geometry(spec["curve"], **spec["params"])
+    def step(precondition=True):
+        if arc is None:
+            geom = ctx.geometry(spec["curve"], **spec["params"])
+        else:
+            geom = ctx.samples(*arc[:3])
         op = geom.discretise(n, w, eta=spec["eta"], bc=bc, precision=spec["precision"],
                              layout=spec["layout"])
+        prec = None
+        if arc is not None and precondition:
+            t0 = time.perf_counter()
+            prec = op.dirprec(spec["curve"], prec_q, DIRPREC_P, **spec["params"])   # synchronous
+            setup_s.append(time.perf_counter() - t0)
+            op.set_preconditioner(prec)
         op.rhs_plane_waves(theta, f)
         x.zero_()
         its, rel, st = op.gmres_solve(f, x, rtol=spec["rtol"], restart=spec["restart"],
                                       maxit=spec["maxit"], allow_noconv=True)
         stats = op.last_stats()
+        if prec is not None:
+            op.set_preconditioner(None)
+            prec.close()
         op.close()
         geom.close()
         return its, rel, stats
 
     pipes = ctx.measure_peaks()
+    unprec = None
+    if arc is not None:
+        # the same solve without the preconditioner, once, for the iteration
+        # counts n_n beside n_p (Tables 1 and 3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its0, rel0, stats0 = step(precondition=False)
+        torch.cuda.synchronize()
+        unprec = {"iterations": [int(v) for v in its0[:4]], "max_relres": float(np.max(rel0)),
+                  "s_per_step": time.perf_counter() - t0, "solve_stats": stats0}
     for _ in range(args.warmup):
         its, rel, stats = step()
     barrier(world)
@@ -380,6 +417,12 @@ def run_ours(args, rank, world):
                                     "fp64_fma_T_per_s": pipes["fp64_fma_per_s"] / 1e12},
             "clocks": clk,
         }
+        if unprec is not None:
+            result["dirprec"] = {"q": prec_q, "p": DIRPREC_P, "nodes": "arclength",
+                                 "iterations_preconditioned": [int(v) for v in its[:4]],
+                                 "setup_s_median": statistics.median(setup_s) if setup_s else None,
+                                 "setup_s_first": setup_s[0] if setup_s else None,
+                                 "unpreconditioned": unprec}
     ctx.close()
     return result
 
@@ -566,9 +609,25 @@ def run_reference(args, rank, world):
     }
 
 
+DIRPREC_P = 8   # points per wavelength of the paper's experiments (Section 3)
+
+
+def dirprec_levels(n, p):
+    """q with n = 4^q p, or None."""
+    q, m = 0, n
+    if m % p:
+        return None
+    m //= p
+    while m > 1 and m % 4 == 0:
+        m //= 4
+        q += 1
+    return q if m == 1 and q >= 1 else None
+
+
 def single_config(spec, world):
+    prec = " arclength nodes, directional preconditioner" if spec.get("nodes") == "arclength" else ""
     return {"workload": f"{spec['name']}: {spec['curve']} {spec['bc']} n={spec['n']} "
-                        f"omega={spec['omega']} {eta_text(spec)} nrhs={spec['nrhs']}",
+                        f"omega={spec['omega']} {eta_text(spec)} nrhs={spec['nrhs']}{prec}",
             "curve": spec["curve"], "bc": spec["bc"], "n": spec["n"], "omega": spec["omega"],
             "nrhs": spec["nrhs"], "eta": spec["eta"], "precision": spec["precision"],
             "rtol": spec["rtol"],

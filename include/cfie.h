@@ -350,6 +350,24 @@ cfie_status cfie_op_set_residual_variant(cfie_op* op, int variant);
  * precision stay FP64 either way.  CFIE_EINVAL for a null op or another value. */
 cfie_status cfie_op_set_inner_basis(cfie_op* op, int fp32);
 
+/* Solve the nrhs right-hand sides of cfie_gmres_solve as one block problem
+ * (on = 1): block GMRES with one Krylov space span{R, A R, A^2 R, ...} shared
+ * by all columns of the residual block R, instead of one GMRES per column
+ * (on = 0, the default; Section 3 runs one GMRES per incident wave).  Each
+ * block step is one block matvec; the basis is orthogonalised by block
+ * classical Gram-Schmidt applied twice and a rank-revealing Cholesky QR
+ * applied twice (directions whose Gram diagonal falls below a relative
+ * 1e-14 (FP64) or 1e-10 (FP32 inner basis) are dropped: repeated or
+ * converged columns shrink the next block), and the block Hessenberg least
+ * squares is solved by Householder QR updated column by column (FP64, host).
+ * For the refined precisions the block solve is the inner solve of the
+ * refinement, with the inner basis in FP32 or FP64 (cfie_op_set_inner_basis).
+ * In cfie_gmres_solve, restart then counts block steps per cycle (0:
+ * unrestarted, up to 512), maxit caps the block steps, and iters_out reports
+ * the block steps for every column.  A right preconditioner set on op applies
+ * as in the per-column solve.  CFIE_EINVAL for a null op or another value. */
+cfie_status cfie_op_set_block_gmres(cfie_op* op, int on);
+
 /* Scattered field at off-surface points from a boundary density (Section 1:
  * u is evaluated through a boundary integral once q is known).  With the
  * operator's curve, omega, eta and boundary condition,

@@ -114,6 +114,7 @@ SIGNATURES = {
     "cfie_op_set_variant": (_I, [_P, _I]),
     "cfie_gmres_solve": (_I, [_P, _P, _P, _I, _D, _I, _I, _IP, _DP]),
     "cfie_op_set_inner_basis": (_I, [_P, _I]),
+    "cfie_op_set_block_gmres": (_I, [_P, _I]),
     "cfie_op_set_residual_variant": (_I, [_P, _I]),
     "cfie_field_eval": (_I, [_P, _P, _I, _I, _P, _P]),
     "cfie_op_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
@@ -574,6 +575,12 @@ class Operator:
         """Refined precisions: inner Krylov basis in FP32 (True, default) or FP64."""
         self.ctx.check(self.ctx.lib.cfie_op_set_inner_basis(self.h, 1 if fp32 else 0),
                        "cfie_op_set_inner_basis")
+
+    def set_block_gmres(self, on):
+        """gmres_solve as one block GMRES over all right-hand sides (True) or
+        one GMRES per right-hand side (False, default)."""
+        self.ctx.check(self.ctx.lib.cfie_op_set_block_gmres(self.h, 1 if on else 0),
+                       "cfie_op_set_block_gmres")
 
     def apply_residual(self, x, y, nrhs=None):
         nrhs = x.numel() // self.n if nrhs is None else nrhs

@@ -440,6 +440,10 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
       pset_uniform(op->ps, op->n, nrhs, st);
       op->ps_nrhs = nrhs;
     }
+    if (op->block_gmres) {
+      block_gmres_solve(op, static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), nrhs,
+                        rtol, restart, maxit, iters_out, relres_out, &result, op->bgws);
+    } else {
     solve_fns fns;
     fns.inner = [op, nrhs](const double2* a, double2* b) { apply_inner(op, a, b, nrhs); };
     fns.fp64 = [op, nrhs](const double2* a, double2* b) { matvec_residual(op, a, b, nrhs); };
@@ -451,6 +455,7 @@ cfie_status cfie_gmres_solve(cfie_op* op, const void* f_dev, void* x_dev, int nr
     gmres_set(st, op->ctx, op->K, op->ps, fns, op->prec != CFIE_FP64,
               static_cast<const double2*>(f_dev), static_cast<double2*>(x_dev), rtol, restart,
               maxit, iters_out, relres_out, &result, op->stats);
+    }
     if (op->layout == CFIE_STORED && stored_take_error(op))
       throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
     if (op->prec == CFIE_FP32_REFINED && tc_take_error(op))
@@ -775,4 +780,10 @@ cfie_status cfie_op_set_preconditioner(cfie_op* op, cfie_dirprec* P) {
                  "the preconditioner was built for another operator or context");
     op->dirprec = P;
   });
+}
+
+cfie_status cfie_op_set_block_gmres(cfie_op* op, int on) {
+  if (!op || (on != 0 && on != 1)) return CFIE_EINVAL;
+  op->block_gmres = on;
+  return CFIE_OK;
 }

@@ -18,8 +18,9 @@
 //  * E: e_ij is the least-squares constant of the rank-1 form on the block
 //    itself, the mean of M(x, y) / (U_i(x, k^i) U_j(y, k^j)) over x in P_i,
 //    y in P_j (the quantity eq. entry approximates from Chebyshev samples):
-//    one CTA per ordered pair of segments, FP64 entries (the FP64 matvec's
-//    entry function), FP64 block sums.
+//    one CTA per ordered pair of segments over the operator's own entries,
+//    FP64 for the FP64 precision, FP32 for the refined ones (the fast
+//    matvec's entries: one pass at FP32 speed instead of an FP64 matvec).
 //  * W~^-1: W~ = A_T + E with A_T the block anti-diagonal of the T_i, one
 //    entry per row, so every row a of W~ owns the unknown pi(a) (its
 //    anti-diagonal partner) with coefficient D_a, and E has one entry per
@@ -39,11 +40,17 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
+
+#include <climits>
 
 #include "hankel64.cuh"
 #include "internal.h"
+#include "pair32.cuh"
 
 namespace {
 
@@ -52,9 +59,22 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int EMAX = 1024;   // largest segment (cfie_dirprec_level's bound)
 
+// Entries in FP64 (the FP64 matvec's pair function), or for the refined
+// precisions the operator's FP32 entries (near band from its table, the rest
+// from the FP32 pair function, as the stored matrix is assembled), summed per
+// thread in the entries' precision and across the block in FP64.
+struct e32_args {
+  omega32 W;
+  geo32 g;
+  const float* w32;
+  const float2* band;
+  int b;
+};
+
+template <bool F32>
 __global__ void __launch_bounds__(256)
 k_dirprec_e(int n, int m, double omega, double eta, double ds, geom_dev g,
-            const double* __restrict__ wtab, const int* __restrict__ first,
+            const double* __restrict__ wtab, e32_args f, const int* __restrict__ first,
             const int* __restrict__ count, const int* __restrict__ level,
             const int* __restrict__ kpair, double2* __restrict__ e) {
   __shared__ double2 phr[EMAX], phc[EMAX];
@@ -82,19 +102,38 @@ k_dirprec_e(int n, int m, double omega, double eta, double ds, geom_dev g,
   __syncthreads();
   const double h = 2.0 * CFIE_PI / n;
   double ar = 0.0, ai = 0.0;
+  float sr32 = 0.f, si32 = 0.f;
   const long long tot = (long long)ci * cj;
   for (long long idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int x = (int)(idx / cj), y = (int)(idx % cj);
     const int gi = fi + x, gj = fj + y;
     int d = gi - gj;
     if (d < 0) d += n;
-    double2 a, unused;
-    pair_entries_fp64<0>(g.x[gi] - g.x[gj], g.y[gi] - g.y[gj], omega, eta, h, wtab[d], g.nx[gj],
-                         g.ny[gj], g.sp[gj], g.nx[gi], g.ny[gi], g.sp[gi], a, unused);
     const double2 u = phr[x], v = phc[y];
     const double pr = u.x * v.x - u.y * v.y, pim = u.x * v.y + u.y * v.x;
-    ar += a.x * pr - a.y * pim;
-    ai += a.x * pim + a.y * pr;
+    if constexpr (F32) {
+      float2 a, unused;
+      const int dd = d <= f.b ? d : (d >= n - f.b ? d - n : INT_MAX);
+      if (dd != INT_MAX)
+        a = f.band[(size_t)gi * (2 * f.b + 1) + dd + f.b];
+      else
+        pair_entries_fp32<0>(f.W, f.g.xh[gi], f.g.xl[gi], f.g.yh[gi], f.g.yl[gi], f.g.nx[gi],
+                             f.g.ny[gi], f.g.sp[gi], f.g.xh[gj], f.g.xl[gj], f.g.yh[gj],
+                             f.g.yl[gj], f.g.nx[gj], f.g.ny[gj], f.g.sp[gj], f.w32[d], a, unused);
+      const float p1 = (float)pr, p2 = (float)pim;
+      sr32 = fmaf(a.x, p1, fmaf(-a.y, p2, sr32));
+      si32 = fmaf(a.x, p2, fmaf(a.y, p1, si32));
+    } else {
+      double2 a, unused;
+      pair_entries_fp64<0>(g.x[gi] - g.x[gj], g.y[gi] - g.y[gj], omega, eta, h, wtab[d], g.nx[gj],
+                           g.ny[gj], g.sp[gj], g.nx[gi], g.ny[gi], g.sp[gi], a, unused);
+      ar += a.x * pr - a.y * pim;
+      ai += a.x * pim + a.y * pr;
+    }
+  }
+  if constexpr (F32) {
+    ar = sr32;
+    ai = si32;
   }
   for (int o = 16; o > 0; o >>= 1) {
     ar += __shfl_xor_sync(0xffffffffu, ar, o);
@@ -122,13 +161,17 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 
 // Step k, one CTA: pivot row p = argmax_{i >= k} |A_ik| (lowest index on
 // ties), rows k and p swapped, row k divided by the pivot with A_kk replaced
-// by its inverse; column k saved (row k as zero) and cleared for the update.
+// by its inverse; column k saved (row k as zero) and cleared for the update,
+// and the rows whose saved entry is non-zero listed (rows[0 .. *cnt)): the
+// coupled block of W~ is sparse and stays so under elimination (a few percent
+// of the rows take part in a step), so the update touches only those rows.
 __global__ void __launch_bounds__(1024)
 k_gj_pivot(int N, int k, double2* __restrict__ A, int* __restrict__ piv,
-           double2* __restrict__ col, double2* __restrict__ row, int* __restrict__ err) {
+           double2* __restrict__ col, double2* __restrict__ row, int* __restrict__ rows,
+           int* __restrict__ cnt, int* __restrict__ err) {
   __shared__ double bv[32];
   __shared__ int bi[32];
-  __shared__ int P;
+  __shared__ int P, C;
   double best = -1.0;
   int arg = k;
   for (int i = k + threadIdx.x; i < N; i += blockDim.x) {
@@ -160,6 +203,7 @@ k_gj_pivot(int N, int k, double2* __restrict__ A, int* __restrict__ piv,
         bi[0] = bi[q];
       }
     P = bi[0];
+    C = 0;
     piv[k] = bi[0];
     if (!(bv[0] > 0.0)) atomicExch(err, 1);   // singular
   }
@@ -185,26 +229,33 @@ k_gj_pivot(int N, int k, double2* __restrict__ A, int* __restrict__ piv,
     if (i == k) {
       col[i] = make_double2(0.0, 0.0);
     } else {
-      col[i] = A[(size_t)i * N + k];
+      const double2 v = A[(size_t)i * N + k];
+      col[i] = v;
       A[(size_t)i * N + k] = make_double2(0.0, 0.0);
+      if (v.x != 0.0 || v.y != 0.0) rows[atomicAdd(&C, 1)] = i;
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) *cnt = C;
 }
 
-// A_ij -= col_i row_j for every i, j (row k has col_k = 0; column k starts at 0,
-// so it receives -A_ik / pivot)
+// A_ij -= col_i row_j for the listed rows i and every j (column k starts at 0,
+// so it receives -A_ik / pivot); rows not listed have col_i = 0
 __global__ void __launch_bounds__(256)
 k_gj_update(int N, double2* __restrict__ A, const double2* __restrict__ col,
-            const double2* __restrict__ row) {
-  const int i = blockIdx.y;
-  const double2 c = col[i];
-  if (c.x == 0.0 && c.y == 0.0) return;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
-    const double2 r = row[j];
-    double2 a = A[(size_t)i * N + j];
-    a.x -= c.x * r.x - c.y * r.y;
-    a.y -= c.x * r.y + c.y * r.x;
-    A[(size_t)i * N + j] = a;
+            const double2* __restrict__ row, const int* __restrict__ rows,
+            const int* __restrict__ cnt) {
+  const int nr = *cnt;
+  for (int q = blockIdx.y; q < nr; q += gridDim.y) {
+    const int i = rows[q];
+    const double2 c = col[i];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x) {
+      const double2 r = row[j];
+      double2 a = A[(size_t)i * N + j];
+      a.x -= c.x * r.x - c.y * r.y;
+      a.y -= c.x * r.y + c.y * r.x;
+      A[(size_t)i * N + j] = a;
+    }
   }
 }
 
@@ -358,6 +409,13 @@ __global__ void k_w_rest(int K, int nRest, int nrhs, wsolve_dev w, const float2*
   r[c * K + w.pi[a]] = cdiv(acc, w.D[a]);
 }
 
+// A[pos[q]] = val[q] (positions distinct)
+__global__ void k_scatter_c128(size_t nz, const int* __restrict__ pos,
+                               const double2* __restrict__ val, double2* __restrict__ A) {
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < nz) A[pos[q]] = val[q];
+}
+
 __global__ void k_c128_to_c64(size_t len, const double2* __restrict__ x, float2* __restrict__ y) {
   const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < len) y[e] = make_float2((float)x[e].x, (float)x[e].y);
@@ -368,6 +426,69 @@ __global__ void k_c64_to_c128(size_t len, const float2* __restrict__ x, double2*
 }
 
 unsigned nblk(size_t len, int t = 256) { return (unsigned)((len + t - 1) / t); }
+
+// Level blocks depend only on (n, p, level, omega, eta, L, t_keep): kept for
+// the process so that preconditioners of the same discretisation (new
+// operators at every solve, other right-hand sides) skip their host setup.
+struct level_blocks {
+  std::vector<double> Binv, U, T, Tt;
+};
+std::mutex g_level_mu;
+std::map<std::tuple<int, int, int, double, double, double, int>, level_blocks> g_levels;
+
+// The curve's n arclength samples (positions) and perimeter, kept for the
+// process per (curve, parameters, n): setups of the same discretisation
+// (a new operator at every solve) reuse them.
+std::mutex g_arc_mu;
+std::map<std::tuple<int, std::vector<double>, int>, std::pair<std::vector<double>, double>> g_arc;
+
+void arclength_nodes(cfie_curve kind, const double* params, int nparams, int n,
+                     std::vector<double>& z, double& L) {
+  CFIE_REQUIRE(nparams >= 0 && nparams <= 128 && (nparams == 0 || params),
+               "invalid curve parameters");
+  const auto key = std::make_tuple((int)kind, std::vector<double>(params, params + nparams), n);
+  {
+    std::lock_guard<std::mutex> lock(g_arc_mu);
+    auto it = g_arc.find(key);
+    if (it != g_arc.end()) {
+      z = it->second.first;
+      L = it->second.second;
+      return;
+    }
+  }
+  z.assign(2 * (size_t)n, 0.0);
+  std::vector<double> dz(2 * (size_t)n), ddz(2 * (size_t)n);
+  CFIE_REQUIRE(cfie_arclength_samples(kind, params, nparams, n, z.data(), dz.data(), ddz.data(),
+                                      &L) == CFIE_OK,
+               "invalid curve for the arclength samples");
+  std::lock_guard<std::mutex> lock(g_arc_mu);
+  if (g_arc.size() >= 16) g_arc.clear();
+  g_arc[key] = std::make_pair(z, L);
+}
+
+level_blocks level_setup(int n, int p, int l, double omega, double eta, double L, int t_keep) {
+  const auto key = std::make_tuple(n, p, l, omega, eta, L, t_keep);
+  {
+    std::lock_guard<std::mutex> lock(g_level_mu);
+    auto it = g_levels.find(key);
+    if (it != g_levels.end()) return it->second;
+  }
+  const int c = (1 << l) * p, K = (1 << (l + 1)) + 1;
+  level_blocks b;
+  b.Binv.resize(2 * (size_t)c * c);
+  b.U.resize(2 * (size_t)c * K);
+  b.T.resize(2 * (size_t)K * K);
+  b.Tt.resize(2 * (size_t)K * K);
+  CFIE_REQUIRE(cfie_dirprec_level(n, p, l, omega, eta, L, nullptr, b.Binv.data(), b.U.data(),
+                                  b.T.data()) == CFIE_OK,
+               "cfie_dirprec_level failed (singular block?)");
+  CFIE_REQUIRE(cfie_dirprec_threshold(K, b.T.data(), t_keep * K, b.Tt.data()) == CFIE_OK,
+               "cfie_dirprec_threshold failed");
+  std::lock_guard<std::mutex> lock(g_level_mu);
+  if (g_levels.size() >= 32) g_levels.clear();   // bounded: a few MB per entry
+  g_levels[key] = b;
+  return b;
+}
 
 // GEMM kinds, in descriptor order: m descriptors each
 enum { G_BINV = 0, G_UT = 1, G_TT = 2, G_U = 3, G_Z = 4 };
@@ -445,11 +566,9 @@ void dirprec_build(cfie_dirprec* P, cfie_op* op, cfie_curve kind, const double* 
   P->eta = op->eta;
 
   // the node set: the operator's nodes must be the curve's arclength samples
-  std::vector<double> z(2 * (size_t)n), dz(2 * (size_t)n), ddz(2 * (size_t)n);
+  std::vector<double> z;
   double L = 0;
-  CFIE_REQUIRE(cfie_arclength_samples(kind, params, nparams, n, z.data(), dz.data(), ddz.data(),
-                                      &L) == CFIE_OK,
-               "invalid curve for the arclength samples");
+  arclength_nodes(kind, params, nparams, n, z, L);
   P->L = L;
   {
     std::vector<double> gx(n), gy(n);
@@ -511,13 +630,11 @@ void dirprec_build(cfie_dirprec* P, cfie_op* op, cfie_curve kind, const double* 
   }
   std::vector<float2> mats_h((size_t)mat_elems);
   for (lvl& b : lvls) {
-    std::vector<double> Binv(2 * (size_t)b.c * b.c), U(2 * (size_t)b.c * b.K),
-        T(2 * (size_t)b.K * b.K), Tt(2 * (size_t)b.K * b.K);
-    CFIE_REQUIRE(cfie_dirprec_level(n, p, b.l, op->omega, op->eta, L, nullptr, Binv.data(),
-                                    U.data(), T.data()) == CFIE_OK,
-                 "cfie_dirprec_level failed (singular block?)");
-    CFIE_REQUIRE(cfie_dirprec_threshold(b.K, T.data(), t_keep * b.K, Tt.data()) == CFIE_OK,
-                 "cfie_dirprec_threshold failed");
+    level_blocks lb = level_setup(n, p, b.l, op->omega, op->eta, L, t_keep);
+    const std::vector<double>& Binv = lb.Binv;
+    const std::vector<double>& U = lb.U;
+    const std::vector<double>& Tt = lb.Tt;
+    std::vector<double>& T = lb.T;
     for (long long e = 0; e < (long long)b.c * b.c; ++e)
       mats_h[b.oBinv + e] = make_float2((float)Binv[2 * e], (float)Binv[2 * e + 1]);
     for (int x = 0; x < b.c; ++x)
@@ -549,9 +666,23 @@ void dirprec_build(cfie_dirprec* P, cfie_op* op, cfie_curve kind, const double* 
                                     cudaMemcpyHostToDevice, st));
     dbuf eb;
     eb.reserve(sizeof(double2) * (size_t)m * m);
-    k_dirprec_e<<<(unsigned)m * m, 256, 0, st>>>(n, m, op->omega, op->eta, L / n, op->g,
-                                                  op->wtab.as<double>(), t, t + m, t + 2 * m,
-                                                  t + 3 * m, eb.as<double2>());
+    e32_args f{};
+    const bool f32 = op->prec == CFIE_FP32_REFINED && op->geo32.p && op->band_b >= 0;
+    if (f32) {
+      float* base = op->geo32.as<float>();
+      f.W = omega32{(float)op->omega, (float)op->eta, (float)op->h};
+      f.g = geo32_at(base, n);
+      f.w32 = base + 7 * n;
+      f.band = op->band.as<float2>();
+      f.b = op->band_b;
+      k_dirprec_e<true><<<(unsigned)m * m, 256, 0, st>>>(n, m, op->omega, op->eta, L / n, op->g,
+                                                          op->wtab.as<double>(), f, t, t + m,
+                                                          t + 2 * m, t + 3 * m, eb.as<double2>());
+    } else {
+      k_dirprec_e<false><<<(unsigned)m * m, 256, 0, st>>>(n, m, op->omega, op->eta, L / n, op->g,
+                                                           op->wtab.as<double>(), f, t, t + m,
+                                                           t + 2 * m, t + 3 * m, eb.as<double2>());
+    }
     CFIE_CHECK_LAUNCH();
     P->e.assign(2 * (size_t)m * m, 0.0);
     CFIE_CHECK_CUDA(cudaMemcpyAsync(P->e.data(), eb.p, sizeof(double2) * (size_t)m * m,
@@ -612,33 +743,46 @@ void dirprec_build(cfie_dirprec* P, cfie_op* op, cfie_curve kind, const double* 
 
   // M_S = D_S + E_SS (row of unknown b is pi(b)), inverted on the GPU in FP64
   if (nS > 0) {
-    std::vector<double> MS(2 * (size_t)nS * nS, 0.0);
+    // its non-zeros: the diagonal D and E's entries on S x S (one per segment
+    // pair at most, so no two share a position), scattered into a zeroed matrix
+    std::vector<int> mpos;
+    std::vector<double2> mval;
     for (int s = 0; s < nS; ++s) {
       const int a = pi[sb[s]];
-      MS[2 * ((size_t)s * nS + s)] = D[2 * a];
-      MS[2 * ((size_t)s * nS + s) + 1] = D[2 * a + 1];
+      mpos.push_back(s * nS + s);
+      mval.push_back(make_double2(D[2 * a], D[2 * a + 1]));
       for (int qq = rowptr[a]; qq < rowptr[a + 1]; ++qq) {
         const int t2 = sidx[ecol[qq]];
         if (t2 < 0) continue;
-        MS[2 * ((size_t)s * nS + t2)] += evald[2 * qq];
-        MS[2 * ((size_t)s * nS + t2) + 1] += evald[2 * qq + 1];
+        mpos.push_back(s * nS + t2);
+        mval.push_back(make_double2(evald[2 * qq], evald[2 * qq + 1]));
       }
     }
-    dbuf A, aux;
+    dbuf A, aux, sp;
     A.reserve(sizeof(double2) * (size_t)nS * nS);
-    aux.reserve(sizeof(double2) * 2 * (size_t)nS + sizeof(int) * (nS + 4) + 64);
+    aux.reserve(sizeof(double2) * 2 * (size_t)nS + sizeof(int) * (2 * (size_t)nS + 8) + 64);
     double2* col = aux.as<double2>();
     double2* row = col + nS;
     int* piv = reinterpret_cast<int*>(row + nS);
-    int* err = piv + nS;
-    CFIE_CHECK_CUDA(cudaMemcpyAsync(A.p, MS.data(), sizeof(double2) * (size_t)nS * nS,
-                                    cudaMemcpyHostToDevice, st));
+    int* rows = piv + nS;
+    int* cnt = rows + nS;
+    int* err = cnt + 1;
+    const size_t nz = mpos.size();
+    sp.reserve((sizeof(double2) + sizeof(int)) * nz + 64);
+    double2* spv = sp.as<double2>();
+    int* spp = reinterpret_cast<int*>(spv + nz);
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(spv, mval.data(), sizeof(double2) * nz, cudaMemcpyHostToDevice, st));
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(spp, mpos.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, st));
+    CFIE_CHECK_CUDA(cudaMemsetAsync(A.p, 0, sizeof(double2) * (size_t)nS * nS, st));
+    k_scatter_c128<<<nblk(nz), 256, 0, st>>>(nz, spp, spv, A.as<double2>());
+    CFIE_CHECK_LAUNCH();
     CFIE_CHECK_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     const unsigned gx = (unsigned)std::max(1, std::min(8, (nS + 255) / 256));
+    const unsigned gy = (unsigned)std::min(nS, 256);
     for (int k = 0; k < nS; ++k) {
-      k_gj_pivot<<<1, 1024, 0, st>>>(nS, k, A.as<double2>(), piv, col, row, err);
+      k_gj_pivot<<<1, 1024, 0, st>>>(nS, k, A.as<double2>(), piv, col, row, rows, cnt, err);
       CFIE_CHECK_LAUNCH();
-      k_gj_update<<<dim3(gx, (unsigned)nS), 256, 0, st>>>(nS, A.as<double2>(), col, row);
+      k_gj_update<<<dim3(gx, gy), 256, 0, st>>>(nS, A.as<double2>(), col, row, rows, cnt);
       CFIE_CHECK_LAUNCH();
     }
     int bad = 0;

@@ -247,6 +247,8 @@ struct cfie_op {
 
   cfie_solve_stats stats{};
   cfie_dirprec* dirprec = nullptr;   // right preconditioner of cfie_gmres_solve (not owned)
+  int block_gmres = 0;               // cfie_gmres_solve as one block GMRES over the columns
+  dbuf bgws;                         // its workspace (basis, blocks, partial sums)
 };
 
 // Directional preconditioner of Section 2 built for one sound-soft operator
@@ -371,3 +373,7 @@ void dirprec_build(cfie_dirprec* P, cfie_op* op, cfie_curve kind, const double* 
 void dirprec_apply(cfie_dirprec* P, const double2* x, double2* y, int nrhs);
 int dirprec_n(const cfie_dirprec* P);
 int dirprec_segments(const cfie_dirprec* P, double* e);
+// block_gmres.cu: block GMRES over the nrhs columns of one operator
+void block_gmres_solve(cfie_op* op, const double2* f, double2* x, int nrhs, double rtol,
+                       int restart, int maxit, int* iters, double* relres, cfie_status* status,
+                       dbuf& ws);

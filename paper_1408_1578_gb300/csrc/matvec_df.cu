@@ -647,7 +647,7 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < RST; ++s) {
-      mbar_init(&S.full[s], RPROD * 32 + 1);
+      mbar_init(&S.full[s], RPROD + 1);   // one arrival per producer warp + the TMA thread
       mbar_init(&S.empty[s], 1);
       S.issued[s] = -1;
     }
@@ -756,8 +756,9 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
       __syncwarp();
       for (int k = sg.z; k < sg.w; ++k, ++it) {
         const int st = it % RST;
-        if (*(volatile int*)&S.abort) break;
-        if (it >= RST && !mbar_wait(&S.empty[st], ((it / RST) - 1) & 1)) {
+        // exits are warp-uniform: the warp arrives on the stage barrier as one
+        if (__any_sync(0xffffffffu, *(volatile int*)&S.abort)) break;
+        if (it >= RST && !__all_sync(0xffffffffu, mbar_wait(&S.empty[st], ((it / RST) - 1) & 1))) {
           if (lane == 0) {
             atomicExch(err, 21);
             S.abort = 1;
@@ -818,7 +819,8 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&S.full[st]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.full[st]);
         if ((k - sg.z) % RCK == 0) {
           // first tile of a chunk: drain the previous chunk
           if (pc >= 0 && !drain(pc, ps, pm0, pfirst)) {
@@ -831,13 +833,15 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
           pfirst = k == sg.z;
         }
       }
-      if (*(volatile int*)&S.abort) stop = true;
+      if (__any_sync(0xffffffffu, *(volatile int*)&S.abort)) stop = true;
     }
     if (!stop && pc >= 0) drain(pc, ps, pm0, pfirst);
   } else if (warp == RWTMA) {
     if (lane == 0) {
-      // ---- TMA: the 2 x 6 density-slice planes of each source tile
+      // ---- TMA: the 2 x 6 density-slice planes of each source tile, kept in
+      // L2 (evict last): every row tile of the operator reads all of them
       asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+      const uint64_t keep = l2_evict_last();
       int it = 0;
       for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
         const int4 sg = segs[s];
@@ -852,7 +856,7 @@ k_resid_tc(df_params P, const int* __restrict__ rowexp, const __grid_constant__ 
           S.issued[st] = (it / RST) & 1;
 #pragma unroll
           for (int p = 0; p < 2 * RSL; ++p)
-            tma_load_2d(&S.B[st][p][0], &tmB, &S.full[st], k * RTK, p * NC);
+            tma_load_2d_hint(&S.B[st][p][0], &tmB, &S.full[st], k * RTK, p * NC, keep);
         }
       }
     }

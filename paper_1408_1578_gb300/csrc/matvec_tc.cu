@@ -117,7 +117,7 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TSTAGES; ++s) {
-      mbar_init(&S.full[s], NPROD * 32 + 1);   // producer threads + the TMA thread
+      mbar_init(&S.full[s], NPROD + 1);        // one arrival per producer warp + the TMA thread
       mbar_init(&S.empty[s], 1);
       mbar_init(&S.sfull[s], 1);
       S.issued[s] = -1;
@@ -170,11 +170,12 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
         const int st = it % TSTAGES;
         const int j0 = k * TBK;
         const int j = j0 + jp;                       // first of the lane's two sources
-        if (*(volatile int*)&S.abort) break;
+        // exits are warp-uniform: the warp arrives on the stage barrier as one
+        if (__any_sync(0xffffffffu, *(volatile int*)&S.abort)) break;
         // this tile's source geometry and Kress window, brought in by the TMA
         // warp once the MMAs of the stage's previous tile were done (so the A
         // planes of the stage are free as well)
-        if (!mbar_wait(&S.sfull[st], (it / TSTAGES) & 1)) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&S.sfull[st], (it / TSTAGES) & 1))) {
           if (lane == 0) {
             atomicExch(err, 15);
             S.abort = 1;
@@ -234,11 +235,13 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
             store_split2(a0, a1, a2, a3, sbase + (uint32_t)(2 * NPROD * 64 * q), e[0], e[1]);
           }
         }
-        // generic-proxy writes become visible to the tensor core's async proxy
+        // generic-proxy writes become visible to the tensor core's async proxy;
+        // the warp's writes are ordered before its one arrival by __syncwarp
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&S.full[st]);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.full[st]);
       }
-      if (*(volatile int*)&S.abort) break;
+      if (__any_sync(0xffffffffu, *(volatile int*)&S.abort)) break;
     }
   } else if (warp == WTMA) {
     if (lane == 0) {

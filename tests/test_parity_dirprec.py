@@ -7,8 +7,8 @@ the oracle's own arclength map on the CPU), p = 8 points per wavelength and
 eta = omega / 2, the setting of Table 1.  Checked:
 
 * the block coefficients e_ij (the nodal least-squares constants of the
-  rank-1 forms, the oracle's e_from="nodes"): FP64 on both sides, within
-  1e-9 of the largest;
+  rank-1 forms, the oracle's e_from="nodes"): from FP64 entries within 1e-9
+  of the largest, from a refined operator's FP32 entries within 1e-5;
 * P v of eq. (eapp) for random right-hand sides against the oracle's apply
   with its sparse LU of W~: the GPU applies in complex64, within 1e-5;
 * GMRES(80) to 1e-6 with P on the right (FP64 operator): the iteration count
@@ -70,6 +70,23 @@ def test_block_coefficients(case):
         want[i, j] = E[ref.koff[i] + ki, ref.koff[j] + kj]
     assert np.all(np.diag(e) == 0)
     assert np.max(np.abs(e - want)) < 1e-9 * np.max(np.abs(want))
+
+
+def test_block_coefficients_from_fp32_entries(ctx, case):
+    """A refined (FP32) operator builds E from its FP32 entries: within 1e-5
+    of the largest e_ij."""
+    ref = case["ref"]
+    op32 = ctx.samples(case["z"], case["dz"], case["ddz"]).discretise(
+        case["n"], case["omega"], eta=case["eta"], precision="fp32")
+    prec = op32.dirprec(case["kind"], case["q"], P_PPW, **case["params"])
+    e = prec.coefficients()
+    want = np.zeros_like(e)
+    E = ref.E.toarray()
+    for (i, j), (ki, kj) in ref.kidx.items():
+        want[i, j] = E[ref.koff[i] + ki, ref.koff[j] + kj]
+    assert np.max(np.abs(e - want)) < 1e-5 * np.max(np.abs(want))
+    prec.close()
+    op32.close()
 
 
 def test_apply_matches_oracle(case):

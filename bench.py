@@ -55,6 +55,9 @@ def parse():
                    help="single-operator sound-soft workloads: nodes equispaced in arclength "
                         "(n = 4^q p, p = 8) and the directional preconditioner of Section 2 on "
                         "the right of every solve (its setup inside each step)")
+    p.add_argument("--block", action="store_true",
+                   help="single-operator workloads: one block GMRES over all right-hand sides "
+                        "(restart in block steps: 40) instead of one GMRES per right-hand side")
     p.add_argument("--oracle-budget", type=float, default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -273,6 +276,9 @@ def run_ours(args, rank, world):
     spec = workload(args.workload, args.precision, args.n, args.nrhs, args.eta_factor)
     if args.rtol:
         spec["rtol"] = args.rtol
+    if args.block:
+        spec["restart"] = 40       # block steps per cycle
+        spec["solver"] = "block GMRES"
     n, w, nrhs, bc = spec["n"], spec["omega"], spec["nrhs"], spec["bc"]
     stream = torch.cuda.current_stream()
     ctx = cfie.Context(dev, stream=stream)
@@ -302,6 +308,8 @@ def run_ours(args, rank, world):
             geom = ctx.samples(*arc[:3])
         op = geom.discretise(n, w, eta=spec["eta"], bc=bc, precision=spec["precision"],
                              layout=spec["layout"])
+        if args.block:
+            op.set_block_gmres(True)
         prec = None
         if arc is not None and precondition:
             t0 = time.perf_counter()
@@ -626,6 +634,8 @@ def dirprec_levels(n, p):
 
 def single_config(spec, world):
     prec = " arclength nodes, directional preconditioner" if spec.get("nodes") == "arclength" else ""
+    if spec.get("solver"):
+        prec += ", " + spec["solver"]
     return {"workload": f"{spec['name']}: {spec['curve']} {spec['bc']} n={spec['n']} "
                         f"omega={spec['omega']} {eta_text(spec)} nrhs={spec['nrhs']}{prec}",
             "curve": spec["curve"], "bc": spec["bc"], "n": spec["n"], "omega": spec["omega"],

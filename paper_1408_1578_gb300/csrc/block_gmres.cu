@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -51,9 +52,11 @@ template <> struct bt<float2> {
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-constexpr int IPT = 16;      // output tile of the inner products (16 x 16)
-constexpr int IPR = 32;      // rows staged per step
-constexpr int IPC = 2048;    // rows per chunk (FP64 sums across chunks)
+// Both products use 64 x 64 output tiles, 4 x 4 per thread (16 outputs from
+// 4 + 4 shared-memory loads per step of the reduction).
+constexpr int BT = 64;       // output tile edge
+constexpr int BR = 16;       // reduction rows staged per step
+constexpr int IPC = 1024;    // rows per chunk of the inner products (FP64 sums across chunks)
 
 // part[chunk][a][b] = sum over the chunk's rows of conj(X[i, a]) Y[i, b]
 // (a < pa, b < pb; X, Y column-major with leading dimension n)
@@ -62,30 +65,50 @@ __global__ void __launch_bounds__(256)
 k_bip(int n, int pa, int pb, const T* __restrict__ X, const T* __restrict__ Y,
       double2* __restrict__ part) {
   using S = typename bt<T>::S;
-  __shared__ T xs[IPR][IPT + 1], ys[IPR][IPT + 1];
-  const int a0 = blockIdx.x * IPT, b0 = blockIdx.y * IPT;
+  __shared__ T xs[BR][BT + 1], ys[BR][BT + 1];
+  const int a0 = blockIdx.x * BT, b0 = blockIdx.y * BT;
   const int r0 = blockIdx.z * IPC, r1 = min(n, r0 + IPC);
-  const int ta = threadIdx.x / IPT, tb = threadIdx.x % IPT;
-  S re = 0, im = 0;
-  for (int i0 = r0; i0 < r1; i0 += IPR) {
-    for (int e = threadIdx.x; e < IPR * IPT; e += 256) {
-      const int rr = e % IPR, c = e / IPR;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  S are[4][4], aim[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) are[i][j] = aim[i][j] = 0;
+  for (int i0 = r0; i0 < r1; i0 += BR) {
+    for (int e = threadIdx.x; e < BR * BT; e += 256) {
+      const int rr = e % BR, c = e / BR;
       const int i = i0 + rr;
       xs[rr][c] = (i < r1 && a0 + c < pa) ? X[(size_t)(a0 + c) * n + i] : bt<T>::make(0.0, 0.0);
       ys[rr][c] = (i < r1 && b0 + c < pb) ? Y[(size_t)(b0 + c) * n + i] : bt<T>::make(0.0, 0.0);
     }
     __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < IPR; ++rr) {
-      const T u = xs[rr][ta], v = ys[rr][tb];
-      re = fma(u.x, v.x, fma(u.y, v.y, re));
-      im = fma(u.x, v.y, fma(-u.y, v.x, im));
+#pragma unroll 4
+    for (int rr = 0; rr < BR; ++rr) {
+      T u[4], v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        u[q] = xs[rr][ty + 16 * q];
+        v[q] = ys[rr][tx + 16 * q];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          are[i][j] = fma(u[i].x, v[j].x, fma(u[i].y, v[j].y, are[i][j]));
+          aim[i][j] = fma(u[i].x, v[j].y, fma(-u[i].y, v[j].x, aim[i][j]));
+        }
     }
     __syncthreads();
   }
-  const int a = a0 + ta, b = b0 + tb;
-  if (a < pa && b < pb)
-    part[((size_t)blockIdx.z * pa + a) * pb + b] = make_double2((double)re, (double)im);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
+      if (a < pa && b < pb)
+        part[((size_t)blockIdx.z * pa + a) * pb + b] =
+            make_double2((double)are[i][j], (double)aim[i][j]);
+    }
 }
 
 // C[a][b] = sum over chunks of part (fixed order)
@@ -103,57 +126,67 @@ __global__ void k_bip_reduce(int chunks, int pa, int pb, const double2* __restri
 }
 
 // Y[i, b] = beta Y[i, b] + alpha sum_a X[i, a] M[a][b]  (i < n, b < pb, a < pa;
-// M row-major pa x pb in FP64); Y may be a different buffer from X
-constexpr int UBM = 64, UBN = 16, UBK = 16;
+// M row-major pa x pb in FP64); Y is a different buffer from X
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_bupd(int n, int pa, int pb, const T* __restrict__ X, const double2* __restrict__ M,
        T* __restrict__ Y, double alpha, double beta) {
   using S = typename bt<T>::S;
-  __shared__ T xs[UBK][UBM + 1];
-  __shared__ T ms[UBK][UBN + 1];
-  const int i0 = blockIdx.x * UBM, b0 = blockIdx.y * UBN;
-  const int col = threadIdx.x & 15, rg = threadIdx.x >> 4;
-  S ar[4] = {0, 0, 0, 0}, ai[4] = {0, 0, 0, 0};
-  for (int k0 = 0; k0 < pa; k0 += UBK) {
-    for (int e = threadIdx.x; e < UBK * UBM; e += 256) {
-      const int r = e % UBM, k = e / UBM;
+  __shared__ T xs[BR][BT + 1];   // [a][row]
+  __shared__ T ms[BR][BT + 1];   // [a][column]
+  const int i0 = blockIdx.x * BT, b0 = blockIdx.y * BT;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  S are[4][4], aim[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) are[i][j] = aim[i][j] = 0;
+  for (int k0 = 0; k0 < pa; k0 += BR) {
+    for (int e = threadIdx.x; e < BR * BT; e += 256) {
+      const int r = e % BT, k = e / BT;
       const int i = i0 + r, a = k0 + k;
       xs[k][r] = (i < n && a < pa) ? X[(size_t)a * n + i] : bt<T>::make(0.0, 0.0);
-    }
-    {
-      const int k = threadIdx.x / UBN, c = threadIdx.x % UBN;
-      const int a = k0 + k, b = b0 + c;
-      const double2 v = (a < pa && b < pb) ? M[(size_t)a * pb + b] : make_double2(0.0, 0.0);
-      ms[k][c] = bt<T>::make(v.x, v.y);
+      const int c = e % BT, kk = e / BT;
+      const int aa = k0 + kk, bb = b0 + c;
+      const double2 v = (aa < pa && bb < pb) ? M[(size_t)aa * pb + bb] : make_double2(0.0, 0.0);
+      ms[kk][c] = bt<T>::make(v.x, v.y);
     }
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < UBK; ++k) {
-      const T mv = ms[k][col];
+#pragma unroll 4
+    for (int k = 0; k < BR; ++k) {
+      T x[4], m[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const T xv = xs[k][rg + 16 * q];
-        ar[q] = fma(xv.x, mv.x, fma(-xv.y, mv.y, ar[q]));
-        ai[q] = fma(xv.x, mv.y, fma(xv.y, mv.x, ai[q]));
+        x[q] = xs[k][ty + 16 * q];
+        m[q] = ms[k][tx + 16 * q];
       }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          are[i][j] = fma(x[i].x, m[j].x, fma(-x[i].y, m[j].y, are[i][j]));
+          aim[i][j] = fma(x[i].x, m[j].y, fma(x[i].y, m[j].x, aim[i][j]));
+        }
     }
     __syncthreads();
   }
-  const int b = b0 + col;
-  if (b >= pb) return;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = i0 + rg + 16 * q;
-    if (i >= n) continue;
-    const size_t o = (size_t)b * n + i;
-    double yr = alpha * (double)ar[q], yi = alpha * (double)ai[q];
-    if (beta != 0.0) {
-      const T y = Y[o];
-      yr += beta * (double)y.x;
-      yi += beta * (double)y.y;
+  for (int i = 0; i < 4; ++i) {
+    const int row = i0 + ty + 16 * i;
+    if (row >= n) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tx + 16 * j;
+      if (b >= pb) continue;
+      const size_t o = (size_t)b * n + row;
+      double yr = alpha * (double)are[i][j], yi = alpha * (double)aim[i][j];
+      if (beta != 0.0) {
+        const T y = Y[o];
+        yr += beta * (double)y.x;
+        yi += beta * (double)y.y;
+      }
+      Y[o] = bt<T>::make(yr, yi);
     }
-    Y[o] = bt<T>::make(yr, yi);
   }
 }
 
@@ -264,6 +297,24 @@ std::vector<cplx> upper_inverse(const std::vector<cplx>& R, int c, int r) {
   return X;
 }
 
+// f(i) for i < count on up to 8 host threads (sequentially when the work is
+// small: `work` is the number of complex multiply-adds it takes)
+template <typename F>
+void parallel_for(int count, double work, F f) {
+  int nt = (int)std::min<unsigned>(8u, std::max(1u, std::thread::hardware_concurrency()));
+  nt = std::min(nt, count);
+  if (nt <= 1 || work < 2e5) {
+    for (int i = 0; i < count; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([=, &f] {
+      for (int i = t; i < count; i += nt) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
 // Least squares of the block Hessenberg system, QR by Householder reflections
 // added column by column: min over Y of ||G - Hbar Y|| per right-hand-side
 // column, with G = [B; 0].
@@ -301,8 +352,30 @@ struct block_ls {
     rows = new_rows;
     for (auto& g : G) g.resize(rows, cplx(0.0));
   }
-  void add_column(std::vector<cplx> col) {   // col has length rows
-    for (size_t j = 0; j < hv.size(); ++j) reflect(hv[j], hstart[j], htau[j], col);
+  // a block of columns (each of length rows): the earlier reflectors applied
+  // to all of them in parallel, then column by column the block's own ones and
+  // a new reflector, which are applied to the right-hand sides in parallel
+  void add_block(std::vector<std::vector<cplx>>& B) {
+    const size_t nprev = hv.size();
+    const int nb = (int)B.size();
+    double len = 0.0;
+    for (size_t j = 0; j < nprev; ++j) len += (double)hv[j].size();
+    parallel_for(nb, len * nb, [&](int c) {
+      for (size_t j = 0; j < nprev; ++j) reflect(hv[j], hstart[j], htau[j], B[c]);
+    });
+    for (int c = 0; c < nb; ++c) {
+      for (size_t j = nprev; j < hv.size(); ++j) reflect(hv[j], hstart[j], htau[j], B[c]);
+      new_reflector(B[c]);
+    }
+    double blen = 0.0;
+    for (size_t j = nprev; j < hv.size(); ++j) blen += (double)hv[j].size();
+    parallel_for(s, blen * s, [&](int b) {
+      for (size_t j = nprev; j < hv.size(); ++j) reflect(hv[j], hstart[j], htau[j], G[b]);
+    });
+  }
+  // the reflector that zeroes column `cols` below its diagonal (earlier
+  // reflectors already applied); the right-hand sides are left to the caller
+  void new_reflector(const std::vector<cplx>& col) {
     const int j = cols;
     double nrm2 = 0.0;
     for (int q = j; q < rows; ++q) nrm2 += std::norm(col[q]);
@@ -323,7 +396,6 @@ struct block_ls {
     hv.push_back(v);
     hstart.push_back(j);
     htau.push_back(tau);
-    for (auto& g : G) reflect(v, j, tau, g);
     ++cols;
   }
   double residual(int b) const {
@@ -334,12 +406,13 @@ struct block_ls {
   // Y (cols x s, row-major) from the triangular system
   std::vector<cplx> solve() const {
     std::vector<cplx> Y((size_t)cols * s, cplx(0.0));
-    for (int b = 0; b < s; ++b)
+    parallel_for(s, 0.5 * (double)cols * cols * s, [&](int b) {
       for (int i = cols - 1; i >= 0; --i) {
         cplx acc = G[b][i];
         for (int k = i + 1; k < cols; ++k) acc -= Rc[k][i] * Y[(size_t)k * s + b];
         Y[(size_t)i * s + b] = acc / Rc[i][i];
       }
+    });
     return Y;
   }
 };
@@ -356,7 +429,8 @@ struct bg_ws {
   double2* vin = nullptr;        // matvec input / output (n x s each)
   double2* vout = nullptr;
   double2* part = nullptr;       // inner-product partials
-  double2* small = nullptr;      // cap x s FP64 matrices (H, Y, Z)
+  double2* small = nullptr;      // cap x s FP64 matrices (Y, Z, Gram)
+  double2 *H1 = nullptr, *H2 = nullptr;   // the two Gram-Schmidt coefficient blocks
   double* nrm = nullptr;
   int chunks = 0;
 };
@@ -369,15 +443,34 @@ struct bg_ctx {
   std::function<void(const double2*, double2*, int)> prec; // right preconditioner (may be empty)
 };
 
+// Hd (device, pa x pb row-major FP64) = X^H Y; asynchronous
 template <typename T>
-void inner_products(const bg_ctx& C, const bg_ws<T>& w, const T* X, int pa, const T* Y, int pb,
-                    std::vector<cplx>& out) {
-  const dim3 grid((unsigned)((pa + IPT - 1) / IPT), (unsigned)((pb + IPT - 1) / IPT),
+void ip_dev(const bg_ctx& C, const bg_ws<T>& w, const T* X, int pa, const T* Y, int pb,
+            double2* Hd) {
+  prof_scope ps(C.op->ctx, CFIE_K_ARNOLDI);
+  const dim3 grid((unsigned)((pa + BT - 1) / BT), (unsigned)((pb + BT - 1) / BT),
                   (unsigned)w.chunks);
   k_bip<T><<<grid, 256, 0, C.st>>>(w.n, pa, pb, X, Y, w.part);
   CFIE_CHECK_LAUNCH();
-  k_bip_reduce<<<nbl((size_t)pa * pb), 256, 0, C.st>>>(w.chunks, pa, pb, w.part, w.small);
+  k_bip_reduce<<<nbl((size_t)pa * pb), 256, 0, C.st>>>(w.chunks, pa, pb, w.part, Hd);
   CFIE_CHECK_LAUNCH();
+}
+
+// Y = beta Y + alpha X Md (Md device, pa x pb row-major FP64); asynchronous
+template <typename T>
+void upd_dev(const bg_ctx& C, const bg_ws<T>& w, const T* X, int pa, const double2* Md, int pb,
+             T* Y, double alpha, double beta) {
+  prof_scope ps(C.op->ctx, CFIE_K_ARNOLDI);
+  const dim3 grid((unsigned)((w.n + BT - 1) / BT), (unsigned)((pb + BT - 1) / BT));
+  k_bupd<T><<<grid, 256, 0, C.st>>>(w.n, pa, pb, X, Md, Y, alpha, beta);
+  CFIE_CHECK_LAUNCH();
+}
+
+// the same with the result (or the matrix) on the host; synchronous
+template <typename T>
+void inner_products(const bg_ctx& C, const bg_ws<T>& w, const T* X, int pa, const T* Y, int pb,
+                    std::vector<cplx>& out) {
+  ip_dev(C, w, X, pa, Y, pb, w.small);
   out.resize((size_t)pa * pb);
   CFIE_CHECK_CUDA(cudaMemcpyAsync(out.data(), w.small, sizeof(double2) * pa * pb,
                                   cudaMemcpyDeviceToHost, C.st));
@@ -389,9 +482,7 @@ void update(const bg_ctx& C, const bg_ws<T>& w, const T* X, int pa, const std::v
             int pb, T* Y, double alpha, double beta) {
   CFIE_CHECK_CUDA(cudaMemcpyAsync(w.small, M.data(), sizeof(double2) * pa * pb,
                                   cudaMemcpyHostToDevice, C.st));
-  const dim3 grid((unsigned)((w.n + UBM - 1) / UBM), (unsigned)((pb + UBN - 1) / UBN));
-  k_bupd<T><<<grid, 256, 0, C.st>>>(w.n, pa, pb, X, w.small, Y, alpha, beta);
-  CFIE_CHECK_LAUNCH();
+  upd_dev(C, w, X, pa, w.small, pb, Y, alpha, beta);
   CFIE_CHECK_CUDA(cudaStreamSynchronize(C.st));   // M dies on return
 }
 
@@ -471,12 +562,16 @@ int cycle(const bg_ctx& C, bg_ws<T>& w, const double2* r, const std::vector<doub
       stats.inner_matvecs++;
     else
       stats.fp64_matvecs++;
-    // block CGS2 against V[:, :p]
-    std::vector<cplx> H1, H2;
-    inner_products(C, w, w.V, p, w.W, sk, H1);
-    update(C, w, w.V, p, H1, sk, w.W, -1.0, 1.0);
-    inner_products(C, w, w.V, p, w.W, sk, H2);
-    update(C, w, w.V, p, H2, sk, w.W, -1.0, 1.0);
+    // block CGS2 against V[:, :p], the coefficients staying on the device
+    ip_dev(C, w, w.V, p, w.W, sk, w.H1);
+    upd_dev(C, w, w.V, p, w.H1, sk, w.W, -1.0, 1.0);
+    ip_dev(C, w, w.V, p, w.W, sk, w.H2);
+    upd_dev(C, w, w.V, p, w.H2, sk, w.W, -1.0, 1.0);
+    std::vector<cplx> H1((size_t)p * sk), H2((size_t)p * sk);
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(H1.data(), w.H1, sizeof(double2) * p * sk,
+                                    cudaMemcpyDeviceToHost, C.st));
+    CFIE_CHECK_CUDA(cudaMemcpyAsync(H2.data(), w.H2, sizeof(double2) * p * sk,
+                                    cudaMemcpyDeviceToHost, C.st));
     stats.arnoldi_elems += 4LL * (long long)n * p * sk;
     const bool room = p + s <= w.cap;
     std::vector<cplx> Rk;
@@ -484,12 +579,12 @@ int cycle(const bg_ctx& C, bg_ws<T>& w, const double2* r, const std::vector<doub
     if (room) rn = block_qr(C, w, w.W, sk, w.V + (size_t)p * n, thresh, Rk);
     // block column [H; R_k] into the least squares
     ls.grow(p + rn);
+    std::vector<std::vector<cplx>> blk(sk, std::vector<cplx>(p + rn, cplx(0.0)));
     for (int j = 0; j < sk; ++j) {
-      std::vector<cplx> col(p + rn, cplx(0.0));
-      for (int i = 0; i < p; ++i) col[i] = H1[(size_t)i * sk + j] + H2[(size_t)i * sk + j];
-      for (int i = 0; i < rn; ++i) col[p + i] = Rk[(size_t)i * sk + j];
-      ls.add_column(col);
+      for (int i = 0; i < p; ++i) blk[j][i] = H1[(size_t)i * sk + j] + H2[(size_t)i * sk + j];
+      for (int i = 0; i < rn; ++i) blk[j][p + i] = Rk[(size_t)i * sk + j];
     }
+    ls.add_block(blk);
     ++steps;
     stats.arnoldi_steps++;
     bool all = true;
@@ -554,8 +649,8 @@ void solve_impl(cfie_op* op, const double2* f, double2* x, int s, double rtol, i
   w.chunks = (n + IPC - 1) / IPC;
   const size_t nv = (size_t)n * s;
   const size_t bytes = sizeof(T) * ((size_t)n * w.cap + 2 * nv) + sizeof(double2) * (2 * nv) +
-                       sizeof(double2) * ((size_t)w.chunks * w.cap * s + (size_t)w.cap * s) +
-                       sizeof(double) * s + 8 * 256;
+                       sizeof(double2) * ((size_t)w.chunks * w.cap * s + 3 * (size_t)w.cap * s) +
+                       sizeof(double) * s + 10 * 256;
   wsb.reserve(bytes);
   char* b = wsb.as<char>();
   size_t o = 0;
@@ -571,6 +666,8 @@ void solve_impl(cfie_op* op, const double2* f, double2* x, int s, double rtol, i
   w.vout = static_cast<double2*>(take(sizeof(double2) * nv));
   w.part = static_cast<double2*>(take(sizeof(double2) * (size_t)w.chunks * w.cap * s));
   w.small = static_cast<double2*>(take(sizeof(double2) * (size_t)w.cap * s));
+  w.H1 = static_cast<double2*>(take(sizeof(double2) * (size_t)w.cap * s));
+  w.H2 = static_cast<double2*>(take(sizeof(double2) * (size_t)w.cap * s));
   w.nrm = static_cast<double*>(take(sizeof(double) * s));
   // outer vectors: residual r, correction d (refined), A x
   op->K.r.reserve(sizeof(double2) * nv);

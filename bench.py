@@ -542,6 +542,7 @@ def reference_specs(args):
         return [{"name": f"stars[{k}]", "curve": "star",
                  "params": {"a": list(stars[k]["a"]), "b": list(stars[k]["b"])},
                  "n": stars[k]["n"], "omega": stars[k]["omega"], "nrhs": stars[k]["nrhs"],
+                 "eta": stars[k]["omega"], "eta_factor": 1.0,
                  "bc": "soft", "precision": "tensor"} for k in pick]
     return [workload(args.workload, args.precision, args.n, args.nrhs, args.eta_factor)]
 
@@ -762,10 +763,16 @@ def run_stars(args):
     f = torch.empty(L, dtype=torch.complex128, device="cuda")
     x = torch.zeros_like(f)
 
+    tuning = {}
+
     def step():
         ops = [ctx.fourier_star(s["a"], s["b"]).discretise(s["n"], s["omega"], precision="tensor",
                                                             layout="stored") for s in specs]
         b = cfie.Batch(ctx, ops, [s["nrhs"] for s in specs])
+        d, ms = b.tuning()
+        tuning["dealing"] = ["round-robin", "greedy", "stream-K"][d]
+        if any(ms):
+            tuning["candidates_ms"] = dict(zip(["round-robin", "greedy", "stream-K"], ms))
         for k, s in enumerate(specs):
             ops[k].rhs_plane_waves(inputs.directions(s["nrhs"]), b.block(f, k))
         x.zero_()
@@ -831,7 +838,8 @@ def run_stars(args):
                    "h2d_bytes_per_step": int(sum(s["nrhs"] for s in specs) * 8),
                    "d2h_bytes_per_step": int(L * 16)},
            "gpu_launches": int(launches), "kernel_ms": {k: round(v[0], 3) for k, v in kt.items()},
-           "kernel_launches": {k: v[1] for k, v in kt.items()}, "roofline": roof, "clocks": clk}
+           "kernel_launches": {k: v[1] for k, v in kt.items()}, "roofline": roof, "clocks": clk,
+           "contraction_tuning": tuning}
     ctx.close()
     return out
 

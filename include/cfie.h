@@ -433,6 +433,23 @@ cfie_status cfie_batch_gmres_solve(cfie_batch* batch, const void* f_dev, void* x
 cfie_status cfie_batch_last_stats(const cfie_batch* batch, cfie_solve_stats* out);
 /* As cfie_op_set_inner_basis, for the lockstep solves of a batch. */
 cfie_status cfie_batch_set_inner_basis(cfie_batch* batch, int fp32);
+/* How the batch's persistent contraction deals its work to the CTAs (one per
+ * SM), picked by cfie_batch_create when every operator is stored: each
+ * candidate's graph replay is timed once (CUDA events, mean of two replays
+ * after one warm-up) and the fastest kept; the choice is remembered for the
+ * process per batch shape (the operators' n and right-hand-side counts).
+ *  0  whole (operator, 128-row tile) units dealt round-robin
+ *  1  whole units, largest first, each to the CTA with the least work so far
+ *  2  stream-K: the (row tile, 64-source tile) pairs split evenly
+ * *dealing receives the choice (-1 when the batch is not all stored); ms
+ * (host, 3 floats, may be NULL) the candidates' replay times in milliseconds,
+ * zeros when the choice came from the process's memory.  CFIE_EINVAL for a
+ * null batch or dealing. */
+cfie_status cfie_batch_tuning(const cfie_batch* batch, int* dealing, float* ms);
+/* Rebuild the batch's contraction plan with the given dealing (0, 1 or 2, as
+ * cfie_batch_tuning lists them) instead of the tuned one.  Synchronous.
+ * CFIE_EINVAL for another value or a batch that is not all stored. */
+cfie_status cfie_batch_set_dealing(cfie_batch* batch, int dealing);
 /* Free a batch (NULL is ignored) after its queued work has finished; its
  * operators stay valid. */
 void cfie_batch_destroy(cfie_batch* batch);

@@ -128,6 +128,8 @@ SIGNATURES = {
     "cfie_batch_gmres_solve": (_I, [_P, _P, _P, _D, _I, _I, _IP, _DP]),
     "cfie_batch_last_stats": (_I, [_P, ctypes.POINTER(cfie_solve_stats)]),
     "cfie_batch_set_inner_basis": (_I, [_P, _I]),
+    "cfie_batch_tuning": (_I, [_P, _IP, ctypes.POINTER(ctypes.c_float)]),
+    "cfie_batch_set_dealing": (_I, [_P, _I]),
     "cfie_batch_destroy": (None, [_P]),
     "cfie_server_create": (_I, [_I, ctypes.c_size_t, _I, ctypes.POINTER(_P)]),
     "cfie_server_submit": (_I, [_P, ctypes.POINTER(cfie_request), ctypes.POINTER(ctypes.c_longlong)]),
@@ -418,6 +420,18 @@ class Batch:
         self.ctx.check(self.ctx.lib.cfie_batch_last_stats(self.h, ctypes.byref(s)),
                        "cfie_batch_last_stats")
         return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def set_dealing(self, dealing):
+        """Force the contraction's work dealing (0 round-robin, 1 greedy, 2 stream-K)."""
+        self.ctx.check(self.ctx.lib.cfie_batch_set_dealing(self.h, int(dealing)),
+                       "cfie_batch_set_dealing")
+
+    def tuning(self):
+        """(dealing, [ms of each candidate]) of the batch's contraction autotuner."""
+        d = ctypes.c_int()
+        ms = (ctypes.c_float * 3)()
+        self.ctx.check(self.ctx.lib.cfie_batch_tuning(self.h, ctypes.byref(d), ms), "cfie_batch_tuning")
+        return d.value, [float(v) for v in ms]
 
     def set_inner_basis(self, fp32):
         self.ctx.check(self.ctx.lib.cfie_batch_set_inner_basis(self.h, 1 if fp32 else 0),

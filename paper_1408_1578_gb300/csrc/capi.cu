@@ -641,7 +641,8 @@ cfie_status cfie_batch_create(cfie_ctx* ctx, int count, cfie_op* const* ops, con
     b->L = (size_t)at;
     b->prec = ops[0]->prec;
     pset_build(b->ps, poff, plen, ctx->stream);
-    if (b->all_stored) gemm_plan_build(b->plan, ctx, b->ops, b->nrhs, b->off);
+    if (b->all_stored)
+      gemm_plan_tune(b->plan, ctx, b->ops, b->nrhs, b->off, b->L, b->tune_ms);
   });
   if (st != CFIE_OK) {
     if (b) cfie_batch_destroy(b);
@@ -786,4 +787,21 @@ cfie_status cfie_op_set_block_gmres(cfie_op* op, int on) {
   if (!op || (on != 0 && on != 1)) return CFIE_EINVAL;
   op->block_gmres = on;
   return CFIE_OK;
+}
+
+cfie_status cfie_batch_tuning(const cfie_batch* b, int* dealing, float* ms) {
+  if (!b || !dealing) return CFIE_EINVAL;
+  *dealing = b->all_stored ? b->plan.dealing : -1;
+  if (ms)
+    for (int d = 0; d < 3; ++d) ms[d] = b->tune_ms[d];
+  return CFIE_OK;
+}
+
+cfie_status cfie_batch_set_dealing(cfie_batch* b, int dealing) {
+  if (!b || dealing < 0 || dealing > 2) return CFIE_EINVAL;
+  return guarded(b->ctx, [&] {
+    CFIE_REQUIRE(b->all_stored, "only a batch of stored operators has a contraction plan");
+    set_device(b->ctx);
+    gemm_plan_build(b->plan, b->ctx, b->ops, b->nrhs, b->off, dealing);
+  });
 }

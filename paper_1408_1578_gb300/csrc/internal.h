@@ -161,8 +161,10 @@ struct geom_dev {
 };
 
 // Plan of the stored-matrix contraction over a list of jobs (stored.cu).
+enum { GEMM_DEAL_AUTO = -1, GEMM_DEAL_ROUND_ROBIN = 0, GEMM_DEAL_GREEDY = 1, GEMM_DEAL_STREAMK = 2 };
 struct gemm_plan {
   int grid = 0, njobs = 0, mt_total = 0, nsegs = 0, max_pitch = 0, launches_per_run = 0;
+  int dealing = GEMM_DEAL_AUTO;   // how the work was dealt to the CTAs
   int stall = 0;   // fault injection for the failure tests (CFIE_FAULT_INJECT=tma_stall)
   dbuf jobs, tables, partial, bt, io, err;
   cudaGraphExec_t exec = nullptr;
@@ -276,6 +278,7 @@ struct cfie_batch {
   size_t L = 0;
   bool all_stored = false;
   int basis32 = 1;
+  float tune_ms[3] = {0.f, 0.f, 0.f};   // contraction time per dealing when tuned
   cfie_precision prec = CFIE_FP64;
   gemm_plan plan;
   krylov_ws K;
@@ -336,7 +339,13 @@ void spectral32_accumulate(cfie_op* op, const float2* t32, double2* y, int nrhs)
 void matvec_fp32(cfie_op* op, const double2* x, double2* y, int nrhs);
 // stored.cu
 void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& ops,
-                     const std::vector<int>& nrhs, const std::vector<long long>& xoff);
+                     const std::vector<int>& nrhs, const std::vector<long long>& xoff,
+                     int dealing);
+// the dealing of a batch's contraction picked by timing each once (cached per
+// batch shape for the process); ms[3] receives the candidates' times (0 when cached)
+int gemm_plan_tune(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& ops,
+                   const std::vector<int>& nrhs, const std::vector<long long>& xoff,
+                   size_t L, float* ms);
 void gemm_plan_run(gemm_plan& G, cfie_ctx* ctx, const double2* x, double2* y);
 int gemm_plan_take_error(gemm_plan& G, cfie_ctx* ctx);
 void gemm_plan_release(gemm_plan& G);

@@ -30,6 +30,7 @@
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -389,7 +390,8 @@ int stored_pitch(int n) { return (n + 63) / 64 * 64; }
 // (B preparation, persistent contraction, reduction) for the given operators
 // and right-hand-side counts; x / y are read from the plan's io slot.
 void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& ops,
-                     const std::vector<int>& nrhs, const std::vector<long long>& xoff) {
+                     const std::vector<int>& nrhs, const std::vector<long long>& xoff,
+                     int dealing) {
   cudaStream_t st = ctx->stream;
   std::vector<gemm_job> jobs;
   std::vector<size_t> bt_off;
@@ -423,8 +425,17 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
       J.tb = make_map(J.bt, 4 * (uint64_t)kNP, (uint64_t)J.pitch, J.pitch, kNP);
     }
   }
-  // one CTA per SM: stream-K split of the (m tile, k tile) pairs when there are
-  // few row tiles, whole row tiles dealt round-robin otherwise
+  // One CTA per SM.  How the (job, row tile, K tile) work is dealt to them:
+  //  GEMM_DEAL_AUTO        stream-K with few row tiles, round-robin with many
+  //  GEMM_DEAL_ROUND_ROBIN whole (job, row tile) units, unit u to CTA u % grid:
+  //                        the CTAs work on neighbouring units of few jobs at any
+  //                        time, so the jobs' right-hand-side planes stay in L2
+  //  GEMM_DEAL_GREEDY      whole units, largest first, each to the CTA with the
+  //                        least work so far (balanced when sizes differ), each
+  //                        CTA's units then taken in job order
+  //  GEMM_DEAL_STREAMK     the (row tile, K tile) pairs split evenly, segments
+  //                        cut at row-tile boundaries (partial sums added by the
+  //                        reduction kernel)
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
   long long W = 0;
@@ -439,15 +450,35 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
   std::vector<int> cbeg(grid + 1, 0);
   std::vector<int2> mt_job(mt_total), mt_seg(mt_total, make_int2(0, 0));
   size_t jk = 0;
-  if (mt_total >= 4 * grid) {
-    // many row tiles (batches): whole (job, row tile) units dealt round-robin,
-    // unit u to CTA u % grid, so that the CTAs work on neighbouring units of
-    // few jobs at any time and the jobs' right-hand-side planes stay in L2
+  if (dealing == GEMM_DEAL_AUTO)
+    dealing = mt_total >= 4 * grid ? GEMM_DEAL_ROUND_ROBIN : GEMM_DEAL_STREAMK;
+  G.dealing = dealing;
+  if (dealing == GEMM_DEAL_ROUND_ROBIN || dealing == GEMM_DEAL_GREEDY) {
     std::vector<std::vector<int4>> per(grid);
-    int u = 0;
-    for (size_t k = 0; k < jobs.size(); ++k) {
-      const int mt = (jobs[k].n + BM - 1) / BM, kt = (jobs[k].n + BK - 1) / BK;
-      for (int m = 0; m < mt; ++m, ++u) per[u % grid].push_back(make_int4((int)k, m, 0, kt));
+    if (dealing == GEMM_DEAL_ROUND_ROBIN) {
+      int u = 0;
+      for (size_t k = 0; k < jobs.size(); ++k) {
+        const int mt = (jobs[k].n + BM - 1) / BM, kt = (jobs[k].n + BK - 1) / BK;
+        for (int m = 0; m < mt; ++m, ++u) per[u % grid].push_back(make_int4((int)k, m, 0, kt));
+      }
+    } else {
+      std::vector<int4> units;
+      for (size_t k = 0; k < jobs.size(); ++k) {
+        const int mt = (jobs[k].n + BM - 1) / BM, kt = (jobs[k].n + BK - 1) / BK;
+        for (int m = 0; m < mt; ++m) units.push_back(make_int4((int)k, m, 0, kt));
+      }
+      std::stable_sort(units.begin(), units.end(),
+                       [](const int4& a, const int4& b) { return a.w > b.w; });
+      std::vector<long long> load(grid, 0);
+      for (const int4& u : units) {
+        const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        per[c].push_back(u);
+        load[c] += u.w;
+      }
+      for (auto& v : per)
+        std::sort(v.begin(), v.end(), [](const int4& a, const int4& b) {
+          return a.x != b.x ? a.x < b.x : a.y < b.y;
+        });
     }
     for (int c = 0; c < grid; ++c) {
       cbeg[c] = (int)segs.size();
@@ -458,7 +489,7 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
       }
     }
   }
-  for (int c = 0; c < grid && mt_total < 4 * grid; ++c) {
+  for (int c = 0; c < grid && dealing == GEMM_DEAL_STREAMK; ++c) {
     const long long b = W * c / grid, e = W * (c + 1) / grid;
     cbeg[c] = (int)segs.size();
     long long t = b;
@@ -555,6 +586,79 @@ void gemm_plan_run(gemm_plan& G, cfie_ctx* ctx, const double2* x, double2* y) {
   g_cfie_launches += G.launches_per_run;
 }
 
+// The autotuner of the batched contraction: each dealing built and its graph
+// replay timed (one warm-up, then the mean of two, CUDA events on the context
+// stream, on zero vectors); the fastest is kept and remembered per batch shape
+// (the sequence of (n, right-hand sides)) for the process.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, int> g_tune;
+}  // namespace
+
+int gemm_plan_tune(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& ops,
+                   const std::vector<int>& nrhs, const std::vector<long long>& xoff, size_t L,
+                   float* ms) {
+  std::vector<long long> key;
+  for (size_t k = 0; k < ops.size(); ++k) {
+    key.push_back(ops[k]->n);
+    key.push_back(nrhs[k]);
+  }
+  ms[0] = ms[1] = ms[2] = 0.f;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      gemm_plan_build(G, ctx, ops, nrhs, xoff, it->second);
+      return it->second;
+    }
+  }
+  cudaStream_t st = ctx->stream;
+  dbuf xy;
+  xy.reserve(sizeof(double2) * 2 * L);
+  CFIE_CHECK_CUDA(cudaMemsetAsync(xy.p, 0, sizeof(double2) * 2 * L, st));
+  const double2* x = xy.as<double2>();
+  double2* y = xy.as<double2>() + L;
+  cudaEvent_t e0, e1;
+  CFIE_CHECK_CUDA(cudaEventCreate(&e0));
+  CFIE_CHECK_CUDA(cudaEventCreate(&e1));
+  ctx->prof_suspend++;
+  int best = GEMM_DEAL_ROUND_ROBIN;
+  float best_ms = 0.f;
+  try {
+    for (int d = GEMM_DEAL_ROUND_ROBIN; d <= GEMM_DEAL_STREAMK; ++d) {
+      gemm_plan_build(G, ctx, ops, nrhs, xoff, d);
+      gemm_plan_run(G, ctx, x, y);
+      CFIE_CHECK_CUDA(cudaEventRecord(e0, st));
+      gemm_plan_run(G, ctx, x, y);
+      gemm_plan_run(G, ctx, x, y);
+      CFIE_CHECK_CUDA(cudaEventRecord(e1, st));
+      CFIE_CHECK_CUDA(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CFIE_CHECK_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      ms[d] = 0.5f * t;
+      if (gemm_plan_take_error(G, ctx))
+        throw cfie_error(CFIE_ETIMEOUT, "tensor-core kernel gave up a bounded wait");
+      if (d == GEMM_DEAL_ROUND_ROBIN || ms[d] < best_ms) {
+        best = d;
+        best_ms = ms[d];
+      }
+    }
+  } catch (...) {
+    ctx->prof_suspend--;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    throw;
+  }
+  ctx->prof_suspend--;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (G.dealing != best) gemm_plan_build(G, ctx, ops, nrhs, xoff, best);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  if (g_tune.size() >= 64) g_tune.clear();
+  g_tune[key] = best;
+  return best;
+}
+
 int gemm_plan_take_error(gemm_plan& G, cfie_ctx* ctx) {
   if (!G.err.p) return 0;
   int e = 0;
@@ -605,7 +709,7 @@ void stored_prepare(cfie_op* op) {
 
 void matvec_stored(cfie_op* op, const double2* x, double2* y, int nrhs) {
   if (op->plan_nrhs != nrhs) {
-    gemm_plan_build(op->plan, op->ctx, {op}, {nrhs}, {0});
+    gemm_plan_build(op->plan, op->ctx, {op}, {nrhs}, {0}, GEMM_DEAL_AUTO);
     op->plan_nrhs = nrhs;
   }
   gemm_plan_run(op->plan, op->ctx, x, y);

@@ -123,3 +123,18 @@ def test_measured_peaks_are_read():
         assert src == "measured" and peaks["hbm_gbs"] > 1000
     else:
         assert src == "fallback" and peaks["hbm_gbs"] == 6800.0
+
+
+def test_reference_specs_of_the_batch_sample_the_oracle():
+    """The batch workload's oracle sample (four of its stars) carries the
+    coupling eta = omega the oracle's rows need."""
+    import argparse
+    bench = _bench_module()
+    args = argparse.Namespace(workload="stars", count=256, precision=None, n=None, nrhs=None,
+                              eta_factor=None)
+    specs = bench.reference_specs(args)
+    assert len(specs) == 4
+    for sp in specs:
+        assert sp["eta"] == sp["omega"]
+    pairs, secs = bench.oracle_sample(specs[0], 2)
+    assert pairs == 2 * specs[0]["n"] and secs > 0

@@ -127,3 +127,39 @@ def test_batch_arguments(ctx, small_batch):
         cfie.Batch(ctx, [ops[0], op64], [1, 1])      # mixed precisions
     with pytest.raises(cfie.CfieError):
         cfie.Batch(ctx, [ops[0]], [0])               # no right-hand side
+
+
+def test_contraction_dealings_and_tuning(ctx, small_batch):
+    """The autotuner times every dealing of the persistent contraction once and
+    keeps one; each dealing gives the oracle's product (they differ only in the
+    order of the FP32 partial sums)."""
+    from paper_1408_1578_gb300 import cfie
+    specs, ops = small_batch
+    b = cfie.Batch(ctx, ops, [s["nrhs"] for s in specs])
+    d, ms = b.tuning()
+    assert d in (0, 1, 2)
+    Xs = [inputs.random_density(s["n"], s["nrhs"], seed=31 + k) for k, s in enumerate(specs)]
+    x = _flat([to_dev(X) for X in Xs])
+    want = []
+    for k, s in enumerate(specs):
+        c = geometry.fourier_star(s["n"], s["a"], s["b"])
+        A = operators.soft_matrix(c, s["omega"], s["omega"])
+        want.append((A @ Xs[k].T).T)
+    outs = []
+    for deal in (0, 1, 2):
+        b.set_dealing(deal)
+        assert b.tuning()[0] == deal
+        y = x.clone()
+        b.apply(x, y)
+        outs.append(to_host(y))
+        for k in range(len(specs)):
+            assert np.max(col_rel(to_host(b.block(y, k)), want[k])) < TOL_STORED
+    assert np.max(np.abs(outs[0] - outs[1])) <= 1e-6 * np.max(np.abs(outs[0]))
+    assert np.max(np.abs(outs[0] - outs[2])) <= 1e-5 * np.max(np.abs(outs[0]))
+    # the same shape again: the choice comes from the process's memory
+    b2 = cfie.Batch(ctx, ops, [s["nrhs"] for s in specs])
+    d2, ms2 = b2.tuning()
+    assert d2 == d and not any(ms2)
+    assert ctx.lib.cfie_batch_set_dealing(b2.h, 3) == cfie.CFIE_EINVAL
+    b2.close()
+    b.close()

@@ -180,7 +180,8 @@ FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)
 # ncu capture of the current kernel at the same launch configuration, keyed by
 # (kernel class, curve, n, nrhs, matvec variant); absent = not captured.
 NCU_TRAFFIC = {
-    ("matvec_fp32", "kite", 32768, 64, 2): 79.151872e6 + 11.139584e6,
+    ("matvec_fp32", "kite", 32768, 64, 2): 79.166720e6 + 11.300864e6,
+    ("matvec_fp64", "kite", 32768, 64, 2): 3.288266e9 + 157.754112e6,
 }
 
 

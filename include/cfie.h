@@ -69,12 +69,17 @@ typedef enum { CFIE_SOUND_SOFT = 0, CFIE_SOUND_HARD = 1 } cfie_bc;
 /* Precision of the operator application used inside GMRES.
  *  CFIE_FP64          FP64 kernel evaluation and FP64 sums everywhere.
  *  CFIE_FP32_REFINED  FP32 on-the-fly kernel evaluation (two-float phase, FP64
- *                     near band) for the inner matvecs; FP64 Arnoldi, FP64
- *                     Hessenberg solve and FP64 true residuals, with iterative
- *                     refinement on the outer residual.
+ *                     near band) for the inner matvecs, with iterative
+ *                     refinement on the outer residual.  The inner Krylov
+ *                     basis, its inner products and updates are FP32 by
+ *                     default (cfie_op_set_inner_basis(op, 0): FP64); the
+ *                     Hessenberg matrix, Givens rotations, least-squares solve
+ *                     and solution update are FP64; the true residuals are
+ *                     FP64-accurate (double-float arithmetic, a few 1e-12
+ *                     relative: cfie_apply_residual).
  *  CFIE_TENSOR_REFINED stored complex matrix contracted on the tensor cores
  *                     (split-complex, FP32 accumulation) for the inner matvecs;
- *                     FP64 Arnoldi / residuals as above. */
+ *                     Krylov basis and residuals as for CFIE_FP32_REFINED. */
 typedef enum { CFIE_FP64 = 0, CFIE_FP32_REFINED = 1, CFIE_TENSOR_REFINED = 2 } cfie_precision;
 
 typedef enum { CFIE_MATRIX_FREE = 0, CFIE_STORED = 1 } cfie_layout;
@@ -306,10 +311,13 @@ cfie_status cfie_apply_fp64(cfie_op* op, const void* x_dev, void* y_dev, int nrh
 cfie_status cfie_apply_fp64_static(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
 
 /* y = A x with the FP64-accurate matvec the refined precisions use for their
- * true residuals: for sound-soft CFIE_FP32_REFINED / CFIE_TENSOR_REFINED
- * operators the same entries as cfie_apply_fp64 evaluated in double-float
- * arithmetic on the FP32 pipe (hi + lo pairs, error-free products and sums;
- * a few 1e-12 relative), otherwise the FP64 matvec.  Arguments as cfie_apply. */
+ * true residuals: for CFIE_FP32_REFINED / CFIE_TENSOR_REFINED operators of
+ * either boundary condition the same entries as cfie_apply_fp64 evaluated in
+ * double-float arithmetic on the FP32 pipe (hi + lo pairs, error-free products
+ * and sums; for the sound-hard operator S and D' so, the spectral derivatives
+ * in FP64; a few 1e-12 relative), otherwise the FP64 matvec (also when the
+ * near band of the double-float form would exceed 4 GB).  Arguments as
+ * cfie_apply. */
 cfie_status cfie_apply_residual(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
 
 /* Solve A x = f for nrhs independent right-hand sides by restarted GMRES

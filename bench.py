@@ -58,6 +58,17 @@ def parse():
     p.add_argument("--block", action="store_true",
                    help="single-operator workloads: one block GMRES over all right-hand sides "
                         "(restart in block steps: 40) instead of one GMRES per right-hand side")
+    p.add_argument("--fp64-basis", action="store_true",
+                   help="refined precisions: FP64 inner Krylov basis instead of FP32")
+    p.add_argument("--serve-batch", type=int, default=8,
+                   help="serve: requests a free slot takes at once and solves as one batch")
+    p.add_argument("--serve-slots", type=int, default=8, help="serve: concurrent slots")
+    p.add_argument("--serve-block-min", type=int, default=8,
+                   help="serve: requests with at least this many directions and --serve-block-min-n "
+                        "nodes use block GMRES (0: off)")
+    p.add_argument("--serve-block-min-n", type=int, default=16384)
+    p.add_argument("--serve-stored-max-n", type=int, default=0,
+                   help="serve: sound-soft requests up to this n use the stored tensor-core form")
     p.add_argument("--oracle-budget", type=float, default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -280,6 +291,9 @@ def run_ours(args, rank, world):
     if args.block:
         spec["restart"] = 40       # block steps per cycle
         spec["solver"] = "block GMRES"
+    if args.fp64_basis:
+        spec["solver"] = (spec.get("solver", "") + ", " if spec.get("solver") else "") + \
+            "FP64 inner basis"
     n, w, nrhs, bc = spec["n"], spec["omega"], spec["nrhs"], spec["bc"]
     stream = torch.cuda.current_stream()
     ctx = cfie.Context(dev, stream=stream)
@@ -311,6 +325,8 @@ def run_ours(args, rank, world):
                              layout=spec["layout"])
         if args.block:
             op.set_block_gmres(True)
+        if args.fp64_basis:
+            op.set_inner_basis(False)
         prec = None
         if arc is not None and precondition:
             t0 = time.perf_counter()
@@ -470,10 +486,9 @@ ORACLE_THREAD_ENV = {k: "1" for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
                                         "BLIS_NUM_THREADS", "NUMEXPR_NUM_THREADS")}
 
 
-def oracle_single_core(args, budget_s):
-    """Time the oracle on one host core in a fresh interpreter (BLAS pinned to
-    one thread) on a bounded sample of the workload; returns the
-    cpu_baseline object."""
+def _oracle_runs(args, budget_s, procs):
+    """Run `procs` copies of the bounded oracle sample at once, each in a fresh
+    interpreter with its BLAS pinned to one thread; returns their JSON results."""
     env = dict(os.environ, **ORACLE_THREAD_ENV)
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-budget", str(budget_s),
            "--workload", args.workload]
@@ -481,12 +496,40 @@ def oracle_single_core(args, budget_s):
         v = getattr(args, k)
         if v is not None:
             cmd += [f"--{k.replace('_', '-')}", str(v)]
-    out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
-    if out.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + out.stderr[-500:])
-    r = json.loads(out.stdout.strip().splitlines()[-1])
+    running = [subprocess.Popen(cmd, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                text=True) for _ in range(procs)]
+    out = []
+    for pr in running:
+        so, se = pr.communicate(timeout=900)
+        if pr.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + se[-500:])
+        out.append(json.loads(so.strip().splitlines()[-1]))
+    return out
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_all_cores(args, budget_s):
+    """The oracle on every host core at once: one bounded-sample process per
+    core (one thread each), their rates added."""
+    cores = host_cores()
+    runs = _oracle_runs(args, budget_s, cores)
+    return {"value": sum(q["value"] for q in runs), "unit": runs[0]["unit"], "cores": cores,
+            "sample": f"{cores} processes at once, one thread each, each: " + runs[0]["sample"]}
+
+
+def oracle_single_core(args, budget_s):
+    """Time the oracle on one host core (BLAS pinned to one thread) on a
+    bounded sample of the workload, then on every host core at once; returns
+    the cpu_baseline object: the one-core figure, the all-core one beside it."""
+    r = _oracle_runs(args, budget_s, 1)[0]
     return {"value": r["value"], "unit": r["unit"], "cores": 1, "kind": "oracle",
-            "sample": r["sample"]}
+            "sample": r["sample"], "all_cores": oracle_all_cores(args, budget_s)}
 
 
 def oracle_budget_main(args):
@@ -579,7 +622,8 @@ def run_reference_serve(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": serve_config(count),
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "dense LU solves of the smallest requests: " + "; ".join(done)},
+                         "sample": "dense LU solves of the smallest requests: " + "; ".join(done),
+                         "all_cores": oracle_all_cores(args, 5.0)},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -614,7 +658,7 @@ def run_reference(args, rank, world):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "all_cores": oracle_all_cores(args, 5.0)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -848,8 +892,11 @@ def run_stars(args):
 def run_serve(args):
     """Poisson stream (200 requests/s) of sound-soft / sound-hard solves on random
     stars, n log-uniform in [1024, 65536], 1..64 directions, served by the
-    library's request server; p50 / p99 latency, solves/s.  A few requests are
-    also run one at a time in the plain FP64 form for comparison."""
+    library's request server (slots taking batches of compatible requests);
+    p50 / p99 latency, solves/s.  A stated sample of the stream (its first
+    requests with n <= 2560, the FP64 form being about 20x slower) is also run
+    one request at a time in the served mixed-precision form and in the plain
+    FP64 form."""
     import numpy as np
     import torch
 
@@ -857,7 +904,13 @@ def run_serve(args):
     count = args.count or 32
     reqs = inputs.poisson_requests(count=count, rate=200.0, seed=1578, n_lo=1024, n_hi=65536)
     free, total = torch.cuda.mem_get_info()
-    srv = cfie.Server(0, hbm_budget_bytes=int(0.8 * free), slots=8)
+    budget = int(0.8 * free)
+    srv = cfie.Server(0, hbm_budget_bytes=budget, slots=args.serve_slots, batch=args.serve_batch,
+                      block_min_rhs=args.serve_block_min, block_min_n=args.serve_block_min_n)
+
+    def form(r):
+        return "tensor" if r["bc"] == "soft" and r["n"] <= args.serve_stored_max_n else "fp32"
+
     clocks = ClockSampler(0)
     clocks.start()
     l0 = cfie.load().cfie_launch_count()
@@ -868,50 +921,73 @@ def run_serve(args):
         if delay > 0:
             time.sleep(delay)
         tickets.append(srv.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"],
-                                  rtol=1e-8, restart=80, maxit=4000))
-    ok = srv.wait_all(3600)
+                                  rtol=1e-8, restart=80, maxit=4000, precision=form(r)))
+    ok = srv.wait_all(7200)
     makespan = time.perf_counter() - t0
     launches = cfie.load().cfie_launch_count() - l0
     clk = clocks.stop()
     res = [srv.poll(t) for t in tickets]
     lat = np.array([q["latency_s"] for q in res])
     svc = np.array([q["service_s"] for q in res])
+    que = np.array([q["queued_s"] for q in res])
     good = [q["status"] == cfie.CFIE_OK for q in res]
     solves = sum(r["nrhs"] for r, g in zip(reqs, good) if g)
+    relres = max(q["relres_max"] for q in res)
     stats = srv.stats()
     srv.close()
-    # the same requests one at a time on an otherwise idle GPU, served (mixed
-    # precision) form against the plain FP64 form: the smallest requests
-    order = np.argsort([r["n"] for r in reqs])[:6]
+    # a stated sample of the same stream one request at a time on an otherwise
+    # idle GPU, served (mixed precision) form against the plain FP64 form
+    sample = [i for i, r in enumerate(reqs) if r["n"] <= 2560][:12]
     cmp = []
-    one = cfie.Server(0, hbm_budget_bytes=int(0.8 * free), slots=1)
-    for i in order:
+    one = cfie.Server(0, hbm_budget_bytes=budget, slots=1, block_min_rhs=args.serve_block_min,
+                      block_min_n=args.serve_block_min_n)
+    plain = cfie.Server(0, hbm_budget_bytes=budget, slots=1)
+    for i in sample:
         r = reqs[i]
-        row = {"n": r["n"], "nrhs": r["nrhs"], "bc": r["bc"]}
-        for prec in ("fp32", "fp64"):
-            t = one.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"],
-                           rtol=1e-8, restart=80, maxit=4000, precision=prec)
-            one.wait_all(3600)
-            row[prec + "_alone_s"] = one.poll(t)["service_s"]
-        row["speedup"] = row["fp64_alone_s"] / row["fp32_alone_s"]
+        row = {"index": i, "n": r["n"], "nrhs": r["nrhs"], "bc": r["bc"]}
+        row["form"] = form(r)
+        for key, prec, sv in (("served", form(r), one), ("fp64", "fp64", plain)):
+            t = sv.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"],
+                          rtol=1e-8, restart=80, maxit=4000, precision=prec)
+            sv.wait_all(3600)
+            q = sv.poll(t)
+            row[key + "_alone_s"] = q["service_s"]
+            row[key + "_ok"] = q["status"] == cfie.CFIE_OK
+            sv.release(t)
+        row["speedup"] = row["fp64_alone_s"] / row["served_alone_s"]
         cmp.append(row)
     one.close()
+    plain.close()
     sub_solves = sum(c["nrhs"] for c in cmp)
-    cmp_summary = {"requests": len(cmp), "solves": sub_solves,
-                   "fp32_refined_solves_per_s": sub_solves / sum(c["fp32_alone_s"] for c in cmp),
-                   "fp64_solves_per_s": sub_solves / sum(c["fp64_alone_s"] for c in cmp)}
+    in_stream = sum(res[c["index"]]["service_s"] for c in cmp)
+    cmp_summary = {
+        "sample": "the first %d requests of the stream with n <= 2560 (arrival order), "
+                  "each alone on the GPU" % len(cmp),
+        "requests": len(cmp), "solves": sub_solves,
+        "served_form_alone_solves_per_s": sub_solves / sum(c["served_alone_s"] for c in cmp),
+        "fp64_solves_per_s": sub_solves / sum(c["fp64_alone_s"] for c in cmp),
+        "served_in_stream_service_s": in_stream,
+        "all_ok": all(c["served_ok"] and c["fp64_ok"] for c in cmp)} if cmp else {}
     return {"metric": SERVE_METRIC,
             "value": solves / makespan, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
             "higher_is_better": True, "data": "synthetic", "dtype": "f32+f64",
-            "config": dict(serve_config(count), slots=8, budget_bytes=int(0.8 * free)),
+            "config": dict(serve_config(count), slots=args.serve_slots, batch=args.serve_batch,
+                           stored_max_n=args.serve_stored_max_n,
+                           block_min_rhs=args.serve_block_min,
+                           block_min_n=args.serve_block_min_n, budget_bytes=budget),
+            "forms": {"tensor": sum(form(r) == "tensor" for r in reqs),
+                      "fp32": sum(form(r) == "fp32" for r in reqs)},
             "all_done": bool(ok), "requests_per_s": count / makespan, "makespan_s": makespan,
+            "arrival_span_s": reqs[-1]["arrival"],
             "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
-            "p50_service_s": float(np.percentile(svc, 50)), "failed": int(len(good) - sum(good)),
+            "p50_queued_s": float(np.percentile(que, 50)),
+            "p50_service_s": float(np.percentile(svc, 50)),
+            "p99_service_s": float(np.percentile(svc, 99)),
+            "max_relres": relres, "failed": int(len(good) - sum(good)),
             "server": stats, "fp64_one_at_a_time": cmp, "one_at_a_time_summary": cmp_summary,
             "gpu_launches": int(launches),
             "clocks": clk}
-
 
 if __name__ == "__main__":
     main()

@@ -425,7 +425,10 @@ typedef struct cfie_batch cfie_batch;
  * the whole batch is one CUDA-graph replay of three kernels: the B-operand
  * preparation of every operator, a persistent stream-K tensor-core contraction
  * over all (operator, row tile, source tile) pairs (one CTA per SM), and the
- * partial-sum reduction.  The operators must outlive the batch.  Synchronous. */
+ * partial-sum reduction.  Otherwise the operators' matvecs run on up to
+ * eight auxiliary streams forked from and joined back into the context stream;
+ * inside a lockstep solve an operator all of whose right-hand sides have
+ * converged is skipped.  The operators must outlive the batch.  Synchronous. */
 cfie_status cfie_batch_create(cfie_ctx* ctx, int count, cfie_op* const* ops, const int* nrhs,
                               cfie_batch** out);
 /* Number of complex128 elements of a batch vector (sum of n_k * nrhs[k]). */
@@ -488,11 +491,14 @@ typedef struct cfie_server cfie_server;
 /* One solve request: a star obstacle r(t) = 1 + sum_k a_k cos kt + b_k sin kt
  * (host arrays of K doubles, copied), n nodes, omega, eta, boundary condition,
  * nrhs plane waves at the host angles theta (copied), residual target rtol,
- * GMRES restart / maxit, and the precision (CFIE_FP32_REFINED, the served
- * mixed-precision form, or CFIE_FP64, the plain form). */
+ * GMRES restart / maxit, and the precision: CFIE_FP32_REFINED (matrix free)
+ * or CFIE_TENSOR_REFINED (sound-soft only: the matrix stored, 8 n^2 bytes, and
+ * contracted on the tensor cores; a batch of such requests runs one
+ * persistent contraction launch per matvec), the served mixed-precision
+ * forms, or CFIE_FP64, the plain form. */
 typedef struct {
   int bc;            /* cfie_bc */
-  int precision;     /* cfie_precision: CFIE_FP32_REFINED or CFIE_FP64 */
+  int precision;     /* cfie_precision */
   int K;
   const double* a;
   const double* b;
@@ -524,6 +530,28 @@ typedef struct {
  * the queue whenever a slot is free and the footprint fits; one that exceeds
  * the budget on its own runs when the GPU is otherwise idle. */
 cfie_status cfie_server_create(int device, size_t hbm_budget_bytes, int slots, cfie_server** out);
+/* Let a slot take up to max_requests queued requests at once (default 1): when
+ * a slot becomes free it takes the first request that fits the budget, then
+ * the further queued requests (in queue order) with the same precision, rtol,
+ * restart and maxit and an n within a factor of two of the first one's that
+ * fit alongside it, and solves them together as one cfie_batch (one lockstep
+ * GMRES over all their right-hand sides: one set of Arnoldi launches and one
+ * host synchronisation per step for the group, the matvecs of the operators
+ * still iterating issued on up to eight concurrent streams).  Each request keeps its own result, iteration
+ * counts, residuals and solution; the times of a group's requests share its
+ * start and end.  Affects requests taken after the call.  CFIE_EINVAL for a
+ * null server or max_requests outside [1, 256].  Not part of the paper (a
+ * serving option). */
+cfie_status cfie_server_set_batching(cfie_server* server, int max_requests);
+/* Solve each request with at least min_rhs right-hand sides (min_rhs >= 1;
+ * 0, the default, turns this off) and at least min_n nodes alone with block
+ * GMRES over its directions (cfie_op_set_block_gmres; restart and maxit count
+ * block steps), never in a lockstep batch.  Block GMRES takes about half the
+ * steps on large obstacles but pays host work per step, which small ones do
+ * not earn back.  Affects requests taken after the call.  CFIE_EINVAL for a
+ * null server, min_rhs outside [0, 1024] or a negative min_n.  Not part of the
+ * paper (a serving option; block GMRES is the block variant of its GMRES). */
+cfie_status cfie_server_set_block_gmres(cfie_server* server, int min_rhs, int min_n);
 /* Queue a request (arguments copied; never blocks).  *ticket identifies it. */
 cfie_status cfie_server_submit(cfie_server* server, const cfie_request* req, long long* ticket);
 /* State of a request; when done and x_host is not NULL, copies the solution

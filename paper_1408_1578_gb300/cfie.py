@@ -140,6 +140,8 @@ SIGNATURES = {
     "cfie_server_last_error": (ctypes.c_char_p, [_P]),
     "cfie_server_request_error": (_I, [_P, ctypes.c_longlong, ctypes.c_char_p, ctypes.c_size_t]),
     "cfie_server_destroy": (None, [_P]),
+    "cfie_server_set_batching": (_I, [_P, _I]),
+    "cfie_server_set_block_gmres": (_I, [_P, _I, _I]),
 }
 
 _lib = None
@@ -457,7 +459,8 @@ class Batch:
 class Server:
     """Request server (cfie_server_*): continuous batching of independent solves."""
 
-    def __init__(self, device=0, hbm_budget_bytes=64 << 30, slots=4):
+    def __init__(self, device=0, hbm_budget_bytes=64 << 30, slots=4, batch=1, block_min_rhs=0,
+                 block_min_n=0):
         lib = load()
         h = _P()
         st = lib.cfie_server_create(device, int(hbm_budget_bytes), int(slots), ctypes.byref(h))
@@ -466,6 +469,23 @@ class Server:
         self.lib = lib
         self.h = h
         self.shapes = {}
+        if batch != 1:
+            self.set_batching(batch)
+        if block_min_rhs:
+            self.set_block_gmres(block_min_rhs, block_min_n)
+
+    def set_block_gmres(self, min_rhs, min_n=0):
+        """Requests with at least min_rhs directions and min_n nodes run alone
+        with block GMRES (min_rhs 0: off)."""
+        st = self.lib.cfie_server_set_block_gmres(self.h, int(min_rhs), int(min_n))
+        if st != CFIE_OK:
+            raise CfieError(st, "min_rhs must be in [0, 1024], min_n >= 0")
+
+    def set_batching(self, max_requests):
+        """Requests a free slot takes at once and solves as one lockstep batch."""
+        st = self.lib.cfie_server_set_batching(self.h, int(max_requests))
+        if st != CFIE_OK:
+            raise CfieError(st, "max_requests must be in [1, 256]")
 
     def submit(self, a, b, n, omega, nrhs=1, theta=None, bc="soft", precision="fp32", eta=None,
                rtol=1e-8, restart=80, maxit=4000):

@@ -561,6 +561,13 @@ void residual_norms(cudaStream_t st, krylov_ws& K, const pset& ps, const ws& W,
   fn.assign(K.host + P, K.host + 2 * P);
 }
 
+// Marks the problems of an Arnoldi step's matvec for the matvec callbacks.
+struct live_scope {
+  std::vector<int>& v;
+  live_scope(std::vector<int>& v_, const std::vector<int>& act) : v(v_) { v = act; }
+  ~live_scope() { v.clear(); }
+};
+
 // One GMRES cycle: starting residual r (norms beta), basis built with the
 // inner or the FP64 matvec, x += V y.  active[p] says which problems take part;
 // tol[p] is the absolute residual-norm target.  Counts steps per problem.
@@ -593,12 +600,15 @@ void gmres_cycle(cudaStream_t st, cfie_ctx* ctx, krylov_ws& K, const pset& ps, c
       fns.prec(vj, K.pz.as<double2>());
       vj = K.pz.as<double2>();
     }
-    if (inner) {
-      stats.inner_matvecs++;
-      fns.inner(vj, W.w);
-    } else {
-      stats.fp64_matvecs++;
-      fns.fp64(vj, W.w);
+    {
+      live_scope ls(K.live, act);
+      if (inner) {
+        stats.inner_matvecs++;
+        fns.inner(vj, W.w);
+      } else {
+        stats.fp64_matvecs++;
+        fns.fp64(vj, W.w);
+      }
     }
     {
       prof_scope ps_(ctx, CFIE_K_ARNOLDI);

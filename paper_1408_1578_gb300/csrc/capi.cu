@@ -548,25 +548,31 @@ long long cfie_launch_count(void) { return g_cfie_launches.load(); }
 // ---------------------------------------------------------------------------
 // batches
 // ---------------------------------------------------------------------------
-static void batch_inner(cfie_batch* b, const double2* x, double2* y) {
-  if (b->all_stored) {
-    gemm_plan_run(b->plan, b->ctx, x, y);
-    return;
-  }
-  for (size_t k = 0; k < b->ops.size(); ++k)
-    apply_inner(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
+// Whether operator k of a batch has a problem in the running Arnoldi step
+// (every operator outside one).  The others' outputs are not read.
+static bool batch_live(const cfie_batch* b, size_t k) {
+  const std::vector<int>& live = b->K.live;
+  if (live.empty()) return true;
+  for (int r = 0; r < b->nrhs[k]; ++r)
+    if (live[(size_t)b->pfirst[k] + r]) return true;
+  return false;
 }
 
-// The operators' residual matvecs are independent: they run on up to eight
-// auxiliary streams forked from and joined back into the context stream (the
-// operators' kernels launch on ctx->stream, which points at the auxiliary
-// stream while that operator's work is issued), timed as one scope.
-static void batch_fp64(cfie_batch* b, const double2* x, double2* y) {
+// The operators' matvecs are independent: fn(k) for every live operator, on
+// up to eight auxiliary streams forked from and joined back into the context
+// stream (the operators' kernels launch on ctx->stream, which points at the
+// auxiliary stream while that operator's work is issued), timed as one scope
+// of class cls.
+extern "C++" {
+template <class F>
+static void batch_each(cfie_batch* b, int cls, F&& fn) {
   cfie_ctx* c = b->ctx;
-  const int K = (int)std::min<size_t>(8, b->ops.size());
+  std::vector<size_t> ks;
+  for (size_t k = 0; k < b->ops.size(); ++k)
+    if (batch_live(b, k)) ks.push_back(k);
+  const int K = (int)std::min<size_t>(8, ks.size());
   if (K <= 1) {
-    for (size_t k = 0; k < b->ops.size(); ++k)
-      matvec_residual(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
+    for (size_t k : ks) fn(k);
     return;
   }
   while ((int)b->aux.size() < K) {
@@ -580,17 +586,11 @@ static void batch_fp64(cfie_batch* b, const double2* x, double2* y) {
   cudaEvent_t fork;
   CFIE_CHECK_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
   cudaStream_t main = c->stream;
-  prof_scope ps(c, CFIE_K_MATVEC_FP64);
+  prof_scope ps(c, cls);
   CFIE_CHECK_CUDA(cudaEventRecord(fork, main));
   for (int q = 0; q < K; ++q) CFIE_CHECK_CUDA(cudaStreamWaitEvent(b->aux[q], fork, 0));
   c->prof_suspend++;
-  try {
-    for (size_t k = 0; k < b->ops.size(); ++k) {
-      c->stream = b->aux[k % K];
-      stream_scope ss(c->stream);
-      matvec_residual(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
-    }
-  } catch (...) {
+  auto join = [&] {
     c->stream = main;
     c->prof_suspend--;
     for (int q = 0; q < K; ++q) {
@@ -598,15 +598,39 @@ static void batch_fp64(cfie_batch* b, const double2* x, double2* y) {
       cudaStreamWaitEvent(main, b->aux_ev[q], 0);
     }
     cudaEventDestroy(fork);
+  };
+  try {
+    for (size_t i = 0; i < ks.size(); ++i) {
+      c->stream = b->aux[i % K];
+      stream_scope ss(c->stream);
+      fn(ks[i]);
+    }
+  } catch (...) {
+    join();
     throw;
   }
-  c->stream = main;
-  c->prof_suspend--;
-  for (int q = 0; q < K; ++q) {
-    CFIE_CHECK_CUDA(cudaEventRecord(b->aux_ev[q], b->aux[q]));
-    CFIE_CHECK_CUDA(cudaStreamWaitEvent(main, b->aux_ev[q], 0));
+  join();
+  CFIE_CHECK_CUDA(cudaGetLastError());
+}
+}  // extern "C++"
+
+static void batch_inner(cfie_batch* b, const double2* x, double2* y) {
+  if (b->all_stored) {
+    gemm_plan_run(b->plan, b->ctx, x, y);
+    return;
   }
-  cudaEventDestroy(fork);
+  const int cls = b->prec == CFIE_FP64              ? CFIE_K_MATVEC_FP64
+                  : b->prec == CFIE_TENSOR_REFINED ? CFIE_K_MATVEC_TENSOR
+                                                   : CFIE_K_MATVEC_FP32;
+  batch_each(b, cls, [&](size_t k) {
+    apply_inner(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
+  });
+}
+
+static void batch_fp64(cfie_batch* b, const double2* x, double2* y) {
+  batch_each(b, CFIE_K_MATVEC_FP64, [&](size_t k) {
+    matvec_residual(b->ops[k], x + b->off[k], y + b->off[k], b->nrhs[k]);
+  });
 }
 
 cfie_status cfie_batch_create(cfie_ctx* ctx, int count, cfie_op* const* ops, const int* nrhs,
@@ -631,6 +655,7 @@ cfie_status cfie_batch_create(cfie_ctx* ctx, int count, cfie_op* const* ops, con
       b->ops.push_back(ops[k]);
       b->nrhs.push_back(nrhs[k]);
       b->off.push_back(at);
+      b->pfirst.push_back((int)poff.size());
       for (int r = 0; r < nrhs[k]; ++r) {
         poff.push_back((size_t)(at + (long long)r * ops[k]->n));
         plen.push_back(ops[k]->n);
@@ -641,8 +666,10 @@ cfie_status cfie_batch_create(cfie_ctx* ctx, int count, cfie_op* const* ops, con
     b->L = (size_t)at;
     b->prec = ops[0]->prec;
     pset_build(b->ps, poff, plen, ctx->stream);
-    if (b->all_stored)
+    if (b->all_stored && ctx->tune_batches)
       gemm_plan_tune(b->plan, ctx, b->ops, b->nrhs, b->off, b->L, b->tune_ms);
+    else if (b->all_stored)
+      gemm_plan_build(b->plan, ctx, b->ops, b->nrhs, b->off, GEMM_DEAL_AUTO);
   });
   if (st != CFIE_OK) {
     if (b) cfie_batch_destroy(b);

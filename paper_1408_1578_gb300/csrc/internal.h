@@ -97,6 +97,7 @@ struct cfie_ctx {
   // per-launch event timing
   bool profiling = false;
   int prof_suspend = 0;   // > 0: per-launch scopes are off (an outer scope times the work)
+  bool tune_batches = true;   // time the contraction's work dealings per batch shape
   struct pending { int cls; cudaEvent_t a, b; };
   std::vector<pending> inflight;
   std::vector<cudaEvent_t> pool;
@@ -138,6 +139,9 @@ struct krylov_ws {
   dbuf V32, w32, vin;       // FP32 basis of the inner solves (refined precisions)
   double* host = nullptr;   // pinned mirror of per-problem norms
   int host_cap = 0;
+  // during an Arnoldi step's matvec: which problems still take part (empty
+  // outside one: all); a batch skips the operators none of whose problems do
+  std::vector<int> live;
 };
 
 #include <functional>
@@ -275,6 +279,7 @@ struct cfie_batch {
   std::vector<cfie_op*> ops;
   std::vector<int> nrhs;
   std::vector<long long> off;
+  std::vector<int> pfirst;   // index of each operator's first problem
   size_t L = 0;
   bool all_stored = false;
   int basis32 = 1;

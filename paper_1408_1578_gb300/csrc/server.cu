@@ -7,7 +7,8 @@
 // basis, work vectors, operator tables, near-field band, matvec scratch) fits in
 // the HBM budget; a request that arrives while others run is admitted as soon as
 // a slot and memory free up, and its kernels overlap on the GPU with the other
-// slots' kernels.  Each slot runs the whole path for its request: geometry and
+// slots' kernels.  With batching on, a free slot takes several compatible
+// queued requests at once and solves them as one lockstep batch.  Each slot runs the whole path for its request: geometry and
 // Kress tables, plane-wave data, refined GMRES; the Krylov basis stays on the
 // device for the life of the solve.  Finished requests keep their solution and
 // timing on the host until released.
@@ -18,6 +19,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <numeric>
 #include <thread>
 #include <unordered_map>
 
@@ -54,6 +56,11 @@ size_t footprint_bytes(const cfie_request& r) {
   f += vec / 2 * (16 * ops + 3);      // FP32 split partials and staging
   f += vec * 4 * ops;                 // FP64 residual partials (a few splits)
   f += n * 200 + ((size_t)64 << 20);  // tables, small buffers, slack
+  if (r.precision == CFIE_TENSOR_REFINED) {
+    const size_t pitch = (n + 63) / 64 * 64;
+    f += 8 * n * pitch;                 // stored bf16 hi/lo planes (re, im)
+    f += vec * 2;                       // contraction operand and partial sums
+  }
   return f;
 }
 
@@ -63,6 +70,9 @@ struct cfie_server {
   int device = 0;
   size_t budget = 0, in_use = 0;
   int slots = 0;
+  int batch_max = 1;   // requests a slot takes at once and solves as one batch
+  int block_min = 0;   // requests with at least this many right-hand sides ...
+  int block_min_n = 0; // ... and nodes: block GMRES (block_min 0: off)
   std::vector<std::thread> workers;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -77,7 +87,12 @@ struct cfie_server {
 
 namespace {
 
-void run_request(cfie_ctx* ctx, request_rec* r, dbuf& fbuf, dbuf& xbuf) {
+// The tensor-core form stores its matrix; the others evaluate it on the fly.
+cfie_layout layout_of(const cfie_request& q) {
+  return q.precision == CFIE_TENSOR_REFINED ? CFIE_STORED : CFIE_MATRIX_FREE;
+}
+
+void run_request(cfie_ctx* ctx, request_rec* r, bool block, dbuf& fbuf, dbuf& xbuf) {
   const cfie_request& q = r->req;
   cfie_geom* geom = nullptr;
   cfie_op* op = nullptr;
@@ -88,9 +103,10 @@ void run_request(cfie_ctx* ctx, request_rec* r, dbuf& fbuf, dbuf& xbuf) {
   cfie_status s = cfie_geometry_fourier_star(ctx, q.K, r->a.data(), r->b.data(), &geom);
   if (s != CFIE_OK) return fail(s);
   s = cfie_discretise(geom, q.n, q.omega, q.eta, (cfie_bc)q.bc, (cfie_precision)q.precision,
-                      CFIE_MATRIX_FREE, &op);
+                      layout_of(q), &op);
   cfie_geom_destroy(geom);
   if (s != CFIE_OK) return fail(s);
+  if (block) cfie_op_set_block_gmres(op, 1);
   const size_t len = (size_t)q.n * q.nrhs;
   try {
     fbuf.reserve(sizeof(double2) * len);
@@ -128,16 +144,122 @@ void run_request(cfie_ctx* ctx, request_rec* r, dbuf& fbuf, dbuf& xbuf) {
   cfie_op_destroy(op);
 }
 
+// Several requests of one slot solved as one batch: their operators in one
+// cfie_batch, one lockstep refined GMRES over all their right-hand sides (one
+// set of Arnoldi launches and one host synchronisation per step for all of
+// them, the matvecs of the operators still iterating issued on concurrent
+// streams), each request's solution copied back from its block.
+void run_batch(cfie_ctx* ctx, const std::vector<request_rec*>& rs, dbuf& fbuf, dbuf& xbuf) {
+  std::vector<cfie_op*> ops;
+  std::vector<request_rec*> live;
+  std::vector<int> nr;
+  for (request_rec* r : rs) {
+    const cfie_request& q = r->req;
+    cfie_geom* geom = nullptr;
+    cfie_op* op = nullptr;
+    cfie_status s = cfie_geometry_fourier_star(ctx, q.K, r->a.data(), r->b.data(), &geom);
+    if (s == CFIE_OK) {
+      s = cfie_discretise(geom, q.n, q.omega, q.eta, (cfie_bc)q.bc, (cfie_precision)q.precision,
+                          layout_of(q), &op);
+      cfie_geom_destroy(geom);
+    }
+    if (s != CFIE_OK) {
+      r->status = s;
+      r->err = cfie_last_error(ctx);
+      continue;
+    }
+    ops.push_back(op);
+    live.push_back(r);
+    nr.push_back(q.nrhs);
+  }
+  auto cleanup = [&] {
+    for (cfie_op* op : ops) cfie_op_destroy(op);
+  };
+  if (live.empty()) return;
+  cfie_batch* batch = nullptr;
+  cfie_status s = cfie_batch_create(ctx, (int)ops.size(), ops.data(), nr.data(), &batch);
+  auto fail_all = [&](cfie_status st, const std::string& m) {
+    for (request_rec* r : live) {
+      r->status = st;
+      r->err = m;
+    }
+  };
+  if (s != CFIE_OK) {
+    fail_all(s, cfie_last_error(ctx));
+    cleanup();
+    return;
+  }
+  const size_t len = (size_t)cfie_batch_length(batch);
+  std::vector<size_t> off(live.size(), 0);
+  for (size_t k = 1; k < live.size(); ++k) off[k] = off[k - 1] + (size_t)ops[k - 1]->n * nr[k - 1];
+  try {
+    fbuf.reserve(sizeof(double2) * len);
+    xbuf.reserve(sizeof(double2) * len);
+    CFIE_CHECK_CUDA(cudaMemsetAsync(xbuf.p, 0, sizeof(double2) * len, ctx->stream));
+  } catch (const cfie_error& e) {
+    fail_all(e.code, e.msg);
+    cfie_batch_destroy(batch);
+    cleanup();
+    return;
+  }
+  for (size_t k = 0; k < live.size(); ++k) {
+    s = cfie_rhs_plane_waves(ops[k], nr[k], live[k]->theta.data(),
+                             fbuf.as<double2>() + off[k]);
+    if (s != CFIE_OK) {
+      fail_all(s, cfie_last_error(ctx));
+      cfie_batch_destroy(batch);
+      cleanup();
+      return;
+    }
+  }
+  const cfie_request& q0 = live[0]->req;
+  std::vector<int> its(len > 0 ? (size_t)std::accumulate(nr.begin(), nr.end(), 0) : 0);
+  std::vector<double> rel(its.size());
+  s = cfie_batch_gmres_solve(batch, fbuf.p, xbuf.p, q0.rtol, q0.restart, q0.maxit, its.data(),
+                             rel.data());
+  const std::string msg = s == CFIE_OK ? std::string() : std::string(cfie_last_error(ctx));
+  size_t col = 0;
+  bool copied = true;
+  for (size_t k = 0; k < live.size(); ++k) {
+    request_rec* r = live[k];
+    r->status = CFIE_OK;
+    for (int c = 0; c < nr[k]; ++c, ++col) {
+      r->iters_max = std::max(r->iters_max, its[col]);
+      r->relres_max = std::max(r->relres_max, rel[col]);
+      if (!(rel[col] <= r->req.rtol)) r->status = s == CFIE_OK ? CFIE_ENOCONV : s;
+    }
+    if (s != CFIE_OK && s != CFIE_ENOCONV) r->status = s;
+    if (r->status != CFIE_OK) r->err = msg;
+    r->x.resize((size_t)ops[k]->n * nr[k]);
+    copied = copied && cudaMemcpyAsync(r->x.data(), xbuf.as<double2>() + off[k],
+                                       sizeof(double2) * r->x.size(), cudaMemcpyDeviceToHost,
+                                       ctx->stream) == cudaSuccess;
+  }
+  copied = copied && cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+  if (!copied)
+    for (request_rec* r : live) {
+      r->status = CFIE_ECUDA;
+      r->err = "copying the solution back failed";
+    }
+  cfie_batch_destroy(batch);
+  cleanup();
+}
+
 void worker_main(cfie_server* S) {
   cudaSetDevice(S->device);
   cudaStream_t stream = nullptr;
   cfie_ctx* ctx = nullptr;
   const bool ok = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess &&
                   cfie_ctx_create(S->device, stream, &ctx) == CFIE_OK;
+  // a served batch's shapes rarely repeat: its stored contraction takes the
+  // default work dealing instead of timing all three for every batch
+  if (ok) ctx->tune_batches = false;
   stream_scope ss(stream);     // the slot's staging buffers live on its stream
   dbuf fbuf, xbuf;
   for (;;) {
     request_rec* r = nullptr;
+    std::vector<request_rec*> group;
+    bool alone = false;
     {
       std::unique_lock<std::mutex> lock(S->mu);
       S->cv_work.wait(lock, [&] {
@@ -155,27 +277,62 @@ void worker_main(cfie_server* S) {
           break;
         }
       }
+      group.push_back(r);
       S->in_use += r->footprint;
+      // a request for block GMRES runs alone: one Krylov space over its own
+      // right-hand sides
+      auto blocked = [&](const request_rec* q) {
+        return S->block_min > 0 && q->req.nrhs >= S->block_min && q->req.n >= S->block_min_n;
+      };
+      alone = blocked(r);
+      // with batching, further queued requests of the same solver settings
+      // and a similar size (n within a factor of two, so that the lockstep
+      // iterations of the group end close together) that fit the budget join
+      // this slot's batch, in queue order
+      for (auto it = S->queue.begin();
+           !alone && it != S->queue.end() && (int)group.size() < S->batch_max;) {
+        const cfie_request& q = (*it)->req;
+        const cfie_request& q0 = r->req;
+        if (q.precision == q0.precision && q.rtol == q0.rtol && q.restart == q0.restart &&
+            q.maxit == q0.maxit && q.n <= 2 * q0.n && 2 * q.n >= q0.n && !blocked(*it) &&
+            (*it)->footprint + S->in_use <= S->budget) {
+          S->in_use += (*it)->footprint;
+          group.push_back(*it);
+          it = S->queue.erase(it);
+        } else {
+          ++it;
+        }
+      }
       S->peak_in_use = std::max(S->peak_in_use, S->in_use);
-      S->running++;
+      S->running += (long long)group.size();
       S->peak_running = std::max(S->peak_running, S->running);
-      r->started = true;
-      r->t_start = clock_type::now();
+      const auto now = clock_type::now();
+      for (request_rec* g : group) {
+        g->started = true;
+        g->t_start = now;
+      }
     }
-    if (ok) {
-      run_request(ctx, r, fbuf, xbuf);
+    if (!ok) {
+      for (request_rec* g : group) {
+        g->status = CFIE_ECUDA;
+        g->err = "slot could not create its CUDA stream / context";
+      }
+    } else if (group.size() == 1) {
+      run_request(ctx, r, alone, fbuf, xbuf);
     } else {
-      r->status = CFIE_ECUDA;
-      r->err = "slot could not create its CUDA stream / context";
+      run_batch(ctx, group, fbuf, xbuf);
     }
     {
       std::lock_guard<std::mutex> lock(S->mu);
-      r->t_done = clock_type::now();
-      r->done = true;
-      S->in_use -= r->footprint;
-      S->running--;
-      S->completed++;
-      if (r->status == CFIE_OK) S->solves += r->req.nrhs;
+      const auto now = clock_type::now();
+      for (request_rec* g : group) {
+        g->t_done = now;
+        g->done = true;
+        S->in_use -= g->footprint;
+        S->running--;
+        S->completed++;
+        if (g->status == CFIE_OK) S->solves += g->req.nrhs;
+      }
     }
     S->cv_done.notify_all();
     S->cv_work.notify_all();
@@ -234,8 +391,11 @@ cfie_status cfie_server_submit(cfie_server* S, const cfie_request* req, long lon
   if (q.nrhs < 1 || q.nrhs > 1024 || !q.theta) return bad("nrhs must be in [1, 1024] with angles");
   if (!(q.omega > 0) || !(q.eta > 0) || !(q.rtol > 0 && q.rtol < 1)) return bad("omega, eta, rtol");
   if (q.bc != CFIE_SOUND_SOFT && q.bc != CFIE_SOUND_HARD) return bad("unknown boundary condition");
-  if (q.precision != CFIE_FP64 && q.precision != CFIE_FP32_REFINED)
-    return bad("served precisions are CFIE_FP64 and CFIE_FP32_REFINED");
+  if (q.precision != CFIE_FP64 && q.precision != CFIE_FP32_REFINED &&
+      q.precision != CFIE_TENSOR_REFINED)
+    return bad("unknown precision");
+  if (q.precision == CFIE_TENSOR_REFINED && q.bc != CFIE_SOUND_SOFT)
+    return bad("the stored tensor-core form serves the sound-soft operator");
   if (q.restart < 0 || q.restart > 512 || q.maxit < 1) return bad("restart / maxit");
   auto r = std::make_unique<request_rec>();
   r->req = q;
@@ -334,6 +494,21 @@ cfie_status cfie_server_request_error(cfie_server* S, long long ticket, char* bu
 }
 
 const char* cfie_server_last_error(cfie_server* S) { return S ? S->err.c_str() : "null server"; }
+
+cfie_status cfie_server_set_batching(cfie_server* S, int max_requests) {
+  if (!S || max_requests < 1 || max_requests > 256) return CFIE_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
+  S->batch_max = max_requests;
+  return CFIE_OK;
+}
+
+cfie_status cfie_server_set_block_gmres(cfie_server* S, int min_rhs, int min_n) {
+  if (!S || min_rhs < 0 || min_rhs > 1024 || min_n < 0) return CFIE_EINVAL;
+  std::lock_guard<std::mutex> lock(S->mu);
+  S->block_min = min_rhs;
+  S->block_min_n = min_n;
+  return CFIE_OK;
+}
 
 void cfie_server_destroy(cfie_server* S) {
   if (!S) return;

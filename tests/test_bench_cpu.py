@@ -29,6 +29,8 @@ def test_reference_arm_prints_the_contract_line():
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and isinstance(cb["sample"], str)
     assert cb["value"] == line["value"]
+    allc = cb["all_cores"]             # the oracle on every host core beside the one-core rate
+    assert allc["cores"] >= 1 and allc["value"] > 0 and allc["unit"] == line["unit"]
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0

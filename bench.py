@@ -173,8 +173,10 @@ def measured_peaks():
 SMS, FP32_LANES = 152, 128
 # FP32 pair entries (two-float phase, asymptotics) by summation variant: the
 # CUDA-core kernel evaluates both hard entries from one phase; the tensor-core
-# kernel folds the per-node factors in and evaluates S and D' in two passes
-ENTRY_OPS = {("soft", 1): 74, ("hard", 1): 87, ("soft", 2): 64, ("hard", 2): 98}
+# kernel folds the per-node factors in, keeps the accuracy of its bf16 hi + lo
+# operands (two-term series, no exact sum in the phase) and evaluates S (36)
+# and D' (42) in two passes
+ENTRY_OPS = {("soft", 1): 74, ("hard", 1): 87, ("soft", 2): 54, ("hard", 2): 36 + 42}
 SUM_OPS = {"soft": 4, "hard": 8}         # FP32 FMAs per pair and right-hand side (CUDA-core sums)
 DF_ENTRY_OPS = 563                       # double-float pair entry of the residual kernel
 # sound hard: the phase and Hankel part (431) with the S assembly (39) and the D'
@@ -191,7 +193,7 @@ FP64_NOMINAL_TFLOPS = 1.25               # GB300 FP64 (nominal; FMA = 2 flops)
 # ncu capture of the current kernel at the same launch configuration, keyed by
 # (kernel class, curve, n, nrhs, matvec variant); absent = not captured.
 NCU_TRAFFIC = {
-    ("matvec_fp32", "kite", 32768, 64, 2): 79.166720e6 + 11.300864e6,
+    ("matvec_fp32", "kite", 32768, 64, 2): 79.033088e6 + 11.152128e6,
     ("matvec_fp64", "kite", 32768, 64, 2): 3.288266e9 + 157.754112e6,
 }
 

@@ -48,6 +48,7 @@ constexpr int WKW = TBM + TBK + 2;   // Kress window of a tile (+ alignment slac
 constexpr int NPROD = 16;    // producer warps
 constexpr int WTMA = NPROD, WMMA = NPROD + 1;   // then the epilogue warps
 constexpr int TNT = (NPROD + 6) * 32;
+constexpr int QI = 2;        // rows whose entries a producer lane evaluates together
 
 struct tc_params {
   int n, b, ktiles;
@@ -198,16 +199,32 @@ k_fused_tc(tc_params P, const __grid_constant__ CUtensorMap tmB, const int4* __r
           float2 wv[QS];
 #pragma unroll
           for (int q = 0; q < QS; ++q) wv[q] = wq[2 * NPROD * q];
+          // QI rows at a time: the phases (special-function ops) of their
+          // 2 QI entries first, then the series and assembly, so that the
+          // independent chains interleave
 #pragma unroll
-          for (int q = 0; q < QS; ++q) {
-            const int il = warp + NPROD * (2 * q + half);
-            const float4 tg = S.tgt[il];
-            const float4 tn = KIND == KIND_DP ? S.tgn[il] : make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 e[2];
+          for (int q0 = 0; q0 < QS; q0 += QI) {
+            pair_phase f[QI][2];
+            float4 tn[QI];
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
-              e[u] = entry_folded32<KIND>(tg, tn, sc[u], sn[u], u ? wv[q].y : wv[q].x);
-            store_split2(a0, a1, a2, a3, sbase + (uint32_t)(2 * NPROD * 64 * q), e[0], e[1]);
+            for (int r = 0; r < QI; ++r) {
+              const int il = warp + NPROD * (2 * (q0 + r) + half);
+              const float4 tg = S.tgt[il];
+              tn[r] = KIND == KIND_DP ? S.tgn[il] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+              for (int u = 0; u < 2; ++u)
+                f[r][u] = pair_phase32_tc(tg.x, tg.y, tg.z, tg.w, sc[u].x, sc[u].y, sc[u].z,
+                                          sc[u].w);
+            }
+#pragma unroll
+            for (int r = 0; r < QI; ++r) {
+              const int q = q0 + r;
+              float2 e[2];
+#pragma unroll
+              for (int u = 0; u < 2; ++u)
+                e[u] = entry_finish32<KIND>(f[r][u], tn[r], sn[u], u ? wv[q].y : wv[q].x);
+              store_split2(a0, a1, a2, a3, sbase + (uint32_t)(2 * NPROD * 64 * q), e[0], e[1]);
+            }
           }
         } else {
 #pragma unroll 1

@@ -105,6 +105,36 @@ __device__ __forceinline__ pair_phase pair_phase32(float txh, float txl, float t
   return f;
 }
 
+// The same distance and phase to the accuracy of the fused tensor-core
+// kernel, whose entries reach the tensor cores as bf16 hi + lo pairs (2^-17
+// relative): the lo part of x comes from H - xh^2 (one fma, of the size of C)
+// plus C instead of from the exact sum H + C, the Cody-Waite constant has two
+// parts (the third, k C3, is 1.6e-12 omega r rad) and the lo part of pi/4 is
+// dropped (2.2e-8 rad).  Phase error a few 1e-7 rad for the kite at
+// omega = 2048.
+__device__ __forceinline__ pair_phase pair_phase32_tc(float txh, float txl, float tyh, float tyl,
+                                                      float sxh, float sxl, float syh, float syl) {
+  pair_phase f;
+  const float dxh = txh - sxh, dxl = txl - sxl;   // dxh, dyh exact
+  const float dyh = tyh - syh, dyl = tyl - syl;
+  const float H = fmaf(dxh, dxh, dyh * dyh);      // exact
+  const float C = fmaf(dxl, fmaf(2.0f, dxh, dxl), dyl * fmaf(2.0f, dyh, dyl));
+  const float x2 = H + C;
+  const float xinv = rsqrt_sfu(x2);
+  const float xh = x2 * xinv;
+  const float xl = (fmaf(-xh, xh, H) + C) * (0.5f * xinv);
+  const float k = rintf(fmaf(xh, kInv2Pi, -0.125f));
+  float chi = fmaf(-k, kC1, xh);                  // exact
+  chi = fmaf(-k, kC2, chi);
+  chi = (chi - kPi4H) + xl;
+  sincos_sfu(chi, &f.s, &f.c);
+  f.dx = dxh + dxl;
+  f.dy = dyh + dyl;
+  f.xinv = xinv;
+  f.ra = rsqrt_sfu(xh);
+  return f;
+}
+
 // Hankel's asymptotic expansion for x >= kX0 (t = 1/x), three terms of each
 // of P and Q (A&S 9.2.9, 9.2.10), without the common factor c0 x^(-1/2):
 // J_m = c0 ra j_m, Y_m = c0 ra y_m.  The remainder is below the first omitted
@@ -116,6 +146,22 @@ __device__ __forceinline__ void hankel_asym32(float ti, float s, float c, float&
   const float Q0 = ti * fmaf(t2, fmaf(t2, -0.22710800170898438f, 0.0732421875f), -0.125f);
   const float P1 = fmaf(t2, fmaf(t2, -0.144195556640625f, 0.1171875f), 1.0f);
   const float Q1 = ti * fmaf(t2, fmaf(t2, 0.2775764465332031f, -0.1025390625f), 0.375f);
+  j0 = fmaf(P0, c, -Q0 * s);
+  y0 = fmaf(P0, s, Q0 * c);
+  j1 = fmaf(P1, s, Q1 * c);
+  y1 = fmaf(Q1, s, -P1 * c);
+}
+
+// Two terms of each of P and Q (the fused tensor-core kernel): the remainder
+// is below the first omitted term, < 2.2e-6 relative for x >= 16 and
+// < 1.4e-8 for x >= 64, near the bf16 hi + lo split's 2^-17.
+__device__ __forceinline__ void hankel_asym32_tc(float ti, float s, float c, float& j0, float& y0,
+                                                 float& j1, float& y1) {
+  const float t2 = ti * ti;
+  const float P0 = fmaf(t2, -0.0703125f, 1.0f);
+  const float Q0 = ti * fmaf(t2, 0.0732421875f, -0.125f);
+  const float P1 = fmaf(t2, 0.1171875f, 1.0f);
+  const float Q1 = ti * fmaf(t2, -0.1025390625f, 0.375f);
   j0 = fmaf(P0, c, -Q0 * s);
   y0 = fmaf(P0, s, Q0 * c);
   j1 = fmaf(P1, s, Q1 * c);
@@ -157,8 +203,9 @@ __device__ __forceinline__ void pair_entries_fp32(const omega32& P, float txh, f
 // operators S, D' of the sound-hard operator of eq. 2
 enum { KIND_SOFT = 0, KIND_S = 1, KIND_DP = 2 };
 
-// The same entries with the per-node factors folded in (fused tensor-core
-// kernel): tg, sc = target and source coordinates, tq = target factors (D'
+// The same entries with the per-node factors folded in, to the fused
+// tensor-core kernel's accuracy (phase and series above): tg, sc = target and
+// source coordinates, tq = target factors (D'
 // only), sq = source factors, wk = Kress weight / (pi h); see the packed
 // layout above.  With A = sq ra and B = omega hq c0 (nu_j . (z_i - z_j)) ra / r,
 //   soft:  re = A j0 - B (y1 + wk j1),      im = B j1 + A (y0 + wk j0)
@@ -166,11 +213,10 @@ enum { KIND_SOFT = 0, KIND_S = 1, KIND_DP = 2 };
 //   D':    re = D (y1 + wk j1),              im = -D j1
 // with D = omega (nu_i . (z_i - z_j)) / |z'_i| hq c0 |z'_j| ra / r.
 template <int KIND>
-__device__ __forceinline__ float2 entry_folded32(float4 tg, float4 tq, float4 sc, float4 sq,
+__device__ __forceinline__ float2 entry_finish32(const pair_phase& f, float4 tq, float4 sq,
                                                  float wk) {
-  const pair_phase f = pair_phase32(tg.x, tg.y, tg.z, tg.w, sc.x, sc.y, sc.z, sc.w);
   float j0, y0, j1, y1;
-  hankel_asym32(f.xinv, f.s, f.c, j0, y0, j1, y1);
+  hankel_asym32_tc(f.xinv, f.s, f.c, j0, y0, j1, y1);
   float2 a;
   if constexpr (KIND == KIND_SOFT) {
     const float A = sq.z * f.ra;
@@ -187,4 +233,11 @@ __device__ __forceinline__ float2 entry_folded32(float4 tg, float4 tq, float4 sc
     a.y = -D * j1;
   }
   return a;
+}
+
+template <int KIND>
+__device__ __forceinline__ float2 entry_folded32(float4 tg, float4 tq, float4 sc, float4 sq,
+                                                 float wk) {
+  return entry_finish32<KIND>(pair_phase32_tc(tg.x, tg.y, tg.z, tg.w, sc.x, sc.y, sc.z, sc.w), tq,
+                              sq, wk);
 }

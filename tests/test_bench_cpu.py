@@ -71,18 +71,21 @@ ALU_PEAK_T = 152 * 128 * 2070e6 / 1e12          # FP32 lanes x clock
 
 
 def test_roofline_fused_fp32_kite():
-    """The reported roofline of the fused FP32 kernel: 64 operations per pair
+    """The reported roofline of the fused FP32 kernel: 54 operations per pair
     over n^2 pairs per launch, divided by the average launch time, against
-    the lane peak; traffic from the ncu table for this exact configuration."""
+    the lane peak; traffic from the ncu table for this exact configuration
+    (null while no capture of the current kernel is recorded)."""
     b = _bench_module()
     n, ms, launches = 32768, 37.0, 10
     spec = {"nrhs": 64, "bc": "soft", "precision": "fp32", "curve": "kite"}
     r = b.kernel_rooflines({"matvec_fp32": (ms, launches)}, spec, {"matvec_variant": 2},
                            PEAKS, "measured", n, 1)["matvec_fp32"]
-    want = 64 * n * n / (ms / 1e3 / launches) / 1e12
+    want = 54 * n * n / (ms / 1e3 / launches) / 1e12
     assert abs(r["achieved"] - want) < 1e-9 * want
     assert abs(r["frac"] - want / ALU_PEAK_T) < 1e-12
-    assert r["bound"] == "alu" and r["traffic"] == 79.166720e6 + 11.300864e6
+    assert r["bound"] == "alu"
+    key = ("matvec_fp32", "kite", n, 64, 2)
+    assert r["traffic"] == b.NCU_TRAFFIC.get(key)
 
 
 @pytest.mark.parametrize("bc,variant,ops", [

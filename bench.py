@@ -867,11 +867,13 @@ def run_stars(args):
         e2e_pairs += pairs_mv * (stats_e["inner_matvecs"] + stats_e["fp64_matvecs"])
     peaks, src = measured_peaks()
     tens_ms, tens_n = kt["matvec_tensor"]
-    gemm_bytes = sum(s["n"] * (s["n"] + 63) // 64 * 64 * 8 for s in specs)
+    gemm_bytes = sum(s["n"] * ((s["n"] + 63) // 64 * 64) * 8 for s in specs)   # n x pitch x 8
     roof = None
     if tens_n:
         gbs = gemm_bytes / (tens_ms / tens_n / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "stored contraction graph (prep + k_gemm_persistent + reduce)",
+        roof = {"bound": "hbm",
+                "kernel": "stored contraction graph (B preparation + k_gemm_persistent "
+                          "[+ reduction for stream-K])",
                 "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
                 "bytes_per_launch": gemm_bytes}

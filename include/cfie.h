@@ -422,10 +422,11 @@ typedef struct cfie_batch cfie_batch;
  * nrhs[k] right-hand sides for operator k.  Batch vectors are the operators'
  * column-major n_k x nrhs[k] blocks concatenated in order (see
  * cfie_batch_length).  When every operator uses CFIE_STORED, one block matvec of
- * the whole batch is one CUDA-graph replay of three kernels: the B-operand
- * preparation of every operator, a persistent stream-K tensor-core contraction
- * over all (operator, row tile, source tile) pairs (one CTA per SM), and the
- * partial-sum reduction.  Otherwise the operators' matvecs run on up to
+ * the whole batch is one CUDA-graph replay: the B-operand preparation of
+ * every operator, then a persistent tensor-core contraction over all
+ * (operator, row tile, source tile) triples (one CTA per SM) that writes y
+ * itself when its work dealing gives whole row tiles, or partial sums that a
+ * third kernel adds when it splits row tiles (stream-K).  Otherwise the operators' matvecs run on up to
  * eight auxiliary streams forked from and joined back into the context stream;
  * inside a lockstep solve an operator all of whose right-hand sides have
  * converged is skipped.  The operators must outlive the batch.  Synchronous. */
@@ -450,7 +451,8 @@ cfie_status cfie_batch_set_inner_basis(cfie_batch* batch, int fp32);
  * after one warm-up) and the fastest kept; the choice is remembered for the
  * process per batch shape (the operators' n and right-hand-side counts).
  *  0  whole (operator, 128-row tile) units dealt round-robin
- *  1  whole units, largest first, each to the CTA with the least work so far
+ *  1  whole units in operator order, each to the CTA with the least work so
+ *     far (balanced within one unit; the CTAs stay on neighbouring units)
  *  2  stream-K: the (row tile, 64-source tile) pairs split evenly
  * *dealing receives the choice (-1 when the batch is not all stored); ms
  * (host, 3 floats, may be NULL) the candidates' replay times in milliseconds,

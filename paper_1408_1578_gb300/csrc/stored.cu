@@ -14,8 +14,9 @@
 // shared-memory ring; one thread issues tcgen05.mma (M = 128, N = 2 * 32,
 // K = 16 per instruction, kind::f16 with bf16 operands), tcgen05.commit frees
 // the stage; after the last K tile the four warps read the 128 x N accumulator
-// back with tcgen05.ld and write FP32 partial sums.  Source ranges are split
-// across CTAs; a reduction kernel adds the partials in FP64 in a fixed order.
+// back with tcgen05.ld and write y (whole row tiles per CTA) or FP32 partial
+// sums (source ranges split across CTAs, stream-K), which a reduction kernel
+// adds in FP64 in a fixed order.
 // Every mbarrier wait is bounded: on timeout the kernel records an error code,
 // stops issuing work, drains its own copies (bounded), frees its tensor memory
 // and returns.
@@ -141,7 +142,9 @@ constexpr size_t pgemm_smem_bytes() {
 
 // Persistent stream-K contraction over every job of a plan.  The (m tile,
 // k tile) pairs of all jobs form one list; CTA c owns a contiguous range of it,
-// cut into segments (one job, one m tile, a run of k tiles).  Warp 0 issues the
+// cut into segments (one job, one m tile, a run of k tiles).  With io set
+// (every m tile one whole segment) the epilogue writes y itself; otherwise it
+// writes FP32 partial sums per segment for the reduction kernel.  Warp 0 issues the
 // TMA loads, warp 1 the MMAs (double-buffered accumulators, 2 x NP TMEM
 // columns), warps 2-5 drain finished accumulators to the partial-sum slot of
 // their segment while the next segment accumulates.
@@ -149,7 +152,7 @@ template <int NP>
 __global__ void __launch_bounds__(192, 1)
 k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ segs,
                   const int* __restrict__ cbeg, float2* __restrict__ partial,
-                  int* __restrict__ err, int stall) {
+                  const gemm_io* __restrict__ io, int* __restrict__ err, int stall) {
   constexpr int NR = NP / 2;
   constexpr uint32_t TMEM_COLS = 2 * NP <= 32 ? 32 : (2 * NP <= 64 ? 64 : (2 * NP <= 128 ? 128 : 256));
   constexpr uint32_t STAGE_BYTES = 4u * BM * BK * 2u + 4u * NP * BK * 2u;
@@ -296,9 +299,22 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
         if (lane == 0) mbar_arrive(&S.tempty[tb]);
       }
       if (stop) break;
-      float2* dst = partial + (size_t)s * BM * NR + row;
+      if (io) {
+        // every row tile is one segment (whole-tile dealings): the sums are
+        // the product itself, written to y without a reduction pass
+        const gemm_job* J = jobs + sg.x;
+        const int i = sg.y * BM + row;
+        if (i < J->n) {
+          double2* y = io->y + J->xoff + i;
 #pragma unroll
-      for (int r = 0; r < NR; ++r) dst[(size_t)r * BM] = make_float2(run[r], run[NR + r]);
+          for (int r = 0; r < NR; ++r)
+            if (r < J->nr) y[(size_t)r * J->n] = make_double2(run[r], run[NR + r]);
+        }
+      } else {
+        float2* dst = partial + (size_t)s * BM * NR + row;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) dst[(size_t)r * BM] = make_float2(run[r], run[NR + r]);
+      }
     }
   }
   __syncthreads();
@@ -322,30 +338,33 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
 }
 
 // B operand planes of every job: B1 = [Xr | Xi], B2 = [-Xi | Xr] (rows = output
-// columns), hi / lo bf16 split; grid (NP, jobs), each CTA striding over the
-// job's pitch
+// columns), hi / lo bf16 split; grid (NR, jobs): right-hand side r fills its
+// columns r and NR + r from one read of x (the split of -Xi is the negated
+// split of Xi), each CTA striding over the job's pitch
 __global__ void k_prep_b_jobs(const gemm_job* __restrict__ jobs, const gemm_io* __restrict__ io,
                               int NP) {
   const gemm_job& J = jobs[blockIdx.y];
-  const int c = blockIdx.x;
+  const int r = blockIdx.x;
   const int NR = NP / 2;
-  const int r = c < NR ? c : c - NR;
   const size_t plane = (size_t)NP * J.pitch;
   for (int j = threadIdx.x; j < J.pitch; j += blockDim.x) {
-    double w1 = 0.0, w2 = 0.0;
-    if (j < J.n && r < J.nr) {
-      const double2 xv = io->x[J.xoff + (long long)r * J.n + j];
-      w1 = c < NR ? xv.x : xv.y;
-      w2 = c < NR ? -xv.y : xv.x;
-    }
-    const __nv_bfloat16 h1 = __float2bfloat16_rn((float)w1), h2 = __float2bfloat16_rn((float)w2);
-    const __nv_bfloat16 l1 = __float2bfloat16_rn((float)(w1 - (double)__bfloat162float(h1)));
-    const __nv_bfloat16 l2 = __float2bfloat16_rn((float)(w2 - (double)__bfloat162float(h2)));
-    const size_t e = (size_t)c * J.pitch + j;
-    J.bt[e] = h1;
-    J.bt[plane + e] = l1;
-    J.bt[2 * plane + e] = h2;
-    J.bt[3 * plane + e] = l2;
+    double2 xv = make_double2(0.0, 0.0);
+    if (j < J.n && r < J.nr) xv = io->x[J.xoff + (long long)r * J.n + j];
+    // the split of the FP32 value (x - hi is exact in FP32; FP64 arithmetic
+    // here would run on the slow FP64 pipe)
+    const float fr = (float)xv.x, fi = (float)xv.y;
+    const __nv_bfloat16 hr = __float2bfloat16_rn(fr), hi = __float2bfloat16_rn(fi);
+    const __nv_bfloat16 lr = __float2bfloat16_rn(fr - __bfloat162float(hr));
+    const __nv_bfloat16 li = __float2bfloat16_rn(fi - __bfloat162float(hi));
+    const size_t e = (size_t)r * J.pitch + j, f = (size_t)(NR + r) * J.pitch + j;
+    J.bt[e] = hr;                      // column r: B1 = Xr, B2 = -Xi
+    J.bt[plane + e] = lr;
+    J.bt[2 * plane + e] = __hneg(hi);
+    J.bt[3 * plane + e] = __hneg(li);
+    J.bt[f] = hi;                      // column NR + r: B1 = Xi, B2 = Xr
+    J.bt[plane + f] = li;
+    J.bt[2 * plane + f] = hr;
+    J.bt[3 * plane + f] = lr;
   }
 }
 
@@ -430,9 +449,10 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
   //  GEMM_DEAL_ROUND_ROBIN whole (job, row tile) units, unit u to CTA u % grid:
   //                        the CTAs work on neighbouring units of few jobs at any
   //                        time, so the jobs' right-hand-side planes stay in L2
-  //  GEMM_DEAL_GREEDY      whole units, largest first, each to the CTA with the
-  //                        least work so far (balanced when sizes differ), each
-  //                        CTA's units then taken in job order
+  //  GEMM_DEAL_GREEDY      whole units in job order, each to the CTA with the
+  //                        least work so far: balanced within one unit when
+  //                        sizes differ (round-robin is not), and the CTAs,
+  //                        progressing evenly, still work on neighbouring units
   //  GEMM_DEAL_STREAMK     the (row tile, K tile) pairs split evenly, segments
   //                        cut at row-tile boundaries (partial sums added by the
   //                        reduction kernel)
@@ -462,23 +482,15 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
         for (int m = 0; m < mt; ++m, ++u) per[u % grid].push_back(make_int4((int)k, m, 0, kt));
       }
     } else {
-      std::vector<int4> units;
+      std::vector<long long> load(grid, 0);
       for (size_t k = 0; k < jobs.size(); ++k) {
         const int mt = (jobs[k].n + BM - 1) / BM, kt = (jobs[k].n + BK - 1) / BK;
-        for (int m = 0; m < mt; ++m) units.push_back(make_int4((int)k, m, 0, kt));
+        for (int m = 0; m < mt; ++m) {
+          const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+          per[c].push_back(make_int4((int)k, m, 0, kt));
+          load[c] += kt;
+        }
       }
-      std::stable_sort(units.begin(), units.end(),
-                       [](const int4& a, const int4& b) { return a.w > b.w; });
-      std::vector<long long> load(grid, 0);
-      for (const int4& u : units) {
-        const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        per[c].push_back(u);
-        load[c] += u.w;
-      }
-      for (auto& v : per)
-        std::sort(v.begin(), v.end(), [](const int4& a, const int4& b) {
-          return a.x != b.x ? a.x < b.x : a.y < b.y;
-        });
     }
     for (int c = 0; c < grid; ++c) {
       cbeg[c] = (int)segs.size();
@@ -522,7 +534,10 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
   G.jobs.reserve(sizeof(gemm_job) * jobs.size());
   G.tables.reserve(sizeof(int4) * segs.size() + sizeof(int) * cbeg.size() +
                    2 * sizeof(int2) * mt_total + 256);
-  G.partial.reserve(sizeof(float2) * (size_t)segs.size() * BM * kNR);
+  // whole-tile dealings give one segment per m tile: y is written by the
+  // contraction's epilogue, with no partial sums and no reduction launch
+  const bool direct = (int)segs.size() == mt_total;
+  if (!direct) G.partial.reserve(sizeof(float2) * (size_t)segs.size() * BM * kNR);
   G.io.reserve(sizeof(gemm_io));
   G.err.reserve(sizeof(int));
   char* tb = G.tables.as<char>();
@@ -547,7 +562,7 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
   // bounded waits run out
   const char* fi = std::getenv("CFIE_FAULT_INJECT");
   G.stall = (fi && std::strcmp(fi, "tma_stall") == 0) ? 1 : 0;
-  // capture the three launches once; replays read x / y from the io slot
+  // capture the two or three launches once; replays read x / y from the io slot
   const size_t smem = pgemm_smem_bytes<kNP>();
   CFIE_CHECK_CUDA(cudaFuncSetAttribute(k_gemm_persistent<kNP>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -558,13 +573,15 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
   if (e1 == cudaSuccess) {
     const gemm_job* dj = G.jobs.as<gemm_job>();
     const gemm_io* io = G.io.as<gemm_io>();
-    k_prep_b_jobs<<<dim3(kNP, G.njobs), 256, 0, cs>>>(dj, io, kNP);
+    k_prep_b_jobs<<<dim3(kNR, G.njobs), 256, 0, cs>>>(dj, io, kNP);
     k_gemm_persistent<kNP><<<grid, 192, smem, cs>>>(
         dj, reinterpret_cast<const int4*>(tb + o_segs), reinterpret_cast<const int*>(tb + o_cbeg),
-        G.partial.as<float2>(), G.err.as<int>(), G.stall);
-    k_reduce_jobs<<<dim3(mt_total, kNR), BM, 0, cs>>>(
-        dj, reinterpret_cast<const int2*>(tb + o_mtj), reinterpret_cast<const int2*>(tb + o_mts),
-        G.partial.as<float2>(), io, kNR);
+        direct ? nullptr : G.partial.as<float2>(), direct ? io : nullptr, G.err.as<int>(),
+        G.stall);
+    if (!direct)
+      k_reduce_jobs<<<dim3(mt_total, kNR), BM, 0, cs>>>(
+          dj, reinterpret_cast<const int2*>(tb + o_mtj),
+          reinterpret_cast<const int2*>(tb + o_mts), G.partial.as<float2>(), io, kNR);
     e1 = cudaStreamEndCapture(cs, &graph);
   }
   cudaStreamDestroy(cs);
@@ -574,7 +591,7 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
   cudaError_t e2 = cudaGraphInstantiate(&G.exec, graph, 0);
   cudaGraphDestroy(graph);
   CFIE_CHECK_CUDA(e2);
-  G.launches_per_run = 3;
+  G.launches_per_run = direct ? 2 : 3;
 }
 
 void gemm_plan_run(gemm_plan& G, cfie_ctx* ctx, const double2* x, double2* y) {

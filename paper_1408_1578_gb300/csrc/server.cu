@@ -57,8 +57,8 @@ size_t footprint_bytes(const cfie_request& r) {
   f += vec * 4 * ops;                 // FP64 residual partials (a few splits)
   f += n * 200 + ((size_t)64 << 20);  // tables, small buffers, slack
   if (r.precision == CFIE_TENSOR_REFINED) {
-    const size_t pitch = (n + 63) / 64 * 64;
-    f += 8 * n * pitch;                 // stored bf16 hi/lo planes (re, im)
+    const size_t pitch = (n + 63) / 64 * 64, rows = (n + 127) / 128 * 128;
+    f += 8 * rows * pitch;              // stored bf16 hi/lo planes (re, im), whole row blocks
     f += vec * 2;                       // contraction operand and partial sums
   }
   return f;

@@ -3,7 +3,10 @@
 // is assembled once per operator and kept in HBM as four bf16 planes
 //     A = (Ahi_re + Alo_re) + i (Ahi_im + Alo_im),   hi = bf16(a), lo = bf16(a - hi),
 // 8 bytes per complex entry, i.e. the bytes of complex64 with ~16 significant
-// bits per component.  Each block matvec Y = A X (up to 32 right-hand sides per
+// bits per component.  Each plane is stored tile by tile: the 128 x 64 tiles
+// (16 KB, row-major inside) of a 128-row block one after another along the
+// sources, the blocks in row order, so that every TMA load of the contraction
+// reads 16 contiguous kilobytes.  Each block matvec Y = A X (up to 32 right-hand sides per
 // pass) is a split-complex contraction on the 5th-generation tensor cores:
 //
 //     [Yr | Yi] = Ar [Xr | Xi] + Ai [-Xi | Xr]
@@ -69,7 +72,9 @@ __global__ void k_rowexp_from_max(int n, unsigned* __restrict__ r) {
   reinterpret_cast<int*>(r)[i] = e;
 }
 
-// planes [4][n][pitch]: hi_re, hi_im, lo_re, lo_im; grid (ceil(pitch / 256), n)
+// planes [4][mt][kt][128][64] (mt = ceil(n / 128) row blocks, kt = pitch / 64
+// source tiles): hi_re, hi_im, lo_re, lo_im; grid (ceil(pitch / 256), n); the
+// rows of the last block past n are zeroed beforehand
 __global__ void __launch_bounds__(256)
 k_assemble(int n, int pitch, int b, int bd, omega32 W, geo32 g, const float* __restrict__ w32,
            const float2* __restrict__ band, __nv_bfloat16* __restrict__ planes,
@@ -101,8 +106,8 @@ k_assemble(int n, int pitch, int b, int bd, omega32 W, geo32 g, const float* __r
   __nv_bfloat16 hr, lr, hi, li;
   split_bf16(a.x, hr, lr);
   split_bf16(a.y, hi, li);
-  const size_t plane = (size_t)n * pitch;
-  const size_t e = (size_t)i * pitch + j;
+  const size_t plane = (size_t)((n + BM - 1) / BM) * BM * pitch;
+  const size_t e = (((size_t)(i / BM) * (pitch / BK) + j / BK) * BM + i % BM) * BK + j % BK;
   planes[e] = hr;
   planes[plane + e] = hi;
   planes[2 * plane + e] = lr;
@@ -112,7 +117,7 @@ k_assemble(int n, int pitch, int b, int bd, omega32 W, geo32 g, const float* __r
 // One GEMM job: 32 right-hand sides of one stored operator.  64-byte aligned
 // (it holds the two tensor maps the TMA unit reads).
 struct alignas(64) gemm_job {
-  CUtensorMap ta;          // A planes [4 n rows][pitch] bf16, box 128 x 64
+  CUtensorMap ta;          // A planes: 4 mt kt tiles of 128 x 64 bf16, box one tile
   CUtensorMap tb;          // B planes [4 NP rows][pitch] bf16, box NP x 64
   __nv_bfloat16* bt;       // B planes of this job
   long long xoff;          // first element of the job's right-hand sides in x / y
@@ -195,7 +200,6 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
       for (int s = sb; s < se && !*(volatile int*)&S.abort; ++s) {
         const int4 sg = segs[s];
         const gemm_job* J = jobs + sg.x;
-        const int m0 = sg.y * BM;
         for (int k = sg.z; k < sg.w; ++k, ++it) {
           const int st = it % STAGES;
           if (it >= STAGES && !mbar_wait(&S.empty[st], ((it / STAGES) - 1) & 1)) {
@@ -209,9 +213,11 @@ k_gemm_persistent(const gemm_job* __restrict__ jobs, const int4* __restrict__ se
           // never issued, so the wait on its barrier runs out
           if (stall && it == 0) continue;
           const int kc = k * BK;
+          const int kt = J->pitch / BK, mt = (J->n + BM - 1) / BM;
 #pragma unroll
           for (int p = 0; p < 4; ++p)
-            tma_load_2d_hint(S.A[st][p], &J->ta, &S.full[st], kc, p * J->n + m0, pol_a);
+            tma_load_3d_hint(S.A[st][p], &J->ta, &S.full[st], 0, 0, (p * mt + sg.y) * kt + k,
+                             pol_a);
 #pragma unroll
           for (int p = 0; p < 4; ++p)
             tma_load_2d_hint(S.B[st][p], &J->tb, &S.full[st], kc, p * NP, pol_b);
@@ -440,7 +446,9 @@ void gemm_plan_build(gemm_plan& G, cfie_ctx* ctx, const std::vector<cfie_op*>& o
     for (int r0 = 0; r0 < nrhs[o]; r0 += kNR, ++k) {
       gemm_job& J = jobs[k];
       J.bt = G.bt.as<__nv_bfloat16>() + bt_off[k];
-      J.ta = make_map(op->stored.p, 4 * (uint64_t)J.n, (uint64_t)J.pitch, J.pitch, BM);
+      J.ta = tc_make_tile_map(op->stored.p, BM, BK,
+                              4 * (uint64_t)((J.n + BM - 1) / BM) * (J.pitch / BK),
+                              CU_TENSOR_MAP_SWIZZLE_128B);
       J.tb = make_map(J.bt, 4 * (uint64_t)kNP, (uint64_t)J.pitch, J.pitch, kNP);
     }
   }
@@ -696,8 +704,10 @@ void stored_prepare(cfie_op* op) {
     throw cfie_error(CFIE_EINVAL, "the stored layout supports the sound-soft operator");
   const int n = op->n;
   const int pitch = stored_pitch(n);
-  const size_t plane = (size_t)n * pitch;
+  const size_t plane = (size_t)((n + BM - 1) / BM) * BM * pitch;   // whole row blocks
   op->stored.reserve(sizeof(__nv_bfloat16) * 4 * plane);
+  CFIE_CHECK_CUDA(cudaMemsetAsync(op->stored.p, 0, sizeof(__nv_bfloat16) * 4 * plane,
+                                  op->ctx->stream));
   float* base = op->geo32.as<float>();
   omega32 W{};
   W.wh = (float)op->omega;

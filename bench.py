@@ -69,6 +69,9 @@ def parse():
     p.add_argument("--serve-block-min-n", type=int, default=16384)
     p.add_argument("--serve-stored-max-n", type=int, default=0,
                    help="serve: sound-soft requests up to this n use the stored tensor-core form")
+    p.add_argument("--no-extras", action="store_true",
+                   help="headline workload only: skip the short runs of the other configurations "
+                        "that the default run appends (other_configs)")
     p.add_argument("--oracle-budget", type=float, default=None, help=argparse.SUPPRESS)
     return p.parse_args()
 
@@ -784,11 +787,62 @@ def main():
         out = run_ours(args, rank, world)
         if rank == 0 and out is not None and world == 1:
             out["cpu_baseline"] = oracle_single_core(args, 12.0)
+            if default_headline(args):
+                out["other_configs"] = run_other_configs(args)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if _PG is not None:
         _PG.destroy_process_group()
 
+
+
+def default_headline(args):
+    """The plain headline run (the kite workload, no overrides), after which
+    the other configurations are measured briefly."""
+    return (args.workload == "kite" and not args.no_extras and args.precision is None
+            and args.n is None and args.nrhs is None and args.eta_factor is None
+            and args.rtol is None and not (args.block or args.dirprec or args.fp64_basis))
+
+
+def _brief(r):
+    keys = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "solves_per_s",
+            "max_relres", "dtype", "gpu_launches", "clocks", "makespan_s", "p50_latency_s",
+            "p99_latency_s", "p50_service_s", "failed", "contraction_tuning")
+    out = {k: r[k] for k in keys if k in r}
+    out["workload"] = r["config"]["workload"]
+    if r.get("roofline"):
+        rf = r["roofline"]
+        out["roofline"] = {k: rf[k] for k in ("bound", "kernel", "achieved", "peak", "unit", "frac")
+                           if k in rf}
+    if "one_at_a_time_summary" in r:
+        out["one_at_a_time_summary"] = r["one_at_a_time_summary"]
+    return out
+
+
+def run_other_configs(args):
+    """Short runs of the suite's other configurations on the same GPU after the
+    headline: the unit circle (FP64, unrestarted GMRES), the sound-hard star in
+    the plain FP64 form and in the FP32 refined form, the 256-star stored batch,
+    and the first 100 requests of the served stream.  Each single-operator and
+    batch run keeps the timing rules (three warm-up steps, CUDA events, L2 as
+    the headline run); steps = min(steps, 3)."""
+    import copy
+    out = {}
+
+    def sub(workload, **kw):
+        a = copy.copy(args)
+        a.workload, a.precision, a.count, a.no_extras = workload, None, None, True
+        a.steps, a.warmup = min(args.steps, 3), max(3, min(args.warmup, 3))
+        for k, v in kw.items():
+            setattr(a, k, v)
+        return a
+
+    out["disk_fp64"] = _brief(run_ours(sub("disk"), 0, 1))
+    out["star_hard_fp64"] = _brief(run_ours(sub("star"), 0, 1))
+    out["star_hard_fp32"] = _brief(run_ours(sub("star", precision="fp32"), 0, 1))
+    out["stars256_stored"] = _brief(run_stars(sub("stars")))
+    out["serve_first100"] = _brief(run_serve(sub("serve", count=100)))
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -1,5 +1,6 @@
 // Stored-matrix path: the sound-soft Nystrom matrix A (eq. 1 of the paper,
-// entries exactly as the FP32 fused matvec evaluates them, near band from FP64)
+// entries exactly as the fused tensor-core matvec evaluates them, near band
+// from FP64)
 // is assembled once per operator and kept in HBM as four bf16 planes
 //     A = (Ahi_re + Alo_re) + i (Ahi_im + Alo_im),   hi = bf16(a), lo = bf16(a - hi),
 // 8 bytes per complex entry, i.e. the bytes of complex64 with ~16 significant
@@ -76,12 +77,12 @@ __global__ void k_rowexp_from_max(int n, unsigned* __restrict__ r) {
 // source tiles): hi_re, hi_im, lo_re, lo_im; grid (ceil(pitch / 256), n); the
 // rows of the last block past n are zeroed beforehand
 __global__ void __launch_bounds__(256)
-k_assemble(int n, int pitch, int b, int bd, omega32 W, geo32 g, const float* __restrict__ w32,
-           const float2* __restrict__ band, __nv_bfloat16* __restrict__ planes,
-           unsigned* __restrict__ rmax) {
+k_assemble(int n, int pitch, int b, int bd, const float4* __restrict__ pk,
+           const float2* __restrict__ wkt, const float2* __restrict__ band,
+           __nv_bfloat16* __restrict__ planes, unsigned* __restrict__ rmax) {
   const int i = blockIdx.y;
   const int j = blockIdx.x * 256 + threadIdx.x;
-  float2 a = make_float2(0.f, 0.f), unused;
+  float2 a = make_float2(0.f, 0.f);
   float far_max = 0.f;
   if (j < n) {
     int d = i - j;
@@ -90,9 +91,11 @@ k_assemble(int n, int pitch, int b, int bd, omega32 W, geo32 g, const float* __r
     if (dd != INT_MAX) {
       a = band[(size_t)i * (2 * b + 1) + dd + b];
     } else {
-      pair_entries_fp32<0>(W, g.xh[i], g.xl[i], g.yh[i], g.yl[i], g.nx[i], g.ny[i], g.sp[i],
-                           g.xh[j], g.xl[j], g.yh[j], g.yl[j], g.nx[j], g.ny[j], g.sp[j], w32[d],
-                           a, unused);
+      // the folded entry of the fused matvec, to the accuracy the bf16 hi + lo
+      // planes keep (packed coordinates and factors, Kress table / (pi h) at
+      // i - j + n)
+      a = entry_folded32<KIND_SOFT>(pk[i], make_float4(0.f, 0.f, 0.f, 0.f), pk[j], pk[n + j],
+                                    wkt[i - j + n].x);
     }
     // largest far entry of the row (outside the double-float band of width bd):
     // the row exponent of the tensor-core residual
@@ -709,10 +712,6 @@ void stored_prepare(cfie_op* op) {
   CFIE_CHECK_CUDA(cudaMemsetAsync(op->stored.p, 0, sizeof(__nv_bfloat16) * 4 * plane,
                                   op->ctx->stream));
   float* base = op->geo32.as<float>();
-  omega32 W{};
-  W.wh = (float)op->omega;
-  W.eta = (float)op->eta;
-  W.h = (float)op->h;
   const dim3 grid(nblk(pitch), n);
   // the row maxima of the far entries come with the assembly (sound soft:
   // the tensor-core residual's row exponents), not from a separate pass
@@ -722,10 +721,10 @@ void stored_prepare(cfie_op* op) {
     rmax = reinterpret_cast<unsigned*>(op->df_rowexp.as<int>());
     CFIE_CHECK_CUDA(cudaMemsetAsync(rmax, 0, sizeof(unsigned) * n, op->ctx->stream));
   }
-  k_assemble<<<grid, 256, 0, op->ctx->stream>>>(n, pitch, op->band_b, op->df_b, W,
-                                                geo32_at(base, n), base + 7 * n,
-                                                op->band.as<float2>(),
-                                                op->stored.as<__nv_bfloat16>(), rmax);
+  k_assemble<<<grid, 256, 0, op->ctx->stream>>>(
+      n, pitch, op->band_b, op->df_b, reinterpret_cast<const float4*>(base + geo32_pack_offset(n)),
+      reinterpret_cast<const float2*>(base + geo32_wk_offset(n)), op->band.as<float2>(),
+      op->stored.as<__nv_bfloat16>(), rmax);
   CFIE_CHECK_LAUNCH();
   if (rmax) {
     k_rowexp_from_max<<<nblk(n), 256, 0, op->ctx->stream>>>(n, rmax);

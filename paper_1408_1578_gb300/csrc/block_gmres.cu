@@ -543,10 +543,9 @@ int cycle(const bg_ctx& C, bg_ws<T>& w, const double2* r, const std::vector<doub
   std::vector<int> bsz{r0};   // block sizes
   int p = r0, steps = 0;
   stats.cycles++;
-  while (true) {
-    const int sk = bsz.back();
-    const T* Vk = w.V + (size_t)(p - sk) * n;
-    // W = A (P) V_k
+  // W = A (P) V_k for the newest block, queued on the stream without waiting
+  auto queue_matvec = [&](int pk, int sk) {
+    const T* Vk = w.V + (size_t)(pk - sk) * n;
     k_bconv<T, double2><<<nbl((size_t)n * sk), 256, 0, C.st>>>((size_t)n * sk, Vk, w.vin);
     CFIE_CHECK_LAUNCH();
     if (C.prec) {
@@ -558,6 +557,12 @@ int cycle(const bg_ctx& C, bg_ws<T>& w, const double2* r, const std::vector<doub
       k_bconv<double2, T><<<nbl((size_t)n * sk), 256, 0, C.st>>>((size_t)n * sk, w.vout, w.W);
     }
     CFIE_CHECK_LAUNCH();
+  };
+  queue_matvec(p, r0);
+  while (true) {
+    const int sk = bsz.back();
+    // the matvec of block k is queued (first block above, later ones ahead of
+    // the previous step's least-squares update)
     if (C.refined)
       stats.inner_matvecs++;
     else
@@ -577,6 +582,10 @@ int cycle(const bg_ctx& C, bg_ws<T>& w, const double2* r, const std::vector<doub
     std::vector<cplx> Rk;
     int rn = 0;
     if (room) rn = block_qr(C, w, w.W, sk, w.V + (size_t)p * n, thresh, Rk);
+    // the next block's matvec goes to the GPU before the host updates the
+    // least squares, so the two overlap; if this step ends the cycle, its
+    // result is simply not read (the stream orders every later use of W)
+    if (rn > 0 && steps + 1 < max_blocks) queue_matvec(p + rn, rn);
     // block column [H; R_k] into the least squares
     ls.grow(p + rn);
     std::vector<std::vector<cplx>> blk(sk, std::vector<cplx>(p + rn, cplx(0.0)));

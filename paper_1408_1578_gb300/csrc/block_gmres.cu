@@ -403,15 +403,19 @@ struct block_ls {
     for (int q = cols; q < rows; ++q) t += std::norm(G[b][q]);
     return std::sqrt(t);
   }
-  // Y (cols x s, row-major) from the triangular system
+  // Y (cols x s, row-major) from the triangular system, by columns of R (each
+  // stored contiguously): y_i = g_i / R_ii, then g_q -= R_qi y_i for q < i
   std::vector<cplx> solve() const {
     std::vector<cplx> Y((size_t)cols * s, cplx(0.0));
     parallel_for(s, 0.5 * (double)cols * cols * s, [&](int b) {
+      std::vector<cplx> y(G[b].begin(), G[b].begin() + cols);
       for (int i = cols - 1; i >= 0; --i) {
-        cplx acc = G[b][i];
-        for (int k = i + 1; k < cols; ++k) acc -= Rc[k][i] * Y[(size_t)k * s + b];
-        Y[(size_t)i * s + b] = acc / Rc[i][i];
+        const std::vector<cplx>& ri = Rc[i];
+        const cplx yi = y[i] / ri[i];
+        y[i] = yi;
+        for (int q = 0; q < i; ++q) y[q] -= ri[q] * yi;
       }
+      for (int i = 0; i < cols; ++i) Y[(size_t)i * s + b] = y[i];
     });
     return Y;
   }

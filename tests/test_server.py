@@ -223,3 +223,37 @@ def test_block_gmres_requests_equal_alone_and_oracle():
         srv.set_block_gmres(8, -1)
     ctx.close()
     srv.close()
+
+
+def test_batched_fp64_requests_equal_alone_and_oracle():
+    """The plain FP64 form batches too (lockstep FP64 GMRES over the group):
+    each request's solution equals its FP64 solve alone and the oracle's LU
+    solution within 1e-8 (both driven to residual 1e-10)."""
+    from paper_1408_1578_gb300 import cfie
+    reqs = inputs.poisson_requests(count=4, rate=200.0, seed=97, n_lo=500, n_hi=900)
+    for k, r in enumerate(reqs):
+        r["nrhs"] = 1 + 2 * k
+    srv = cfie.Server(0, hbm_budget_bytes=16 << 30, slots=1, batch=4)
+    tickets = [srv.submit(r["a"], r["b"], r["n"], r["omega"], nrhs=r["nrhs"], bc=r["bc"],
+                          rtol=1e-10, restart=60, precision="fp64") for r in reqs]
+    assert srv.wait_all(300)
+    ctx = cfie.Context(0)
+    for r, t in zip(reqs, tickets):
+        out = srv.poll(t, want_x=True)
+        assert out["done"] and out["status"] == cfie.CFIE_OK, out.get("error")
+        assert out["relres_max"] <= 1e-10
+        op = ctx.fourier_star(r["a"], r["b"]).discretise(r["n"], r["omega"], bc=r["bc"],
+                                                          precision="fp64")
+        f = zeros(r["nrhs"], r["n"])
+        op.rhs_plane_waves(inputs.directions(r["nrhs"]), f)
+        x = zeros(r["nrhs"], r["n"])
+        op.gmres_solve(f, x, rtol=1e-10, restart=60, maxit=4000)
+        assert np.max(col_rel(out["x"], to_host(x))) < 1e-8
+        c = geometry.fourier_star(r["n"], r["a"], r["b"])
+        A = operators.cfie_matrix(c, r["omega"], r["omega"], r["bc"])
+        Q = solvers.lu_solve(A, to_host(f).T).T
+        assert np.max(col_rel(out["x"], Q)) < 1e-8
+        op.close()
+        srv.release(t)
+    ctx.close()
+    srv.close()

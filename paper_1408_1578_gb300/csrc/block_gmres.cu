@@ -254,10 +254,15 @@ int chol_pivoted(std::vector<cplx> G, int c, double thresh, std::vector<cplx>& R
     const double d = std::sqrt(best);
     R[(size_t)j * c + j] = d;
     for (int q = j + 1; q < c; ++q) R[(size_t)j * c + q] = G[(size_t)j * c + q] / d;
-    // Schur complement of the remaining block
-    for (int a = j + 1; a < c; ++a)
-      for (int b = j + 1; b < c; ++b)
-        G[(size_t)a * c + b] -= std::conj(R[(size_t)j * c + a]) * R[(size_t)j * c + b];
+    // Schur complement of the remaining block: the upper triangle, then its
+    // mirror (the block stays Hermitian)
+    for (int a = j + 1; a < c; ++a) {
+      const cplx ra = std::conj(R[(size_t)j * c + a]);
+      cplx* ga = &G[(size_t)a * c];
+      const cplx* rj = &R[(size_t)j * c];
+      for (int b = a; b < c; ++b) ga[b] -= ra * rj[b];
+      for (int b = a + 1; b < c; ++b) G[(size_t)b * c + a] = std::conj(ga[b]);
+    }
     ++r;
   }
   return r;
@@ -490,15 +495,39 @@ void update(const bg_ctx& C, const bg_ws<T>& w, const T* X, int pa, const std::v
   CFIE_CHECK_CUDA(cudaStreamSynchronize(C.st));   // M dies on return
 }
 
+// The factors of one block QR: W P = Q1 R (pivoted Cholesky QR), Q1 = Q2 S
+// (the second pass); R_out = S R P^T follows from them (qr_rout).
+struct qr_parts {
+  int r = 0, c = 0;
+  std::vector<cplx> R, S;
+  std::vector<int> perm;
+};
+
+// W (c columns) = Q R_out, R_out r x c row-major, from the factors
+std::vector<cplx> qr_rout(const qr_parts& f) {
+  const int r = f.r, c = f.c;
+  std::vector<cplx> RP((size_t)r * c, cplx(0.0));
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < c; ++j) RP[(size_t)i * c + f.perm[j]] = f.R[(size_t)i * c + j];
+  std::vector<cplx> Rout((size_t)r * c, cplx(0.0));
+  for (int i = 0; i < r; ++i)
+    for (int k = i; k < r; ++k) {
+      const cplx a = f.S[(size_t)i * r + k];
+      for (int j = 0; j < c; ++j) Rout[(size_t)i * c + j] += a * RP[(size_t)k * c + j];
+    }
+  return Rout;
+}
+
 // W (c columns) = Q R_out with Q written to `dst` (r orthonormal columns);
-// returns r (0: W is numerically zero).  R_out is r x c, row-major.
+// returns r (0: W is numerically zero) and the factors of R_out.
 template <typename T>
-int block_qr(const bg_ctx& C, bg_ws<T>& w, T* Wc, int c, T* dst, double thresh,
-             std::vector<cplx>& Rout) {
+int block_qr(const bg_ctx& C, bg_ws<T>& w, T* Wc, int c, T* dst, double thresh, qr_parts& f) {
   std::vector<cplx> G, R;
   std::vector<int> perm;
   inner_products(C, w, Wc, c, Wc, c, G);
   const int r = chol_pivoted(G, c, thresh, R, perm);
+  f.r = r;
+  f.c = c;
   if (r == 0) return 0;
   // Z = P[:, :r] R11^-1: column j of Z is R11^-1's column j placed on the pivoted rows
   const std::vector<cplx> R11i = upper_inverse(R, c, r);
@@ -513,15 +542,9 @@ int block_qr(const bg_ctx& C, bg_ws<T>& w, T* Wc, int c, T* dst, double thresh,
   const std::vector<cplx> Si = upper_inverse(S, r, r);
   update(C, w, w.Q, r, Si, r, dst, 1.0, 0.0);
   // W P = Q R  ->  W = Q (R P^T), then Q = Q2 S: W = Q2 (S R P^T)
-  std::vector<cplx> RP((size_t)r * c, cplx(0.0));
-  for (int i = 0; i < r; ++i)
-    for (int j = 0; j < c; ++j) RP[(size_t)i * c + perm[j]] = R[(size_t)i * c + j];
-  Rout.assign((size_t)r * c, cplx(0.0));
-  for (int i = 0; i < r; ++i)
-    for (int k = i; k < r; ++k) {
-      const cplx a = S[(size_t)i * r + k];
-      for (int j = 0; j < c; ++j) Rout[(size_t)i * c + j] += a * RP[(size_t)k * c + j];
-    }
+  f.R = std::move(R);
+  f.S = std::move(S);
+  f.perm = std::move(perm);
   return r;
 }
 
@@ -536,12 +559,13 @@ int cycle(const bg_ctx& C, bg_ws<T>& w, const double2* r, const std::vector<doub
   // first block: QR of the residual
   k_bconv<double2, T><<<nbl((size_t)n * s), 256, 0, C.st>>>((size_t)n * s, r, w.W);
   CFIE_CHECK_LAUNCH();
-  std::vector<cplx> B;
-  const int r0 = block_qr(C, w, w.W, s, w.V, thresh, B);
+  qr_parts f0;
+  const int r0 = block_qr(C, w, w.W, s, w.V, thresh, f0);
   if (r0 == 0) {
     *met = true;
     return 0;
   }
+  const std::vector<cplx> B = qr_rout(f0);
   block_ls ls;
   ls.start(B, r0, s);
   std::vector<int> bsz{r0};   // block sizes
@@ -583,13 +607,15 @@ int cycle(const bg_ctx& C, bg_ws<T>& w, const double2* r, const std::vector<doub
                                     cudaMemcpyDeviceToHost, C.st));
     stats.arnoldi_elems += 4LL * (long long)n * p * sk;
     const bool room = p + s <= w.cap;
-    std::vector<cplx> Rk;
+    qr_parts fk;
     int rn = 0;
-    if (room) rn = block_qr(C, w, w.W, sk, w.V + (size_t)p * n, thresh, Rk);
-    // the next block's matvec goes to the GPU before the host updates the
-    // least squares, so the two overlap; if this step ends the cycle, its
-    // result is simply not read (the stream orders every later use of W)
+    if (room) rn = block_qr(C, w, w.W, sk, w.V + (size_t)p * n, thresh, fk);
+    // the next block's matvec goes to the GPU before the host forms R_k and
+    // updates the least squares, so the two overlap; if this step ends the
+    // cycle, its result is simply not read (the stream orders every later use
+    // of W)
     if (rn > 0 && steps + 1 < max_blocks) queue_matvec(p + rn, rn);
+    const std::vector<cplx> Rk = rn > 0 ? qr_rout(fk) : std::vector<cplx>();
     // block column [H; R_k] into the least squares
     ls.grow(p + rn);
     std::vector<std::vector<cplx>> blk(sk, std::vector<cplx>(p + rn, cplx(0.0)));

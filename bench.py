@@ -837,11 +837,17 @@ def run_other_configs(args):
             setattr(a, k, v)
         return a
 
-    out["disk_fp64"] = _brief(run_ours(sub("disk"), 0, 1))
-    out["star_hard_fp64"] = _brief(run_ours(sub("star"), 0, 1))
-    out["star_hard_fp32"] = _brief(run_ours(sub("star", precision="fp32"), 0, 1))
-    out["stars256_stored"] = _brief(run_stars(sub("stars")))
-    out["serve_first100"] = _brief(run_serve(sub("serve", count=100)))
+    runs = [("disk_fp64", lambda: run_ours(sub("disk"), 0, 1)),
+            ("star_hard_fp64", lambda: run_ours(sub("star"), 0, 1)),
+            ("star_hard_fp32", lambda: run_ours(sub("star", precision="fp32"), 0, 1)),
+            ("stars256_stored", lambda: run_stars(sub("stars"))),
+            ("serve_first100", lambda: run_serve(sub("serve", count=100)))]
+    for name, fn in runs:
+        # a failure here is reported beside the headline, which stands
+        try:
+            out[name] = _brief(fn())
+        except Exception as e:   # noqa: BLE001
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:300]}
     return out
 
 

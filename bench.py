@@ -873,8 +873,11 @@ def run_stars(args):
     tuning = {}
 
     def step():
-        ops = [ctx.fourier_star(s["a"], s["b"]).discretise(s["n"], s["omega"], precision="tensor",
-                                                            layout="stored") for s in specs]
+        geoms = [ctx.fourier_star(s["a"], s["b"]) for s in specs]
+        ops = ctx.discretise_many(geoms, [s["n"] for s in specs], [s["omega"] for s in specs],
+                                  precision="tensor", layout="stored")
+        for g in geoms:
+            g.close()
         b = cfie.Batch(ctx, ops, [s["nrhs"] for s in specs])
         d, ms = b.tuning()
         tuning["dealing"] = ["round-robin", "greedy", "stream-K"][d]

@@ -256,6 +256,19 @@ void cfie_dirprec_destroy(cfie_dirprec* P);
  * usual choice, Section 1 asks for eta = O(omega)).  Synchronous. */
 cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cfie_bc bc,
                             cfie_precision precision, cfie_layout layout, cfie_op** out);
+/* cfie_discretise for count operators at once: geoms[k] (all of one context),
+ * n[k], omega[k], eta[k] (host arrays of count entries) and one boundary
+ * condition, precision and layout; out[k] receives operator k (host array of
+ * count handles).  The set-up runs on up to eight worker threads, each with
+ * its own CUDA stream, so that the set-up kernels of different operators
+ * (sampling, Kress tables, near bands, assembly) overlap on the GPU; the
+ * operators then belong to the geometries' context as if made one by one,
+ * with the same entries.  Synchronous.  On failure no operator is kept (every
+ * out[k] NULL), the status is the first failing one's and its message is the
+ * context's.  Not part of the paper (a set-up convenience for batches). */
+cfie_status cfie_discretise_many(int count, cfie_geom* const* geoms, const int* n,
+                                 const double* omega, const double* eta, cfie_bc bc,
+                                 cfie_precision precision, cfie_layout layout, cfie_op** out);
 /* Free an operator and its device buffers (NULL is ignored) after the work
  * queued on the context stream has finished.  Batches holding it must be
  * destroyed first. */

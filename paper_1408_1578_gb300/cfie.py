@@ -104,6 +104,8 @@ SIGNATURES = {
     "cfie_op_set_preconditioner": (_I, [_P, _P]),
     "cfie_dirprec_destroy": (None, [_P]),
     "cfie_discretise": (_I, [_P, _I, _D, _D, _I, _I, _I, ctypes.POINTER(_P)]),
+    "cfie_discretise_many": (_I, [_I, ctypes.POINTER(_P), _IP, _DP, _DP, _I, _I, _I,
+                                  ctypes.POINTER(_P)]),
     "cfie_op_destroy": (None, [_P]),
     "cfie_op_n": (_I, [_P]),
     "cfie_rhs_plane_waves": (_I, [_P, _I, _DP, _P]),
@@ -373,6 +375,24 @@ class Context:
         ddz = np.ascontiguousarray(ddz, dtype=np.float64)
         return self._geom(self.lib.cfie_geometry_samples, int(z.shape[0]), _dptr(z), _dptr(dz),
                           _dptr(ddz))
+
+    def discretise_many(self, geoms, n, omega, eta=None, bc="soft", precision="fp64",
+                        layout="matrix_free"):
+        """cfie_discretise for many geometries of this context at once (their
+        set-up overlapping on the GPU); returns the operators in order."""
+        count = len(geoms)
+        hs = (_P * count)(*[g.h for g in geoms])
+        nn = np.ascontiguousarray(n, dtype=np.int32)
+        om = np.ascontiguousarray(omega, dtype=np.float64)
+        et = np.ascontiguousarray(om if eta is None else eta, dtype=np.float64)
+        out = (_P * count)()
+        self.check(self.lib.cfie_discretise_many(count, hs, nn.ctypes.data_as(_IP), _dptr(om),
+                                                 _dptr(et), BC[bc], PRECISION[precision],
+                                                 LAYOUT[layout], out), "cfie_discretise_many")
+        ops = [Operator(self, _P(out[k]), int(nn[k])) for k in range(count)]
+        for op in ops:
+            self._children.add(op)
+        return ops
 
     def geometry(self, kind, **params):
         if kind == "circle":

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 #include <new>
 #include <tuple>
 
@@ -283,6 +284,70 @@ cfie_status cfie_geometry_samples(cfie_ctx* ctx, int n, const double* z, const d
 }
 
 void cfie_geom_destroy(cfie_geom* geom) { delete geom; }
+
+cfie_status cfie_discretise_many(int count, cfie_geom* const* geoms, const int* n,
+                                 const double* omega, const double* eta, cfie_bc bc,
+                                 cfie_precision precision, cfie_layout layout, cfie_op** out) {
+  if (count < 1 || !geoms || !n || !omega || !eta || !out || !geoms[0] || !geoms[0]->ctx)
+    return CFIE_EINVAL;
+  cfie_ctx* ctx = geoms[0]->ctx;
+  for (int k = 0; k < count; ++k) out[k] = nullptr;
+  for (int k = 0; k < count; ++k)
+    if (!geoms[k] || geoms[k]->ctx != ctx) {
+      ctx->err = "every geometry must belong to one context";
+      return CFIE_EINVAL;
+    }
+  // each worker sets its operators up on a context and stream of its own
+  // (the request server's slots do the same), then hands them to the
+  // geometries' context once its stream has finished
+  const int K = std::min(count, 8);
+  std::vector<cfie_status> st(count, CFIE_OK);
+  std::vector<std::string> msg(count);
+  std::vector<std::thread> workers;
+  for (int t = 0; t < K; ++t)
+    workers.emplace_back([&, t] {
+      cudaSetDevice(ctx->device);
+      cudaStream_t s = nullptr;
+      cfie_ctx* wc = nullptr;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+          cfie_ctx_create(ctx->device, s, &wc) != CFIE_OK) {
+        for (int k = t; k < count; k += K) {
+          st[k] = CFIE_ECUDA;
+          msg[k] = "could not create a worker stream / context";
+        }
+        if (s) cudaStreamDestroy(s);
+        return;
+      }
+      for (int k = t; k < count; k += K) {
+        cfie_geom g = *geoms[k];   // the same curve, on the worker's context
+        g.ctx = wc;
+        st[k] = cfie_discretise(&g, n[k], omega[k], eta[k], bc, precision, layout, &out[k]);
+        if (st[k] != CFIE_OK) msg[k] = wc->err;
+      }
+      if (cudaStreamSynchronize(s) != cudaSuccess)
+        for (int k = t; k < count; k += K)
+          if (st[k] == CFIE_OK) {
+            st[k] = CFIE_ECUDA;
+            msg[k] = "worker stream failed";
+          }
+      for (int k = t; k < count; k += K)
+        if (out[k]) out[k]->ctx = ctx;
+      cfie_ctx_destroy(wc);
+      cudaStreamDestroy(s);
+    });
+  for (auto& w : workers) w.join();
+  for (int k = 0; k < count; ++k)
+    if (st[k] != CFIE_OK) {
+      for (int q = 0; q < count; ++q) {
+        cfie_op_destroy(out[q]);
+        out[q] = nullptr;
+      }
+      ctx->err = msg[k];
+      return st[k];
+    }
+  ctx->err.clear();
+  return CFIE_OK;
+}
 
 cfie_status cfie_discretise(cfie_geom* geom, int n, double omega, double eta, cfie_bc bc,
                             cfie_precision precision, cfie_layout layout, cfie_op** out) {

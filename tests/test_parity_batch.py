@@ -10,7 +10,7 @@ import pytest
 
 from oracle import geometry, operators, solvers
 from paper_1408_1578_gb300 import inputs
-from tests.gpu_util import col_rel, to_dev, to_host
+from tests.gpu_util import col_rel, empty, to_dev, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -163,3 +163,36 @@ def test_contraction_dealings_and_tuning(ctx, small_batch):
     assert ctx.lib.cfie_batch_set_dealing(b2.h, 3) == cfie.CFIE_EINVAL
     b2.close()
     b.close()
+
+
+def test_discretise_many_equals_one_by_one(ctx):
+    """cfie_discretise_many sets operators up on worker streams; each one is
+    the operator cfie_discretise makes (the same products, bit for bit), for
+    the stored and the matrix-free forms; geometries of two contexts are
+    refused."""
+    from paper_1408_1578_gb300 import cfie
+    specs = inputs.random_stars(count=5, seed=33, n_lo=300, n_hi=900, nrhs=3)
+    for prec, layout in (("tensor", "stored"), ("fp32", "matrix_free")):
+        geoms = [ctx.fourier_star(s["a"], s["b"]) for s in specs]
+        many = ctx.discretise_many(geoms, [s["n"] for s in specs], [s["omega"] for s in specs],
+                                   precision=prec, layout=layout)
+        for k, s in enumerate(specs):
+            one = geoms[k].discretise(s["n"], s["omega"], precision=prec, layout=layout)
+            X = to_dev(inputs.random_density(s["n"], 3, seed=40 + k))
+            y1, y2 = empty(3, s["n"]), empty(3, s["n"])
+            many[k].apply(X, y1)
+            one.apply(X, y2)
+            assert np.array_equal(to_host(y1), to_host(y2))
+            one.close()
+            many[k].close()
+        for g in geoms:
+            g.close()
+    other = cfie.Context(0)
+    g1 = ctx.fourier_star(specs[0]["a"], specs[0]["b"])
+    g2 = other.fourier_star(specs[1]["a"], specs[1]["b"])
+    with pytest.raises(cfie.CfieError):
+        ctx.discretise_many([g1, g2], [specs[0]["n"], specs[1]["n"]],
+                            [specs[0]["omega"], specs[1]["omega"]], precision="fp32")
+    g1.close()
+    g2.close()
+    other.close()

@@ -67,7 +67,7 @@ def parse():
                    help="serve: requests with at least this many directions and --serve-block-min-n "
                         "nodes use block GMRES (0: off)")
     p.add_argument("--serve-block-min-n", type=int, default=16384)
-    p.add_argument("--serve-stored-max-n", type=int, default=0,
+    p.add_argument("--serve-stored-max-n", type=int, default=16384,
                    help="serve: sound-soft requests up to this n use the stored tensor-core form")
     p.add_argument("--no-extras", action="store_true",
                    help="headline workload only: skip the short runs of the other configurations "

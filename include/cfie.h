@@ -551,10 +551,11 @@ cfie_status cfie_server_create(int device, size_t hbm_budget_bytes, int slots, c
  * restart and maxit and an n within a factor of two of the first one's that
  * fit alongside it, and solves them together as one cfie_batch (one lockstep
  * GMRES over all their right-hand sides: one set of Arnoldi launches and one
- * host synchronisation per step for the group, the matvecs of the operators
- * still iterating issued on up to eight concurrent streams).  Each request keeps its own result, iteration
- * counts, residuals and solution; the times of a group's requests share its
- * start and end.  Affects requests taken after the call.  CFIE_EINVAL for a
+ * host synchronisation per step for the group; stored operators share one
+ * persistent contraction launch per matvec, matrix-free ones still iterating
+ * have their matvecs issued on up to eight concurrent streams).  Each request
+ * keeps its own result, iteration counts, residuals and solution; the times
+ * of a group's requests share its start and end.  Affects requests taken after the call.  CFIE_EINVAL for a
  * null server or max_requests outside [1, 256].  Not part of the paper (a
  * serving option). */
 cfie_status cfie_server_set_batching(cfie_server* server, int max_requests);

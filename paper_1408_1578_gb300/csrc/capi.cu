@@ -304,37 +304,49 @@ cfie_status cfie_discretise_many(int count, cfie_geom* const* geoms, const int* 
   std::vector<cfie_status> st(count, CFIE_OK);
   std::vector<std::string> msg(count);
   std::vector<std::thread> workers;
-  for (int t = 0; t < K; ++t)
-    workers.emplace_back([&, t] {
-      cudaSetDevice(ctx->device);
-      cudaStream_t s = nullptr;
-      cfie_ctx* wc = nullptr;
-      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-          cfie_ctx_create(ctx->device, s, &wc) != CFIE_OK) {
-        for (int k = t; k < count; k += K) {
-          st[k] = CFIE_ECUDA;
-          msg[k] = "could not create a worker stream / context";
-        }
-        if (s) cudaStreamDestroy(s);
-        return;
-      }
+  auto work = [&](int t) {
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = nullptr;
+    cfie_ctx* wc = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cfie_ctx_create(ctx->device, s, &wc) != CFIE_OK) {
       for (int k = t; k < count; k += K) {
+        st[k] = CFIE_ECUDA;
+        msg[k] = "could not create a worker stream / context";
+      }
+      if (s) cudaStreamDestroy(s);
+      return;
+    }
+    for (int k = t; k < count; k += K) {
+      try {
         cfie_geom g = *geoms[k];   // the same curve, on the worker's context
         g.ctx = wc;
         st[k] = cfie_discretise(&g, n[k], omega[k], eta[k], bc, precision, layout, &out[k]);
         if (st[k] != CFIE_OK) msg[k] = wc->err;
+      } catch (...) {
+        st[k] = CFIE_ENOMEM;
+        msg[k] = "host allocation failed";
       }
-      if (cudaStreamSynchronize(s) != cudaSuccess)
-        for (int k = t; k < count; k += K)
-          if (st[k] == CFIE_OK) {
-            st[k] = CFIE_ECUDA;
-            msg[k] = "worker stream failed";
-          }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess)
       for (int k = t; k < count; k += K)
-        if (out[k]) out[k]->ctx = ctx;
-      cfie_ctx_destroy(wc);
-      cudaStreamDestroy(s);
-    });
+        if (st[k] == CFIE_OK) {
+          st[k] = CFIE_ECUDA;
+          msg[k] = "worker stream failed";
+        }
+    for (int k = t; k < count; k += K)
+      if (out[k]) out[k]->ctx = ctx;
+    cfie_ctx_destroy(wc);
+    cudaStreamDestroy(s);
+  };
+  // a worker thread that cannot be started does its share on this thread
+  for (int t = 0; t < K; ++t) {
+    try {
+      workers.emplace_back(work, t);
+    } catch (...) {
+      work(t);
+    }
+  }
   for (auto& w : workers) w.join();
   for (int k = 0; k < count; ++k)
     if (st[k] != CFIE_OK) {

@@ -317,10 +317,20 @@ void worker_main(cfie_server* S) {
         g->status = CFIE_ECUDA;
         g->err = "slot could not create its CUDA stream / context";
       }
-    } else if (group.size() == 1) {
-      run_request(ctx, r, alone, fbuf, xbuf);
     } else {
-      run_batch(ctx, group, fbuf, xbuf);
+      // no exception leaves the slot's thread: a host allocation that fails
+      // fails the requests in hand
+      try {
+        if (group.size() == 1)
+          run_request(ctx, r, alone, fbuf, xbuf);
+        else
+          run_batch(ctx, group, fbuf, xbuf);
+      } catch (...) {
+        for (request_rec* g : group) {
+          g->status = CFIE_ENOMEM;
+          g->err = "host allocation failed";
+        }
+      }
     }
     {
       std::lock_guard<std::mutex> lock(S->mu);

@@ -295,8 +295,10 @@ cfie_status cfie_apply(cfie_op* op, const void* x_dev, void* y_dev, int nrhs);
  * faster), 1 = register-blocked FP32 sums on the CUDA cores (any operator),
  * 2 = tensor cores (entries split bf16 hi + lo, tcgen05 contraction; for the
  * sound-hard operator S is applied to the three vectors of Maue's identity and
- * D' to the density, each a pass of the same kernel).  Both evaluate the same
- * FP32 entries. */
+ * D' to the density, each a pass of the same kernel).  Variant 1 evaluates the
+ * FP32 entries to full FP32 accuracy, variant 2 to the accuracy its bf16
+ * hi + lo operands keep (two-term Hankel series, a few 1e-6 relative next to
+ * the near band); both stay far inside the 1e-4 of a raw FP32 matvec. */
 cfie_status cfie_op_set_variant(cfie_op* op, int variant);
 
 /* y = A x in FP64 whatever the operator's precision (the matvec used for true

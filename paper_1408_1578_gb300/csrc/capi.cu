@@ -109,11 +109,10 @@ std::map<std::tuple<int, int, int>, int> g_tuned;
 
 int tuned_variant(cfie_op* op, const double2* x, double2* y, int nrhs) {
   if (op->variant) return op->variant;
-  if (nrhs < 8) return 1;
   // decisions are shared by operators of similar shape (n up to the next power
   // of two, right-hand sides in octaves), so that a server seeing a new n and
   // nrhs with every request does not time both variants every time
-  int nb = 1, rb = 8;
+  int nb = 1, rb = 1;
   while (nb < op->n) nb *= 2;
   while (rb * 2 <= std::min(nrhs, 64)) rb *= 2;
   const auto key = std::make_tuple((int)op->bc, nb, rb);

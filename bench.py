@@ -217,7 +217,10 @@ def kernel_rooflines(kt, spec, stats, peaks, src, n, solves_timed):
         if cls == "matvec_fp32":
             v = stats.get("matvec_variant", 1)
             ops = ENTRY_OPS[(bc, 2 if v == 2 else 1)] + (SUM_OPS[bc] * nrhs if v == 1 else 0)
-            a = ops * n * n / avg / 1e12
+            # per matvec (the sound-hard tensor-core form, and passes of more
+            # than 64 right-hand sides, take several launches per matvec)
+            mv = stats.get("inner_matvecs", 0) * solves_timed
+            a = ops * n * n / (sec / mv if mv else avg) / 1e12
             out[cls] = {"bound": "alu", "achieved": a, "peak": fp32_peak, "unit": "Top/s",
                         "frac": a / fp32_peak, "traffic": None,
                         "work": f"{ops} FP32 ops per pair (variant {v}: "

@@ -84,6 +84,13 @@ def test_roofline_fused_fp32_kite():
     assert abs(r["achieved"] - want) < 1e-9 * want
     assert abs(r["frac"] - want / ALU_PEAK_T) < 1e-12
     assert r["bound"] == "alu"
+    # with the matvec count known, the work is per matvec, not per launch
+    # (a sound-hard tensor-core matvec takes an S and a D' launch)
+    spec_h = {"nrhs": 4, "bc": "hard", "precision": "fp32", "curve": "star"}
+    rh = b.kernel_rooflines({"matvec_fp32": (20.0, 10)}, spec_h,
+                            {"matvec_variant": 2, "inner_matvecs": 5}, PEAKS, "measured", n, 1)
+    want_h = (36 + 42) * n * n / (20.0 / 1e3 / 5) / 1e12
+    assert abs(rh["matvec_fp32"]["achieved"] - want_h) < 1e-9 * want_h
     key = ("matvec_fp32", "kite", n, 64, 2)
     assert r["traffic"] == b.NCU_TRAFFIC.get(key)
 

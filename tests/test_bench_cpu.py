@@ -150,3 +150,34 @@ def test_reference_specs_of_the_batch_sample_the_oracle():
         assert sp["eta"] == sp["omega"]
     pairs, secs = bench.oracle_sample(specs[0], 2)
     assert pairs == 2 * specs[0]["n"] and secs > 0
+
+
+def test_other_configs_only_after_the_plain_headline():
+    """The default run appends the brief runs of the other configurations;
+    any override of the headline (another workload, n, precision, solver
+    option) or --no-extras turns them off."""
+    b = _bench_module()
+    assert b.default_headline(_args(b, []))
+    for extra in (["--no-extras"], ["--workload", "star"], ["--n", "8192"], ["--block"],
+                  ["--precision", "fp64"], ["--fp64-basis"], ["--rtol", "1e-6"]):
+        assert not b.default_headline(_args(b, extra)), extra
+
+
+def _args(b, argv):
+    old = sys.argv
+    try:
+        sys.argv = ["bench.py"] + argv
+        return b.parse()
+    finally:
+        sys.argv = old
+
+
+def test_brief_summary_of_a_run():
+    b = _bench_module()
+    run = {"metric": "m", "value": 2.0, "unit": "u", "steps": 3, "warmup": 3, "ms_per_step": 5.0,
+           "config": {"workload": "w"}, "kernel_ms": {"x": 1.0},
+           "roofline": {"bound": "hbm", "achieved": 1.0, "peak": 2.0, "unit": "GB/s", "frac": 0.5,
+                        "traffic": None}}
+    out = b._brief(run)
+    assert out["workload"] == "w" and out["value"] == 2.0 and "kernel_ms" not in out
+    assert out["roofline"]["frac"] == 0.5 and "traffic" not in out["roofline"]

@@ -22,7 +22,11 @@
  * directional preconditioner of Section 2 (cfie_dirprec_plan,
  * cfie_dirprec_level, cfie_dirprec_threshold, cfie_dirprec_w_pattern).  The
  * preconditioner itself: cfie_dirprec_create -> cfie_op_set_preconditioner /
- * cfie_dirprec_apply -> cfie_dirprec_destroy.
+ * cfie_dirprec_apply -> cfie_dirprec_destroy.  Many operators at once:
+ * cfie_discretise_many (set-up overlapped) and cfie_batch_* (lockstep solves,
+ * one persistent tensor-core launch per matvec for stored operators); one
+ * Krylov space over all directions: cfie_op_set_block_gmres; a stream of
+ * requests: cfie_server_* (batched slots, admission by HBM footprint).
  *
  * Conventions for every entry point:
  *  - All compute runs on the context's CUDA device and stream; calls that take
